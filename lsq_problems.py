@@ -1,0 +1,96 @@
+"""Seeded synthetic least-squares problems shared by the tests, the bench and
+the smoke check.
+
+This module only builds inputs (A, b and the known solution); it holds none of
+the solvers' arithmetic, so both the CUDA path and the CPU oracle can take
+their inputs from it without sharing any method code.
+
+Generators
+----------
+``problem_svd``  -- A = U diag(sigma) V^T with U (m x n) and V (n x n) the
+    orthonormal factors of QR decompositions of seeded standard Gaussians
+    (columns sign-fixed by sign(R_ii), which makes them Haar distributed),
+    sigma log-spaced from 1 down to 1/kappa, x_true a standard Gaussian
+    scaled to unit norm, and r a Gaussian projected (twice) onto the
+    orthogonal complement of range(U) and scaled to the requested norm;
+    b = A x_true + r.  This is the construction of the paper's Fig. 1 and
+    Table 1 problems (Sec. 1: log-spaced singular values, Haar singular
+    vectors, residual of a given norm orthogonal to range(A)).
+``problem_gaussian`` -- A = (G / sqrt(m)) diag(sigma) V^T with G an m x n
+    standard Gaussian, V Haar, sigma log-spaced 1..1/kappa, and
+    b = A x_true + noise * g with x_true and g standard Gaussian.
+
+Randomness: numpy's PCG64 Generator seeded by ``seed``; every draw happens
+in a fixed order, so a (generator, shape, seed) triple always gives the
+same problem on one machine.
+"""
+import numpy as np
+
+
+def haar_orthonormal(rng, rows, cols):
+    """Orthonormal rows x cols factor of a seeded Gaussian, columns sign-fixed."""
+    g = rng.standard_normal((rows, cols))
+    q, r = np.linalg.qr(g)
+    s = np.sign(np.diag(r))
+    s[s == 0] = 1.0
+    return q * s
+
+
+def log_sigma(n, kappa):
+    """n singular values 10^{p_i}, p_i equally spaced in [0, -log10(kappa)]."""
+    if n == 1:
+        return np.ones(1)
+    return 10.0 ** (-np.linspace(0.0, np.log10(kappa), n))
+
+
+def problem_svd(m, n, kappa, resid_norm, seed, keep_factors=True):
+    """Constructed problem with known solution x_true (see module docstring)."""
+    rng = np.random.default_rng(seed)
+    U = haar_orthonormal(rng, m, n)
+    V = haar_orthonormal(rng, n, n)
+    sigma = log_sigma(n, kappa)
+    A = np.ascontiguousarray((U * sigma) @ V.T)
+    x = rng.standard_normal(n)
+    x /= np.linalg.norm(x)
+    g = rng.standard_normal(m)
+    r = g - U @ (U.T @ g)
+    r = r - U @ (U.T @ r)
+    nr = np.linalg.norm(r)
+    r = r * (resid_norm / nr) if nr > 0 else r
+    b = A @ x + r
+    out = {"A": A, "b": b, "x_true": x, "kappa": kappa, "resid_norm": resid_norm}
+    if keep_factors:
+        out.update({"U": U, "sigma": sigma, "V": V, "r_true": r})
+    return out
+
+
+def problem_gaussian(m, n, kappa, noise, seed, dtype=np.float64):
+    """A = (G/sqrt(m)) diag(sigma) V^T, b = A x_true + noise * g."""
+    rng = np.random.default_rng(seed)
+    V = haar_orthonormal(rng, n, n)
+    sigma = log_sigma(n, kappa)
+    W = np.ascontiguousarray((sigma[:, None] * V.T) / np.sqrt(m))
+    A = np.empty((m, n), dtype=np.float64)
+    x = rng.standard_normal(n)
+    b = np.empty(m)
+    step = 65536
+    for i0 in range(0, m, step):
+        i1 = min(m, i0 + step)
+        G = rng.standard_normal((i1 - i0, n))
+        A[i0:i1] = G @ W
+    g = rng.standard_normal(m)
+    b[:] = A @ x + noise * g
+    return {"A": A, "b": b, "x_true": x, "kappa": kappa, "noise": noise,
+            "sigma": sigma, "V": V}
+
+
+def problem_multi_rhs(m, n, k, kappa, noise, seed):
+    """A built as in problem_svd (no residual), B = A X_true + noise * G (m x k)."""
+    rng = np.random.default_rng(seed)
+    U = haar_orthonormal(rng, m, n)
+    V = haar_orthonormal(rng, n, n)
+    sigma = log_sigma(n, kappa)
+    A = np.ascontiguousarray((U * sigma) @ V.T)
+    X = rng.standard_normal((n, k))
+    B = np.ascontiguousarray(A @ X + noise * rng.standard_normal((m, k)))
+    return {"A": A, "B": B, "X_true": X, "kappa": kappa, "noise": noise}

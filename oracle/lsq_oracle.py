@@ -1,0 +1,378 @@
+"""Oracle: plain, slow, CPU FP64 reference for FOSSILS and SPIR.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and
+bench.py's CPU-baseline leg may import this module.  It shares no code with
+the CUDA library and never calls it.
+
+Every function names the passage of Epperly, Meier, Nakatsukasa,
+"Fast randomized least-squares solvers can be just as accurate and stable as
+classical direct solvers" (arXiv 2406.03468) that it follows.  Heavy loops
+(Householder QR, triangular solves, compensated residuals) are plain C in
+oracle/liboracle.c; matrix-vector products with A use numpy (a library
+matvec serving as a step); sums are never blocked, fused or reordered beyond
+what the definition states.
+
+Readings of the paper that this oracle takes (each is listed in the design doc):
+  * u = 2^-53 (unit roundoff of IEEE double, the standard model of Sec. 1.4).
+  * alpha, beta from eta = sqrt(n/d) (Sec. 4.2), i.e. beta = eta^2,
+    alpha = (1 - beta)^2 (Sec. 2.3, optimal coefficients); Alg. 4's "beta <- d/n" is read as n/d.
+  * normest = sigma_max(R), condest = sigma_max(R)/sigma_min(R): with a QR
+    preconditioner the singular values of R equal those of SA, which Alg. 4
+    reads off the SVD.
+  * Step-1 stop (Sec. 4.2, "Adaptive stopping", item 1): stop after the first
+    update Delta with ||Delta|| <= u (gamma normest ||x_0|| +
+    rho condest ||b - A x_0||), gamma = 1, rho = 0.04, at most 100 updates.
+  * Step-2 count: q0 of Theorem 7.1 (Sec. 7) with kappa replaced by condest and the
+    distortion 1.01 eta; Alg. 5 returns the iterate dy_(q) after q - 1 updates,
+    so step 2 runs ceil(q0) - 1 updates (capped at 100).
+  * SPIR's CG starts from dy = 0 and uses the same two stopping rules, with
+    Delta = gamma_k p_k the CG update of dy.
+  * Column scaling (Alg. 4, first line) is on by default and is applied
+    explicitly, A <- A diag(d)^{-1}; x is unscaled at the end (Alg. 4, last
+    line).
+"""
+import ctypes
+import math
+
+import numpy as np
+
+from . import _cbuild
+from .philox import sparse_sign_matrix
+
+U_ROUNDOFF = 2.0 ** -53
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        lib = ctypes.CDLL(_cbuild.build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64 = ctypes.c_int64
+        lib.or_householder_qr.argtypes = [i64, i64, dp, i64, dp]
+        lib.or_apply_qt.argtypes = [i64, i64, dp, dp]
+        lib.or_backsub.argtypes = [i64, dp, i64, dp, dp]
+        lib.or_backsub_t.argtypes = [i64, dp, i64, dp, dp]
+        lib.or_resid_dot2.argtypes = [i64, i64, dp, i64, dp, dp, dp, dp, dp]
+        for f in (lib.or_householder_qr, lib.or_apply_qt, lib.or_backsub,
+                  lib.or_backsub_t, lib.or_resid_dot2):
+            f.restype = ctypes.c_int
+        _LIB = lib
+    return _LIB
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Dense building blocks
+# ---------------------------------------------------------------------------
+
+def householder_qr(M):
+    """Householder QR of M (rows >= cols): Sec. 2.1 (sketch and QR) and Lemma 6.3
+    (the analysis assumes Householder QR).
+
+    Returns (R, V): R is the cols x cols upper-triangular factor and V the
+    rows x cols matrix of unit reflector vectors (Q = H_0 H_1 ... with
+    H_k = I - 2 v_k v_k^T).
+    """
+    W = np.array(M, dtype=np.float64, order="C", copy=True)
+    rows, cols = W.shape
+    if rows < cols:
+        raise ValueError("householder_qr needs rows >= cols")
+    V = np.empty((rows, cols), dtype=np.float64)
+    _lib().or_householder_qr(rows, cols, _p(W), cols, _p(V))
+    return np.ascontiguousarray(W[:cols, :cols]), V
+
+
+def apply_qt(V, y):
+    """Q^T y with the reflectors V returned by householder_qr."""
+    out = _c64(y).copy()
+    rows, cols = V.shape
+    _lib().or_apply_qt(rows, cols, _p(_c64(V)), _p(out))
+    return out
+
+
+def backsub(R, y):
+    """R^{-1} y by back substitution (Sec. 6, notation: triangular solves are
+    computed by back substitution)."""
+    R = _c64(R)
+    n = R.shape[0]
+    x = _c64(y).copy()
+    _lib().or_backsub(n, _p(R), n, _p(x), _p(x))
+    return x
+
+
+def backsub_t(R, y):
+    """R^{-T} y by forward substitution on R^T."""
+    R = _c64(R)
+    n = R.shape[0]
+    x = _c64(y).copy()
+    _lib().or_backsub_t(n, _p(R), n, _p(x), _p(x))
+    return x
+
+
+def qr_solve(A, b, return_R=False):
+    """Least-squares solution of min ||b - A x|| (Sec. 1) by Householder QR:
+    x = R^{-1} (Q^T b)[:n].  This is the classical direct solver the paper
+    uses as its accuracy yardstick (Sec. 1, Fig. 1, Table 1)."""
+    A = _c64(A)
+    n = A.shape[1]
+    R, V = householder_qr(A)
+    y = apply_qt(V, b)[:n]
+    x = backsub(R, y)
+    return (x, R) if return_R else x
+
+
+def column_norms(A):
+    """d_j = ||A[:, j]||_2 (Alg. 4, ColumnNorms)."""
+    return np.sqrt(np.einsum("ij,ij->j", A, A))
+
+
+def sketch(A, b, d, zeta, seed):
+    """S [A b] with S the sparse sign embedding of Sec. 4.2 (Choice of
+    embedding): S = zeta^{-1/2} [s_1 ... s_m].  The +-1 pattern is summed
+    first and the factor zeta^{-1/2} applied once to the result."""
+    m = A.shape[0]
+    S = sparse_sign_matrix(m, d, zeta, seed)
+    S = S.sign()  # the +-1 pattern
+    c = 1.0 / math.sqrt(zeta)
+    SA = np.asarray(S @ A) * c
+    Sb = np.asarray(S @ b).ravel() * c
+    return SA, Sb
+
+
+def sigma_extremes(R):
+    """(sigma_max, sigma_min) of R via the LAPACK SVD (a library step)."""
+    s = np.linalg.svd(R, compute_uv=False)
+    return float(s[0]), float(s[-1])
+
+
+def q0_count(condest, eta, u=U_ROUNDOFF):
+    """q0 of Theorem 7.1 (Sec. 7): max(1 + 2 log(1/(kappa u)) / log(1/(1.01 eta)), 11)."""
+    e = 1.01 * eta
+    if e <= 0.0:
+        return 11.0
+    val = 1.0 + 2.0 * math.log(1.0 / (condest * u)) / math.log(1.0 / e)
+    return max(val, 11.0)
+
+
+def step2_updates(condest, eta, max_inner=100):
+    """Number of inner updates in the second refinement step: Alg. 5 with
+    q = ceil(q0) produces dy_(q) after q - 1 updates."""
+    q = int(math.ceil(q0_count(condest, eta)))
+    return max(1, min(max_inner, q - 1))
+
+
+# ---------------------------------------------------------------------------
+# FOSSILS and SPIR
+# ---------------------------------------------------------------------------
+
+class _Problem:
+    """Scaled problem data shared by FOSSILS and SPIR (Alg. 4 setup)."""
+
+    def __init__(self, A, b, d, zeta, seed, eta, col_scale):
+        A = _c64(A)
+        b = _c64(b)
+        self.m, self.n = A.shape
+        self.d = int(d) if d else 12 * self.n
+        self.zeta = zeta
+        self.eta = eta if eta else math.sqrt(self.n / self.d)
+        self.beta = self.eta ** 2
+        self.alpha = (1.0 - self.beta) ** 2
+        if col_scale:
+            self.dcol = column_norms(A)
+            self.As = A / self.dcol
+        else:
+            self.dcol = np.ones(self.n)
+            self.As = A
+        self.b = b
+        self.SA, self.Sb = sketch(self.As, b, self.d, zeta, seed)
+        self.R, V = householder_qr(self.SA)
+        self.t = apply_qt(V, self.Sb)[: self.n]
+        smax, smin = sigma_extremes(self.R)
+        self.normest = smax
+        self.condest = smax / smin if smin > 0 else math.inf
+
+    def apply(self, z):
+        """z -> R^{-T}(A^T(A(R^{-1} z))) in that order (Alg. 1; Sec. 6)."""
+        w = backsub(self.R, z)
+        return backsub_t(self.R, self.As.T @ (self.As @ w))
+
+    def rhs(self, x):
+        """c = R^{-T}(A^T(b - A x)) (Alg. 1, refinement right-hand side)."""
+        r = self.b - self.As @ x
+        return backsub_t(self.R, self.As.T @ r), r
+
+
+def _polyak(P, c, alpha, beta, max_updates, thresh):
+    """Polyak heavy ball on (R^{-T}A^T A R^{-1}) dy = c (Alg. 5 / Alg. 4 loop):
+    dy = dy_old = c; Delta = alpha (c - M dy) + beta (dy - dy_old);
+    (dy, dy_old) <- (dy + Delta, dy).  Stops after an update with
+    ||Delta|| <= thresh when thresh is given."""
+    dy = c.copy()
+    dy_old = c.copy()
+    k = 0
+    for _ in range(max_updates):
+        delta = alpha * (c - P.apply(dy)) + beta * (dy - dy_old)
+        dy_old = dy
+        dy = dy + delta
+        k += 1
+        if thresh is not None and np.linalg.norm(delta) <= thresh:
+            break
+    return dy, k
+
+
+def _cg(P, c, max_updates, thresh):
+    """Conjugate gradient on M dy = c from dy = 0 (Alg. 3's inner solver)."""
+    dy = np.zeros_like(c)
+    res = c.copy()
+    p = res.copy()
+    rho = float(res @ res)
+    k = 0
+    for _ in range(max_updates):
+        if rho == 0.0:
+            break
+        q = P.apply(p)
+        gam = rho / float(p @ q)
+        step = gam * p
+        dy = dy + step
+        res = res - gam * q
+        rho_new = float(res @ res)
+        p = res + (rho_new / rho) * p
+        rho = rho_new
+        k += 1
+        if thresh is not None and np.linalg.norm(step) <= thresh:
+            break
+    return dy, k
+
+
+def _solve(method, A, b, d, zeta, seed, eta, col_scale, max_inner, stop_gamma,
+           stop_rho, n_refine, fixed_updates):
+    P = _Problem(A, b, d, zeta, seed, eta, col_scale)
+    x = backsub(P.R, P.t)  # sketch-and-solve x0 (Sec. 2.3)
+    r0 = P.b - P.As @ x
+    thresh1 = U_ROUNDOFF * (stop_gamma * P.normest * np.linalg.norm(x)
+                            + stop_rho * P.condest * np.linalg.norm(r0))
+    q2 = step2_updates(P.condest, P.eta, max_inner)
+    xs = [x.copy()]
+    cnorms = []
+    iters = []
+    for i in range(n_refine):
+        c, _ = P.rhs(x)
+        cnorms.append(float(np.linalg.norm(c)))
+        if fixed_updates is not None:
+            nmax, th = fixed_updates, None
+        elif i == 0:
+            nmax, th = max_inner, thresh1
+        else:
+            nmax, th = q2, None
+        if method == "fossils":
+            dy, k = _polyak(P, c, P.alpha, P.beta, nmax, th)
+        else:
+            dy, k = _cg(P, c, nmax, th)
+        iters.append(k)
+        x = x + backsub(P.R, dy)
+        xs.append(x.copy())
+    return {
+        "x": x / P.dcol,
+        "iterates": [v / P.dcol for v in xs],
+        "iters": iters,
+        "cnorms": cnorms,
+        "condest": P.condest,
+        "normest": P.normest,
+        "thresh1": thresh1,
+        "q2": q2,
+        "alpha": P.alpha,
+        "beta": P.beta,
+        "d": P.d,
+        "R": P.R,
+        "dcol": P.dcol,
+    }
+
+
+def fossils(A, b, d=None, zeta=8, seed=0, eta=None, col_scale=True, max_inner=100,
+            stop_gamma=1.0, stop_rho=0.04, n_refine=2, fixed_updates=None):
+    """FOSSILS (Alg. 2 with the practical rules of Sec. 4.2 / Alg. 4, QR
+    preconditioner): sketch, Householder QR, sketch-and-solve x0, then
+    n_refine (default 2) refinement steps with the Polyak inner solver."""
+    return _solve("fossils", A, b, d, zeta, seed, eta, col_scale, max_inner,
+                  stop_gamma, stop_rho, n_refine, fixed_updates)
+
+
+def spir(A, b, d=None, zeta=8, seed=0, eta=None, col_scale=True, max_inner=100,
+         stop_gamma=1.0, stop_rho=0.04, n_refine=2, fixed_updates=None):
+    """SPIR (Alg. 3): as FOSSILS with conjugate gradient as inner solver."""
+    return _solve("spir", A, b, d, zeta, seed, eta, col_scale, max_inner,
+                  stop_gamma, stop_rho, n_refine, fixed_updates)
+
+
+# ---------------------------------------------------------------------------
+# Quality measures
+# ---------------------------------------------------------------------------
+
+def residual_dot2(A, b, x):
+    """(r_hi, r_lo, g): r = b - A x and g = A^T r with compensated dot products."""
+    A = _c64(A)
+    m, n = A.shape
+    x = _c64(x)
+    r_hi = np.empty(m)
+    r_lo = np.empty(m)
+    g = np.empty(n)
+    _lib().or_resid_dot2(m, n, _p(A), n, _p(_c64(b)), _p(x), _p(r_hi), _p(r_lo), _p(g))
+    return r_hi, r_lo, g
+
+
+def kw_estimate(A, b, xhat, theta=None, R_A=None):
+    """Karlson-Walden estimate of the backward error (Sec. 4.1, the display
+    defining BE-hat_theta):
+
+        theta / sqrt(1 + theta^2 ||x||^2) *
+            || (A^T A + lam I)^{-1/2} A^T r ||,
+        lam = theta^2 ||r||^2 / (1 + theta^2 ||x||^2),  r = b - A x.
+
+    theta defaults to ||A||_F / ||b|| (Sec. 4.2, "Adaptive stopping", item 2).
+    (A^T A + lam I) = R_lam^T R_lam with R_lam the R factor of [R_A; sqrt(lam) I]
+    (a QR of A makes the estimate O(mn), as Sec. 4.1 notes), so the norm is
+    ||R_lam^{-T} A^T r||.  r and A^T r use compensated dot products.
+    Returns the absolute estimate; divide by ||A||_F for the relative one.
+    """
+    A = _c64(A)
+    b = _c64(b)
+    xhat = _c64(xhat)
+    n = A.shape[1]
+    if theta is None:
+        theta = np.linalg.norm(A) / np.linalg.norm(b)
+    if R_A is None:
+        R_A, _ = householder_qr(A)
+    r_hi, r_lo, g = residual_dot2(A, b, xhat)
+    nr = np.linalg.norm(r_hi)
+    nx = np.linalg.norm(xhat)
+    lam = theta ** 2 * nr ** 2 / (1.0 + theta ** 2 * nx ** 2)
+    stacked = np.vstack([R_A, math.sqrt(lam) * np.eye(n)])
+    R_lam, _ = householder_qr(stacked)
+    y = backsub_t(R_lam, g)
+    return theta / math.sqrt(1.0 + theta ** 2 * nx ** 2) * float(np.linalg.norm(y))
+
+
+def kw_relative(A, b, xhat, R_A=None):
+    """BE-hat_theta(x) / ||A||_F with theta = ||A||_F/||b|| (the target
+    quantity of Sec. 4.2 item 2: backward stable when below ~u)."""
+    return kw_estimate(A, b, xhat, R_A=R_A) / float(np.linalg.norm(A))
+
+
+def forward_error(x, x_ref):
+    return float(np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref))
+
+
+def wedin_bound(kappa, normA, x, resid, u=U_ROUNDOFF):
+    """First-order Wedin forward-error bound relative to ||x||:
+    Fact 2.4 (Wedin) with eps = u, 2.23 kappa (||x|| + kappa ||r|| / ||A||) u / ||x||."""
+    nx = float(np.linalg.norm(x))
+    return 2.23 * kappa * (nx + kappa * resid / normA) * u / nx

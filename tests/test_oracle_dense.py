@@ -1,0 +1,98 @@
+"""Pins for the oracle's dense kernels (oracle/liboracle.c).
+
+* Householder QR against LAPACK (numpy.linalg.qr): same R up to row signs,
+  orthogonal Q, Q R = A.
+* Triangular solves against SciPy's solve_triangular.
+* The QR least-squares solve against an extended-precision (mpmath, 60
+  digits) normal-equations solve on tiny inputs, and against LAPACK lstsq.
+* Compensated residual against an exact rational evaluation.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+from oracle import lsq_oracle as O
+from lsq_problems import problem_svd
+
+mpmath = pytest.importorskip("mpmath")
+
+
+@pytest.mark.parametrize("m,n", [(50, 7), (300, 40), (64, 64), (1000, 3)])
+def test_householder_matches_lapack(m, n):
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n)) * np.logspace(0, -6, n)
+    R, V = O.householder_qr(A)
+    _, R_ref = np.linalg.qr(A)
+    s = np.sign(np.diag(R)) * np.sign(np.diag(R_ref))
+    assert np.allclose(R, s[:, None] * R_ref, rtol=0, atol=1e-13 * np.abs(R_ref).max())
+    assert np.allclose(np.tril(R, -1), 0.0)
+    # Q^T A = [R; 0] with Q^T applied column by column
+    QtA = np.stack([O.apply_qt(V, A[:, j]) for j in range(n)], axis=1)
+    assert np.allclose(QtA[:n], R, atol=1e-13 * np.abs(A).max())
+    assert np.allclose(QtA[n:], 0.0, atol=1e-13 * np.abs(A).max())
+    # Q^T is orthogonal: it preserves norms
+    y = rng.standard_normal(m)
+    assert abs(np.linalg.norm(O.apply_qt(V, y)) - np.linalg.norm(y)) < 1e-13 * np.linalg.norm(y)
+
+
+def test_householder_zero_column():
+    A = np.zeros((6, 3))
+    A[:, 0] = 1.0
+    A[:, 2] = np.arange(6.0)
+    R, _ = O.householder_qr(A)
+    assert abs(abs(R[0, 0]) - np.sqrt(6.0)) < 1e-14
+    assert np.isfinite(R).all()
+
+
+@pytest.mark.parametrize("n", [1, 5, 60])
+def test_triangular_solves(n):
+    rng = np.random.default_rng(n)
+    R = np.triu(rng.standard_normal((n, n))) + 3 * np.eye(n)
+    y = rng.standard_normal(n)
+    assert np.allclose(O.backsub(R, y), sl.solve_triangular(R, y), rtol=1e-13, atol=1e-14)
+    assert np.allclose(O.backsub_t(R, y), sl.solve_triangular(R, y, trans="T"), rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_qr_solve_extended_precision(seed):
+    rng = np.random.default_rng(seed)
+    m, n = 9, 3
+    A = rng.standard_normal((m, n))
+    A[:, 2] = A[:, 0] + 1e-5 * A[:, 2]            # moderately ill-conditioned
+    b = rng.standard_normal(m)
+    x = O.qr_solve(A, b)
+    mpmath.mp.dps = 60
+    Am = mpmath.matrix(A.tolist())
+    bm = mpmath.matrix(b.tolist())
+    xm = mpmath.lu_solve(Am.T * Am, Am.T * bm)   # exact-ish normal equations
+    x_ref = np.array([float(v) for v in xm])
+    kappa = np.linalg.cond(A)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 50 * kappa ** 2 * 2.0 ** -53 * 10
+
+
+def test_qr_solve_matches_lstsq_constructed():
+    P = problem_svd(2000, 30, 1e6, 1e-4, seed=8)
+    x = O.qr_solve(P["A"], P["b"])
+    x_l = np.linalg.lstsq(P["A"], P["b"], rcond=None)[0]
+    wb = O.wedin_bound(1e6, 1.0, P["x_true"], 1e-4)
+    assert O.forward_error(x, P["x_true"]) < wb
+    assert O.forward_error(x, x_l) < 2 * wb
+
+
+def test_residual_dot2_exact():
+    rng = np.random.default_rng(5)
+    m, n = 40, 6
+    A = rng.standard_normal((m, n))
+    x = rng.standard_normal(n)
+    b = A @ x + 1e-12 * rng.standard_normal(m)     # heavy cancellation in b - A x
+    r_hi, r_lo, g = O.residual_dot2(A, b, x)
+    F = [[Fraction(v) for v in row] for row in A]
+    fx = [Fraction(v) for v in x]
+    r_ex = [Fraction(b[i]) - sum(F[i][j] * fx[j] for j in range(n)) for i in range(m)]
+    g_ex = [sum(F[i][j] * r_ex[i] for i in range(m)) for j in range(n)]
+    r_ex_f = np.array([float(v) for v in r_ex])
+    g_ex_f = np.array([float(v) for v in g_ex])
+    assert np.allclose(r_hi, r_ex_f, rtol=4e-16, atol=0)
+    assert np.allclose(g, g_ex_f, rtol=1e-14, atol=1e-16 * np.abs(g_ex_f).max())
