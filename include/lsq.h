@@ -1,0 +1,176 @@
+/*
+ * lsq.h -- C ABI of the GB300 (sm_103a) least-squares library: FOSSILS and
+ * SPIR, the backward-stable randomized solvers of Epperly, Meier and
+ * Nakatsukasa (arXiv 2406.03468), for min ||b - A x||_2 with A tall and
+ * dense (m >> n).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout     A is m x n, row-major, FP64, leading dimension lda >= n (in
+ *            doubles).  Vectors are contiguous FP64.  Pointers named d*
+ *            are DEVICE pointers on the plan's device; h* are host pointers.
+ * Ownership  The caller owns every buffer it passes.  Buffers are borrowed
+ *            for the duration of the call only; every entry point returns
+ *            after its work on the plan's stream has finished (the solve
+ *            entry points wait for the stream).  The plan owns its
+ *            workspace (sketch, R, iterates, partial sums), allocated once
+ *            at lsq_plan_create and freed by lsq_plan_destroy.
+ * Errors     Status codes only; nothing is thrown across the ABI.  After a
+ *            status < 0, lsq_last_error() returns a message for the calling
+ *            thread.  Device-side waits are bounded: a wait that runs out
+ *            returns LSQ_ERR_TIMEOUT instead of hanging.
+ * Threads    A plan is used by one thread at a time.  Different plans may be
+ *            used concurrently from different threads.
+ * CUDA       A CUDA library failure returns LSQ_ERR_CUDA.  There is no CPU
+ *            fallback: without a usable GPU every compute call fails.
+ */
+#ifndef LSQ_H
+#define LSQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LSQ_OK = 0,
+  LSQ_PENDING = 1,               /* lsq_poll: the request is not finished yet */
+  LSQ_WARN_RANK_DEFICIENT = 2,   /* solved, but condest > 1/(30u) (Sec. 4.2) */
+  LSQ_ERR_INVALID = -1,          /* bad argument (sizes, null pointers, options) */
+  LSQ_ERR_OOM = -2,              /* device allocation or admission failed */
+  LSQ_ERR_CUDA = -3,             /* a CUDA call failed */
+  LSQ_ERR_NOT_CONVERGED = -4,    /* refinement monitor never met its target */
+  LSQ_ERR_TIMEOUT = -5,          /* a bounded device-side wait ran out */
+  LSQ_ERR_NONFINITE = -6         /* A or b holds NaN or Inf */
+} lsq_status;
+
+/* Arithmetic of the inner iterations (north of the residual, which is FP64). */
+enum {
+  LSQ_PREC_AUTO = 0,        /* FP32 inner passes when condest < fp32_cond_max, else FP64 */
+  LSQ_PREC_FP64 = 1,        /* every step in FP64 */
+  LSQ_PREC_FP32_INNER = 2   /* sketch and inner passes read an FP32 copy of A */
+};
+
+typedef struct lsq_plan_s *lsq_plan;
+
+typedef struct {
+  int64_t m, n;          /* problem size, m >= n >= 1, n <= LSQ_MAX_N */
+  int64_t lda;           /* leading dimension of A in doubles (0 => n) */
+  int32_t d;             /* sketch rows (0 => 12 n), n <= d */
+  int32_t zeta;          /* nonzeros per sketch column (0 => 8), 1..32, <= d */
+  uint64_t seed;         /* Philox key of the sparse sign embedding */
+  double eta;            /* distortion for alpha, beta (0 => sqrt(n/d)) */
+  int32_t col_scale;     /* 1: scale columns of A to unit norm (Alg. 4), 0: off */
+  int32_t max_inner;     /* cap on inner updates per refinement step (0 => 100) */
+  int32_t max_refine;    /* refinement steps (0 => 2 on FP64; FP32 tier: up to 6) */
+  int32_t precision;     /* LSQ_PREC_* (default LSQ_PREC_FP64) */
+  double fp32_cond_max;  /* FP32-inner gate on condest (0 => 1e5) */
+  double stop_gamma;     /* step-1 stop constant gamma (Sec. 4.2; default 1) */
+  double stop_rho;       /* step-1 stop constant rho (Sec. 4.2; default 0.04) */
+  int32_t fixed_inner;   /* > 0: every refinement step runs exactly this many updates */
+  int32_t reserved[9];
+} lsq_options;
+
+#define LSQ_MAX_N 1024
+#define LSQ_MAX_REFINE 8
+
+typedef struct {
+  int32_t iters[LSQ_MAX_REFINE];  /* inner updates run in each refinement step */
+  int32_t refine_steps;           /* refinement steps run */
+  int32_t path;                   /* LSQ_PREC_FP64 or LSQ_PREC_FP32_INNER */
+  int32_t passes;                 /* streaming passes over A (sketch + residuals + inner) */
+  int32_t status;                 /* same value as the return code */
+  double condest;                 /* sigma_max(R) / sigma_min(R) estimate */
+  double normest;                 /* sigma_max(R) estimate */
+  double cnorm[LSQ_MAX_REFINE];   /* ||c_i|| = ||R^{-T} A^T (b - A x_i)|| per step */
+  double resid0;                  /* ||b - A x_0|| (sketch-and-solve) */
+  double thresh1;                 /* step-1 stop threshold */
+  float ms_sketch, ms_qr, ms_refine, ms_total;  /* device time of the phases */
+} lsq_info;
+
+/* Fill *o with the defaults listed above (m, n, lda left 0). */
+void lsq_options_default(lsq_options *o);
+
+/* Create a plan for problems of size opt->m x opt->n on the current CUDA
+ * device, working on the given CUDA stream (cudaStream_t; NULL = legacy
+ * default stream).  Allocates the whole workspace (device memory) once.
+ * Errors: LSQ_ERR_INVALID on bad options, LSQ_ERR_OOM, LSQ_ERR_CUDA. */
+lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *out);
+
+/* Free the plan and its workspace.  NULL is ignored. */
+void lsq_plan_destroy(lsq_plan plan);
+
+/* Sketch, column scaling and preconditioner (Alg. 1, the lines before the
+ * refinement loop; Alg. 4's column scaling): colnorms d_j of A,
+ * [SA Sb] = S [A diag(d)^{-1}, b] with S the Philox sparse sign embedding
+ * (Sec. 4.2), Householder QR [SA Sb] -> R and t = (Q^T Sb)[0:n],
+ * the condest / normest estimates of R, and the sketch-and-solve x0 =
+ * R^{-1} t (Sec. 2.3).  Keeps R, t, x0 in the plan.
+ * dA: m x n row-major (lda), db: m.  Errors: LSQ_ERR_NONFINITE if A or b is
+ * not finite, LSQ_ERR_INVALID for a zero column (with col_scale). */
+lsq_status lsq_sketch(lsq_plan plan, const double *dA, const double *db);
+
+/* FOSSILS (Alg. 2 with the stopping rules of Sec. 4.2): lsq_sketch, then
+ * refinement steps x_{i+1} = x_i + R^{-1} dy_i with the Polyak heavy ball
+ * (Alg. 5) on R^{-T} A^T A R^{-1} dy = c_i.  Writes the solution (original
+ * column scaling) to dx (n, device).  info may be NULL.
+ * Returns LSQ_OK or LSQ_WARN_RANK_DEFICIENT on success. */
+lsq_status lsq_solve_fossils(lsq_plan plan, const double *dA, const double *db, double *dx,
+                             lsq_info *info);
+
+/* SPIR (Alg. 3): as lsq_solve_fossils with conjugate gradient (from dy = 0)
+ * as the inner solver. */
+lsq_status lsq_solve_spir(lsq_plan plan, const double *dA, const double *db, double *dx,
+                          lsq_info *info);
+
+/* As lsq_solve_fossils / lsq_solve_spir with HOST buffers hA (m x n, lda),
+ * hb (m) and hx (n): copies A and b to plan-owned device memory (allocated
+ * on first use, kept with the plan), solves, and copies x back.  method: 0 =
+ * FOSSILS, 1 = SPIR. */
+lsq_status lsq_solve_host(lsq_plan plan, int method, const double *hA, const double *hb,
+                          double *hx, lsq_info *info);
+
+/* ---- step-level entry points (each one step of the path, for composing
+ * ---- the path and for checking each step on its own) -------------------- */
+
+/* Rows and signs of S: d_rows (m x zeta int32, device), d_signbits (m
+ * uint32, device; bit k set => the k-th nonzero of column j is -1).  The
+ * embedding is the Philox4x64-10 spec of Sec. 4.2's sparse sign embedding
+ * described in the design doc. */
+lsq_status lsq_sketch_pattern(lsq_plan plan, int32_t *d_rows, uint32_t *d_signbits);
+
+/* After lsq_sketch: copy the scaled sketch [SA Sb] (d x (n+1), column-major,
+ * leading dimension d) and the column norms d_j (n) to device buffers. */
+lsq_status lsq_get_sketch(lsq_plan plan, double *dSAb, double *dcolnorm);
+
+/* After lsq_sketch: copy R (n x n, row-major, zeros below the diagonal),
+ * t = (Q^T Sb)[0:n] and x0 (scaled coordinates) to device buffers (any may
+ * be NULL), and the condest / normest estimates to host doubles (may be NULL). */
+lsq_status lsq_get_R(lsq_plan plan, double *dR, double *dt, double *dx0, double *condest,
+                     double *normest);
+
+/* One fused streaming pass over A: dh = A^T (A dz) (the operator of
+ * Sec. 2.1's preconditioned normal equations before the R solves; Alg. 1's
+ * Apply).  dz, dh: n, device.  No scaling is applied. */
+lsq_status lsq_apply_normal(lsq_plan plan, const double *dA, const double *dz, double *dh);
+
+/* One fused streaming pass over A: dg = A^T (db - A dx) and *r2 = ||b - A x||^2
+ * (Alg. 1, the refinement right-hand side before the R^{-T} solve).  r2 is a
+ * host pointer and may be NULL. */
+lsq_status lsq_residual(lsq_plan plan, const double *dA, const double *db, const double *dx,
+                        double *dg, double *r2);
+
+/* Triangular solve with the plan's R by back substitution (Sec. 6): dx =
+ * R^{-1} dy (trans = 0) or R^{-T} dy (trans = 1).  dx may equal dy. */
+lsq_status lsq_trsv(lsq_plan plan, int trans, const double *dy, double *dx);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char *lsq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSQ_H */

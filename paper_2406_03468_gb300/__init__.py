@@ -1,0 +1,231 @@
+"""Python binding of liblsq (include/lsq.h): FOSSILS and SPIR least-squares
+solvers on GB300 (sm_103a).
+
+The functions here carry the C ABI's names and only marshal arguments:
+torch tensors (or raw device pointers) go in as pointers, status codes come
+back as exceptions.  Every step of a solve runs in the CUDA library; there is
+no CPU fallback, and importing fails loudly when the library cannot be built
+or loaded.
+"""
+import ctypes
+import os
+
+from . import _build
+
+__all__ = [
+    "LsqError", "LsqOptions", "LsqInfo", "lsq_options_default", "lsq_plan_create",
+    "lsq_plan_destroy", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir", "lsq_solve_host",
+    "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_R", "lsq_apply_normal", "lsq_residual",
+    "lsq_trsv", "lsq_last_error", "Plan", "library_path", "EXPORTED",
+    "LSQ_PREC_AUTO", "LSQ_PREC_FP64", "LSQ_PREC_FP32_INNER",
+]
+
+LSQ_OK = 0
+LSQ_PENDING = 1
+LSQ_WARN_RANK_DEFICIENT = 2
+LSQ_PREC_AUTO, LSQ_PREC_FP64, LSQ_PREC_FP32_INNER = 0, 1, 2
+LSQ_MAX_REFINE = 8
+
+_STATUS = {0: "LSQ_OK", 1: "LSQ_PENDING", 2: "LSQ_WARN_RANK_DEFICIENT", -1: "LSQ_ERR_INVALID",
+           -2: "LSQ_ERR_OOM", -3: "LSQ_ERR_CUDA", -4: "LSQ_ERR_NOT_CONVERGED",
+           -5: "LSQ_ERR_TIMEOUT", -6: "LSQ_ERR_NONFINITE"}
+
+
+class LsqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class LsqOptions(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("d", ctypes.c_int32), ("zeta", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("eta", ctypes.c_double), ("col_scale", ctypes.c_int32),
+                ("max_inner", ctypes.c_int32), ("max_refine", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("fp32_cond_max", ctypes.c_double),
+                ("stop_gamma", ctypes.c_double), ("stop_rho", ctypes.c_double),
+                ("fixed_inner", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+
+
+class LsqInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32 * LSQ_MAX_REFINE), ("refine_steps", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("passes", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("condest", ctypes.c_double), ("normest", ctypes.c_double),
+                ("cnorm", ctypes.c_double * LSQ_MAX_REFINE), ("resid0", ctypes.c_double),
+                ("thresh1", ctypes.c_double), ("ms_sketch", ctypes.c_float),
+                ("ms_qr", ctypes.c_float), ("ms_refine", ctypes.c_float),
+                ("ms_total", ctypes.c_float)]
+
+    def as_dict(self):
+        k = self.refine_steps
+        return {"iters": list(self.iters[:k]), "refine_steps": k, "path": self.path,
+                "passes": self.passes, "status": self.status, "condest": self.condest,
+                "normest": self.normest, "cnorm": list(self.cnorm[:k]), "resid0": self.resid0,
+                "thresh1": self.thresh1, "ms_sketch": self.ms_sketch, "ms_qr": self.ms_qr,
+                "ms_refine": self.ms_refine, "ms_total": self.ms_total}
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int
+_dp = ctypes.POINTER(ctypes.c_double)
+# name -> (restype, argtypes); every function of include/lsq.h
+EXPORTED = {
+    "lsq_options_default": (None, [ctypes.POINTER(LsqOptions)]),
+    "lsq_plan_create": (_i32, [ctypes.POINTER(LsqOptions), _vp, ctypes.POINTER(_vp)]),
+    "lsq_plan_destroy": (None, [_vp]),
+    "lsq_sketch": (_i32, [_vp, _vp, _vp]),
+    "lsq_solve_fossils": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
+    "lsq_solve_spir": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
+    "lsq_solve_host": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
+    "lsq_sketch_pattern": (_i32, [_vp, _vp, _vp]),
+    "lsq_get_sketch": (_i32, [_vp, _vp, _vp]),
+    "lsq_get_R": (_i32, [_vp, _vp, _vp, _vp, _dp, _dp]),
+    "lsq_apply_normal": (_i32, [_vp, _vp, _vp, _vp]),
+    "lsq_residual": (_i32, [_vp, _vp, _vp, _vp, _vp, _dp]),
+    "lsq_trsv": (_i32, [_vp, _i32, _vp, _vp]),
+    "lsq_last_error": (ctypes.c_char_p, []),
+}
+
+_LIB = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def _lib():
+    """Load liblsq.so (building it with nvcc when missing or stale)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError("liblsq.so is missing and could not be built")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTED.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (or an int pointer, or None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _check(status):
+    if status < 0:
+        raise LsqError(status, lsq_last_error())
+    return status
+
+
+def lsq_last_error():
+    return (_lib().lsq_last_error() or b"").decode()
+
+
+def lsq_options_default(**kw):
+    o = LsqOptions()
+    _lib().lsq_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError("unknown option %r" % k)
+        setattr(o, k, v)
+    return o
+
+
+def lsq_plan_create(opts, stream=None):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None (default stream)."""
+    h = _vp()
+    s = getattr(stream, "cuda_stream", stream)
+    _check(_lib().lsq_plan_create(ctypes.byref(opts), s, ctypes.byref(h)))
+    return h
+
+
+def lsq_plan_destroy(plan):
+    _lib().lsq_plan_destroy(plan)
+
+
+def lsq_sketch(plan, A, b):
+    return _check(_lib().lsq_sketch(plan, _ptr(A), _ptr(b)))
+
+
+def _solve(fn, plan, A, b, x, info):
+    inf = info if info is not None else LsqInfo()
+    st = _check(fn(plan, _ptr(A), _ptr(b), _ptr(x), ctypes.byref(inf)))
+    return st, inf
+
+
+def lsq_solve_fossils(plan, A, b, x, info=None):
+    return _solve(_lib().lsq_solve_fossils, plan, A, b, x, info)
+
+
+def lsq_solve_spir(plan, A, b, x, info=None):
+    return _solve(_lib().lsq_solve_spir, plan, A, b, x, info)
+
+
+def lsq_solve_host(plan, method, A, b, x, info=None):
+    """Host-buffer solve: A, b, x are host tensors / numpy arrays (pointer via
+    .data_ptr() or .ctypes.data)."""
+    def hp(a):
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+    inf = info if info is not None else LsqInfo()
+    st = _check(_lib().lsq_solve_host(plan, int(method), hp(A), hp(b), hp(x), ctypes.byref(inf)))
+    return st, inf
+
+
+def lsq_sketch_pattern(plan, rows, signbits):
+    return _check(_lib().lsq_sketch_pattern(plan, _ptr(rows), _ptr(signbits)))
+
+
+def lsq_get_sketch(plan, SAb, colnorm):
+    return _check(_lib().lsq_get_sketch(plan, _ptr(SAb), _ptr(colnorm)))
+
+
+def lsq_get_R(plan, R=None, t=None, x0=None):
+    ce = ctypes.c_double()
+    ne = ctypes.c_double()
+    _check(_lib().lsq_get_R(plan, _ptr(R), _ptr(t), _ptr(x0), ctypes.byref(ce), ctypes.byref(ne)))
+    return ce.value, ne.value
+
+
+def lsq_apply_normal(plan, A, z, h):
+    return _check(_lib().lsq_apply_normal(plan, _ptr(A), _ptr(z), _ptr(h)))
+
+
+def lsq_residual(plan, A, b, x, g):
+    r2 = ctypes.c_double()
+    _check(_lib().lsq_residual(plan, _ptr(A), _ptr(b), _ptr(x), _ptr(g), ctypes.byref(r2)))
+    return r2.value
+
+
+def lsq_trsv(plan, trans, y, x):
+    return _check(_lib().lsq_trsv(plan, int(trans), _ptr(y), _ptr(x)))
+
+
+class Plan:
+    """Owns an lsq_plan (destroyed with the object)."""
+
+    def __init__(self, m, n, stream=None, **opts):
+        self.opts = lsq_options_default(m=m, n=n, **opts)
+        self.handle = lsq_plan_create(self.opts, stream)
+
+    def close(self):
+        if self.handle:
+            lsq_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, A, b, x, method="fossils"):
+        fn = lsq_solve_fossils if method == "fossils" else lsq_solve_spir
+        st, info = fn(self.handle, A, b, x)
+        return st, info.as_dict()

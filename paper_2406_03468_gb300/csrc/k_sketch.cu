@@ -1,0 +1,245 @@
+// Sparse sign embedding and the sketch pass S [A b] (Sec. 4.2, "Choice of
+// embedding"; Alg. 1, first line).
+//
+// S = zeta^{-1/2} [s_1 ... s_m]: column j of S has zeta nonzeros +-1 at
+// distinct rows.  The rows and signs follow this library's Philox4x64-10
+// spec (counter (j, t, 0, 0), key (seed, 0); 32-bit halves of each block,
+// low half first; the first half of block 0 carries the sign bits; the rest
+// are candidate rows floor(u d / 2^32) accepted unless repeated).
+//
+// The pass reads each row of A once (one warp per row, 16-byte loads) and
+// scatters +-a_j into the zeta rows of the row-major, L2-resident sketch
+// with FP64 reductions performed in L2; it also accumulates the column sums
+// of squares for the column scaling of Alg. 4.  The finalize kernel turns
+// the sums into column norms, applies diag(d)^{-1} and zeta^{-1/2}, and
+// transposes the sketch to the column-major layout the QR works on.
+#include "lsq_common.cuh"
+
+namespace lsq {
+
+namespace {
+
+constexpr uint64_t kPhiloxM0 = 0xD2E7470EE14C6C93ull;
+constexpr uint64_t kPhiloxM1 = 0xCA5A826395121157ull;
+constexpr uint64_t kPhiloxW0 = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kPhiloxW1 = 0xBB67AE8584CAA73Bull;
+
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    const uint64_t hi0 = __umul64hi(kPhiloxM0, c[0]), lo0 = kPhiloxM0 * c[0];
+    const uint64_t hi1 = __umul64hi(kPhiloxM1, c[2]), lo1 = kPhiloxM1 * c[2];
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// One thread per column j of S (row j of A).
+__global__ void pattern_kernel(int64_t m, int d, int zeta, uint64_t seed, int32_t *rows,
+                               uint32_t *signbits) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  int h[kMaxZeta];
+  int cnt = 0;
+  uint32_t sb = 0;
+  // Bounded: at most 1<<16 blocks (the expected count is < 20 even for d = zeta = 32).
+  for (uint64_t t = 0; cnt < zeta && t < (1ull << 16); t++) {
+    uint64_t c[4] = {(uint64_t)j, t, 0ull, 0ull};
+    philox4x64_10(c, seed, 0ull);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const uint32_t u = (q & 1) ? (uint32_t)(c[q >> 1] >> 32) : (uint32_t)(c[q >> 1]);
+      if (t == 0 && q == 0) {
+        sb = u;
+        continue;
+      }
+      if (cnt >= zeta) continue;
+      const int hh = (int)(((uint64_t)u * (uint64_t)d) >> 32);
+      bool dup = false;
+      for (int k = 0; k < cnt; k++) dup |= (h[k] == hh);
+      if (!dup) h[cnt++] = hh;
+    }
+  }
+  for (int k = 0; k < zeta; k++) rows[j * zeta + k] = (k < cnt) ? h[k] : -1;
+  signbits[j] = sb;
+}
+
+template <int NC, bool VEC>
+__device__ __forceinline__ void load_row(const double *__restrict__ row, int n, int lane,
+                                         double (&a)[2 * NC]) {
+#pragma unroll
+  for (int k = 0; k < NC; k++) {
+    const int col = 64 * k + 2 * lane;
+    if (VEC && col + 1 < n) {
+      const double2 v = __ldcs(reinterpret_cast<const double2 *>(row + col));
+      a[2 * k] = v.x;
+      a[2 * k + 1] = v.y;
+    } else {
+      a[2 * k] = (col < n) ? __ldcs(row + col) : 0.0;
+      a[2 * k + 1] = (col + 1 < n) ? __ldcs(row + col + 1) : 0.0;
+    }
+  }
+}
+
+__device__ __forceinline__ double flip_sign(double a, bool neg) {
+  return __longlong_as_double(__double_as_longlong(a) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
+}
+
+template <int NC, bool VEC>
+__global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
+    sketch_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
+                  const double *__restrict__ b, int d, int zeta, const int32_t *__restrict__ rows,
+                  const uint32_t *__restrict__ signbits, double *__restrict__ SAb,
+                  double *__restrict__ colsq_part, int npad) {
+  __shared__ double acc[NC * 64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = min(m, (int64_t)blockIdx.x * per), r1 = min(m, r0 + per);
+  const int ldsa = n + 1;
+  double sq[2 * NC];
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) sq[k] = 0.0;
+
+  for (int64_t i = r0 + warp; i < r1; i += nw) {
+    double a[2 * NC];
+    load_row<NC, VEC>(A + i * lda, n, lane, a);
+    const int myh = (lane < zeta) ? rows[i * zeta + lane] : 0;
+    const uint32_t sb = signbits[i];
+#pragma unroll
+    for (int k = 0; k < 2 * NC; k++) sq[k] = fma(a[k], a[k], sq[k]);
+    if (lane < zeta && (unsigned)myh < (unsigned)d) {
+      atomicAdd(SAb + (size_t)myh * ldsa + n, flip_sign(b[i], (sb >> lane) & 1u));
+    }
+    for (int t = 0; t < zeta; t++) {
+      const int h = __shfl_sync(0xffffffffu, myh, t);
+      if ((unsigned)h >= (unsigned)d) continue;
+      const bool neg = (sb >> t) & 1u;
+      double *dst = SAb + (size_t)h * ldsa;
+#pragma unroll
+      for (int k = 0; k < NC; k++) {
+        const int col = 64 * k + 2 * lane;
+        if (col < n) atomicAdd(dst + col, flip_sign(a[2 * k], neg));
+        if (col + 1 < n) atomicAdd(dst + col + 1, flip_sign(a[2 * k + 1], neg));
+      }
+    }
+  }
+  for (int i = threadIdx.x; i < NC * 64; i += blockDim.x) acc[i] = 0.0;
+  for (int w = 0; w < nw; w++) {
+    __syncthreads();
+    if (warp == w) {
+#pragma unroll
+      for (int k = 0; k < NC; k++) {
+        const int col = 64 * k + 2 * lane;
+        acc[col] += sq[2 * k];
+        acc[col + 1] += sq[2 * k + 1];
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < npad; i += blockDim.x)
+    colsq_part[(size_t)blockIdx.x * npad + i] = acc[i];
+}
+
+__global__ void colnorm_kernel(const double *__restrict__ part, int grid, int npad, int n,
+                               int col_scale, double *dcol, double *dinv, DevState *st) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int g = 0; g < grid; g++) s += part[(size_t)g * npad + j];
+  const double nrm = sqrt(s);
+  if (!isfinite(nrm)) atomicExch(&st->nonfinite, 1);
+  if (col_scale && nrm == 0.0) atomicExch(&st->zero_col, 1);
+  dcol[j] = col_scale ? nrm : 1.0;
+  dinv[j] = col_scale ? 1.0 / nrm : 1.0;
+}
+
+// W[c * d + h] = SAb[h * (n+1) + c] * scale_c, scale_c = dinv_c zeta^{-1/2}
+// (c < n) or zeta^{-1/2} (c == n).  32 x 32 tiles through shared memory.
+__global__ void transpose_scale_kernel(const double *__restrict__ SAb, int n, int d,
+                                       const double *__restrict__ dinv, double zinv,
+                                       double *__restrict__ W, DevState *st) {
+  __shared__ double tile[32][33];
+  const int ncols = n + 1;
+  const int c0 = blockIdx.x * 32, h0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int h = h0 + r, c = c0 + threadIdx.x;
+    if (h < d && c < ncols) {
+      const double v = SAb[(size_t)h * ncols + c];
+      if (!isfinite(v)) atomicExch(&st->nonfinite, 1);
+      tile[r][threadIdx.x] = v;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int c = c0 + r, h = h0 + threadIdx.x;
+    if (h < d && c < ncols) {
+      const double sc = (c < n) ? dinv[c] * zinv : zinv;
+      W[(size_t)c * d + h] = tile[threadIdx.x][r] * sc;
+    }
+  }
+}
+
+}  // namespace
+
+int pass_npad(int n) {
+  int nc = 1;
+  while (nc * 64 < n) nc *= 2;
+  return nc * 64;
+}
+
+cudaError_t launch_sketch_pattern(int64_t m, int d, int zeta, uint64_t seed, int32_t *rows,
+                                  uint32_t *signbits, cudaStream_t s) {
+  const int th = 128;
+  const int64_t blocks = (m + th - 1) / th;
+  pattern_kernel<<<(unsigned)blocks, th, 0, s>>>(m, d, zeta, seed, rows, signbits);
+  return cudaGetLastError();
+}
+
+template <int NC>
+static void sketch_dispatch(bool vec, int grid, cudaStream_t s, const double *A, int64_t lda,
+                            int64_t m, int n, const double *b, int d, int zeta,
+                            const int32_t *rows, const uint32_t *sb, double *SAb, double *part,
+                            int npad) {
+  if (vec)
+    sketch_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, d, zeta, rows, sb, SAb,
+                                                          part, npad);
+  else
+    sketch_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, d, zeta, rows, sb,
+                                                           SAb, part, npad);
+}
+
+cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, const double *b, int d,
+                          int zeta, const int32_t *rows, const uint32_t *signbits, double *SAb,
+                          double *colsq_part, int grid, int npad, cudaStream_t s) {
+  const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 2 == 0);
+  switch (npad / 64) {
+    case 1: sketch_dispatch<1>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad); break;
+    case 2: sketch_dispatch<2>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad); break;
+    case 4: sketch_dispatch<4>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad); break;
+    case 8: sketch_dispatch<8>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad); break;
+    case 16: sketch_dispatch<16>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad, int n, int d,
+                                   int zeta, int col_scale, const double *SAb, double *W,
+                                   double *dcol, double *dinv, DevState *st, cudaStream_t s) {
+  colnorm_kernel<<<(n + 255) / 256, 256, 0, s>>>(colsq_part, grid, npad, n, col_scale, dcol, dinv,
+                                                 st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 blk(32, 8), grd((n + 1 + 31) / 32, (d + 31) / 32);
+  transpose_scale_kernel<<<grd, blk, 0, s>>>(SAb, n, d, dinv, 1.0 / sqrt((double)zeta), W, st);
+  return cudaGetLastError();
+}
+
+}  // namespace lsq

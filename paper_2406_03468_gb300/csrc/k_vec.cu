@@ -1,0 +1,132 @@
+// n-vector steps of the inner solvers, one CTA each (n <= LSQ_MAX_N):
+//   Polyak heavy ball (Alg. 5, in the loop form of Alg. 4):
+//     Delta = alpha (c - M dy) + beta (dy - dy_old);  (dy, dy_old) <- (dy + Delta, dy)
+//   conjugate gradient on M dy = c from dy = 0 (Alg. 3's inner solver)
+// and the step-1 stopping rule of Sec. 4.2 ("Adaptive stopping", item 1):
+//   stop once ||Delta|| <= u (gamma normest ||x_0|| + rho condest ||b - A x_0||).
+// The stop decision is taken on the device (DevState::done) so that the
+// host never waits between iterations.
+#include "lsq_common.cuh"
+
+namespace lsq {
+
+namespace {
+
+__global__ void __launch_bounds__(kVecThreads)
+    inner_init_kernel(int method, int n, const double *__restrict__ c, double *dy,
+                      double *dy_old, double *res, double *p, int max_iters, int use_thresh,
+                      DevState *st) {
+  __shared__ double scratch[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double ci = c[i];
+    if (method == 0) {
+      dy[i] = ci;
+      dy_old[i] = ci;
+    } else {
+      dy[i] = 0.0;
+      res[i] = ci;
+      p[i] = ci;
+      s = fma(ci, ci, s);
+    }
+  }
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) {
+    st->rho = s;
+    st->iters = 0;
+    st->max_iters = max_iters;
+    st->use_thresh = use_thresh;
+    st->dnorm2 = 0.0;
+    st->done = (max_iters <= 0) ? 1 : 0;
+  }
+}
+
+__device__ __forceinline__ void finish_update(DevState *st, double dn2, bool exhausted) {
+  const int it = st->iters + 1;
+  st->iters = it;
+  st->dnorm2 = dn2;
+  bool stop = it >= st->max_iters || exhausted;
+  if (st->use_thresh && sqrt(dn2) <= st->thresh1) stop = true;
+  if (stop) st->done = 1;
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+    polyak_update_kernel(int n, const double *__restrict__ c, const double *__restrict__ w,
+                         double *dy, double *dy_old, DevState *st) {
+  if (*(volatile int *)&st->done) return;
+  __shared__ double scratch[32];
+  const double alpha = st->alpha, beta = st->beta;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double y = dy[i];
+    const double delta = alpha * (c[i] - w[i]) + beta * (y - dy_old[i]);
+    dy_old[i] = y;
+    dy[i] = y + delta;
+    s = fma(delta, delta, s);
+  }
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) finish_update(st, s, false);
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+    cg_update_kernel(int n, const double *__restrict__ q, double *p, double *res, double *dy,
+                     DevState *st) {
+  if (*(volatile int *)&st->done) return;
+  __shared__ double scratch[32];
+  double pq = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) pq = fma(p[i], q[i], pq);
+  pq = block_sum(pq, scratch);
+  const double rho = st->rho;
+  const double gam = rho / pq;
+  double rr = 0.0, ss = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double step = gam * p[i];
+    dy[i] += step;
+    const double r = res[i] - gam * q[i];
+    res[i] = r;
+    rr = fma(r, r, rr);
+    ss = fma(step, step, ss);
+  }
+  rr = block_sum(rr, scratch);
+  ss = block_sum(ss, scratch);
+  const double bet = rr / rho;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = res[i] + bet * p[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->rho = rr;
+    finish_update(st, ss, !(rr > 0.0));
+  }
+}
+
+__global__ void set_thresh_kernel(double gamma, double rho, DevState *st) {
+  st->thresh1 = kU * (gamma * st->normest * sqrt(st->x0norm2) + rho * st->condest * sqrt(st->r2));
+}
+
+}  // namespace
+
+cudaError_t launch_inner_init(int method, int n, const double *c, double *dy, double *dy_old,
+                              double *res, double *p, int max_iters, int use_thresh,
+                              DevState *st, cudaStream_t s) {
+  inner_init_kernel<<<1, kVecThreads, 0, s>>>(method, n, c, dy, dy_old, res, p, max_iters,
+                                              use_thresh, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_polyak_update(int n, const double *c, const double *w, double *dy,
+                                 double *dy_old, DevState *st, cudaStream_t s) {
+  polyak_update_kernel<<<1, kVecThreads, 0, s>>>(n, c, w, dy, dy_old, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(int n, const double *q, double *p, double *res, double *dy,
+                             DevState *st, cudaStream_t s) {
+  cg_update_kernel<<<1, kVecThreads, 0, s>>>(n, q, p, res, dy, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_thresh(double gamma, double rho, DevState *st, cudaStream_t s) {
+  set_thresh_kernel<<<1, 1, 0, s>>>(gamma, rho, st);
+  return cudaGetLastError();
+}
+
+}  // namespace lsq

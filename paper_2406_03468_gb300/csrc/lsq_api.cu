@@ -1,0 +1,451 @@
+// Host driver and C ABI (include/lsq.h) of the least-squares library.
+//
+// A solve is Alg. 1 of the paper with FOSSILS' Polyak (Alg. 2, Alg. 5) or
+// SPIR's conjugate gradient (Alg. 3) as the inner solver and the practical
+// rules of Sec. 4.2 / Alg. 4 (column scaling, d = 12n, zeta = 8,
+// eta = sqrt(n/d), the step-1 stopping rule, the q0 count of Theorem 7.1 for
+// step 2).  Every step is one of this library's kernels, enqueued on the
+// plan's stream; the host only waits (a) once after the sketch and QR, for
+// condest and the input checks, and (b) every few inner iterations of step 1
+// to learn whether the device-side stop test has fired.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "lsq_common.cuh"
+
+using namespace lsq;
+
+namespace {
+
+thread_local std::string g_err;
+
+lsq_status fail(lsq_status st, const std::string &msg) {
+  g_err = msg;
+  return st;
+}
+
+#define LSQ_CU(call)                                                                     \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(LSQ_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+#define LSQ_TRY(expr)                 \
+  do {                                \
+    lsq_status s_ = (expr);           \
+    if (s_ < 0) return s_;            \
+  } while (0)
+
+constexpr uint64_t kBarrierTimeoutNs = 5ull * 1000 * 1000 * 1000;  // 5 s per grid barrier
+constexpr int kCondestIters = 10;
+constexpr int kStopPollEvery = 4;  // step 1: read the device stop flag every 4 updates
+
+}  // namespace
+
+struct lsq_plan_s {
+  lsq_options o{};
+  cudaStream_t s = nullptr;
+  int dev = 0, nsm = 0;
+  int64_t m = 0, n = 0, lda = 0;
+  int d = 0, zeta = 0, npad = 0, gpass = 0, gqr = 0;
+  double eta = 0, alpha = 0, beta = 0;
+  int32_t *pat_rows = nullptr;
+  uint32_t *pat_sb = nullptr;
+  bool pat_valid = false;
+  double *SAb = nullptr, *W = nullptr, *part = nullptr, *r2part = nullptr, *cpart = nullptr;
+  double *dcol = nullptr, *dinv = nullptr, *Rcm = nullptr, *Rrm = nullptr, *rinv = nullptr;
+  double *t = nullptr, *vbuf = nullptr;
+  double *xs = nullptr, *xo = nullptr, *c = nullptr, *g = nullptr, *dy = nullptr;
+  double *dyold = nullptr, *z = nullptr, *h = nullptr, *w = nullptr, *res = nullptr, *p = nullptr;
+  DevState *st = nullptr;
+  DevState *st_host = nullptr;
+  unsigned int *bar = nullptr;
+  cudaEvent_t ev[5] = {};
+  double *stageA = nullptr, *stageb = nullptr, *stagex = nullptr;
+  bool sketched = false;
+};
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+  return cudaMalloc((void **)p, count * sizeof(T) + 16);
+}
+
+lsq_status validate(const lsq_options *o) {
+  if (!o) return fail(LSQ_ERR_INVALID, "options is NULL");
+  if (o->n < 1 || o->m < o->n) return fail(LSQ_ERR_INVALID, "need m >= n >= 1");
+  if (o->n > LSQ_MAX_N) return fail(LSQ_ERR_INVALID, "n exceeds LSQ_MAX_N");
+  if (o->lda != 0 && o->lda < o->n) return fail(LSQ_ERR_INVALID, "lda < n");
+  const int64_t d = o->d ? o->d : 12 * o->n;
+  if (d < o->n || d > (int64_t)1 << 24) return fail(LSQ_ERR_INVALID, "need n <= d <= 2^24");
+  const int zeta = o->zeta ? o->zeta : 8;
+  if (zeta < 1 || zeta > kMaxZeta || zeta > d) return fail(LSQ_ERR_INVALID, "need 1 <= zeta <= min(32, d)");
+  if (o->max_inner < 0 || o->max_refine < 0 || o->max_refine > LSQ_MAX_REFINE)
+    return fail(LSQ_ERR_INVALID, "max_inner / max_refine out of range");
+  if (o->eta < 0 || o->eta >= 1) return fail(LSQ_ERR_INVALID, "eta must be in [0, 1)");
+  if (o->precision < LSQ_PREC_AUTO || o->precision > LSQ_PREC_FP32_INNER)
+    return fail(LSQ_ERR_INVALID, "unknown precision");
+  return LSQ_OK;
+}
+
+// Step-2 inner count: q0 of Theorem 7.1 with kappa -> condest and distortion
+// 1.01 eta; Alg. 5 returns dy_(q) after q - 1 updates.
+int step2_updates(double condest, double eta, int max_inner) {
+  const double e = 1.01 * eta;
+  double q0 = 11.0;
+  if (e > 0.0 && std::isfinite(condest) && condest > 0.0) {
+    const double v = 1.0 + 2.0 * std::log(1.0 / (condest * kU)) / std::log(1.0 / e);
+    q0 = v > 11.0 ? v : 11.0;
+  }
+  int q = (int)std::ceil(q0) - 1;
+  if (q < 1) q = 1;
+  if (q > max_inner) q = max_inner;
+  return q;
+}
+
+lsq_status read_state(lsq_plan P) {
+  LSQ_CU(cudaMemcpyAsync(P->st_host, P->st, sizeof(DevState), cudaMemcpyDeviceToHost, P->s));
+  LSQ_CU(cudaStreamSynchronize(P->s));
+  if (P->st_host->err != 0) return fail((lsq_status)P->st_host->err, "device-side wait timed out");
+  return LSQ_OK;
+}
+
+lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
+  if (!dA || !db) return fail(LSQ_ERR_INVALID, "A or b is NULL");
+  const int n = (int)P->n;
+  // fresh device state with alpha, beta
+  std::memset(P->st_host, 0, sizeof(DevState));
+  P->st_host->alpha = P->alpha;
+  P->st_host->beta = P->beta;
+  LSQ_CU(cudaMemcpyAsync(P->st, P->st_host, sizeof(DevState), cudaMemcpyHostToDevice, P->s));
+  LSQ_CU(cudaEventRecord(P->ev[0], P->s));
+  if (!P->pat_valid) {
+    LSQ_CU(launch_sketch_pattern(P->m, P->d, P->zeta, P->o.seed, P->pat_rows, P->pat_sb, P->s));
+    P->pat_valid = true;
+  }
+  LSQ_CU(cudaMemsetAsync(P->SAb, 0, sizeof(double) * (size_t)P->d * (n + 1), P->s));
+  LSQ_CU(launch_sketch(dA, P->lda, P->m, n, db, P->d, P->zeta, P->pat_rows, P->pat_sb, P->SAb,
+                       P->cpart, P->gpass, P->npad, P->s));
+  LSQ_CU(launch_sketch_finalize(P->cpart, P->gpass, P->npad, n, P->d, P->zeta, P->o.col_scale,
+                                P->SAb, P->W, P->dcol, P->dinv, P->st, P->s));
+  LSQ_CU(cudaEventRecord(P->ev[1], P->s));
+  LSQ_CU(launch_qr(P->W, P->d, n, P->vbuf, P->bar, P->st, P->gqr, kBarrierTimeoutNs, P->s));
+  LSQ_CU(launch_extract_r(P->W, P->d, n, P->Rcm, P->Rrm, P->rinv, P->t, P->s));
+  LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, n, kCondestIters, P->st, P->s));
+  // sketch-and-solve x0 = R^{-1} t (scaled coordinates) and x0 / d (original)
+  LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->t, nullptr, P->xs, P->dinv, P->xo,
+                     nullptr, &P->st->x0norm2, nullptr, P->s));
+  LSQ_CU(cudaEventRecord(P->ev[2], P->s));
+  LSQ_TRY(read_state(P));
+  if (P->st_host->nonfinite) return fail(LSQ_ERR_NONFINITE, "A or b holds NaN or Inf");
+  if (P->st_host->zero_col) return fail(LSQ_ERR_INVALID, "A has a zero column (column scaling)");
+  P->sketched = true;
+  return LSQ_OK;
+}
+
+lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db, double *dx,
+                     lsq_info *info) {
+  if (!dx) return fail(LSQ_ERR_INVALID, "x is NULL");
+  const int n = (int)P->n;
+  LSQ_TRY(do_sketch(P, dA, db));
+  const double condest = P->st_host->condest;
+  const int max_inner = P->o.max_inner ? P->o.max_inner : 100;
+  const int nref = P->o.max_refine ? P->o.max_refine : 2;
+  const int q2 = step2_updates(condest, P->eta, max_inner);
+  const double gam = P->o.stop_gamma, rho = P->o.stop_rho;
+  int passes = 1;
+  int iters[LSQ_MAX_REFINE] = {0};
+  double resid0 = 0.0;
+  for (int i = 0; i < nref; i++) {
+    LSQ_CU(launch_pass_resid(dA, P->lda, P->m, n, db, P->xo, P->part, P->r2part, P->gpass,
+                             P->npad, P->s));
+    LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->g, P->r2part, &P->st->r2,
+                         nullptr, P->s));
+    passes++;
+    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 1, P->g, nullptr, P->c, nullptr, nullptr,
+                       nullptr, &P->st->cnorm2[i], nullptr, P->s));
+    if (i == 0) LSQ_CU(launch_set_thresh(gam, rho, P->st, P->s));
+    const bool fixed = P->o.fixed_inner > 0;
+    const int cap = fixed ? P->o.fixed_inner : (i == 0 ? max_inner : q2);
+    const int use_thresh = (!fixed && i == 0) ? 1 : 0;
+    LSQ_CU(launch_inner_init(method, n, P->c, P->dy, P->dyold, P->res, P->p, cap, use_thresh,
+                             P->st, P->s));
+    for (int it = 0; it < cap; it++) {
+      const double *src = (method == 0) ? P->dy : P->p;
+      // z = D^{-1} R^{-1} src;  h = D^{-1} A^T (A z);  w = R^{-T} h
+      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, src, nullptr, nullptr, P->dinv, P->z,
+                         nullptr, nullptr, P->st, P->s));
+      LSQ_CU(launch_pass_atax(dA, P->lda, P->m, n, P->z, P->part, P->gpass, P->npad, P->st,
+                              P->s));
+      LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->h, nullptr, nullptr, P->st,
+                           P->s));
+      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 1, P->h, nullptr, P->w, nullptr, nullptr,
+                         nullptr, nullptr, P->st, P->s));
+      if (method == 0)
+        LSQ_CU(launch_polyak_update(n, P->c, P->w, P->dy, P->dyold, P->st, P->s));
+      else
+        LSQ_CU(launch_cg_update(n, P->w, P->p, P->res, P->dy, P->st, P->s));
+      if (use_thresh && (it % kStopPollEvery) == kStopPollEvery - 1 && it + 1 < cap) {
+        LSQ_TRY(read_state(P));
+        if (P->st_host->done) break;
+      }
+    }
+    // x_s += R^{-1} dy ; x_o = D^{-1} x_s
+    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->dy, nullptr, nullptr, P->dinv, P->xo,
+                       P->xs, nullptr, nullptr, P->s));
+    LSQ_TRY(read_state(P));
+    iters[i] = P->st_host->iters;
+    if (i == 0) resid0 = std::sqrt(P->st_host->r2);
+    passes += iters[i];
+  }
+  LSQ_CU(cudaMemcpyAsync(dx, P->xo, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->s));
+  LSQ_CU(cudaEventRecord(P->ev[3], P->s));
+  LSQ_TRY(read_state(P));
+  const DevState &S = *P->st_host;
+  lsq_status status = LSQ_OK;
+  if (S.condest > 1.0 / (30.0 * kU)) status = LSQ_WARN_RANK_DEFICIENT;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    for (int i = 0; i < nref; i++) {
+      info->iters[i] = iters[i];
+      info->cnorm[i] = std::sqrt(S.cnorm2[i]);
+    }
+    info->refine_steps = nref;
+    info->path = LSQ_PREC_FP64;
+    info->passes = passes;
+    info->status = status;
+    info->condest = S.condest;
+    info->normest = S.normest;
+    info->thresh1 = S.thresh1;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, P->ev[0], P->ev[1]);
+    info->ms_sketch = ms;
+    cudaEventElapsedTime(&ms, P->ev[1], P->ev[2]);
+    info->ms_qr = ms;
+    cudaEventElapsedTime(&ms, P->ev[2], P->ev[3]);
+    info->ms_refine = ms;
+    cudaEventElapsedTime(&ms, P->ev[0], P->ev[3]);
+    info->ms_total = ms;
+  }
+  if (info) info->resid0 = resid0;
+  return status;
+}
+
+void free_plan(lsq_plan P) {
+  if (!P) return;
+  void *bufs[] = {P->pat_rows, P->pat_sb, P->SAb, P->W, P->part, P->r2part, P->cpart, P->dcol, P->dinv,
+                  P->Rcm, P->Rrm, P->rinv, P->t, P->vbuf, P->xs, P->xo, P->c, P->g, P->dy,
+                  P->dyold, P->z, P->h, P->w, P->res, P->p, P->st, P->bar, P->stageA,
+                  P->stageb, P->stagex};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  if (P->st_host) cudaFreeHost(P->st_host);
+  for (auto &e : P->ev)
+    if (e) cudaEventDestroy(e);
+  delete P;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lsq_options_default(lsq_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->zeta = 8;
+  o->col_scale = 1;
+  o->max_inner = 100;
+  o->max_refine = 2;
+  o->precision = LSQ_PREC_FP64;
+  o->fp32_cond_max = 1e5;
+  o->stop_gamma = 1.0;
+  o->stop_rho = 0.04;
+}
+
+const char *lsq_last_error(void) { return g_err.c_str(); }
+
+lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *out) {
+  if (!out) return fail(LSQ_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  LSQ_TRY(validate(opt));
+  lsq_plan P = new lsq_plan_s();
+  P->o = *opt;
+  P->s = (cudaStream_t)cuda_stream;
+  P->m = opt->m;
+  P->n = opt->n;
+  P->lda = opt->lda ? opt->lda : opt->n;
+  P->d = opt->d ? opt->d : (int)(12 * opt->n);
+  P->zeta = opt->zeta ? opt->zeta : 8;
+  P->eta = opt->eta > 0 ? opt->eta : std::sqrt((double)P->n / (double)P->d);
+  P->beta = P->eta * P->eta;
+  P->alpha = (1.0 - P->beta) * (1.0 - P->beta);
+  if (P->o.max_inner == 0) P->o.max_inner = 100;
+  if (P->o.max_refine == 0) P->o.max_refine = 2;
+  const int n = (int)P->n;
+  cudaError_t e = cudaGetDevice(&P->dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, P->dev);
+  if (e != cudaSuccess) {
+    free_plan(P);
+    return fail(LSQ_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+  }
+  P->npad = pass_npad(n);
+  P->gpass = P->nsm * kPassCtasPerSm;
+  P->gqr = qr_grid(n, P->nsm);
+  const size_t nn = (size_t)n * n, dn1 = (size_t)P->d * (n + 1);
+  e = cudaSuccess;
+  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  A(dalloc(&P->pat_rows, (size_t)P->m * P->zeta));
+  A(dalloc(&P->pat_sb, (size_t)P->m));
+  A(dalloc(&P->SAb, dn1));
+  A(dalloc(&P->W, dn1));
+  A(dalloc(&P->part, (size_t)P->gpass * P->npad));
+  A(dalloc(&P->r2part, (size_t)P->gpass));
+  A(dalloc(&P->cpart, (size_t)P->gpass * P->npad));
+  A(dalloc(&P->dcol, n));
+  A(dalloc(&P->dinv, n));
+  A(dalloc(&P->Rcm, nn));
+  A(dalloc(&P->Rrm, nn));
+  A(dalloc(&P->rinv, n));
+  A(dalloc(&P->t, n));
+  A(dalloc(&P->vbuf, 2 * (size_t)P->d));
+  double **vecs[] = {&P->xs, &P->xo, &P->c, &P->g, &P->dy, &P->dyold, &P->z, &P->h, &P->w, &P->res, &P->p};
+  for (double **v : vecs) A(dalloc(v, n));
+  A(dalloc(&P->st, 1));
+  A(dalloc(&P->bar, 2));
+  A(cudaMallocHost((void **)&P->st_host, sizeof(DevState)));
+  for (auto &ev : P->ev) A(cudaEventCreate(&ev));
+  if (e != cudaSuccess) {
+    const bool oom = (e == cudaErrorMemoryAllocation);
+    free_plan(P);
+    return fail(oom ? LSQ_ERR_OOM : LSQ_ERR_CUDA, std::string("plan allocation: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemsetAsync(P->st, 0, sizeof(DevState), P->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
+  if (e != cudaSuccess) {
+    free_plan(P);
+    return fail(LSQ_ERR_CUDA, std::string("plan init: ") + cudaGetErrorString(e));
+  }
+  std::memset(P->st_host, 0, sizeof(DevState));
+  *out = P;
+  return LSQ_OK;
+}
+
+void lsq_plan_destroy(lsq_plan plan) { free_plan(plan); }
+
+lsq_status lsq_sketch(lsq_plan plan, const double *dA, const double *db) {
+  if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  return do_sketch(plan, dA, db);
+}
+
+lsq_status lsq_solve_fossils(lsq_plan plan, const double *dA, const double *db, double *dx,
+                             lsq_info *info) {
+  if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  return run_solve(plan, 0, dA, db, dx, info);
+}
+
+lsq_status lsq_solve_spir(lsq_plan plan, const double *dA, const double *db, double *dx,
+                          lsq_info *info) {
+  if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  return run_solve(plan, 1, dA, db, dx, info);
+}
+
+lsq_status lsq_solve_host(lsq_plan P, int method, const double *hA, const double *hb, double *hx,
+                          lsq_info *info) {
+  if (!P) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  if (!hA || !hb || !hx) return fail(LSQ_ERR_INVALID, "host buffer is NULL");
+  if (method != 0 && method != 1) return fail(LSQ_ERR_INVALID, "method must be 0 or 1");
+  const size_t an = (size_t)P->m * P->lda;
+  if (!P->stageA) {
+    cudaError_t e = dalloc(&P->stageA, an);
+    if (e == cudaSuccess) e = dalloc(&P->stageb, (size_t)P->m);
+    if (e == cudaSuccess) e = dalloc(&P->stagex, (size_t)P->n);
+    if (e != cudaSuccess) return fail(LSQ_ERR_OOM, "staging allocation failed");
+  }
+  LSQ_CU(cudaMemcpyAsync(P->stageA, hA, an * sizeof(double), cudaMemcpyHostToDevice, P->s));
+  LSQ_CU(cudaMemcpyAsync(P->stageb, hb, (size_t)P->m * sizeof(double), cudaMemcpyHostToDevice, P->s));
+  lsq_status st = run_solve(P, method, P->stageA, P->stageb, P->stagex, info);
+  if (st < 0) return st;
+  LSQ_CU(cudaMemcpyAsync(hx, P->stagex, (size_t)P->n * sizeof(double), cudaMemcpyDeviceToHost, P->s));
+  LSQ_CU(cudaStreamSynchronize(P->s));
+  return st;
+}
+
+lsq_status lsq_sketch_pattern(lsq_plan P, int32_t *d_rows, uint32_t *d_signbits) {
+  if (!P || !d_rows || !d_signbits) return fail(LSQ_ERR_INVALID, "NULL argument");
+  if (!P->pat_valid) {
+    LSQ_CU(launch_sketch_pattern(P->m, P->d, P->zeta, P->o.seed, P->pat_rows, P->pat_sb, P->s));
+    P->pat_valid = true;
+  }
+  LSQ_CU(cudaMemcpyAsync(d_rows, P->pat_rows, sizeof(int32_t) * (size_t)P->m * P->zeta,
+                         cudaMemcpyDeviceToDevice, P->s));
+  LSQ_CU(cudaMemcpyAsync(d_signbits, P->pat_sb, sizeof(uint32_t) * (size_t)P->m,
+                         cudaMemcpyDeviceToDevice, P->s));
+  LSQ_CU(cudaStreamSynchronize(P->s));
+  return LSQ_OK;
+}
+
+lsq_status lsq_get_sketch(lsq_plan P, double *dSAb, double *dcolnorm) {
+  if (!P) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  if (!P->sketched) return fail(LSQ_ERR_INVALID, "call lsq_sketch first");
+  // W is overwritten by the QR; the scaled sketch is rebuilt from SAb.
+  if (dSAb) {
+    const int n = (int)P->n;
+    LSQ_CU(launch_sketch_finalize(P->cpart, P->gpass, P->npad, n, P->d, P->zeta, P->o.col_scale,
+                                  P->SAb, dSAb, P->dcol, P->dinv, P->st, P->s));
+  }
+  if (dcolnorm)
+    LSQ_CU(cudaMemcpyAsync(dcolnorm, P->dcol, sizeof(double) * P->n, cudaMemcpyDeviceToDevice, P->s));
+  LSQ_CU(cudaStreamSynchronize(P->s));
+  return LSQ_OK;
+}
+
+lsq_status lsq_get_R(lsq_plan P, double *dR, double *dt, double *dx0, double *condest,
+                     double *normest) {
+  if (!P) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  if (!P->sketched) return fail(LSQ_ERR_INVALID, "call lsq_sketch first");
+  const size_t n = (size_t)P->n;
+  if (dR) LSQ_CU(cudaMemcpyAsync(dR, P->Rrm, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, P->s));
+  if (dt) LSQ_CU(cudaMemcpyAsync(dt, P->t, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->s));
+  if (dx0) LSQ_CU(cudaMemcpyAsync(dx0, P->xs, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->s));
+  LSQ_CU(cudaStreamSynchronize(P->s));
+  if (condest) *condest = P->st_host->condest;
+  if (normest) *normest = P->st_host->normest;
+  return LSQ_OK;
+}
+
+lsq_status lsq_apply_normal(lsq_plan P, const double *dA, const double *dz, double *dh) {
+  if (!P || !dA || !dz || !dh) return fail(LSQ_ERR_INVALID, "NULL argument");
+  const int n = (int)P->n;
+  LSQ_CU(launch_pass_atax(dA, P->lda, P->m, n, dz, P->part, P->gpass, P->npad, nullptr, P->s));
+  LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, nullptr, dh, nullptr, nullptr, nullptr, P->s));
+  LSQ_CU(cudaStreamSynchronize(P->s));
+  return LSQ_OK;
+}
+
+lsq_status lsq_residual(lsq_plan P, const double *dA, const double *db, const double *dx,
+                        double *dg, double *r2) {
+  if (!P || !dA || !db || !dx || !dg) return fail(LSQ_ERR_INVALID, "NULL argument");
+  const int n = (int)P->n;
+  LSQ_CU(launch_pass_resid(dA, P->lda, P->m, n, db, dx, P->part, P->r2part, P->gpass, P->npad, P->s));
+  LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, nullptr, dg, P->r2part, &P->st->r2, nullptr, P->s));
+  LSQ_TRY(read_state(P));
+  if (r2) *r2 = P->st_host->r2;
+  return LSQ_OK;
+}
+
+lsq_status lsq_trsv(lsq_plan P, int trans, const double *dy, double *dx) {
+  if (!P || !dy || !dx) return fail(LSQ_ERR_INVALID, "NULL argument");
+  if (!P->sketched) return fail(LSQ_ERR_INVALID, "call lsq_sketch first");
+  LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, (int)P->n, trans ? 1 : 0, dy, nullptr, dx, nullptr,
+                     nullptr, nullptr, nullptr, nullptr, P->s));
+  LSQ_CU(cudaStreamSynchronize(P->s));
+  return LSQ_OK;
+}
+
+}  // extern "C"

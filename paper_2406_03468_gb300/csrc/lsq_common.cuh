@@ -1,0 +1,162 @@
+// Internal declarations shared by the CUDA translation units of liblsq.
+// Nothing here is part of the C ABI (include/lsq.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lsq.h"
+
+namespace lsq {
+
+constexpr double kU = 1.1102230246251565e-16;  // unit roundoff of IEEE double, 2^-53
+constexpr int kPassThreads = 256;               // threads per CTA of the streaming passes
+constexpr int kPassCtasPerSm = 2;
+constexpr int kVecThreads = 1024;               // threads of the single-CTA vector kernels
+constexpr int kMaxZeta = 32;
+
+// Device-resident scalars of one solve.  Kernels of the inner loop read
+// `done` first and return at once when it is set, so the host may enqueue a
+// few iterations ahead of the stopping decision.
+struct DevState {
+  double normest, condest;
+  double thresh1;        // step-1 stop threshold
+  double alpha, beta;    // Polyak coefficients
+  double dnorm2;         // ||Delta||^2 of the last inner update
+  double rho;            // CG: r^T r
+  double r2;             // ||b - A x||^2 of the last residual pass
+  double x0norm2;        // ||x0||^2 (scaled coordinates)
+  double cnorm2[LSQ_MAX_REFINE];
+  int done;              // inner loop of the current step has stopped
+  int iters;             // inner updates in the current step
+  int max_iters;         // cap of the current step
+  int use_thresh;        // 1: stop when ||Delta|| <= thresh1
+  int err;               // device-side error (LSQ_ERR_TIMEOUT)
+  int nonfinite;         // NaN / Inf seen in A or b
+  int zero_col;          // a column norm is zero
+  int pad;
+};
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; every thread gets the result.  `scratch` needs
+// blockDim.x / 32 doubles of shared memory.  Fixed order for a fixed blockDim.
+__device__ __forceinline__ double block_sum(double v, double *scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; w++) s += scratch[w];
+  return s;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded grid-wide barrier for cooperative launches.  count/gen live in
+// global memory (count == 0 at launch).  Returns false, after recording
+// LSQ_ERR_TIMEOUT in *err, when the other blocks did not arrive within
+// timeout_ns; every block then leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned int *count, volatile unsigned int *gen,
+                                             int *err, uint64_t timeout_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    unsigned int g = *gen;
+    __threadfence();
+    unsigned int arrived = atomicAdd(count, 1u);
+    if (arrived == gridDim.x - 1) {
+      *count = 0;
+      __threadfence();
+      atomicAdd((unsigned int *)gen, 1u);
+    } else {
+      uint64_t t0 = global_ns();
+      while (*gen == g) {
+        if (*(volatile int *)err != 0) { ok = 0; break; }
+        if (global_ns() - t0 > timeout_ns) {
+          atomicExch(err, (int)LSQ_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// ---------------------------------------------------------------- launchers
+// Every launcher enqueues on `s` and returns the launch's cudaError_t.
+
+// Sparse sign pattern (Philox4x64-10 spec): rows (m x zeta), signbits (m).
+cudaError_t launch_sketch_pattern(int64_t m, int d, int zeta, uint64_t seed, int32_t *rows,
+                                  uint32_t *signbits, cudaStream_t s);
+// Unscaled +-1 sketch of [A b] into SAb (d x (n+1), row-major, must be
+// zeroed first) and column sums of squares partials (grid x npad).
+cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, const double *b,
+                          int d, int zeta, const int32_t *rows, const uint32_t *signbits,
+                          double *SAb, double *colsq_part, int grid, int npad, cudaStream_t s);
+// Column norms from partials, scaling, transpose into column-major W (ld d).
+cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad, int n, int d,
+                                   int zeta, int col_scale, const double *SAb, double *W,
+                                   double *dcol, double *dinv, DevState *st, cudaStream_t s);
+// Householder QR of W (d x (n+1), column-major) in place (cooperative).
+cudaError_t launch_qr(double *W, int d, int n, double *vbuf, unsigned int *bar, DevState *st,
+                      int grid, uint64_t timeout_ns, cudaStream_t s);
+int qr_grid(int n, int nsm);
+// R (upper n x n of W) to Rcm / Rrm, 1/R_ii, t = W[0:n, n].
+cudaError_t launch_extract_r(const double *W, int d, int n, double *Rcm, double *Rrm,
+                             double *rinv, double *t, cudaStream_t s);
+// condest / normest of R by power and inverse power iteration.
+cudaError_t launch_condest(const double *Rcm, const double *Rrm, const double *rinv, int n,
+                           int iters, DevState *st, cudaStream_t s);
+// Triangular solve on one CTA.  trans 0: R x = y, 1: R^T x = y.
+//   y_eff = y (* in_scale if given); sol = solution;
+//   accum != NULL:   accum += sol, out = accum, out_scaled = out_scale * accum
+//   accum == NULL:   out = sol, out_scaled = out_scale * sol  (outputs may be NULL)
+//   norm2_out != NULL: *norm2_out = ||out||^2
+//   gate != NULL: return at once when gate->done.
+cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv, int n, int trans,
+                        const double *y, const double *in_scale, double *out,
+                        const double *out_scale, double *out_scaled, double *accum,
+                        double *norm2_out, const DevState *gate, cudaStream_t s);
+// Fused passes (partials: grid x npad doubles, r2_part: grid doubles).
+cudaError_t launch_pass_atax(const double *A, int64_t lda, int64_t m, int n, const double *z,
+                             double *part, int grid, int npad, const DevState *gate,
+                             cudaStream_t s);
+cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, const double *b,
+                              const double *x, double *part, double *r2_part, int grid, int npad,
+                              cudaStream_t s);
+// out[j] = scale[j] * sum_g part[g][j] (scale may be NULL); r2 (if non-NULL)
+// = sum_g r2_part[g]; gated.
+cudaError_t launch_reduce(const double *part, int grid, int npad, int n, const double *scale,
+                          double *out, const double *r2_part, double *r2, const DevState *gate,
+                          cudaStream_t s);
+int pass_npad(int n);
+
+// Inner-solver kernels (single CTA).
+cudaError_t launch_inner_init(int method, int n, const double *c, double *dy, double *dy_old,
+                              double *res, double *p, int max_iters, int use_thresh,
+                              DevState *st, cudaStream_t s);
+cudaError_t launch_polyak_update(int n, const double *c, const double *w, double *dy,
+                                 double *dy_old, DevState *st, cudaStream_t s);
+cudaError_t launch_cg_update(int n, const double *q, double *p, double *res, double *dy,
+                             DevState *st, cudaStream_t s);
+// thresh1 = u (gamma normest ||x0|| + rho condest sqrt(r2)); records cnorm2[0].
+cudaError_t launch_set_thresh(double gamma, double rho, DevState *st, cudaStream_t s);
+
+}  // namespace lsq

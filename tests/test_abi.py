@@ -1,0 +1,62 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads without a
+GPU, exports every function include/lsq.h declares, and the ctypes
+structures match the C layout.  No compute call is made here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2406_03468_gb300 as lsq
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lsq.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lsq_[A-Za-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(lsq.library_path() if os.path.exists(lsq.library_path()) else lsq._build.build())
+    names = declared_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in lsq.EXPORTED, name
+
+
+def test_struct_layout_matches_c(tmp_path):
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include "lsq.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                    'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(lsq_options), '
+                    'sizeof(lsq_info), offsetof(lsq_options, fixed_inner), '
+                    'offsetof(lsq_info, ms_total)); return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert int(out[0]) == ctypes.sizeof(lsq.LsqOptions)
+    assert int(out[1]) == ctypes.sizeof(lsq.LsqInfo)
+    assert int(out[2]) == lsq.LsqOptions.fixed_inner.offset
+    assert int(out[3]) == lsq.LsqInfo.ms_total.offset
+
+
+def test_defaults_and_validation_without_gpu():
+    o = lsq.lsq_options_default(m=100, n=10)
+    assert o.zeta == 8 and o.col_scale == 1 and o.max_inner == 100 and o.max_refine == 2
+    assert abs(o.stop_rho - 0.04) < 1e-15 and o.stop_gamma == 1.0
+    bad = lsq.lsq_options_default(m=5, n=10)          # m < n is rejected before any CUDA call
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.lsq_plan_create(bad)
+    assert e.value.status == -1
+    bad = lsq.lsq_options_default(m=100, n=10, zeta=40)
+    with pytest.raises(lsq.LsqError):
+        lsq.lsq_plan_create(bad)
+
+
+def test_build_targets_sm103a_only():
+    from paper_2406_03468_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

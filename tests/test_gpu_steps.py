@@ -1,0 +1,185 @@
+"""GPU parity of each step of the hot path against the CPU oracle, through
+the C ABI (paper_2406_03468_gb300 is a ctypes binding of liblsq.so).
+
+Sizes span several CTAs and row blocks with ragged tails (m = 20011 rows,
+n = 130 or 37 columns, lda > n).  Bars:
+  * sketch pattern: bit-exact (index work);
+  * sums (sketch, passes): within the standard summation error bound
+    gamma_k sum |terms| with k the number of terms, written per element;
+  * QR / triangular solves: normwise backward-error level, kappa(R) u.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2406_03468_gb300 as lsq
+from gpu_util import DEV, H, T, empty
+from lsq_problems import problem_gaussian, problem_svd
+from oracle.philox import sparse_sign_matrix, sparse_sign_pattern
+
+pytestmark = pytest.mark.gpu
+u = 2.0 ** -53
+
+
+@pytest.mark.parametrize("m,n,d,zeta,seed", [
+    (20011, 50, 600, 8, 3),        # the paper's d = 12n, zeta = 8
+    (3000, 4, 10, 8, 5),           # heavy rejection sampling
+    (1000, 4, 8, 8, 1),            # d = zeta: every row of S hit
+    (5000, 4, 37, 3, 2 ** 63 + 5),
+    (777, 2, 5, 1, 0),
+])
+def test_pattern_bit_exact(m, n, d, zeta, seed):
+    plan = lsq.Plan(m, n, d=d, zeta=zeta, seed=seed)
+    rows = empty(m * zeta, torch.int32)
+    sb = empty(m, torch.int32)
+    lsq.lsq_sketch_pattern(plan.handle, rows, sb)
+    r_or, s_or = sparse_sign_pattern(m, d, zeta, seed)
+    assert np.array_equal(H(rows).reshape(m, zeta), r_or)
+    bits = H(sb).view(np.uint32).astype(np.uint64)
+    neg = (bits[:, None] >> np.arange(zeta, dtype=np.uint64)[None, :]) & np.uint64(1)
+    assert np.array_equal(np.where(neg == 1, -1.0, 1.0), s_or)
+
+
+def _problem(m, n, kappa, seed, lda=None):
+    P = problem_svd(m, n, kappa, 1e-4, seed=seed, keep_factors=False)
+    A = P["A"]
+    if lda is not None and lda > n:
+        Af = np.zeros((m, lda))
+        Af[:, :n] = A
+        Af[:, n:] = np.nan          # padding must never be read
+        return P, Af
+    return P, A
+
+
+@pytest.mark.parametrize("m,n,lda", [(20011, 130, None), (20011, 37, None), (9001, 64, 70)])
+def test_sketch_and_column_norms(m, n, lda):
+    P, Afull = _problem(m, n, 1e3, seed=1, lda=lda)
+    A, b = P["A"], P["b"]
+    plan = lsq.Plan(m, n, lda=(lda or 0), seed=11)
+    lsq.lsq_sketch(plan.handle, T(Afull), T(b))
+    d = 12 * n
+    SAb = empty(d * (n + 1))
+    cn = empty(n)
+    lsq.lsq_get_sketch(plan.handle, SAb, cn)
+    SAb = H(SAb).reshape(n + 1, d).T
+    dcol = oracle.column_norms(A)
+    assert np.allclose(H(cn), dcol, rtol=1e-13, atol=0)
+    SA, Sb = oracle.sketch(A / dcol, b, d, 8, 11)
+    S = abs(sparse_sign_matrix(m, d, 8, 11))
+    k = int(S.sum(axis=1).max() * math.sqrt(8)) + 2       # terms per sketch entry
+    bound_A = (S @ np.abs(A / dcol)) * (k * u) * 4 + 1e-300
+    bound_b = (S @ np.abs(b)) * (k * u) * 4 + 1e-300
+    assert (np.abs(SAb[:, :n] - SA) <= bound_A).all()
+    assert (np.abs(SAb[:, n] - Sb) <= bound_b).all()
+
+
+@pytest.mark.parametrize("m,n", [(20011, 130), (4000, 50), (3001, 7)])
+def test_qr_of_sketch(m, n):
+    P, A = _problem(m, n, 1e3, seed=2)
+    plan = lsq.Plan(m, n, seed=4)
+    lsq.lsq_sketch(plan.handle, T(A), T(P["b"]))
+    d = 12 * n
+    SAb = empty(d * (n + 1))
+    lsq.lsq_get_sketch(plan.handle, SAb, None)
+    SAb = H(SAb).reshape(n + 1, d).T
+    R = empty(n * n)
+    t = empty(n)
+    x0 = empty(n)
+    ce, ne = lsq.lsq_get_R(plan.handle, R, t, x0)
+    R = H(R).reshape(n, n)
+    R_or, V = oracle.householder_qr(SAb[:, :n])
+    t_or = oracle.apply_qt(V, SAb[:, n])[:n]
+    nR = np.linalg.norm(R_or, 2)
+    assert np.allclose(np.tril(R, -1), 0.0)
+    assert np.linalg.norm(R - R_or, 2) <= 1e3 * n * u * nR
+    assert np.linalg.norm(H(t) - t_or) <= 1e3 * n * u * np.linalg.norm(SAb[:, n])
+    # sketch-and-solve x0 = R^{-1} t
+    x0_or = oracle.backsub(R_or, t_or)
+    assert np.linalg.norm(H(x0) - x0_or) <= 1e-9 * np.linalg.norm(x0_or)
+    # condest / normest against the exact singular values of R
+    smax, smin = oracle.sigma_extremes(R_or)
+    assert 0.7 * smax <= ne <= 1.0001 * smax
+    # power iteration approaches the extreme singular values from inside
+    assert 0.8 * smax / smin <= ce <= 1.0001 * smax / smin
+
+
+@pytest.mark.parametrize("n", [130, 37])
+def test_triangular_solves(n):
+    P, A = _problem(20011, n, 1e6, seed=3)
+    plan = lsq.Plan(20011, n, seed=5)
+    lsq.lsq_sketch(plan.handle, T(A), T(P["b"]))
+    R = empty(n * n)
+    lsq.lsq_get_R(plan.handle, R)
+    R = H(R).reshape(n, n)
+    y = np.random.default_rng(0).standard_normal(n)
+    for trans in (0, 1):
+        out = empty(n)
+        lsq.lsq_trsv(plan.handle, trans, T(y), out)
+        ref = oracle.backsub(R, y) if trans == 0 else oracle.backsub_t(R, y)
+        # backward stable solve: residual at the level n u |R| |x|
+        Rop = R if trans == 0 else R.T
+        res = np.abs(Rop @ H(out) - y)
+        assert (res <= 4 * n * u * (np.abs(Rop) @ np.abs(H(out))) + 1e-300).all()
+        kap = np.linalg.cond(R)
+        assert np.linalg.norm(H(out) - ref) <= 10 * n * kap * u * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("m,n,lda", [(20011, 130, None), (20011, 37, None), (9001, 64, 70),
+                                     (4097, 1000, None), (333, 1, None)])
+def test_fused_passes(m, n, lda):
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n))
+    Afull = A
+    if lda:
+        Afull = np.full((m, lda), np.nan)
+        Afull[:, :n] = A
+    z = rng.standard_normal(n)
+    b = rng.standard_normal(m)
+    plan = lsq.Plan(m, n, lda=(lda or 0), seed=1)
+    dA = T(Afull)
+    h = empty(n)
+    lsq.lsq_apply_normal(plan.handle, dA, T(z), h)
+    t_ref = A @ z
+    h_ref = A.T @ t_ref
+    bound = 4 * (n + m) * u * (np.abs(A).T @ (np.abs(A) @ np.abs(z)))
+    assert (np.abs(H(h) - h_ref) <= bound).all()
+    # residual pass against the compensated oracle
+    g = empty(n)
+    r2 = lsq.lsq_residual(plan.handle, dA, T(b), T(z), g)
+    r_hi, r_lo, g_ref = oracle.residual_dot2(A, b, z)
+    bound = 4 * (n + m) * u * (np.abs(A).T @ (np.abs(b) + np.abs(A) @ np.abs(z)))
+    assert (np.abs(H(g) - g_ref) <= bound).all()
+    assert abs(r2 - float(r_hi @ r_hi)) <= 1e-12 * float(r_hi @ r_hi)
+
+
+def test_invalid_inputs():
+    m, n = 500, 10
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal(m)
+    x = empty(n)
+    plan = lsq.Plan(m, n)
+    Abad = A.copy()
+    Abad[7, 3] = np.nan
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.lsq_solve_fossils(plan.handle, T(Abad), T(b), x)
+    assert e.value.status == -6
+    bbad = b.copy()
+    bbad[0] = np.inf
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.lsq_solve_spir(plan.handle, T(A), T(bbad), x)
+    assert e.value.status == -6
+    Az = A.copy()
+    Az[:, 4] = 0.0
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.lsq_solve_fossils(plan.handle, T(Az), T(b), x)
+    assert e.value.status == -1
+    with pytest.raises(lsq.LsqError):
+        lsq.lsq_solve_fossils(plan.handle, None, T(b), x)
+    # the plan still works after the errors
+    st, info = lsq.lsq_solve_fossils(plan.handle, T(A), T(b), x)
+    assert st == 0
+    assert np.allclose(H(x), np.linalg.lstsq(A, b, rcond=None)[0], rtol=1e-12, atol=1e-13)
