@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""Throughput of the FOSSILS least-squares hot path on GB300.
+
+One step = one complete FOSSILS solve (sketch S[A b], Householder QR of the
+sketch, sketch-and-solve start, two refinement steps with the Polyak inner
+solver) of the 1,000,000 x 500 FP64 problem A = (G/sqrt(m)) diag(sigma) V^T,
+sigma log-spaced 1..1e-10, b = A x + 1e-4 g, d = 12n, zeta = 8, with A and b
+resident in HBM.  A (4 GB) is larger than the 129 MB L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its
+own replica of the problem on its own GPU ("replicas only": the solve has no
+cross-GPU exchange); only the step timer is reduced (max over ranks).
+
+--impl reference times the CPU oracle (oracle/, plain FP64 loops and numpy
+BLAS) on the host cores, on a bounded row sample of the same problem, scaled
+to the full problem's solves/s.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FOSSILS solves/s & HBM GB/s at BE≤1e-13 vs plain GPU; served p50/p99 latency"
+UNIT = "solves/s"
+M, N, KAPPA, NOISE, SEED = 1_000_000, 500, 1e10, 1e-4, 5
+SKETCH_SEED = 9
+WORKLOAD = "fossils_fp64_m1000000_n500_kappa1e10_d6000_zeta8"
+REF_SAMPLE_ROWS = 100_000      # oracle sample per reference step
+CPU_BASELINE_ROWS = 250_000    # oracle sample for the cpu_baseline object
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="override m (small cases for ncu captures; not a bench line)")
+    args = ap.parse_args()
+    if args.rows:
+        global M, WORKLOAD
+        M = args.rows
+        WORKLOAD = "fossils_fp64_m%d_n500_kappa1e10_d6000_zeta8" % M
+    return args
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def config(extra=None):
+    c = {"workload": WORKLOAD, "m": M, "n": N, "d": 12 * N, "zeta": 8, "kappa": KAPPA,
+         "method": "fossils", "refinement_steps": 2,
+         "l2": "A is %.1f GB, larger than L2: no flush needed" % (8.0 * M * N / 1e9),
+         "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def make_problem(rows=None):
+    from lsq_problems import problem_gaussian
+    return problem_gaussian(rows or M, N, KAPPA, NOISE, seed=SEED)
+
+
+# --------------------------------------------------------------------------
+# oracle (CPU) timing: the cpu_baseline object and the reference arm
+# --------------------------------------------------------------------------
+
+def oracle_time(P, rows, reps=1):
+    """Seconds per oracle FOSSILS solve on the first `rows` rows of P."""
+    import oracle
+    A = P["A"][:rows]
+    b = P["b"][:rows]
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.fossils(A, b, seed=SKETCH_SEED)
+        ts.append(time.perf_counter() - t0)
+    return ts
+
+
+def cpu_baseline_obj(P, rows):
+    ts = oracle_time(P, rows, reps=1)
+    per_solve_full = ts[0] * (M / rows)
+    return {"value": 1.0 / per_solve_full, "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "oracle FOSSILS (numpy BLAS + plain C, FP64) on the first %d of %d rows "
+                      "of the same A, b; %.2f s, time scaled by m/rows (passes are O(mn))"
+                      % (rows, M, ts[0])}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    P = make_problem(REF_SAMPLE_ROWS)
+    oracle_time(P, REF_SAMPLE_ROWS, reps=max(0, args.warmup))
+    ts = oracle_time(P, REF_SAMPLE_ROWS, reps=args.steps)
+    per_full = statistics.mean(ts) * (M / REF_SAMPLE_ROWS)
+    value = 1.0 / per_full
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_full * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config({"sample_rows": REF_SAMPLE_ROWS}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": "each step: oracle FOSSILS on %d of %d rows, time "
+                                       "scaled by m/rows" % (REF_SAMPLE_ROWS, M)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpus):
+        self.gpus = set(gpus)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or not f[0].isdigit() or int(f[0]) not in self.gpus:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_per_launch():
+    """dram read+write bytes per launch of the inner pass from the committed
+    ncu summary, or None when the kernel source changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "atax_kernel_traffic.txt")
+    src = os.path.join(ROOT, "paper_2406_03468_gb300", "csrc", "k_pass.cu")
+    try:
+        rec = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("k_pass_sha256") != h:
+            return None
+        return float(rec["bytes_per_launch_full"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2406_03468_gb300 as lsq
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    P = make_problem()
+    dev = torch.device("cuda", local)
+    A = torch.from_numpy(P["A"]).to(dev)
+    b = torch.from_numpy(P["b"]).to(dev)
+    x = torch.empty(N, dtype=torch.float64, device=dev)
+    plan = lsq.Plan(M, N, seed=SKETCH_SEED, timing=1)
+    h = plan.handle
+
+    for _ in range(args.warmup):
+        lsq.lsq_solve_fossils(h, A, b, x)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(range(args.gpus)) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    infos = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        st, inf = lsq.lsq_solve_fossils(h, A, b, x)
+        infos.append(inf.as_dict())
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = args.steps * world / (ms / 1e3)
+
+    # roofline of the dominant kernel: the fused A^T(A z) pass
+    n_in = sum(i["n_inner_pass"] for i in infos)
+    ms_in = sum(i["ms_inner_pass"] for i in infos)
+    pk, pk_kind = peaks()
+    bytes_pass = 8.0 * M * N
+    avg_s = (ms_in / n_in) / 1e3
+    achieved = bytes_pass / avg_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic_per_launch(),
+            "kernel": "atax_kernel (fused A^T(A z) pass)", "launches_timed": n_in,
+            "avg_launch_ms": avg_s * 1e3, "peak_kind": pk_kind}
+    passes = statistics.mean(i["passes"] for i in infos)
+    hbm_solve = passes * bytes_pass / (ms / args.steps / 1e3) / 1e9
+
+    # SPIR on the same plan (context)
+    xs = torch.empty_like(x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    spir_infos = []
+    for _ in range(max(1, args.steps // 2)):
+        st, inf = lsq.lsq_solve_spir(h, A, b, xs)
+        spir_infos.append(inf.as_dict())
+    torch.cuda.synchronize()
+    spir_rate = len(spir_infos) / (time.perf_counter() - t0)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.from_numpy(P["A"]).pin_memory()
+        hb = torch.from_numpy(P["b"]).pin_memory()
+        hx = torch.empty(N, dtype=torch.float64).pin_memory()
+        lsq.lsq_solve_host(h, 0, hA, hb, hx)
+        torch.cuda.synchronize()
+        k2 = max(1, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            lsq.lsq_solve_host(h, 0, hA, hb, hx)
+        dt = time.perf_counter() - t0
+        rate = k2 * world / dt
+        if dist:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            rate = k2 * world / float(t.item())
+        e2e = {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 8 * M * N + 8 * M,
+               "d2h_bytes_per_step": 8 * N}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_obj(P, CPU_BASELINE_ROWS)
+
+    if rank == 0:
+        last = infos[-1]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": config({"hbm_gbs_per_solve": hbm_solve,
+                                  "passes_per_solve": passes,
+                                  "iters": last["iters"], "condest": last["condest"],
+                                  "phase_ms": {"sketch": last["ms_sketch"], "qr": last["ms_qr"],
+                                               "refine": last["ms_refine"]},
+                                  "sketch_pass_ms": last["ms_sketch_pass"],
+                                  "spir_solves_per_s": spir_rate,
+                                  "spir_iters": spir_infos[-1]["iters"]}),
+                "clocks": clocks, "e2e": e2e,
+                "gpu_launches": int(sum(i["launches"] for i in infos)),
+                "roofline": roof, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

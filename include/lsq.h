@@ -70,7 +70,8 @@ typedef struct {
   double stop_gamma;     /* step-1 stop constant gamma (Sec. 4.2; default 1) */
   double stop_rho;       /* step-1 stop constant rho (Sec. 4.2; default 0.04) */
   int32_t fixed_inner;   /* > 0: every refinement step runs exactly this many updates */
-  int32_t reserved[9];
+  int32_t timing;        /* 1: time every streaming pass with CUDA events (lsq_info) */
+  int32_t reserved[8];
 } lsq_options;
 
 #define LSQ_MAX_N 1024
@@ -88,6 +89,13 @@ typedef struct {
   double resid0;                  /* ||b - A x_0|| (sketch-and-solve) */
   double thresh1;                 /* step-1 stop threshold */
   float ms_sketch, ms_qr, ms_refine, ms_total;  /* device time of the phases */
+  int32_t launches;               /* kernels launched by the call (gated no-ops included) */
+  int32_t n_inner_pass;           /* timing: inner A^T(A z) passes that did work */
+  float ms_inner_pass;            /* timing: their summed device time */
+  int32_t n_resid_pass;           /* timing: residual passes */
+  float ms_resid_pass;            /* timing: their summed device time */
+  float ms_sketch_pass;           /* timing: the sketch pass */
+  int32_t reserved[4];
 } lsq_info;
 
 /* Fill *o with the defaults listed above (m, n, lda left 0). */

@@ -44,7 +44,8 @@ class LsqOptions(ctypes.Structure):
                 ("max_inner", ctypes.c_int32), ("max_refine", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("fp32_cond_max", ctypes.c_double),
                 ("stop_gamma", ctypes.c_double), ("stop_rho", ctypes.c_double),
-                ("fixed_inner", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("fixed_inner", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
 
 
 class LsqInfo(ctypes.Structure):
@@ -54,7 +55,10 @@ class LsqInfo(ctypes.Structure):
                 ("cnorm", ctypes.c_double * LSQ_MAX_REFINE), ("resid0", ctypes.c_double),
                 ("thresh1", ctypes.c_double), ("ms_sketch", ctypes.c_float),
                 ("ms_qr", ctypes.c_float), ("ms_refine", ctypes.c_float),
-                ("ms_total", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("launches", ctypes.c_int32),
+                ("n_inner_pass", ctypes.c_int32), ("ms_inner_pass", ctypes.c_float),
+                ("n_resid_pass", ctypes.c_int32), ("ms_resid_pass", ctypes.c_float),
+                ("ms_sketch_pass", ctypes.c_float), ("reserved", ctypes.c_int32 * 4)]
 
     def as_dict(self):
         k = self.refine_steps
@@ -62,7 +66,10 @@ class LsqInfo(ctypes.Structure):
                 "passes": self.passes, "status": self.status, "condest": self.condest,
                 "normest": self.normest, "cnorm": list(self.cnorm[:k]), "resid0": self.resid0,
                 "thresh1": self.thresh1, "ms_sketch": self.ms_sketch, "ms_qr": self.ms_qr,
-                "ms_refine": self.ms_refine, "ms_total": self.ms_total}
+                "ms_refine": self.ms_refine, "ms_total": self.ms_total,
+                "launches": self.launches, "n_inner_pass": self.n_inner_pass,
+                "ms_inner_pass": self.ms_inner_pass, "n_resid_pass": self.n_resid_pass,
+                "ms_resid_pass": self.ms_resid_pass, "ms_sketch_pass": self.ms_sketch_pass}
 
 
 _vp = ctypes.c_void_p

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "lsq_common.cuh"
 
@@ -68,6 +69,9 @@ struct lsq_plan_s {
   cudaEvent_t ev[5] = {};
   double *stageA = nullptr, *stageb = nullptr, *stagex = nullptr;
   bool sketched = false;
+  int launches = 0;                 // kernels launched by the current call
+  std::vector<cudaEvent_t> tev;     // timing: pass begin/end event pairs
+  int tev_used = 0;
 };
 
 namespace {
@@ -116,9 +120,29 @@ lsq_status read_state(lsq_plan P) {
   return LSQ_OK;
 }
 
+// Timing events (opt-in): a growing pool of begin/end pairs.
+cudaError_t tev_pair(lsq_plan P, int *idx) {
+  while ((int)P->tev.size() < 2 * (P->tev_used + 1)) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    P->tev.push_back(e);
+  }
+  *idx = P->tev_used++;
+  return cudaSuccess;
+}
+
+float tev_ms(lsq_plan P, int idx) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, P->tev[2 * idx], P->tev[2 * idx + 1]);
+  return ms;
+}
+
 lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
   if (!dA || !db) return fail(LSQ_ERR_INVALID, "A or b is NULL");
   const int n = (int)P->n;
+  P->launches = 0;
+  P->tev_used = 0;
   // fresh device state with alpha, beta
   std::memset(P->st_host, 0, sizeof(DevState));
   P->st_host->alpha = P->alpha;
@@ -128,13 +152,21 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
   if (!P->pat_valid) {
     LSQ_CU(launch_sketch_pattern(P->m, P->d, P->zeta, P->o.seed, P->pat_rows, P->pat_sb, P->s));
     P->pat_valid = true;
+    P->launches++;
   }
   LSQ_CU(cudaMemsetAsync(P->SAb, 0, sizeof(double) * (size_t)P->d * (n + 1), P->s));
+  int tk = -1;
+  if (P->o.timing) {
+    LSQ_CU(tev_pair(P, &tk));
+    LSQ_CU(cudaEventRecord(P->tev[2 * tk], P->s));
+  }
   LSQ_CU(launch_sketch(dA, P->lda, P->m, n, db, P->d, P->zeta, P->pat_rows, P->pat_sb, P->SAb,
                        P->cpart, P->gpass, P->npad, P->s));
+  if (tk >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tk + 1], P->s));
   LSQ_CU(launch_sketch_finalize(P->cpart, P->gpass, P->npad, n, P->d, P->zeta, P->o.col_scale,
                                 P->SAb, P->W, P->dcol, P->dinv, P->st, P->s));
   LSQ_CU(cudaEventRecord(P->ev[1], P->s));
+  P->launches += 3 + 4;  // sketch, colnorm, transpose; qr, extract, condest, x0 solve
   LSQ_CU(launch_qr(P->W, P->d, n, P->vbuf, P->bar, P->st, P->gqr, kBarrierTimeoutNs, P->s));
   LSQ_CU(launch_extract_r(P->W, P->d, n, P->Rcm, P->Rrm, P->rinv, P->t, P->s));
   LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, n, kCondestIters, P->st, P->s));
@@ -162,9 +194,18 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
   int passes = 1;
   int iters[LSQ_MAX_REFINE] = {0};
   double resid0 = 0.0;
+  std::vector<int> resid_ev, inner_ev[LSQ_MAX_REFINE];
   for (int i = 0; i < nref; i++) {
+    int tk = -1;
+    if (P->o.timing) {
+      LSQ_CU(tev_pair(P, &tk));
+      resid_ev.push_back(tk);
+      LSQ_CU(cudaEventRecord(P->tev[2 * tk], P->s));
+    }
     LSQ_CU(launch_pass_resid(dA, P->lda, P->m, n, db, P->xo, P->part, P->r2part, P->gpass,
                              P->npad, P->s));
+    if (tk >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tk + 1], P->s));
+    P->launches += 3 + (i == 0 ? 1 : 0) + 1;  // resid, reduce, trsv, [thresh], init
     LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->g, P->r2part, &P->st->r2,
                          nullptr, P->s));
     passes++;
@@ -181,8 +222,16 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
       // z = D^{-1} R^{-1} src;  h = D^{-1} A^T (A z);  w = R^{-T} h
       LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, src, nullptr, nullptr, P->dinv, P->z,
                          nullptr, nullptr, P->st, P->s));
+      int tj = -1;
+      if (P->o.timing) {
+        LSQ_CU(tev_pair(P, &tj));
+        inner_ev[i].push_back(tj);
+        LSQ_CU(cudaEventRecord(P->tev[2 * tj], P->s));
+      }
       LSQ_CU(launch_pass_atax(dA, P->lda, P->m, n, P->z, P->part, P->gpass, P->npad, P->st,
                               P->s));
+      if (tj >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tj + 1], P->s));
+      P->launches += 5;
       LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->h, nullptr, nullptr, P->st,
                            P->s));
       LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 1, P->h, nullptr, P->w, nullptr, nullptr,
@@ -199,6 +248,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     // x_s += R^{-1} dy ; x_o = D^{-1} x_s
     LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->dy, nullptr, nullptr, P->dinv, P->xo,
                        P->xs, nullptr, nullptr, P->s));
+    P->launches++;
     LSQ_TRY(read_state(P));
     iters[i] = P->st_host->iters;
     if (i == 0) resid0 = std::sqrt(P->st_host->r2);
@@ -232,6 +282,20 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     info->ms_refine = ms;
     cudaEventElapsedTime(&ms, P->ev[0], P->ev[3]);
     info->ms_total = ms;
+    info->launches = P->launches;
+    if (P->o.timing) {
+      for (int k : resid_ev) {
+        info->ms_resid_pass += tev_ms(P, k);
+        info->n_resid_pass++;
+      }
+      // only the launches before the stop decision did work
+      for (int i = 0; i < nref; i++)
+        for (int j = 0; j < (int)inner_ev[i].size() && j < iters[i]; j++) {
+          info->ms_inner_pass += tev_ms(P, inner_ev[i][j]);
+          info->n_inner_pass++;
+        }
+      info->ms_sketch_pass = tev_ms(P, 0);
+    }
   }
   if (info) info->resid0 = resid0;
   return status;
@@ -248,6 +312,7 @@ void free_plan(lsq_plan P) {
   if (P->st_host) cudaFreeHost(P->st_host);
   for (auto &e : P->ev)
     if (e) cudaEventDestroy(e);
+  for (auto &e : P->tev) cudaEventDestroy(e);
   delete P;
 }
 
