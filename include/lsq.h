@@ -67,11 +67,14 @@ typedef struct {
   int32_t max_refine;    /* refinement steps (0 => 2 on FP64; FP32 tier: up to 6) */
   int32_t precision;     /* LSQ_PREC_* (default LSQ_PREC_FP64) */
   double fp32_cond_max;  /* FP32-inner gate on condest (0 => 1e5) */
-  double stop_gamma;     /* step-1 stop constant gamma (Sec. 4.2; default 1) */
-  double stop_rho;       /* step-1 stop constant rho (Sec. 4.2; default 0.04) */
+  double stop_gamma;     /* step-1 stop constant gamma (Alg. 4: 10; Sec. 4.2 text: 1) */
+  double stop_rho;       /* step-1 stop constant rho (Alg. 4: 0.4; Sec. 4.2 text: 0.04) */
   int32_t fixed_inner;   /* > 0: every refinement step runs exactly this many updates */
   int32_t timing;        /* 1: time every streaming pass with CUDA events (lsq_info) */
-  int32_t reserved[8];
+  int32_t inner_fp64_fma;/* 1: inner pass with two FP64 FMAs per element; 0 (default):
+                            row products on the FP32 pipe (exact splits, double-float
+                            sums) when every column norm is within 2^20 of the largest */
+  int32_t reserved[7];
 } lsq_options;
 
 #define LSQ_MAX_N 1024
@@ -95,7 +98,8 @@ typedef struct {
   int32_t n_resid_pass;           /* timing: residual passes */
   float ms_resid_pass;            /* timing: their summed device time */
   float ms_sketch_pass;           /* timing: the sketch pass */
-  int32_t reserved[4];
+  int32_t inner_kernel;           /* 0: FP64-FMA inner pass, 1: FP32-pipe row products */
+  int32_t reserved[3];
 } lsq_info;
 
 /* Fill *o with the defaults listed above (m, n, lda left 0). */
@@ -161,7 +165,10 @@ lsq_status lsq_get_R(lsq_plan plan, double *dR, double *dt, double *dx0, double 
 
 /* One fused streaming pass over A: dh = A^T (A dz) (the operator of
  * Sec. 2.1's preconditioned normal equations before the R solves; Alg. 1's
- * Apply).  dz, dh: n, device.  No scaling is applied. */
+ * Apply), with the inner-pass kernel the solve would use: after lsq_sketch
+ * and unless inner_fp64_fma is set, the FP32-pipe row products when the
+ * column norms allow it; otherwise two FP64 FMAs per element.  dz, dh: n,
+ * device.  No scaling is applied. */
 lsq_status lsq_apply_normal(lsq_plan plan, const double *dA, const double *dz, double *dh);
 
 /* One fused streaming pass over A: dg = A^T (db - A dx) and *r2 = ||b - A x||^2

@@ -21,7 +21,11 @@ Readings of the paper that this oracle takes (each is listed in the design doc):
     reads off the SVD.
   * Step-1 stop (Sec. 4.2, "Adaptive stopping", item 1): stop after the first
     update Delta with ||Delta|| <= u (gamma normest ||x_0|| +
-    rho condest ||b - A x_0||), gamma = 1, rho = 0.04, at most 100 updates.
+    rho condest ||b - A x_0||), at most 100 updates.  The text quotes
+    gamma = 1, rho = 0.04; Alg. 4 uses 10 and 0.4.  The default is Alg. 4's:
+    with the text's constants the threshold sits at the rounding-noise floor
+    of ||Delta|| on ill-conditioned problems, where the update that first
+    crosses it is a matter of rounding order (or never comes).
   * Step-2 count: q0 of Theorem 7.1 (Sec. 7) with kappa replaced by condest and the
     distortion 1.01 eta; Alg. 5 returns the iterate dy_(q) after q - 1 updates,
     so step 2 runs ceil(q0) - 1 updates (capped at 100).
@@ -298,7 +302,7 @@ def _solve(method, A, b, d, zeta, seed, eta, col_scale, max_inner, stop_gamma,
 
 
 def fossils(A, b, d=None, zeta=8, seed=0, eta=None, col_scale=True, max_inner=100,
-            stop_gamma=1.0, stop_rho=0.04, n_refine=2, fixed_updates=None):
+            stop_gamma=10.0, stop_rho=0.4, n_refine=2, fixed_updates=None):
     """FOSSILS (Alg. 2 with the practical rules of Sec. 4.2 / Alg. 4, QR
     preconditioner): sketch, Householder QR, sketch-and-solve x0, then
     n_refine (default 2) refinement steps with the Polyak inner solver."""
@@ -307,7 +311,7 @@ def fossils(A, b, d=None, zeta=8, seed=0, eta=None, col_scale=True, max_inner=10
 
 
 def spir(A, b, d=None, zeta=8, seed=0, eta=None, col_scale=True, max_inner=100,
-         stop_gamma=1.0, stop_rho=0.04, n_refine=2, fixed_updates=None):
+         stop_gamma=10.0, stop_rho=0.4, n_refine=2, fixed_updates=None):
     """SPIR (Alg. 3): as FOSSILS with conjugate gradient as inner solver."""
     return _solve("spir", A, b, d, zeta, seed, eta, col_scale, max_inner,
                   stop_gamma, stop_rho, n_refine, fixed_updates)

@@ -45,7 +45,7 @@ class LsqOptions(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("fp32_cond_max", ctypes.c_double),
                 ("stop_gamma", ctypes.c_double), ("stop_rho", ctypes.c_double),
                 ("fixed_inner", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("inner_fp64_fma", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class LsqInfo(ctypes.Structure):
@@ -58,7 +58,8 @@ class LsqInfo(ctypes.Structure):
                 ("ms_total", ctypes.c_float), ("launches", ctypes.c_int32),
                 ("n_inner_pass", ctypes.c_int32), ("ms_inner_pass", ctypes.c_float),
                 ("n_resid_pass", ctypes.c_int32), ("ms_resid_pass", ctypes.c_float),
-                ("ms_sketch_pass", ctypes.c_float), ("reserved", ctypes.c_int32 * 4)]
+                ("ms_sketch_pass", ctypes.c_float), ("inner_kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
     def as_dict(self):
         k = self.refine_steps
@@ -69,7 +70,8 @@ class LsqInfo(ctypes.Structure):
                 "ms_refine": self.ms_refine, "ms_total": self.ms_total,
                 "launches": self.launches, "n_inner_pass": self.n_inner_pass,
                 "ms_inner_pass": self.ms_inner_pass, "n_resid_pass": self.n_resid_pass,
-                "ms_resid_pass": self.ms_resid_pass, "ms_sketch_pass": self.ms_sketch_pass}
+                "ms_resid_pass": self.ms_resid_pass, "ms_sketch_pass": self.ms_sketch_pass,
+                "inner_kernel": self.inner_kernel}
 
 
 _vp = ctypes.c_void_p

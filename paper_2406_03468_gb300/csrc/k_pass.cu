@@ -89,6 +89,127 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
   cta_store_partial<NC>(h, sh, part, npad);
 }
 
+// ---------------------------------------------------------------------------
+// Inner pass with the row dot products on the FP32 pipe.
+//
+// GB300 runs FP64 at about 2 FMA / clock / SM, so two FP64 FMAs per element
+// (t_i += a_ij z_j and h_j += a_ij t_i) cap the pass near 30% of HBM.  Here
+// t_i is evaluated exactly enough without FP64 arithmetic:
+//   * a_ij (FP64, times 2^-Eg) is split into two FP32 words with integer
+//     operations: hi = the leading 24 significant bits (exact), lo = the
+//     remaining 29 bits rounded to FP32, so |a - hi - lo| <= 2^-48 |a|;
+//   * z_j (times 2^Eg 2^-Fz, Fz from max |z'|) is split hi/lo by rounding;
+//   * products hi*hi are exact as a pair (TwoProd with fmaf), the cross
+//     terms hi*lo + lo*hi are added to the pair's error word, and the pairs
+//     are summed with TwoSum (double-float accumulation), across the warp too;
+//   * the resulting double-float t is converted to FP64 with integer
+//     operations and one FP64 add.
+// h_j += a_ij t_i stays a single FP64 FMA per element, so h keeps full FP64
+// accumulation.  Power-of-two scalings are exact; h is scaled back by 2^Fz.
+// The host takes this kernel only when every column norm is within 2^20 of
+// the largest, which keeps every significant entry of A in FP32 range.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// a * 2^-Eg split into hi + lo (ebias = 896 + Eg).
+__device__ __forceinline__ void split_f64(double a, int ebias, float &hi, float &lo) {
+  const unsigned hw = (unsigned)__double2hiint(a), lw = (unsigned)__double2loint(a);
+  const int ef = (int)((hw >> 20) & 0x7ffu) - ebias;
+  const unsigned sign = hw & 0x80000000u;
+  const unsigned hib = sign | ((unsigned)ef << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
+  const int lf = ef - 52;
+  const float l = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), __int_as_float((lf > 0 ? lf : 1) << 23));
+  hi = (ef > 0) ? __uint_as_float(hib) : 0.0f;
+  lo = (lf > 0) ? __uint_as_float(__float_as_uint(l) | sign) : 0.0f;
+}
+
+// Exact FP32 -> FP64 widening with integer operations (normal and zero inputs).
+__device__ __forceinline__ double widen(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0) return 0.0;
+  const unsigned hw = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hw, (int)(b << 29));
+}
+
+template <int NC, bool VEC>
+__global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
+    atax_eft_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
+                    const double *__restrict__ z, int ebias, double zscale,
+                    double *__restrict__ part, int npad, const DevState *gate) {
+  if (gate != nullptr && *(volatile const int *)&gate->done) return;
+  __shared__ double sh[NC * 64];
+  __shared__ double wmax[kPassThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = min(m, (int64_t)blockIdx.x * per), r1 = min(m, r0 + per);
+  // z' = z * 2^Eg, then a common power of two 2^-Fz keeps z'' <= 1.
+  double zr[2 * NC];
+  load_vec<NC>(z, n, lane, zr);
+  double zmax = 0.0;
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) {
+    zr[k] *= zscale;
+    zmax = fmax(zmax, fabs(zr[k]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+  if (lane == 0) wmax[warp] = zmax;
+  __syncthreads();
+  zmax = 0.0;
+  for (int w = 0; w < nw; w++) zmax = fmax(zmax, wmax[w]);
+  int fz = 0;
+  if (zmax > 0.0) frexp(zmax, &fz);
+  const double down = ldexp(1.0, -fz), up = ldexp(1.0, fz);
+  float zh[2 * NC], zl[2 * NC];
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) {
+    const double v = zr[k] * down;
+    zh[k] = __double2float_rn(v);
+    zl[k] = __double2float_rn(v - (double)zh[k]);
+  }
+  double h[2 * NC];
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) h[k] = 0.0;
+  for (int64_t i = r0 + warp; i < r1; i += nw) {
+    double a[2 * NC];
+    load_row<NC, VEC>(A + i * lda, n, lane, a);
+    float sh_ = 0.0f, sl_ = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 2 * NC; k++) {
+      float ah, al;
+      split_f64(a[k], ebias, ah, al);
+      const float p = __fmul_rn(ah, zh[k]);
+      const float e = __fmaf_rn(ah, zh[k], -p);
+      const float c = __fmaf_rn(ah, zl[k], __fmaf_rn(al, zh[k], e));
+      float s, err;
+      two_sum_f(sh_, p, s, err);
+      sh_ = s;
+      sl_ = __fadd_rn(sl_, __fadd_rn(err, c));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, sh_, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, sl_, o);
+      float s, err;
+      two_sum_f(sh_, oh, s, err);
+      sh_ = s;
+      sl_ = __fadd_rn(__fadd_rn(sl_, ol), err);
+    }
+    const double t = widen(sh_) + widen(sl_);
+#pragma unroll
+    for (int k = 0; k < 2 * NC; k++) h[k] = fma(a[k], t, h[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) h[k] *= up;
+  cta_store_partial<NC>(h, sh, part, npad);
+}
+
 template <int NC, bool VEC>
 __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     resid_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
@@ -166,6 +287,19 @@ cudaError_t launch_pass_atax(const double *A, int64_t lda, int64_t m, int n, con
   LSQ_PASS_SWITCH(npad, {
     if (vec) atax_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, z, part, npad, gate);
     else atax_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, z, part, npad, gate);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_atax_eft(const double *A, int64_t lda, int64_t m, int n, const double *z,
+                                 int col_exp, double *part, int grid, int npad,
+                                 const DevState *gate, cudaStream_t s) {
+  const bool vec = vec_ok(A, lda);
+  const int ebias = 896 + col_exp;
+  const double zscale = ldexp(1.0, col_exp);
+  LSQ_PASS_SWITCH(npad, {
+    if (vec) atax_eft_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, z, ebias, zscale, part, npad, gate);
+    else atax_eft_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, z, ebias, zscale, part, npad, gate);
   });
   return cudaGetLastError();
 }

@@ -3,7 +3,10 @@
 // triangle and t = (Q^T Sb)[0:n] in the last column (the augmented column of
 // Alg. 1's sketch-and-solve start).  The paper's analysis assumes Householder
 // QR (Lemma 6.3), so this is plain column-by-column Householder:
-//   v = x + sign(x_1) ||x|| e_1,  v <- v / ||v||,  A <- A - 2 v (v^T A).
+//   v = x + sign(x_1) ||x|| e_1,  v <- v / ||v||,  A <- A - 2 v (v^T A),
+// with ||v|| from the identity ||v||^2 = 2 ||x|| (||x|| + |x_1|) and v scaled
+// by the reciprocal 1/||v|| (one rounding more per entry than a division; the
+// FP64 divide runs on GB300's narrow FP64 pipe and dominated the step).
 //
 // GB300 design: one persistent cooperative launch.  Column j belongs to CTA
 // j mod G for the whole factorisation, so its data stays with one SM (the
@@ -41,14 +44,10 @@ __global__ void __launch_bounds__(kQrThreads, 1)
       const double x0 = col[k];
       const double sg = (x0 >= 0.0) ? 1.0 : -1.0;
       const double v0 = x0 + sg * nx;
-      double sv = 0.0;
-      for (int i = k + 1 + tid; i < d; i += nt) sv = fma(col[i], col[i], sv);
-      sv = block_sum(sv, red) + v0 * v0;
-      const double nv = sqrt(sv);
-      for (int i = k + tid; i < d; i += nt) {
-        const double vi = (i == k) ? v0 : col[i];
-        v[i] = (nv > 0.0) ? vi / nv : 0.0;
-      }
+      // ||v||^2 = ||x||^2 - x0^2 + (x0 + sign(x0) ||x||)^2 = 2 ||x|| (||x|| + |x0|)
+      const double nv = sqrt(2.0 * nx * (nx + fabs(x0)));
+      const double inv = (nv > 0.0) ? 1.0 / nv : 0.0;
+      for (int i = k + tid; i < d; i += nt) v[i] = ((i == k) ? v0 : col[i]) * inv;
       __syncthreads();
       for (int i = k + tid; i < d; i += nt) col[i] = (i == k) ? -sg * nx : 0.0;
     }

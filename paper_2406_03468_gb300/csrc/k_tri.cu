@@ -18,26 +18,36 @@ namespace lsq {
 
 namespace {
 
+// tile: 32 x 33 doubles of shared memory for the diagonal block.
 __device__ void block_trsv(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
-                           const double *__restrict__ rinv, int n, int trans, double *sy) {
+                           const double *__restrict__ rinv, int n, int trans, double *sy,
+                           double *tile) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nt = blockDim.x;
   const int nb = (n + 31) / 32;
   for (int bb = 0; bb < nb; bb++) {
     const int blk = trans ? bb : nb - 1 - bb;
     const int j0 = blk * 32, j1 = min(n, j0 + 32), len = j1 - j0;
+    // stage the diagonal block: tile[jj][l] = column jj (trans 0) / row jj (trans 1) entry l
+    const double *src = trans ? Rrm : Rcm;
+    for (int e = threadIdx.x; e < 32 * 32; e += nt) {
+      const int jj = e >> 5, l = e & 31;
+      tile[jj * 33 + l] = (jj < len && l < len) ? src[(size_t)(j0 + jj) * n + j0 + l] : 0.0;
+    }
+    __syncthreads();
     if (warp == 0) {
       double yl = (lane < len) ? sy[j0 + lane] : 0.0;
+      const double ri = (lane < len) ? rinv[j0 + lane] : 0.0;
       if (!trans) {
         for (int jj = len - 1; jj >= 0; jj--) {
-          const double xj = __shfl_sync(0xffffffffu, yl, jj) * rinv[j0 + jj];
+          const double xj = __shfl_sync(0xffffffffu, yl * ri, jj);
           if (lane == jj) yl = xj;
-          else if (lane < jj) yl = fma(-Rcm[(size_t)(j0 + jj) * n + j0 + lane], xj, yl);
+          else if (lane < jj) yl = fma(-tile[jj * 33 + lane], xj, yl);
         }
       } else {
         for (int jj = 0; jj < len; jj++) {
-          const double xj = __shfl_sync(0xffffffffu, yl, jj) * rinv[j0 + jj];
+          const double xj = __shfl_sync(0xffffffffu, yl * ri, jj);
           if (lane == jj) yl = xj;
-          else if (lane > jj && lane < len) yl = fma(-Rrm[(size_t)(j0 + jj) * n + j0 + lane], xj, yl);
+          else if (lane > jj && lane < len) yl = fma(-tile[jj * 33 + lane], xj, yl);
         }
       }
       if (lane < len) sy[j0 + lane] = yl;
@@ -68,10 +78,11 @@ __global__ void __launch_bounds__(kVecThreads)
   if (gate != nullptr && *(volatile const int *)&gate->done) return;
   extern __shared__ double sy[];
   double *scratch = sy + n;
+  double *tile = scratch + 32;
   for (int i = threadIdx.x; i < n; i += blockDim.x)
     sy[i] = in_scale ? y[i] * in_scale[i] : y[i];
   __syncthreads();
-  block_trsv(Rcm, Rrm, rinv, n, trans, sy);
+  block_trsv(Rcm, Rrm, rinv, n, trans, sy, tile);
   double nrm = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double x = sy[i];
@@ -120,7 +131,7 @@ __global__ void __launch_bounds__(kVecThreads)
     condest_kernel(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
                    const double *__restrict__ rinv, int n, int iters, DevState *st) {
   extern __shared__ double sm[];
-  double *v = sm, *y = sm + n, *scratch = sm + 2 * n;
+  double *v = sm, *y = sm + n, *scratch = sm + 2 * n, *tile = scratch + 32;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.0 + 0.25 * (double)((i * 7919) % 17);
   __syncthreads();
   block_normalize(v, n, scratch);
@@ -138,10 +149,10 @@ __global__ void __launch_bounds__(kVecThreads)
   block_normalize(v, n, scratch);
   double winv = 0.0;
   for (int it = 0; it <= iters; it++) {
-    block_trsv(Rcm, Rrm, rinv, n, 1, v);  // v <- R^{-T} v
+    block_trsv(Rcm, Rrm, rinv, n, 1, v, tile);  // v <- R^{-T} v
     winv = block_normalize(v, n, scratch);
     if (it == iters) break;
-    block_trsv(Rcm, Rrm, rinv, n, 0, v);  // v <- R^{-1} v
+    block_trsv(Rcm, Rrm, rinv, n, 0, v, tile);  // v <- R^{-1} v
     block_normalize(v, n, scratch);
   }
   if (threadIdx.x == 0) {
@@ -157,7 +168,7 @@ cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv
                         const double *y, const double *in_scale, double *out,
                         const double *out_scale, double *out_scaled, double *accum,
                         double *norm2_out, const DevState *gate, cudaStream_t s) {
-  const size_t smem = (size_t)(n + 32) * sizeof(double);
+  const size_t smem = (size_t)(n + 32 + 32 * 33) * sizeof(double);
   trsv_kernel<<<1, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, n, trans, y, in_scale, out, out_scale,
                                            out_scaled, accum, norm2_out, gate);
   return cudaGetLastError();
@@ -165,7 +176,7 @@ cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv
 
 cudaError_t launch_condest(const double *Rcm, const double *Rrm, const double *rinv, int n,
                            int iters, DevState *st, cudaStream_t s) {
-  const size_t smem = (size_t)(2 * n + 32) * sizeof(double);
+  const size_t smem = (size_t)(2 * n + 32 + 32 * 33) * sizeof(double);
   condest_kernel<<<1, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, n, iters, st);
   return cudaGetLastError();
 }

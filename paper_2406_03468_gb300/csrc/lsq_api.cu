@@ -69,6 +69,9 @@ struct lsq_plan_s {
   cudaEvent_t ev[5] = {};
   double *stageA = nullptr, *stageb = nullptr, *stagex = nullptr;
   bool sketched = false;
+  bool use_eft = false;              // inner pass on the FP32 pipe
+  int col_exp = 0;                   // all |A_ij| < 2^col_exp
+  double *dcol_host = nullptr;
   int launches = 0;                 // kernels launched by the current call
   std::vector<cudaEvent_t> tev;     // timing: pass begin/end event pairs
   int tev_used = 0;
@@ -138,6 +141,26 @@ float tev_ms(lsq_plan P, int idx) {
   return ms;
 }
 
+// The FP32-pipe inner pass needs every significant entry of A in FP32
+// range after one common power-of-two scaling: all column norms within 2^20
+// of the largest (column norms are the dcol of the column scaling).
+void choose_inner_kernel(lsq_plan P) {
+  P->use_eft = false;
+  if (P->o.inner_fp64_fma) return;
+  double mx = 0.0, mn = INFINITY;
+  for (int j = 0; j < (int)P->n; j++) {
+    const double v = P->dcol_host[j];
+    if (!(v > 0.0) || !std::isfinite(v)) return;
+    mx = v > mx ? v : mx;
+    mn = v < mn ? v : mn;
+  }
+  int e = 0;
+  std::frexp(mx, &e);  // mx < 2^e
+  if (mn < std::ldexp(1.0, e - 20) || e > 100 || e < -100) return;
+  P->col_exp = e;
+  P->use_eft = true;
+}
+
 lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
   if (!dA || !db) return fail(LSQ_ERR_INVALID, "A or b is NULL");
   const int n = (int)P->n;
@@ -174,7 +197,9 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
   LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->t, nullptr, P->xs, P->dinv, P->xo,
                      nullptr, &P->st->x0norm2, nullptr, P->s));
   LSQ_CU(cudaEventRecord(P->ev[2], P->s));
+  LSQ_CU(cudaMemcpyAsync(P->dcol_host, P->dcol, sizeof(double) * n, cudaMemcpyDeviceToHost, P->s));
   LSQ_TRY(read_state(P));
+  choose_inner_kernel(P);
   if (P->st_host->nonfinite) return fail(LSQ_ERR_NONFINITE, "A or b holds NaN or Inf");
   if (P->st_host->zero_col) return fail(LSQ_ERR_INVALID, "A has a zero column (column scaling)");
   P->sketched = true;
@@ -228,8 +253,12 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
         inner_ev[i].push_back(tj);
         LSQ_CU(cudaEventRecord(P->tev[2 * tj], P->s));
       }
-      LSQ_CU(launch_pass_atax(dA, P->lda, P->m, n, P->z, P->part, P->gpass, P->npad, P->st,
-                              P->s));
+      if (P->use_eft)
+        LSQ_CU(launch_pass_atax_eft(dA, P->lda, P->m, n, P->z, P->col_exp, P->part, P->gpass,
+                                    P->npad, P->st, P->s));
+      else
+        LSQ_CU(launch_pass_atax(dA, P->lda, P->m, n, P->z, P->part, P->gpass, P->npad, P->st,
+                                P->s));
       if (tj >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tj + 1], P->s));
       P->launches += 5;
       LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->h, nullptr, nullptr, P->st,
@@ -283,6 +312,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     cudaEventElapsedTime(&ms, P->ev[0], P->ev[3]);
     info->ms_total = ms;
     info->launches = P->launches;
+    info->inner_kernel = P->use_eft ? 1 : 0;
     if (P->o.timing) {
       for (int k : resid_ev) {
         info->ms_resid_pass += tev_ms(P, k);
@@ -310,6 +340,7 @@ void free_plan(lsq_plan P) {
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->st_host) cudaFreeHost(P->st_host);
+  if (P->dcol_host) cudaFreeHost(P->dcol_host);
   for (auto &e : P->ev)
     if (e) cudaEventDestroy(e);
   for (auto &e : P->tev) cudaEventDestroy(e);
@@ -329,8 +360,8 @@ void lsq_options_default(lsq_options *o) {
   o->max_refine = 2;
   o->precision = LSQ_PREC_FP64;
   o->fp32_cond_max = 1e5;
-  o->stop_gamma = 1.0;
-  o->stop_rho = 0.04;
+  o->stop_gamma = 10.0;  // Alg. 4 (the Sec. 4.2 text quotes 1 and 0.04)
+  o->stop_rho = 0.4;
 }
 
 const char *lsq_last_error(void) { return g_err.c_str(); }
@@ -384,6 +415,7 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   A(dalloc(&P->st, 1));
   A(dalloc(&P->bar, 2));
   A(cudaMallocHost((void **)&P->st_host, sizeof(DevState)));
+  A(cudaMallocHost((void **)&P->dcol_host, sizeof(double) * n));
   for (auto &ev : P->ev) A(cudaEventCreate(&ev));
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);
@@ -487,7 +519,11 @@ lsq_status lsq_get_R(lsq_plan P, double *dR, double *dt, double *dx0, double *co
 lsq_status lsq_apply_normal(lsq_plan P, const double *dA, const double *dz, double *dh) {
   if (!P || !dA || !dz || !dh) return fail(LSQ_ERR_INVALID, "NULL argument");
   const int n = (int)P->n;
-  LSQ_CU(launch_pass_atax(dA, P->lda, P->m, n, dz, P->part, P->gpass, P->npad, nullptr, P->s));
+  if (P->sketched && P->use_eft)
+    LSQ_CU(launch_pass_atax_eft(dA, P->lda, P->m, n, dz, P->col_exp, P->part, P->gpass, P->npad,
+                                nullptr, P->s));
+  else
+    LSQ_CU(launch_pass_atax(dA, P->lda, P->m, n, dz, P->part, P->gpass, P->npad, nullptr, P->s));
   LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, nullptr, dh, nullptr, nullptr, nullptr, P->s));
   LSQ_CU(cudaStreamSynchronize(P->s));
   return LSQ_OK;

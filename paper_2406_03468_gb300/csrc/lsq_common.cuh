@@ -138,6 +138,12 @@ cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv
 cudaError_t launch_pass_atax(const double *A, int64_t lda, int64_t m, int n, const double *z,
                              double *part, int grid, int npad, const DevState *gate,
                              cudaStream_t s);
+// As launch_pass_atax with the row products on the FP32 pipe (k_pass.cu);
+// col_exp: A's entries are below 2^col_exp and every column norm is above
+// 2^(col_exp - 20).
+cudaError_t launch_pass_atax_eft(const double *A, int64_t lda, int64_t m, int n, const double *z,
+                                 int col_exp, double *part, int grid, int npad,
+                                 const DevState *gate, cudaStream_t s);
 cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, const double *b,
                               const double *x, double *part, double *r2_part, int grid, int npad,
                               cudaStream_t s);

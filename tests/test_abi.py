@@ -47,7 +47,7 @@ def test_struct_layout_matches_c(tmp_path):
 def test_defaults_and_validation_without_gpu():
     o = lsq.lsq_options_default(m=100, n=10)
     assert o.zeta == 8 and o.col_scale == 1 and o.max_inner == 100 and o.max_refine == 2
-    assert abs(o.stop_rho - 0.04) < 1e-15 and o.stop_gamma == 1.0
+    assert abs(o.stop_rho - 0.4) < 1e-15 and o.stop_gamma == 10.0
     bad = lsq.lsq_options_default(m=5, n=10)          # m < n is rejected before any CUDA call
     with pytest.raises(lsq.LsqError) as e:
         lsq.lsq_plan_create(bad)

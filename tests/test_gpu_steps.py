@@ -183,3 +183,48 @@ def test_invalid_inputs():
     st, info = lsq.lsq_solve_fossils(plan.handle, T(A), T(b), x)
     assert st == 0
     assert np.allclose(H(x), np.linalg.lstsq(A, b, rcond=None)[0], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("m,n", [(20011, 130), (20011, 37), (4097, 1000), (60000, 500)])
+def test_inner_pass_fp32_pipe(m, n):
+    """The FP32-pipe inner pass (exact hi/lo splits, double-float row sums,
+    FP64 column sums) against a compensated-arithmetic reference, on a z with
+    16 decades of dynamic range (as z = R^{-1} dy has on ill-conditioned
+    problems), with the same per-element bound as the FP64 pass."""
+    rng = np.random.default_rng(m + 3 * n)
+    A = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-2, 2, n)
+    b = rng.standard_normal(m)
+    z = rng.standard_normal(n) * 10.0 ** rng.uniform(-8, 8, n)
+    out = {}
+    for flag in (0, 1):
+        plan = lsq.Plan(m, n, seed=1, inner_fp64_fma=flag)
+        dA = T(A)
+        lsq.lsq_sketch(plan.handle, dA, T(b))
+        h = empty(n)
+        lsq.lsq_apply_normal(plan.handle, dA, T(z), h)
+        out[flag] = H(h)
+        plan.close()
+    _, _, h_ref = oracle.residual_dot2(A, np.zeros(m), -z)    # A^T (A z), compensated
+    scale = np.abs(A).T @ (np.abs(A) @ np.abs(z))
+    bound = 4 * (n + m) * u * scale
+    for flag in (0, 1):
+        assert (np.abs(out[flag] - h_ref) <= bound).all(), flag
+    err_eft = float(np.max(np.abs(out[0] - h_ref) / scale))
+    err_f64 = float(np.max(np.abs(out[1] - h_ref) / scale))
+    print("max relative error: fp32-pipe %.3g  fp64 %.3g  (u = %.3g)" % (err_eft, err_f64, u))
+
+
+def test_inner_kernel_choice_badly_scaled_columns():
+    """Column norms 2^30 apart: the FP32-pipe pass is not taken, the FP64 one
+    is, and the solve is still backward stable."""
+    P = problem_svd(20000, 40, 1e6, 1e-5, seed=4)
+    A = P["A"].copy()
+    A[:, :20] *= 2.0 ** 30
+    b = P["b"]
+    for Am, expect in ((P["A"], 1), (A, 0)):
+        plan = lsq.Plan(20000, 40, seed=2)
+        x = empty(40)
+        st, info = plan.solve(T(Am), T(b), x, "fossils")
+        assert info["inner_kernel"] == expect
+        assert oracle.kw_relative(Am, b, H(x)) <= 1e-13
+        plan.close()
