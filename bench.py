@@ -258,7 +258,8 @@ def run_ours(args):
     achieved = bytes_pass / avg_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": traffic_per_launch(),
-            "kernel": "atax_kernel (fused A^T(A z) pass)", "launches_timed": n_in,
+            "kernel": ("atax_eft_kernel" if infos[-1]["inner_kernel"] else "atax_kernel")
+                      + " (fused A^T(A z) inner pass)", "launches_timed": n_in,
             "avg_launch_ms": avg_s * 1e3, "peak_kind": pk_kind}
     passes = statistics.mean(i["passes"] for i in infos)
     hbm_solve = passes * bytes_pass / (ms / args.steps / 1e3) / 1e9
