@@ -181,6 +181,23 @@ lsq_status lsq_residual(lsq_plan plan, const double *dA, const double *db, const
  * R^{-1} dy (trans = 0) or R^{-T} dy (trans = 1).  dx may equal dy. */
 lsq_status lsq_trsv(lsq_plan plan, int trans, const double *dy, double *dx);
 
+/* One fused pass dh = A^T (A dz) that allocates no device memory, for
+ * callers that cannot call cudaMalloc: code inside a framework that owns all
+ * device memory through its own pool, or a latency-critical loop that cannot
+ * afford cudaMalloc's implicit synchronisation or its failure.  The paper
+ * has no counterpart; it is a packaging of lsq_apply_normal's FP64 pass.
+ * No plan is needed.  dA: m x n row-major (lda, 0 => n), dz, dh: n, all
+ * device pointers owned by the caller; cuda_stream: cudaStream_t (NULL =
+ * default stream); returns after the stream has finished the call.
+ * Scratch: a fixed 2 MiB device array inside the library (held by every GPU
+ * that loads it until the process exits).  The first call on a device looks
+ * up the array's device address and must come before any stream capture.
+ * Calls that overlap on the GPU share the array and race.
+ * Errors: LSQ_ERR_INVALID for NULL pointers, lda < n or n > LSQ_MAX_N;
+ * LSQ_ERR_CUDA when a launch fails. */
+lsq_status lsq_apply_normal_noalloc(const double *dA, int64_t m, int64_t n, int64_t lda,
+                                    const double *dz, double *dh, void *cuda_stream);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char *lsq_last_error(void);
 

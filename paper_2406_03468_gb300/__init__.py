@@ -16,7 +16,7 @@ __all__ = [
     "LsqError", "LsqOptions", "LsqInfo", "lsq_options_default", "lsq_plan_create",
     "lsq_plan_destroy", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir", "lsq_solve_host",
     "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_R", "lsq_apply_normal", "lsq_residual",
-    "lsq_trsv", "lsq_last_error", "Plan", "library_path", "EXPORTED",
+    "lsq_trsv", "lsq_apply_normal_noalloc", "lsq_last_error", "Plan", "library_path", "EXPORTED",
     "LSQ_PREC_AUTO", "LSQ_PREC_FP64", "LSQ_PREC_FP32_INNER",
 ]
 
@@ -92,6 +92,8 @@ EXPORTED = {
     "lsq_apply_normal": (_i32, [_vp, _vp, _vp, _vp]),
     "lsq_residual": (_i32, [_vp, _vp, _vp, _vp, _vp, _dp]),
     "lsq_trsv": (_i32, [_vp, _i32, _vp, _vp]),
+    "lsq_apply_normal_noalloc": (_i32, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                        _vp, _vp, _vp]),
     "lsq_last_error": (ctypes.c_char_p, []),
 }
 
@@ -210,6 +212,13 @@ def lsq_residual(plan, A, b, x, g):
     r2 = ctypes.c_double()
     _check(_lib().lsq_residual(plan, _ptr(A), _ptr(b), _ptr(x), _ptr(g), ctypes.byref(r2)))
     return r2.value
+
+
+def lsq_apply_normal_noalloc(A, m, n, lda, z, h, stream=None):
+    """dh = A^T (A dz) without any device allocation (see include/lsq.h)."""
+    s = getattr(stream, "cuda_stream", stream)
+    return _check(_lib().lsq_apply_normal_noalloc(_ptr(A), int(m), int(n), int(lda), _ptr(z),
+                                                  _ptr(h), s))
 
 
 def lsq_trsv(plan, trans, y, x):

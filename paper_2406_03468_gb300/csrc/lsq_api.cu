@@ -48,6 +48,8 @@ constexpr int kStopPollEvery = 4;  // step 1: read the device stop flag every 4 
 
 }  // namespace
 
+void lsq::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 struct lsq_plan_s {
   lsq_options o{};
   cudaStream_t s = nullptr;

@@ -99,6 +99,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, volatile unsig
   return ok != 0;
 }
 
+// Message returned by lsq_last_error() on the calling thread (lsq_api.cu).
+void set_last_error(const char *msg);
+
 // ---------------------------------------------------------------- launchers
 // Every launcher enqueues on `s` and returns the launch's cudaError_t.
 
