@@ -49,11 +49,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rows", type=int, default=0,
                     help="override m (small cases for ncu captures; not a bench line)")
+    ap.add_argument("--cols", type=int, default=0,
+                    help="override n (small cases for ncu captures; not a bench line)")
     args = ap.parse_args()
+    global M, N, WORKLOAD
     if args.rows:
-        global M, WORKLOAD
         M = args.rows
-        WORKLOAD = "fossils_fp64_m%d_n500_kappa1e10_d6000_zeta8" % M
+    if args.cols:
+        N = args.cols
+    if args.rows or args.cols:
+        WORKLOAD = "fossils_fp64_m%d_n%d_kappa1e10_d%d_zeta8" % (M, N, 12 * N)
     return args
 
 

@@ -65,7 +65,12 @@ typedef struct {
   int32_t col_scale;     /* 1: scale columns of A to unit norm (Alg. 4), 0: off */
   int32_t max_inner;     /* cap on inner updates per refinement step (0 => 100) */
   int32_t max_refine;    /* refinement steps (0 => 2 on FP64; FP32 tier: up to 6) */
-  int32_t precision;     /* LSQ_PREC_* (default LSQ_PREC_FP64) */
+  int32_t precision;     /* LSQ_PREC_* (default LSQ_PREC_FP64).  AUTO and FP32_INNER make
+                            the sketch pass also write an FP32 copy of A (4 m n bytes
+                            more device memory); the FP32 tier then runs its inner
+                            passes on it, the residual, A^T r, x update, QR and
+                            triangular solves staying FP64, and refines until ||c_i||
+                            stops halving (at least 2, at most max(max_refine, 6) steps) */
   double fp32_cond_max;  /* FP32-inner gate on condest (0 => 1e5) */
   double stop_gamma;     /* step-1 stop constant gamma (Alg. 4: 10; Sec. 4.2 text: 1) */
   double stop_rho;       /* step-1 stop constant rho (Alg. 4: 0.4; Sec. 4.2 text: 0.04) */
@@ -98,8 +103,10 @@ typedef struct {
   int32_t n_resid_pass;           /* timing: residual passes */
   float ms_resid_pass;            /* timing: their summed device time */
   float ms_sketch_pass;           /* timing: the sketch pass */
-  int32_t inner_kernel;           /* 0: FP64-FMA inner pass, 1: FP32-pipe row products */
-  int32_t reserved[3];
+  int32_t inner_kernel;           /* 0: FP64-FMA inner pass, 1: FP32-pipe row products,
+                                     2: FP32 tier pass on the FP32 copy of A */
+  double bytes_a;                 /* bytes of A (and its FP32 copy) streamed by the solve */
+  int32_t reserved[2];
 } lsq_info;
 
 /* Fill *o with the defaults listed above (m, n, lda left 0). */

@@ -59,7 +59,7 @@ class LsqInfo(ctypes.Structure):
                 ("n_inner_pass", ctypes.c_int32), ("ms_inner_pass", ctypes.c_float),
                 ("n_resid_pass", ctypes.c_int32), ("ms_resid_pass", ctypes.c_float),
                 ("ms_sketch_pass", ctypes.c_float), ("inner_kernel", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("bytes_a", ctypes.c_double), ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self):
         k = self.refine_steps
@@ -71,7 +71,7 @@ class LsqInfo(ctypes.Structure):
                 "launches": self.launches, "n_inner_pass": self.n_inner_pass,
                 "ms_inner_pass": self.ms_inner_pass, "n_resid_pass": self.n_resid_pass,
                 "ms_resid_pass": self.ms_resid_pass, "ms_sketch_pass": self.ms_sketch_pass,
-                "inner_kernel": self.inner_kernel}
+                "inner_kernel": self.inner_kernel, "bytes_a": self.bytes_a}
 
 
 _vp = ctypes.c_void_p

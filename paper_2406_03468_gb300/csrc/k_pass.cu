@@ -210,6 +210,83 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
   cta_store_partial<NC>(h, sh, part, npad);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 inner pass of the mixed-precision tier (condest below the gate): reads
+// the FP32 copy of A (4 bytes per element), FP32 row products, FP32 column
+// sums flushed into FP64 accumulators every 32 rows (bounds the FP32
+// accumulation error at about 32 u_32 per block).  z is scaled by a common
+// power of two so that it sits in FP32 range; h is scaled back.
+// ---------------------------------------------------------------------------
+template <int NC>
+__global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
+    atax32_kernel(const float *__restrict__ A32, int64_t ld32, int64_t m, int n,
+                  const double *__restrict__ z, double *__restrict__ part, int npad,
+                  const DevState *gate) {
+  if (gate != nullptr && *(volatile const int *)&gate->done) return;
+  __shared__ double sh[NC * 64];
+  __shared__ double wmax[kPassThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = min(m, (int64_t)blockIdx.x * per), r1 = min(m, r0 + per);
+  double zr[2 * NC];
+  load_vec<NC>(z, n, lane, zr);
+  double zmax = 0.0;
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) zmax = fmax(zmax, fabs(zr[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+  if (lane == 0) wmax[warp] = zmax;
+  __syncthreads();
+  zmax = 0.0;
+  for (int w = 0; w < nw; w++) zmax = fmax(zmax, wmax[w]);
+  int fz = 0;
+  if (zmax > 0.0) frexp(zmax, &fz);
+  const double down = ldexp(1.0, -fz), up = ldexp(1.0, fz);
+  float zf[2 * NC], hf[2 * NC];
+  double hd[2 * NC];
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) {
+    zf[k] = __double2float_rn(zr[k] * down);
+    hf[k] = 0.0f;
+    hd[k] = 0.0;
+  }
+  int blk = 0;
+  for (int64_t i = r0 + warp; i < r1; i += nw) {
+    const float *row = A32 + i * ld32;
+    float a[2 * NC];
+#pragma unroll
+    for (int k = 0; k < NC; k++) {
+      const int col = 64 * k + 2 * lane;
+      if (col + 1 < n) {
+        const float2 v = __ldcs(reinterpret_cast<const float2 *>(row + col));
+        a[2 * k] = v.x;
+        a[2 * k + 1] = v.y;
+      } else {
+        a[2 * k] = (col < n) ? __ldcs(row + col) : 0.0f;
+        a[2 * k + 1] = 0.0f;
+      }
+    }
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 2 * NC; k++) t = __fmaf_rn(a[k], zf[k], t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+#pragma unroll
+    for (int k = 0; k < 2 * NC; k++) hf[k] = __fmaf_rn(a[k], t, hf[k]);
+    if (++blk == 32) {
+      blk = 0;
+#pragma unroll
+      for (int k = 0; k < 2 * NC; k++) {
+        hd[k] += (double)hf[k];
+        hf[k] = 0.0f;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) hd[k] = (hd[k] + (double)hf[k]) * up;
+  cta_store_partial<NC>(hd, sh, part, npad);
+}
+
 template <int NC, bool VEC>
 __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     resid_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
@@ -300,6 +377,15 @@ cudaError_t launch_pass_atax_eft(const double *A, int64_t lda, int64_t m, int n,
   LSQ_PASS_SWITCH(npad, {
     if (vec) atax_eft_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, z, ebias, zscale, part, npad, gate);
     else atax_eft_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, z, ebias, zscale, part, npad, gate);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_atax32(const float *A32, int64_t ld32, int64_t m, int n, const double *z,
+                               double *part, int grid, int npad, const DevState *gate,
+                               cudaStream_t s) {
+  LSQ_PASS_SWITCH(npad, {
+    atax32_kernel<NC><<<grid, kPassThreads, 0, s>>>(A32, ld32, m, n, z, part, npad, gate);
   });
   return cudaGetLastError();
 }

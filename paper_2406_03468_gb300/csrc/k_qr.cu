@@ -8,13 +8,14 @@
 // by the reciprocal 1/||v|| (one rounding more per entry than a division; the
 // FP64 divide runs on GB300's narrow FP64 pipe and dominated the step).
 //
-// GB300 design: one persistent cooperative launch.  Column j belongs to CTA
-// j mod G for the whole factorisation, so its data stays with one SM (the
-// L1 of that SM never holds another CTA's column).  Step k: the owner of
-// column k forms v_k into one of two global buffers (alternating by the
-// parity of k), one bounded grid barrier, then every CTA applies H_k to the
-// columns it owns.  One barrier per column; the double buffer keeps the
-// owner of column k+1 from overwriting v_k while others still read it.
+// GB300 design: one persistent cooperative launch, one CTA per SM.  Column
+// j belongs to CTA j mod G for the whole factorisation and, when the CTA's
+// columns fit (d = 12n up to n ~ 600), lives in that CTA's shared memory
+// from start to end.  Step k: every CTA applies H_k (v_k from one of two
+// global buffers, alternating with the parity of k) to its columns j > k;
+// the owner of column k+1 does that column first and then builds v_{k+1}
+// into the other buffer (lookahead), so no CTA waits for a serial reflector
+// step; one bounded grid barrier closes the step.
 #include "lsq_common.cuh"
 
 namespace lsq {
@@ -24,74 +25,110 @@ namespace {
 constexpr int kQrThreads = 512;
 constexpr int kQrBatch = 8;  // columns updated together by one CTA
 
+// Householder vector of column `col` at step k (col holds rows 0..d-1, the
+// entries below row k are the current trailing column): writes
+// v = (x + sign(x_k)||x|| e_k) / ||v|| to v[k..d-1] and R_kk = -sign(x_k)||x||
+// to col[k].  Whole CTA.
+__device__ void make_reflector(double *col, int k, int d, double *v, double *red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double s = 0.0;
+  for (int i = k + tid; i < d; i += nt) s = fma(col[i], col[i], s);
+  s = block_sum(s, red);
+  const double nx = sqrt(s);
+  const double x0 = col[k];
+  const double sg = (x0 >= 0.0) ? 1.0 : -1.0;
+  const double v0 = x0 + sg * nx;
+  // ||v||^2 = ||x||^2 - x0^2 + (x0 + sign(x0) ||x||)^2 = 2 ||x|| (||x|| + |x0|)
+  const double nv = sqrt(2.0 * nx * (nx + fabs(x0)));
+  const double inv = (nv > 0.0) ? 1.0 / nv : 0.0;
+  for (int i = k + tid; i < d; i += nt) v[i] = ((i == k) ? v0 : col[i]) * inv;
+  __syncthreads();
+  if (tid == 0) col[k] = -sg * nx;
+}
+
+// Apply H_k = I - 2 v v^T (v from global memory, rows k..d-1) to `cnt` <= kQrBatch
+// columns cols[0..cnt).  Whole CTA.
+__device__ void apply_reflector(double *const *cols, int cnt, int k, int d, const double *v,
+                                double *red, double *wsh) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  double acc[kQrBatch];
+#pragma unroll
+  for (int c = 0; c < kQrBatch; c++) acc[c] = 0.0;
+  for (int i = k + tid; i < d; i += nt) {
+    const double vi = __ldcg(v + i);
+#pragma unroll
+    for (int c = 0; c < kQrBatch; c++)
+      if (c < cnt) acc[c] = fma(vi, cols[c][i], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < kQrBatch; c++)
+    if (c < cnt) acc[c] = warp_sum(acc[c]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < kQrBatch; c++)
+      if (c < cnt) red[warp * kQrBatch + c] = acc[c];
+  }
+  __syncthreads();
+  if (tid < cnt) {
+    double sacc = 0.0;
+    for (int w = 0; w < nw; w++) sacc += red[w * kQrBatch + tid];
+    wsh[tid] = 2.0 * sacc;
+  }
+  __syncthreads();
+  for (int i = k + tid; i < d; i += nt) {
+    const double vi = __ldcg(v + i);
+#pragma unroll
+    for (int c = 0; c < kQrBatch; c++)
+      if (c < cnt) cols[c][i] = fma(-wsh[c], vi, cols[c][i]);
+  }
+  __syncthreads();
+}
+
+// SMEM: the CTA's columns live in shared memory for the whole factorisation.
+template <bool SMEM>
 __global__ void __launch_bounds__(kQrThreads, 1)
-    qr_kernel(double *__restrict__ W, int d, int n, double *__restrict__ vbuf,
-              unsigned int *bar, DevState *st, uint64_t timeout_ns) {
+    qr_kernel(double *__restrict__ W, int d, int n, double *__restrict__ vbuf, unsigned int *bar,
+              DevState *st, uint64_t timeout_ns) {
+  extern __shared__ double dsm[];
   __shared__ double red[kQrThreads / 32 * kQrBatch];
   __shared__ double wsh[kQrBatch];
   const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int ncols = n + 1;
-  for (int k = 0; k < n; k++) {
-    double *v = vbuf + (size_t)(k & 1) * d;
+  const int nloc = (ncols - me + G - 1) / G;  // local columns j = me + l G
+  auto colp = [&](int l) -> double * {
+    return SMEM ? dsm + (size_t)l * d : W + (size_t)(me + l * G) * d;
+  };
+  if (SMEM) {
+    for (int l = 0; l < nloc; l++)
+      for (int i = tid; i < d; i += nt) dsm[(size_t)l * d + i] = W[(size_t)(me + l * G) * d + i];
     __syncthreads();
-    if (k % G == me) {
-      double *col = W + (size_t)k * d;
-      double s = 0.0;
-      for (int i = k + tid; i < d; i += nt) s = fma(col[i], col[i], s);
-      s = block_sum(s, red);
-      const double nx = sqrt(s);
-      const double x0 = col[k];
-      const double sg = (x0 >= 0.0) ? 1.0 : -1.0;
-      const double v0 = x0 + sg * nx;
-      // ||v||^2 = ||x||^2 - x0^2 + (x0 + sign(x0) ||x||)^2 = 2 ||x|| (||x|| + |x0|)
-      const double nv = sqrt(2.0 * nx * (nx + fabs(x0)));
-      const double inv = (nv > 0.0) ? 1.0 / nv : 0.0;
-      for (int i = k + tid; i < d; i += nt) v[i] = ((i == k) ? v0 : col[i]) * inv;
-      __syncthreads();
-      for (int i = k + tid; i < d; i += nt) col[i] = (i == k) ? -sg * nx : 0.0;
+  }
+  if (me == 0) make_reflector(colp(0), 0, d, vbuf, red);
+  if (!grid_barrier(bar, bar + 1, &st->err, timeout_ns)) return;
+  double *cols[kQrBatch];
+  for (int k = 0; k < n; k++) {
+    const double *v = vbuf + (size_t)(k & 1) * d;
+    const int l0 = (k + 1 > me) ? (k + 1 - me + G - 1) / G : 0;  // first local column > k
+    int l = l0;
+    // Lookahead: the owner of column k+1 applies H_k to it first and builds
+    // v_{k+1} into the other buffer while the rest of the grid is updating.
+    if (k + 1 < n && (k + 1) % G == me && l < nloc) {
+      cols[0] = colp(l);
+      apply_reflector(cols, 1, k, d, v, red, wsh);
+      make_reflector(colp(l), k + 1, d, vbuf + (size_t)((k + 1) & 1) * d, red);
+      l++;
+    }
+    while (l < nloc) {
+      int cnt = 0;
+      for (; cnt < kQrBatch && l < nloc; cnt++, l++) cols[cnt] = colp(l);
+      apply_reflector(cols, cnt, k, d, v, red, wsh);
     }
     if (!grid_barrier(bar, bar + 1, &st->err, timeout_ns)) return;
-    // Apply H_k to the owned columns j > k (the augmented column n included).
-    const int jf = k + 1 + (((me - (k + 1)) % G) + G) % G;
-    for (int jb = jf; jb < ncols; jb += G * kQrBatch) {
-      double acc[kQrBatch];
-#pragma unroll
-      for (int c = 0; c < kQrBatch; c++) acc[c] = 0.0;
-      for (int i = k + tid; i < d; i += nt) {
-        const double vi = __ldcg(v + i);
-#pragma unroll
-        for (int c = 0; c < kQrBatch; c++) {
-          const int j = jb + c * G;
-          if (j < ncols) acc[c] = fma(vi, W[(size_t)j * d + i], acc[c]);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < kQrBatch; c++) acc[c] = warp_sum(acc[c]);
-      __syncthreads();
-      if (lane == 0) {
-#pragma unroll
-        for (int c = 0; c < kQrBatch; c++) red[warp * kQrBatch + c] = acc[c];
-      }
-      __syncthreads();
-      if (tid < kQrBatch) {
-        double sacc = 0.0;
-        for (int w = 0; w < nw; w++) sacc += red[w * kQrBatch + tid];
-        wsh[tid] = 2.0 * sacc;
-      }
-      __syncthreads();
-      for (int i = k + tid; i < d; i += nt) {
-        const double vi = __ldcg(v + i);
-#pragma unroll
-        for (int c = 0; c < kQrBatch; c++) {
-          const int j = jb + c * G;
-          if (j < ncols) {
-            double *p = W + (size_t)j * d + i;
-            *p = fma(-wsh[c], vi, *p);
-          }
-        }
-      }
-    }
+  }
+  if (SMEM) {
+    for (int l2 = 0; l2 < nloc; l2++)
+      for (int i = tid; i < d; i += nt) W[(size_t)(me + l2 * G) * d + i] = dsm[(size_t)l2 * d + i];
   }
 }
 
@@ -115,13 +152,25 @@ __global__ void extract_r_kernel(const double *__restrict__ W, int d, int n, dou
 
 int qr_grid(int n, int nsm) { return (n + 1) < nsm ? (n + 1) : nsm; }
 
+// Largest dynamic shared memory the columns may use (227 KB opt-in minus the static part).
+constexpr size_t kQrSmemMax = 225 * 1024;
+
 cudaError_t launch_qr(double *W, int d, int n, double *vbuf, unsigned int *bar, DevState *st,
                       int grid, uint64_t timeout_ns, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   void *args[] = {&W, &d, &n, &vbuf, &bar, &st, &timeout_ns};
-  return cudaLaunchCooperativeKernel((const void *)qr_kernel, dim3(grid), dim3(kQrThreads), args,
-                                     0, s);
+  const int nloc_max = (n + 1 + grid - 1) / grid;
+  const size_t smem = (size_t)nloc_max * d * sizeof(double);
+  if (smem <= kQrSmemMax) {
+    e = cudaFuncSetAttribute((const void *)qr_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((const void *)qr_kernel<true>, dim3(grid),
+                                       dim3(kQrThreads), args, smem, s);
+  }
+  return cudaLaunchCooperativeKernel((const void *)qr_kernel<false>, dim3(grid), dim3(kQrThreads),
+                                     args, 0, s);
 }
 
 cudaError_t launch_extract_r(const double *W, int d, int n, double *Rcm, double *Rrm,

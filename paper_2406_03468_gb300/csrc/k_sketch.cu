@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     sketch_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
                   const double *__restrict__ b, int d, int zeta, const int32_t *__restrict__ rows,
                   const uint32_t *__restrict__ signbits, double *__restrict__ SAb,
-                  double *__restrict__ colsq_part, int npad) {
+                  double *__restrict__ colsq_part, int npad, float *__restrict__ A32,
+                  int64_t ld32) {
   __shared__ double acc[NC * 64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t per = (m + gridDim.x - 1) / gridDim.x;
@@ -112,6 +113,18 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     load_row<NC, VEC>(A + i * lda, n, lane, a);
     const int myh = (lane < zeta) ? rows[i * zeta + lane] : 0;
     const uint32_t sb = signbits[i];
+    if (A32 != nullptr) {  // FP32 copy of the row (rounded to nearest), written as it streams
+#pragma unroll
+      for (int k = 0; k < NC; k++) {
+        const int col = 64 * k + 2 * lane;
+        float *dst = A32 + i * ld32 + col;
+        if (col + 1 < n)
+          __stcs(reinterpret_cast<float2 *>(dst), make_float2(__double2float_rn(a[2 * k]),
+                                                               __double2float_rn(a[2 * k + 1])));
+        else if (col < n)
+          __stcs(dst, __double2float_rn(a[2 * k]));
+      }
+    }
 #pragma unroll
     for (int k = 0; k < 2 * NC; k++) sq[k] = fma(a[k], a[k], sq[k]);
     if (lane < zeta && (unsigned)myh < (unsigned)d) {
@@ -206,25 +219,26 @@ template <int NC>
 static void sketch_dispatch(bool vec, int grid, cudaStream_t s, const double *A, int64_t lda,
                             int64_t m, int n, const double *b, int d, int zeta,
                             const int32_t *rows, const uint32_t *sb, double *SAb, double *part,
-                            int npad) {
+                            int npad, float *A32, int64_t ld32) {
   if (vec)
     sketch_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, d, zeta, rows, sb, SAb,
-                                                          part, npad);
+                                                          part, npad, A32, ld32);
   else
     sketch_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, d, zeta, rows, sb,
-                                                           SAb, part, npad);
+                                                           SAb, part, npad, A32, ld32);
 }
 
 cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, const double *b, int d,
                           int zeta, const int32_t *rows, const uint32_t *signbits, double *SAb,
-                          double *colsq_part, int grid, int npad, cudaStream_t s) {
+                          double *colsq_part, int grid, int npad, float *A32, int64_t ld32,
+                          cudaStream_t s) {
   const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 2 == 0);
   switch (npad / 64) {
-    case 1: sketch_dispatch<1>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad); break;
-    case 2: sketch_dispatch<2>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad); break;
-    case 4: sketch_dispatch<4>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad); break;
-    case 8: sketch_dispatch<8>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad); break;
-    case 16: sketch_dispatch<16>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad); break;
+    case 1: sketch_dispatch<1>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, A32, ld32); break;
+    case 2: sketch_dispatch<2>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, A32, ld32); break;
+    case 4: sketch_dispatch<4>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, A32, ld32); break;
+    case 8: sketch_dispatch<8>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, A32, ld32); break;
+    case 16: sketch_dispatch<16>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, A32, ld32); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -53,18 +53,22 @@ __device__ void block_trsv(const double *__restrict__ Rcm, const double *__restr
       if (lane < len) sy[j0 + lane] = yl;
     }
     __syncthreads();
-    if (!trans) {
-      for (int i = threadIdx.x; i < j0; i += nt) {
-        double acc = 0.0;
-        for (int j = j0; j < j1; j++) acc = fma(Rcm[(size_t)j * n + i], sy[j], acc);
-        sy[i] -= acc;
+    // Remaining rows: subtract this block's contribution.  Four independent
+    // accumulators per row keep the FP64 FMA chains short (the FP64 pipe's
+    // latency, not its throughput, bounds a one-CTA solve).
+    const double *Rb = trans ? Rrm : Rcm;
+    const int ib = trans ? j1 : 0, ie = trans ? n : j0;
+    for (int i = ib + threadIdx.x; i < ie; i += nt) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int j = j0;
+      for (; j + 3 < j1; j += 4) {
+        a0 = fma(Rb[(size_t)j * n + i], sy[j], a0);
+        a1 = fma(Rb[(size_t)(j + 1) * n + i], sy[j + 1], a1);
+        a2 = fma(Rb[(size_t)(j + 2) * n + i], sy[j + 2], a2);
+        a3 = fma(Rb[(size_t)(j + 3) * n + i], sy[j + 3], a3);
       }
-    } else {
-      for (int i = j1 + threadIdx.x; i < n; i += nt) {
-        double acc = 0.0;
-        for (int j = j0; j < j1; j++) acc = fma(Rrm[(size_t)j * n + i], sy[j], acc);
-        sy[i] -= acc;
-      }
+      for (; j < j1; j++) a0 = fma(Rb[(size_t)j * n + i], sy[j], a0);
+      sy[i] -= (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
   }

@@ -10,6 +10,7 @@
 // to learn whether the device-side stop test has fired.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -72,6 +73,9 @@ struct lsq_plan_s {
   double *stageA = nullptr, *stageb = nullptr, *stagex = nullptr;
   bool sketched = false;
   bool use_eft = false;              // inner pass on the FP32 pipe
+  bool want32 = false;               // keep an FP32 copy of A (tier)
+  float *A32 = nullptr;
+  int64_t ld32 = 0;
   int col_exp = 0;                   // all |A_ij| < 2^col_exp
   double *dcol_host = nullptr;
   int launches = 0;                 // kernels launched by the current call
@@ -116,6 +120,38 @@ int step2_updates(double condest, double eta, int max_inner) {
   if (q < 1) q = 1;
   if (q > max_inner) q = max_inner;
   return q;
+}
+
+// Inner updates per refinement step of the FP32 tier: the q0 count of
+// Theorem 7.1 with the FP32 unit roundoff 2^-24 in place of u (the inner
+// solve only has to reach the accuracy its FP32 passes allow), at least 4.
+int tier_updates(double condest, double eta, int max_inner) {
+  const double u32 = 5.9604644775390625e-08;
+  const double e = 1.01 * eta;
+  double q0 = 4.0;
+  if (e > 0.0 && std::isfinite(condest) && condest > 0.0) {
+    const double v = 1.0 + 2.0 * std::log(1.0 / (condest * u32)) / std::log(1.0 / e);
+    q0 = v > 4.0 ? v : 4.0;
+  }
+  int q = (int)std::ceil(q0) - 1;
+  if (q < 1) q = 1;
+  if (q > max_inner) q = max_inner;
+  return q;
+}
+
+// FP32 tier gate: the FP32 copy exists, the precision option asks for it (or
+// AUTO and condest below the gate), and every column norm is in FP32 range.
+bool tier_ok(lsq_plan P) {
+  if (!P->want32) return false;
+  const int prec = P->o.precision;
+  if (prec == LSQ_PREC_FP64) return false;
+  const double gate = P->o.fp32_cond_max > 0 ? P->o.fp32_cond_max : 1e5;
+  if (prec == LSQ_PREC_AUTO && !(P->st_host->condest < gate)) return false;
+  for (int j = 0; j < (int)P->n; j++) {
+    const double v = P->dcol_host[j];
+    if (!(v >= std::ldexp(1.0, -100) && v <= std::ldexp(1.0, 100))) return false;
+  }
+  return true;
 }
 
 lsq_status read_state(lsq_plan P) {
@@ -186,7 +222,8 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
     LSQ_CU(cudaEventRecord(P->tev[2 * tk], P->s));
   }
   LSQ_CU(launch_sketch(dA, P->lda, P->m, n, db, P->d, P->zeta, P->pat_rows, P->pat_sb, P->SAb,
-                       P->cpart, P->gpass, P->npad, P->s));
+                       P->cpart, P->gpass, P->npad, P->want32 ? P->A32 : nullptr, P->ld32,
+                       P->s));
   if (tk >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tk + 1], P->s));
   LSQ_CU(launch_sketch_finalize(P->cpart, P->gpass, P->npad, n, P->d, P->zeta, P->o.col_scale,
                                 P->SAb, P->W, P->dcol, P->dinv, P->st, P->s));
@@ -218,11 +255,17 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
   const int nref = P->o.max_refine ? P->o.max_refine : 2;
   const int q2 = step2_updates(condest, P->eta, max_inner);
   const double gam = P->o.stop_gamma, rho = P->o.stop_rho;
+  const bool tier = tier_ok(P);
+  const int q32 = tier_updates(condest, P->eta, max_inner);
+  const int nsteps_max = tier ? std::min(LSQ_MAX_REFINE, std::max(nref, 6)) : nref;
+  const double mn8 = 8.0 * (double)P->m * (double)n;
+  double bytes_a = mn8 + (P->want32 ? mn8 / 2 : 0.0);  // sketch pass (+ FP32 copy)
   int passes = 1;
   int iters[LSQ_MAX_REFINE] = {0};
-  double resid0 = 0.0;
+  double resid0 = 0.0, cprev = INFINITY;
+  int nsteps = 0;
   std::vector<int> resid_ev, inner_ev[LSQ_MAX_REFINE];
-  for (int i = 0; i < nref; i++) {
+  for (int i = 0; i < nsteps_max; i++) {
     int tk = -1;
     if (P->o.timing) {
       LSQ_CU(tev_pair(P, &tk));
@@ -239,9 +282,18 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 1, P->g, nullptr, P->c, nullptr, nullptr,
                        nullptr, &P->st->cnorm2[i], nullptr, P->s));
     if (i == 0) LSQ_CU(launch_set_thresh(gam, rho, P->st, P->s));
+    bytes_a += mn8;
+    if (tier) {
+      // refine until ||c_i|| stops halving (the FP64 residual's noise floor)
+      LSQ_TRY(read_state(P));
+      const double cn = std::sqrt(P->st_host->cnorm2[i]);
+      if (i == 0) resid0 = std::sqrt(P->st_host->r2);
+      if ((i >= 2 && !(cn <= 0.5 * cprev)) || cn == 0.0) break;
+      cprev = cn;
+    }
     const bool fixed = P->o.fixed_inner > 0;
-    const int cap = fixed ? P->o.fixed_inner : (i == 0 ? max_inner : q2);
-    const int use_thresh = (!fixed && i == 0) ? 1 : 0;
+    const int cap = fixed ? P->o.fixed_inner : tier ? q32 : (i == 0 ? max_inner : q2);
+    const int use_thresh = (!fixed && !tier && i == 0) ? 1 : 0;
     LSQ_CU(launch_inner_init(method, n, P->c, P->dy, P->dyold, P->res, P->p, cap, use_thresh,
                              P->st, P->s));
     for (int it = 0; it < cap; it++) {
@@ -255,7 +307,10 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
         inner_ev[i].push_back(tj);
         LSQ_CU(cudaEventRecord(P->tev[2 * tj], P->s));
       }
-      if (P->use_eft)
+      if (tier)
+        LSQ_CU(launch_pass_atax32(P->A32, P->ld32, P->m, n, P->z, P->part, P->gpass, P->npad,
+                                  P->st, P->s));
+      else if (P->use_eft)
         LSQ_CU(launch_pass_atax_eft(dA, P->lda, P->m, n, P->z, P->col_exp, P->part, P->gpass,
                                     P->npad, P->st, P->s));
       else
@@ -282,8 +337,10 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     P->launches++;
     LSQ_TRY(read_state(P));
     iters[i] = P->st_host->iters;
-    if (i == 0) resid0 = std::sqrt(P->st_host->r2);
+    if (i == 0 && !tier) resid0 = std::sqrt(P->st_host->r2);
     passes += iters[i];
+    bytes_a += (tier ? mn8 / 2 : mn8) * iters[i];
+    nsteps = i + 1;
   }
   LSQ_CU(cudaMemcpyAsync(dx, P->xo, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->s));
   LSQ_CU(cudaEventRecord(P->ev[3], P->s));
@@ -293,12 +350,13 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
   if (S.condest > 1.0 / (30.0 * kU)) status = LSQ_WARN_RANK_DEFICIENT;
   if (info) {
     std::memset(info, 0, sizeof(*info));
-    for (int i = 0; i < nref; i++) {
+    for (int i = 0; i < nsteps; i++) {
       info->iters[i] = iters[i];
       info->cnorm[i] = std::sqrt(S.cnorm2[i]);
     }
-    info->refine_steps = nref;
-    info->path = LSQ_PREC_FP64;
+    info->refine_steps = nsteps;
+    info->path = tier ? LSQ_PREC_FP32_INNER : LSQ_PREC_FP64;
+    info->bytes_a = bytes_a;
     info->passes = passes;
     info->status = status;
     info->condest = S.condest;
@@ -314,14 +372,14 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     cudaEventElapsedTime(&ms, P->ev[0], P->ev[3]);
     info->ms_total = ms;
     info->launches = P->launches;
-    info->inner_kernel = P->use_eft ? 1 : 0;
+    info->inner_kernel = tier ? 2 : P->use_eft ? 1 : 0;
     if (P->o.timing) {
       for (int k : resid_ev) {
         info->ms_resid_pass += tev_ms(P, k);
         info->n_resid_pass++;
       }
       // only the launches before the stop decision did work
-      for (int i = 0; i < nref; i++)
+      for (int i = 0; i < nsteps; i++)
         for (int j = 0; j < (int)inner_ev[i].size() && j < iters[i]; j++) {
           info->ms_inner_pass += tev_ms(P, inner_ev[i][j]);
           info->n_inner_pass++;
@@ -338,7 +396,7 @@ void free_plan(lsq_plan P) {
   void *bufs[] = {P->pat_rows, P->pat_sb, P->SAb, P->W, P->part, P->r2part, P->cpart, P->dcol, P->dinv,
                   P->Rcm, P->Rrm, P->rinv, P->t, P->vbuf, P->xs, P->xo, P->c, P->g, P->dy,
                   P->dyold, P->z, P->h, P->w, P->res, P->p, P->st, P->bar, P->stageA,
-                  P->stageb, P->stagex};
+                  P->stageb, P->stagex, P->A32};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->st_host) cudaFreeHost(P->st_host);
@@ -418,6 +476,9 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   A(dalloc(&P->bar, 2));
   A(cudaMallocHost((void **)&P->st_host, sizeof(DevState)));
   A(cudaMallocHost((void **)&P->dcol_host, sizeof(double) * n));
+  P->want32 = (P->o.precision == LSQ_PREC_AUTO || P->o.precision == LSQ_PREC_FP32_INNER);
+  P->ld32 = (n + 3) / 4 * 4;
+  if (P->want32) A(dalloc(&P->A32, (size_t)P->m * P->ld32));
   for (auto &ev : P->ev) A(cudaEventCreate(&ev));
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);

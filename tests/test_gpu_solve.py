@@ -110,3 +110,36 @@ def test_edge_shapes(m, n):
         st, info, x = _gpu_solve(method, A, b, seed=1)
         assert st == 0
         assert oracle.kw_relative(A, b, x) <= 1e-13
+
+
+@pytest.mark.parametrize("method", ["fossils", "spir"])
+@pytest.mark.parametrize("kappa,path", [(1e4, lsq.LSQ_PREC_FP32_INNER), (1e10, lsq.LSQ_PREC_FP64)])
+def test_fp32_tier_gate(method, kappa, path):
+    """Config-5 construction at reduced m: with precision AUTO, kappa = 1e4
+    takes the FP32-inner tier and kappa = 1e10 the all-FP64 path; both give
+    a backward-stable x within 10x of the oracle QR's forward error."""
+    P = problem_svd(60000, 500, kappa, 1e-4, seed=21)
+    A, b, xt = P["A"], P["b"], P["x_true"]
+    st, info, x = _gpu_solve(method, A, b, seed=4, precision=lsq.LSQ_PREC_AUTO)
+    assert info["path"] == path, info
+    x_qr, R_A = oracle.qr_solve(A, b, return_R=True)
+    be = oracle.kw_relative(A, b, x, R_A=R_A)
+    assert be <= 1e-13, (be, info)
+    assert oracle.forward_error(x, xt) <= 10 * oracle.forward_error(x_qr, xt)
+    if path == lsq.LSQ_PREC_FP32_INNER:
+        assert info["inner_kernel"] == 2 and 2 <= info["refine_steps"] <= 6
+
+
+def test_fp32_tier_forced_and_bytes():
+    """FP32_INNER forces the tier; its inner passes stream half the bytes of
+    the FP64 ones (bytes_a accounting)."""
+    P = problem_svd(30000, 130, 1e3, 1e-5, seed=22)
+    A, b = P["A"], P["b"]
+    st, info, x = _gpu_solve("fossils", A, b, seed=1, precision=lsq.LSQ_PREC_FP32_INNER)
+    assert info["path"] == lsq.LSQ_PREC_FP32_INNER
+    assert oracle.kw_relative(A, b, x) <= 1e-13
+    mn8 = 8.0 * 30000 * 130
+    steps = info["refine_steps"]
+    resid_passes = steps + (1 if steps < 6 else 0)
+    expect = 1.5 * mn8 + mn8 * resid_passes + 0.5 * mn8 * sum(info["iters"])
+    assert abs(info["bytes_a"] - expect) <= 1e-9 * expect, (info["bytes_a"], expect, info)
