@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tier", action="store_true",
+                    help="skip the mixed-precision (FP32-inner) comparison on 1e6 x 1000")
     ap.add_argument("--rows", type=int, default=0,
                     help="override m (small cases for ncu captures; not a bench line)")
     ap.add_argument("--cols", type=int, default=0,
@@ -204,6 +206,47 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def tier_compare(lsq, torch, dev, steps):
+    """Config 5: 1e6 x 1000, A built as for the Fig. 1 problems at kappa = 1e4,
+    solved by FOSSILS on the all-FP64 path and on the FP32-inner tier (AUTO),
+    and the automatic FP64 fallback at kappa = 1e10."""
+    from lsq_problems import problem_svd_torch
+    m, n = 1_000_000, 1000
+    out = {"workload": "fossils_m1000000_n1000_kappa1e4_d12000_zeta8", "steps": steps}
+    P = problem_svd_torch(m, n, 1e4, 1e-4, seed=31, device=dev)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    for name, prec in (("fp64", lsq.LSQ_PREC_FP64), ("auto", lsq.LSQ_PREC_AUTO)):
+        plan = lsq.Plan(m, n, seed=7, precision=prec, timing=1)
+        lsq.lsq_solve_fossils(plan.handle, P["A"], P["b"], x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = []
+        for _ in range(steps):
+            st, inf = lsq.lsq_solve_fossils(plan.handle, P["A"], P["b"], x)
+            infos.append(inf.as_dict())
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / steps
+        last = infos[-1]
+        out[name] = {"solves_per_s": 1.0 / dt, "ms_per_solve": dt * 1e3, "path": last["path"],
+                     "refine_steps": last["refine_steps"], "iters": last["iters"],
+                     "bytes_a_gb": last["bytes_a"] / 1e9,
+                     "phase_ms": {"sketch": last["ms_sketch"], "qr": last["ms_qr"],
+                                  "refine": last["ms_refine"]},
+                     "inner_pass_ms": (last["ms_inner_pass"] / max(1, last["n_inner_pass"]))}
+        plan.close()
+    del P
+    torch.cuda.empty_cache()
+    P = problem_svd_torch(m, n, 1e10, 1e-4, seed=32, device=dev)
+    plan = lsq.Plan(m, n, seed=7, precision=lsq.LSQ_PREC_AUTO)
+    st, inf = lsq.lsq_solve_fossils(plan.handle, P["A"], P["b"], x)
+    out["auto_kappa1e10_path"] = inf.as_dict()["path"]
+    out["auto_kappa1e10_condest"] = inf.as_dict()["condest"]
+    plan.close()
+    del P
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -301,6 +344,12 @@ def run_ours(args):
         e2e = {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 8 * M * N + 8 * M,
                "d2h_bytes_per_step": 8 * N}
 
+    tier = None
+    if not args.no_tier and not args.rows and not args.cols:
+        del A
+        torch.cuda.empty_cache()
+        tier = tier_compare(lsq, torch, dev, max(2, args.steps // 3))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_obj(P, CPU_BASELINE_ROWS)
@@ -318,7 +367,8 @@ def run_ours(args):
                                                "refine": last["ms_refine"]},
                                   "sketch_pass_ms": last["ms_sketch_pass"],
                                   "spir_solves_per_s": spir_rate,
-                                  "spir_iters": spir_infos[-1]["iters"]}),
+                                  "spir_iters": spir_infos[-1]["iters"],
+                                  "fp32_tier_1e6x1000": tier}),
                 "clocks": clocks, "e2e": e2e,
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "roofline": roof, "cpu_baseline": cpu}

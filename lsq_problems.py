@@ -94,3 +94,33 @@ def problem_multi_rhs(m, n, k, kappa, noise, seed):
     X = rng.standard_normal((n, k))
     B = np.ascontiguousarray(A @ X + noise * rng.standard_normal((m, k)))
     return {"A": A, "B": B, "X_true": X, "kappa": kappa, "noise": noise}
+
+
+def problem_svd_torch(m, n, kappa, resid_norm, seed, device="cuda"):
+    """problem_svd's construction generated with torch on `device` (seeded
+    torch.Generator; factors from torch.linalg.qr), for sizes where host
+    LAPACK would take minutes (m = 1e6, n = 1000).  Returns device tensors."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    f64 = torch.float64
+
+    def haar(rows, cols):
+        q, r = torch.linalg.qr(torch.randn(rows, cols, generator=g, dtype=f64, device=device))
+        s = torch.sign(torch.diagonal(r))
+        s[s == 0] = 1.0
+        return q * s
+
+    U = haar(m, n)
+    V = haar(n, n)
+    sigma = torch.from_numpy(log_sigma(n, kappa)).to(device)
+    A = ((U * sigma) @ V.T).contiguous()
+    x = torch.randn(n, generator=g, dtype=f64, device=device)
+    x /= torch.linalg.norm(x)
+    gv = torch.randn(m, generator=g, dtype=f64, device=device)
+    r = gv - U @ (U.T @ gv)
+    r = r - U @ (U.T @ r)
+    r *= resid_norm / torch.linalg.norm(r)
+    b = A @ x + r
+    del U
+    return {"A": A, "b": b, "x_true": x, "kappa": kappa, "resid_norm": resid_norm}
