@@ -79,7 +79,9 @@ typedef struct {
   int32_t inner_fp64_fma;/* 1: inner pass with two FP64 FMAs per element; 0 (default):
                             row products on the FP32 pipe (exact splits, double-float
                             sums) when every column norm is within 2^20 of the largest */
-  int32_t reserved[7];
+  int32_t nrhs;          /* > 0: plan for lsq_solve_fossils_multi with this many
+                            right-hand sides (multiple of 8, <= 64; n <= 256) */
+  int32_t reserved[6];
 } lsq_options;
 
 #define LSQ_MAX_N 1024
@@ -143,6 +145,17 @@ lsq_status lsq_solve_fossils(lsq_plan plan, const double *dA, const double *db, 
  * as the inner solver. */
 lsq_status lsq_solve_spir(lsq_plan plan, const double *dA, const double *db, double *dx,
                           lsq_info *info);
+
+/* FOSSILS for k = opt.nrhs right-hand sides sharing one sketch S [A B] and
+ * one QR (Alg. 1 with the augmented columns Q^T S B; Alg. 2 / Alg. 5 per
+ * column, each column with its own Polyak vectors and step-1 threshold, the
+ * step ending when every column meets its own).  The refinement passes
+ * G = A^T (B - A X) and H = A^T (A Z) are FP64 tensor-core (DMMA)
+ * contractions over row blocks of A.  dB: m x k row-major with leading
+ * dimension ldb >= k (0 => k); dX: n x k row-major (device).  Requires
+ * n <= 256.  info (may be NULL) reports the largest ||c_i|| over columns. */
+lsq_status lsq_solve_fossils_multi(lsq_plan plan, const double *dA, const double *dB,
+                                   int64_t ldb, double *dX, lsq_info *info);
 
 /* As lsq_solve_fossils / lsq_solve_spir with HOST buffers hA (m x n, lda),
  * hb (m) and hx (n): copies A and b to plan-owned device memory (allocated

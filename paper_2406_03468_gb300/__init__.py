@@ -15,6 +15,7 @@ from . import _build
 __all__ = [
     "LsqError", "LsqOptions", "LsqInfo", "lsq_options_default", "lsq_plan_create",
     "lsq_plan_destroy", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir", "lsq_solve_host",
+    "lsq_solve_fossils_multi",
     "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_R", "lsq_apply_normal", "lsq_residual",
     "lsq_trsv", "lsq_apply_normal_noalloc", "lsq_last_error", "Plan", "library_path", "EXPORTED",
     "LSQ_PREC_AUTO", "LSQ_PREC_FP64", "LSQ_PREC_FP32_INNER",
@@ -45,7 +46,8 @@ class LsqOptions(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("fp32_cond_max", ctypes.c_double),
                 ("stop_gamma", ctypes.c_double), ("stop_rho", ctypes.c_double),
                 ("fixed_inner", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("inner_fp64_fma", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("inner_fp64_fma", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class LsqInfo(ctypes.Structure):
@@ -86,6 +88,8 @@ EXPORTED = {
     "lsq_solve_fossils": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
     "lsq_solve_spir": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
     "lsq_solve_host": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
+    "lsq_solve_fossils_multi": (_i32, [_vp, _vp, _vp, ctypes.c_int64, _vp,
+                                       ctypes.POINTER(LsqInfo)]),
     "lsq_sketch_pattern": (_i32, [_vp, _vp, _vp]),
     "lsq_get_sketch": (_i32, [_vp, _vp, _vp]),
     "lsq_get_R": (_i32, [_vp, _vp, _vp, _vp, _dp, _dp]),
@@ -177,6 +181,13 @@ def lsq_solve_fossils(plan, A, b, x, info=None):
 
 def lsq_solve_spir(plan, A, b, x, info=None):
     return _solve(_lib().lsq_solve_spir, plan, A, b, x, info)
+
+
+def lsq_solve_fossils_multi(plan, A, B, ldb, X, info=None):
+    inf = info if info is not None else LsqInfo()
+    st = _check(_lib().lsq_solve_fossils_multi(plan, _ptr(A), _ptr(B), int(ldb), _ptr(X),
+                                               ctypes.byref(inf)))
+    return st, inf
 
 
 def lsq_solve_host(plan, method, A, b, x, info=None):

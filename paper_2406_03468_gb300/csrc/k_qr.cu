@@ -88,13 +88,12 @@ __device__ void apply_reflector(double *const *cols, int cnt, int k, int d, cons
 // SMEM: the CTA's columns live in shared memory for the whole factorisation.
 template <bool SMEM>
 __global__ void __launch_bounds__(kQrThreads, 1)
-    qr_kernel(double *__restrict__ W, int d, int n, double *__restrict__ vbuf, unsigned int *bar,
-              DevState *st, uint64_t timeout_ns) {
+    qr_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vbuf,
+              unsigned int *bar, DevState *st, uint64_t timeout_ns) {
   extern __shared__ double dsm[];
   __shared__ double red[kQrThreads / 32 * kQrBatch];
   __shared__ double wsh[kQrBatch];
   const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  const int ncols = n + 1;
   const int nloc = (ncols - me + G - 1) / G;  // local columns j = me + l G
   auto colp = [&](int l) -> double * {
     return SMEM ? dsm + (size_t)l * d : W + (size_t)(me + l * G) * d;
@@ -132,7 +131,7 @@ __global__ void __launch_bounds__(kQrThreads, 1)
   }
 }
 
-__global__ void extract_r_kernel(const double *__restrict__ W, int d, int n, double *Rcm,
+__global__ void extract_r_kernel(const double *__restrict__ W, int d, int n, int nb, double *Rcm,
                                  double *Rrm, double *rinv, double *t) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nn = (int64_t)n * n;
@@ -142,25 +141,27 @@ __global__ void extract_r_kernel(const double *__restrict__ W, int d, int n, dou
     Rcm[(size_t)j * n + i] = v;
     Rrm[(size_t)i * n + j] = v;
   }
-  if (idx < n) {
-    rinv[idx] = 1.0 / W[(size_t)idx * d + idx];
-    t[idx] = W[(size_t)n * d + idx];
+  if (idx < n) rinv[idx] = 1.0 / W[(size_t)idx * d + idx];
+  // t (n x nb, column-major) = rows 0..n-1 of the augmented columns
+  if (idx < (int64_t)n * nb) {
+    const int c = (int)(idx / n), i = (int)(idx % n);
+    t[idx] = W[(size_t)(n + c) * d + i];
   }
 }
 
 }  // namespace
 
-int qr_grid(int n, int nsm) { return (n + 1) < nsm ? (n + 1) : nsm; }
+int qr_grid(int ncols, int nsm) { return ncols < nsm ? ncols : nsm; }
 
 // Largest dynamic shared memory the columns may use (227 KB opt-in minus the static part).
 constexpr size_t kQrSmemMax = 225 * 1024;
 
-cudaError_t launch_qr(double *W, int d, int n, double *vbuf, unsigned int *bar, DevState *st,
-                      int grid, uint64_t timeout_ns, cudaStream_t s) {
+cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vbuf, unsigned int *bar,
+                      DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  void *args[] = {&W, &d, &n, &vbuf, &bar, &st, &timeout_ns};
-  const int nloc_max = (n + 1 + grid - 1) / grid;
+  void *args[] = {&W, &d, &n, &ncols, &vbuf, &bar, &st, &timeout_ns};
+  const int nloc_max = (ncols + grid - 1) / grid;
   const size_t smem = (size_t)nloc_max * d * sizeof(double);
   if (smem <= kQrSmemMax) {
     e = cudaFuncSetAttribute((const void *)qr_kernel<true>,
@@ -173,11 +174,11 @@ cudaError_t launch_qr(double *W, int d, int n, double *vbuf, unsigned int *bar, 
                                      args, 0, s);
 }
 
-cudaError_t launch_extract_r(const double *W, int d, int n, double *Rcm, double *Rrm,
+cudaError_t launch_extract_r(const double *W, int d, int n, int nb, double *Rcm, double *Rrm,
                              double *rinv, double *t, cudaStream_t s) {
-  const int64_t nn = (int64_t)n * n;
+  const int64_t nn = (int64_t)n * (n > nb ? n : nb);
   const int th = 256;
-  extract_r_kernel<<<(unsigned)((nn + th - 1) / th), th, 0, s>>>(W, d, n, Rcm, Rrm, rinv, t);
+  extract_r_kernel<<<(unsigned)((nn + th - 1) / th), th, 0, s>>>(W, d, n, nb, Rcm, Rrm, rinv, t);
   return cudaGetLastError();
 }
 

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     }
 #pragma unroll
     for (int k = 0; k < 2 * NC; k++) sq[k] = fma(a[k], a[k], sq[k]);
-    if (lane < zeta && (unsigned)myh < (unsigned)d) {
+    if (b != nullptr && lane < zeta && (unsigned)myh < (unsigned)d) {
       atomicAdd(SAb + (size_t)myh * ldsa + n, flip_sign(b[i], (sb >> lane) & 1u));
     }
     for (int t = 0; t < zeta; t++) {

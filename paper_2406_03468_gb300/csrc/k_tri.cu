@@ -78,8 +78,15 @@ __global__ void __launch_bounds__(kVecThreads)
     trsv_kernel(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
                 const double *__restrict__ rinv, int n, int trans, const double *y,
                 const double *in_scale, double *out, const double *out_scale, double *out_scaled,
-                double *accum, double *norm2_out, const DevState *gate) {
+                double *accum, double *norm2_out, const DevState *gate, int64_t bstride) {
   if (gate != nullptr && *(volatile const int *)&gate->done) return;
+  // batched: CTA b solves the b-th vector of each operand (offset b * bstride)
+  const int64_t off = (int64_t)blockIdx.x * bstride;
+  y += off;
+  if (out) out += off;
+  if (out_scaled) out_scaled += off;
+  if (accum) accum += off;
+  if (norm2_out) norm2_out += blockIdx.x;
   extern __shared__ double sy[];
   double *scratch = sy + n;
   double *tile = scratch + 32;
@@ -171,10 +178,12 @@ __global__ void __launch_bounds__(kVecThreads)
 cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv, int n, int trans,
                         const double *y, const double *in_scale, double *out,
                         const double *out_scale, double *out_scaled, double *accum,
-                        double *norm2_out, const DevState *gate, cudaStream_t s) {
+                        double *norm2_out, const DevState *gate, cudaStream_t s, int batch,
+                        int64_t bstride) {
   const size_t smem = (size_t)(n + 32 + 32 * 33) * sizeof(double);
-  trsv_kernel<<<1, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, n, trans, y, in_scale, out, out_scale,
-                                           out_scaled, accum, norm2_out, gate);
+  trsv_kernel<<<batch, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, n, trans, y, in_scale, out,
+                                               out_scale, out_scaled, accum, norm2_out, gate,
+                                               bstride);
   return cudaGetLastError();
 }
 

@@ -78,6 +78,11 @@ struct lsq_plan_s {
   int64_t ld32 = 0;
   int col_exp = 0;                   // all |A_ij| < 2^col_exp
   double *dcol_host = nullptr;
+  // many right-hand sides (nrhs > 0)
+  int k = 0;
+  double *SBb = nullptr, *cpartB = nullptr, *mpart = nullptr, *mr2part = nullptr, *mT = nullptr;
+  double *mXs = nullptr, *mXo = nullptr, *mC = nullptr, *mG = nullptr, *mDY = nullptr;
+  double *mDYold = nullptr, *mZ = nullptr, *mH = nullptr, *mW = nullptr, *mstate = nullptr;
   int launches = 0;                 // kernels launched by the current call
   std::vector<cudaEvent_t> tev;     // timing: pass begin/end event pairs
   int tev_used = 0;
@@ -104,6 +109,8 @@ lsq_status validate(const lsq_options *o) {
   if (o->eta < 0 || o->eta >= 1) return fail(LSQ_ERR_INVALID, "eta must be in [0, 1)");
   if (o->precision < LSQ_PREC_AUTO || o->precision > LSQ_PREC_FP32_INNER)
     return fail(LSQ_ERR_INVALID, "unknown precision");
+  if (o->nrhs < 0 || (o->nrhs > 0 && !multi_supported((int)o->n, o->nrhs)))
+    return fail(LSQ_ERR_INVALID, "nrhs must be a multiple of 8 in [8, 64] with n <= 256");
   return LSQ_OK;
 }
 
@@ -229,8 +236,9 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
                                 P->SAb, P->W, P->dcol, P->dinv, P->st, P->s));
   LSQ_CU(cudaEventRecord(P->ev[1], P->s));
   P->launches += 3 + 4;  // sketch, colnorm, transpose; qr, extract, condest, x0 solve
-  LSQ_CU(launch_qr(P->W, P->d, n, P->vbuf, P->bar, P->st, P->gqr, kBarrierTimeoutNs, P->s));
-  LSQ_CU(launch_extract_r(P->W, P->d, n, P->Rcm, P->Rrm, P->rinv, P->t, P->s));
+  LSQ_CU(launch_qr(P->W, P->d, n, n + 1, P->vbuf, P->bar, P->st, qr_grid(n + 1, P->nsm),
+                   kBarrierTimeoutNs, P->s));
+  LSQ_CU(launch_extract_r(P->W, P->d, n, 1, P->Rcm, P->Rrm, P->rinv, P->t, P->s));
   LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, n, kCondestIters, P->st, P->s));
   // sketch-and-solve x0 = R^{-1} t (scaled coordinates) and x0 / d (original)
   LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->t, nullptr, P->xs, P->dinv, P->xo,
@@ -391,12 +399,134 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
   return status;
 }
 
+// FOSSILS for k right-hand sides sharing one sketch and one QR.
+lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64_t ldb,
+                           double *dX, lsq_info *info) {
+  if (P->k <= 0) return fail(LSQ_ERR_INVALID, "plan was created with nrhs = 0");
+  if (!dA || !dB || !dX) return fail(LSQ_ERR_INVALID, "NULL argument");
+  const int n = (int)P->n, k = P->k, d = P->d;
+  if (ldb == 0) ldb = k;
+  if (ldb < k) return fail(LSQ_ERR_INVALID, "ldb < nrhs");
+  P->launches = 0;
+  P->tev_used = 0;
+  double *dn2 = P->mstate, *thr = P->mstate + k, *x0n2 = P->mstate + 2 * k;
+  double *r2 = P->mstate + 3 * k, *cn2 = P->mstate + 4 * k;
+  std::memset(P->st_host, 0, sizeof(DevState));
+  P->st_host->alpha = P->alpha;
+  P->st_host->beta = P->beta;
+  LSQ_CU(cudaMemcpyAsync(P->st, P->st_host, sizeof(DevState), cudaMemcpyHostToDevice, P->s));
+  LSQ_CU(cudaEventRecord(P->ev[0], P->s));
+  if (!P->pat_valid) {
+    LSQ_CU(launch_sketch_pattern(P->m, d, P->zeta, P->o.seed, P->pat_rows, P->pat_sb, P->s));
+    P->pat_valid = true;
+  }
+  // one sketch S for [A B]: A's columns (with their norms), then B's
+  LSQ_CU(cudaMemsetAsync(P->SAb, 0, sizeof(double) * (size_t)d * (n + 1), P->s));
+  LSQ_CU(cudaMemsetAsync(P->SBb, 0, sizeof(double) * (size_t)d * (k + 1), P->s));
+  LSQ_CU(launch_sketch(dA, P->lda, P->m, n, nullptr, d, P->zeta, P->pat_rows, P->pat_sb, P->SAb,
+                       P->cpart, P->gpass, P->npad, nullptr, 0, P->s));
+  LSQ_CU(launch_sketch(dB, ldb, P->m, k, nullptr, d, P->zeta, P->pat_rows, P->pat_sb, P->SBb,
+                       P->cpartB, P->gpass, pass_npad(k), nullptr, 0, P->s));
+  LSQ_CU(launch_sketch_finalize(P->cpart, P->gpass, P->npad, n, d, P->zeta, P->o.col_scale,
+                                P->SAb, P->W, P->dcol, P->dinv, P->st, P->s));
+  LSQ_CU(launch_sketch_b_to_w(P->SBb, d, n, k, P->zeta, P->W, P->st, P->s));
+  LSQ_CU(cudaEventRecord(P->ev[1], P->s));
+  LSQ_CU(launch_qr(P->W, d, n, n + k, P->vbuf, P->bar, P->st, qr_grid(n + k, P->nsm),
+                   kBarrierTimeoutNs, P->s));
+  LSQ_CU(launch_extract_r(P->W, d, n, k, P->Rcm, P->Rrm, P->rinv, P->mT, P->s));
+  LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, n, kCondestIters, P->st, P->s));
+  LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->mT, nullptr, P->mXs, P->dinv, P->mXo,
+                     nullptr, x0n2, nullptr, P->s, k, n));
+  LSQ_CU(cudaEventRecord(P->ev[2], P->s));
+  P->launches += 11;
+  LSQ_TRY(read_state(P));
+  if (P->st_host->nonfinite) return fail(LSQ_ERR_NONFINITE, "A or B holds NaN or Inf");
+  if (P->st_host->zero_col) return fail(LSQ_ERR_INVALID, "A has a zero column (column scaling)");
+  const int max_inner = P->o.max_inner ? P->o.max_inner : 100;
+  const int nref = P->o.max_refine ? P->o.max_refine : 2;
+  const int q2 = step2_updates(P->st_host->condest, P->eta, max_inner);
+  int iters[LSQ_MAX_REFINE] = {0};
+  double cmax[LSQ_MAX_REFINE] = {0};
+  std::vector<double> hc(k);
+  for (int i = 0; i < nref; i++) {
+    LSQ_CU(launch_multi_resid(dA, P->lda, P->m, n, k, dB, ldb, P->mXo, P->mpart, P->mr2part,
+                              P->nsm, P->s));
+    LSQ_CU(launch_multi_reduce(P->mpart, P->nsm, n, k, P->dinv, P->mG, P->mr2part, r2, nullptr,
+                               P->s));
+    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 1, P->mG, nullptr, P->mC, nullptr, nullptr,
+                       nullptr, cn2, nullptr, P->s, k, n));
+    if (i == 0)
+      LSQ_CU(launch_multi_thresh(k, P->o.stop_gamma, P->o.stop_rho, x0n2, r2, thr, P->st, P->s));
+    const bool fixed = P->o.fixed_inner > 0;
+    const int cap = fixed ? P->o.fixed_inner : (i == 0 ? max_inner : q2);
+    const int use_thresh = (!fixed && i == 0) ? 1 : 0;
+    LSQ_CU(launch_multi_init(n, k, P->mC, P->mDY, P->mDYold, cap, use_thresh, P->st, P->s));
+    P->launches += 5;
+    for (int it = 0; it < cap; it++) {
+      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->mDY, nullptr, nullptr, P->dinv, P->mZ,
+                         nullptr, nullptr, P->st, P->s, k, n));
+      LSQ_CU(launch_multi_atax(dA, P->lda, P->m, n, k, P->mZ, P->mpart, P->nsm, P->st, P->s));
+      LSQ_CU(launch_multi_reduce(P->mpart, P->nsm, n, k, P->dinv, P->mH, nullptr, nullptr, P->st,
+                                 P->s));
+      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 1, P->mH, nullptr, P->mW, nullptr, nullptr,
+                         nullptr, nullptr, P->st, P->s, k, n));
+      LSQ_CU(launch_multi_polyak(n, k, P->mC, P->mW, P->mDY, P->mDYold, dn2, thr, P->st, P->s));
+      P->launches += 6;
+      if (use_thresh && (it % kStopPollEvery) == kStopPollEvery - 1 && it + 1 < cap) {
+        LSQ_TRY(read_state(P));
+        if (P->st_host->done) break;
+      }
+    }
+    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->mDY, nullptr, nullptr, P->dinv, P->mXo,
+                       P->mXs, nullptr, nullptr, P->s, k, n));
+    P->launches++;
+    LSQ_CU(cudaMemcpyAsync(hc.data(), cn2, sizeof(double) * k, cudaMemcpyDeviceToHost, P->s));
+    LSQ_TRY(read_state(P));
+    iters[i] = P->st_host->iters;
+    for (int c = 0; c < k; c++) cmax[i] = std::max(cmax[i], std::sqrt(hc[c]));
+  }
+  LSQ_CU(launch_cm_to_rm(P->mXo, n, k, dX, P->s));
+  LSQ_CU(cudaEventRecord(P->ev[3], P->s));
+  P->launches++;
+  LSQ_TRY(read_state(P));
+  const DevState &S = *P->st_host;
+  lsq_status status = (S.condest > 1.0 / (30.0 * kU)) ? LSQ_WARN_RANK_DEFICIENT : LSQ_OK;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    for (int i = 0; i < nref; i++) {
+      info->iters[i] = iters[i];
+      info->cnorm[i] = cmax[i];
+    }
+    info->refine_steps = nref;
+    info->path = LSQ_PREC_FP64;
+    info->passes = 2 + nref + iters[0] + iters[1];
+    info->status = status;
+    info->condest = S.condest;
+    info->normest = S.normest;
+    info->launches = P->launches;
+    info->bytes_a = 8.0 * (double)P->m * n * (1 + nref + iters[0] + (nref > 1 ? iters[1] : 0));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, P->ev[0], P->ev[1]);
+    info->ms_sketch = ms;
+    cudaEventElapsedTime(&ms, P->ev[1], P->ev[2]);
+    info->ms_qr = ms;
+    cudaEventElapsedTime(&ms, P->ev[2], P->ev[3]);
+    info->ms_refine = ms;
+    cudaEventElapsedTime(&ms, P->ev[0], P->ev[3]);
+    info->ms_total = ms;
+  }
+  P->sketched = false;  // the plan's single-RHS R / x0 no longer describe one problem
+  return status;
+}
+
 void free_plan(lsq_plan P) {
   if (!P) return;
   void *bufs[] = {P->pat_rows, P->pat_sb, P->SAb, P->W, P->part, P->r2part, P->cpart, P->dcol, P->dinv,
                   P->Rcm, P->Rrm, P->rinv, P->t, P->vbuf, P->xs, P->xo, P->c, P->g, P->dy,
                   P->dyold, P->z, P->h, P->w, P->res, P->p, P->st, P->bar, P->stageA,
-                  P->stageb, P->stagex, P->A32};
+                  P->stageb, P->stagex, P->A32, P->SBb, P->cpartB, P->mpart, P->mr2part,
+                  P->mT, P->mXs, P->mXo, P->mC, P->mG, P->mDY, P->mDYold, P->mZ, P->mH,
+                  P->mW, P->mstate};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->st_host) cudaFreeHost(P->st_host);
@@ -458,8 +588,20 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(dalloc(&P->pat_rows, (size_t)P->m * P->zeta));
   A(dalloc(&P->pat_sb, (size_t)P->m));
+  P->k = opt->nrhs > 0 ? opt->nrhs : 0;
   A(dalloc(&P->SAb, dn1));
-  A(dalloc(&P->W, dn1));
+  A(dalloc(&P->W, (size_t)P->d * (n + (P->k > 1 ? P->k : 1))));
+  if (P->k > 0) {
+    const size_t nk = (size_t)n * P->k, np8k = (size_t)multi_np8(n) * P->k;
+    A(dalloc(&P->SBb, (size_t)P->d * (P->k + 1)));
+    A(dalloc(&P->cpartB, (size_t)P->gpass * pass_npad(P->k)));
+    A(dalloc(&P->mpart, (size_t)P->nsm * np8k));
+    A(dalloc(&P->mr2part, (size_t)P->nsm * P->k));
+    double **mv[] = {&P->mT, &P->mXs, &P->mXo, &P->mC, &P->mG, &P->mDY, &P->mDYold, &P->mZ,
+                     &P->mH, &P->mW};
+    for (double **v : mv) A(dalloc(v, nk));
+    A(dalloc(&P->mstate, 5 * (size_t)P->k));
+  }
   A(dalloc(&P->part, (size_t)P->gpass * P->npad));
   A(dalloc(&P->r2part, (size_t)P->gpass));
   A(dalloc(&P->cpart, (size_t)P->gpass * P->npad));
@@ -513,6 +655,12 @@ lsq_status lsq_solve_spir(lsq_plan plan, const double *dA, const double *db, dou
                           lsq_info *info) {
   if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
   return run_solve(plan, 1, dA, db, dx, info);
+}
+
+lsq_status lsq_solve_fossils_multi(lsq_plan plan, const double *dA, const double *dB,
+                                   int64_t ldb, double *dX, lsq_info *info) {
+  if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  return run_solve_multi(plan, dA, dB, ldb, dX, info);
 }
 
 lsq_status lsq_solve_host(lsq_plan P, int method, const double *hA, const double *hb, double *hx,

@@ -120,11 +120,12 @@ cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad,
                                    int zeta, int col_scale, const double *SAb, double *W,
                                    double *dcol, double *dinv, DevState *st, cudaStream_t s);
 // Householder QR of W (d x (n+1), column-major) in place (cooperative).
-cudaError_t launch_qr(double *W, int d, int n, double *vbuf, unsigned int *bar, DevState *st,
-                      int grid, uint64_t timeout_ns, cudaStream_t s);
-int qr_grid(int n, int nsm);
-// R (upper n x n of W) to Rcm / Rrm, 1/R_ii, t = W[0:n, n].
-cudaError_t launch_extract_r(const double *W, int d, int n, double *Rcm, double *Rrm,
+// ncols = n + number of augmented columns (right-hand sides).
+cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vbuf, unsigned int *bar,
+                      DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s);
+int qr_grid(int ncols, int nsm);
+// R (upper n x n of W) to Rcm / Rrm, 1/R_ii, t = W[0:n, n:n+nb] (column-major n x nb).
+cudaError_t launch_extract_r(const double *W, int d, int n, int nb, double *Rcm, double *Rrm,
                              double *rinv, double *t, cudaStream_t s);
 // condest / normest of R by power and inverse power iteration.
 cudaError_t launch_condest(const double *Rcm, const double *Rrm, const double *rinv, int n,
@@ -135,10 +136,12 @@ cudaError_t launch_condest(const double *Rcm, const double *Rrm, const double *r
 //   accum == NULL:   out = sol, out_scaled = out_scale * sol  (outputs may be NULL)
 //   norm2_out != NULL: *norm2_out = ||out||^2
 //   gate != NULL: return at once when gate->done.
+//   batch > 1: CTA b solves the vectors at offset b * bstride (norm2_out[b]).
 cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv, int n, int trans,
                         const double *y, const double *in_scale, double *out,
                         const double *out_scale, double *out_scaled, double *accum,
-                        double *norm2_out, const DevState *gate, cudaStream_t s);
+                        double *norm2_out, const DevState *gate, cudaStream_t s, int batch = 1,
+                        int64_t bstride = 0);
 // Fused passes (partials: grid x npad doubles, r2_part: grid doubles).
 cudaError_t launch_pass_atax(const double *A, int64_t lda, int64_t m, int n, const double *z,
                              double *part, int grid, int npad, const DevState *gate,
@@ -163,6 +166,30 @@ cudaError_t launch_reduce(const double *part, int grid, int npad, int n, const d
                           double *out, const double *r2_part, double *r2, const DevState *gate,
                           cudaStream_t s);
 int pass_npad(int n);
+
+// Many right-hand sides (k_multi.cu): DMMA row-block passes and per-column steps.
+int multi_np8(int n);
+bool multi_supported(int n, int k);
+cudaError_t launch_multi_atax(const double *A, int64_t lda, int64_t m, int n, int k,
+                              const double *Z, double *part, int grid, const DevState *gate,
+                              cudaStream_t s);
+cudaError_t launch_multi_resid(const double *A, int64_t lda, int64_t m, int n, int k,
+                               const double *B, int64_t ldb, const double *X, double *part,
+                               double *r2part, int grid, cudaStream_t s);
+cudaError_t launch_multi_reduce(const double *part, int grid, int n, int k, const double *scale,
+                                double *out, const double *r2part, double *r2,
+                                const DevState *gate, cudaStream_t s);
+cudaError_t launch_multi_polyak(int n, int k, const double *C, const double *Wv, double *DY,
+                                double *DYold, double *dn2, const double *thresh, DevState *st,
+                                cudaStream_t s);
+cudaError_t launch_multi_init(int n, int k, const double *C, double *DY, double *DYold,
+                              int max_iters, int use_thresh, DevState *st, cudaStream_t s);
+cudaError_t launch_multi_thresh(int k, double gamma, double rho, const double *x0n2,
+                                const double *r2, double *thresh, const DevState *st,
+                                cudaStream_t s);
+cudaError_t launch_sketch_b_to_w(const double *SBb, int d, int n, int k, int zeta, double *W,
+                                 DevState *st, cudaStream_t s);
+cudaError_t launch_cm_to_rm(const double *Xcm, int n, int k, double *X, cudaStream_t s);
 
 // Inner-solver kernels (single CTA).
 cudaError_t launch_inner_init(int method, int n, const double *c, double *dy, double *dy_old,

@@ -143,3 +143,40 @@ def test_fp32_tier_forced_and_bytes():
     resid_passes = steps + (1 if steps < 6 else 0)
     expect = 1.5 * mn8 + mn8 * resid_passes + 0.5 * mn8 * sum(info["iters"])
     assert abs(info["bytes_a"] - expect) <= 1e-9 * expect, (info["bytes_a"], expect, info)
+
+
+@pytest.mark.parametrize("m,n,k,kappa", [(40000, 200, 16, 1e8), (30011, 100, 8, 1e6),
+                                         (20000, 200, 64, 1e8)])
+def test_multi_rhs_shared_sketch(m, n, k, kappa):
+    """k right-hand sides on one A (config-4 construction at reduced m):
+    every column of X is backward stable and within 10x of the oracle QR
+    solution's Wedin-bound yardstick; the same column solved alone on the
+    single-RHS path agrees to that level."""
+    from lsq_problems import problem_multi_rhs
+    P = problem_multi_rhs(m, n, k, kappa, 1e-5, seed=41)
+    A, B = P["A"], P["B"]
+    plan = lsq.Plan(m, n, seed=6, nrhs=k)
+    X = torch.empty((n, k), dtype=torch.float64, device="cuda")
+    st, info = lsq.lsq_solve_fossils_multi(plan.handle, T(A), T(B), k, X)
+    assert st == 0
+    Xh = H(X)
+    R_A, V = oracle.householder_qr(A)
+    for c in range(k):
+        b = B[:, c]
+        x_qr = oracle.backsub(R_A, oracle.apply_qt(V, b)[:n])
+        be = oracle.kw_relative(A, b, Xh[:, c], R_A=R_A)
+        assert be <= 1e-13, (c, be)
+        r = b - A @ x_qr
+        wed = oracle.wedin_bound(kappa, 1.0, x_qr, float(np.linalg.norm(r)))
+        assert oracle.forward_error(Xh[:, c], x_qr) <= 10 * max(wed, 1e-15), c
+    plan.close()
+    # column 0 alone through the single-RHS FOSSILS path
+    st, info1, x0 = _gpu_solve("fossils", A, B[:, 0].copy(), seed=6)
+    assert np.linalg.norm(x0 - Xh[:, 0]) <= 10 * max(wed, 1e-15) * np.linalg.norm(x0)
+
+
+def test_multi_rhs_rejects_unsupported():
+    with pytest.raises(lsq.LsqError):
+        lsq.Plan(1000, 300, nrhs=8)       # n > 256
+    with pytest.raises(lsq.LsqError):
+        lsq.Plan(1000, 100, nrhs=12)      # not a multiple of 8
