@@ -124,3 +124,26 @@ def problem_svd_torch(m, n, kappa, resid_norm, seed, device="cuda"):
     b = A @ x + r
     del U
     return {"A": A, "b": b, "x_true": x, "kappa": kappa, "resid_norm": resid_norm}
+
+
+def problem_multi_rhs_torch(m, n, k, kappa, noise, seed, device="cuda"):
+    """problem_multi_rhs's construction with torch on `device` (for m = 2e6)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    f64 = torch.float64
+
+    def haar(rows, cols):
+        q, r = torch.linalg.qr(torch.randn(rows, cols, generator=g, dtype=f64, device=device))
+        s = torch.sign(torch.diagonal(r))
+        s[s == 0] = 1.0
+        return q * s
+
+    U = haar(m, n)
+    V = haar(n, n)
+    sigma = torch.from_numpy(log_sigma(n, kappa)).to(device)
+    A = ((U * sigma) @ V.T).contiguous()
+    del U
+    X = torch.randn(n, k, generator=g, dtype=f64, device=device)
+    B = (A @ X + noise * torch.randn(m, k, generator=g, dtype=f64, device=device)).contiguous()
+    return {"A": A, "B": B, "X_true": X, "kappa": kappa, "noise": noise}

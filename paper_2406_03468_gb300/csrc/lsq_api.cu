@@ -448,6 +448,7 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
   int iters[LSQ_MAX_REFINE] = {0};
   double cmax[LSQ_MAX_REFINE] = {0};
   std::vector<double> hc(k);
+  std::vector<int> inner_ev[LSQ_MAX_REFINE];
   for (int i = 0; i < nref; i++) {
     LSQ_CU(launch_multi_resid(dA, P->lda, P->m, n, k, dB, ldb, P->mXo, P->mpart, P->mr2part,
                               P->nsm, P->s));
@@ -465,7 +466,14 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
     for (int it = 0; it < cap; it++) {
       LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->mDY, nullptr, nullptr, P->dinv, P->mZ,
                          nullptr, nullptr, P->st, P->s, k, n));
+      int tj = -1;
+      if (P->o.timing) {
+        LSQ_CU(tev_pair(P, &tj));
+        inner_ev[i].push_back(tj);
+        LSQ_CU(cudaEventRecord(P->tev[2 * tj], P->s));
+      }
       LSQ_CU(launch_multi_atax(dA, P->lda, P->m, n, k, P->mZ, P->mpart, P->nsm, P->st, P->s));
+      if (tj >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tj + 1], P->s));
       LSQ_CU(launch_multi_reduce(P->mpart, P->nsm, n, k, P->dinv, P->mH, nullptr, nullptr, P->st,
                                  P->s));
       LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 1, P->mH, nullptr, P->mW, nullptr, nullptr,
@@ -514,6 +522,12 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
     info->ms_refine = ms;
     cudaEventElapsedTime(&ms, P->ev[0], P->ev[3]);
     info->ms_total = ms;
+    if (P->o.timing)
+      for (int i = 0; i < nref; i++)
+        for (int j = 0; j < (int)inner_ev[i].size() && j < iters[i]; j++) {
+          info->ms_inner_pass += tev_ms(P, inner_ev[i][j]);
+          info->n_inner_pass++;
+        }
   }
   P->sketched = false;  // the plan's single-RHS R / x0 no longer describe one problem
   return status;
