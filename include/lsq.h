@@ -218,6 +218,47 @@ lsq_status lsq_trsv(lsq_plan plan, int trans, const double *dy, double *dx);
 lsq_status lsq_apply_normal_noalloc(const double *dA, int64_t m, int64_t n, int64_t lda,
                                     const double *dz, double *dh, void *cuda_stream);
 
+/* ---- served stream: continuous batching of independent solves ---------- */
+
+typedef struct lsq_server_s *lsq_server;
+
+/* Create a request server on the current device.  arena_bytes of device
+ * memory hold the admitted requests' A, b and x; max_slots solves run at
+ * once, each on its own stream with a plan sized for m_max x n_max (plus that
+ * plan's workspace, outside the arena).  The paper has no serving layer
+ * (its solvers are one-shot); this is the library's own.
+ * Errors: LSQ_ERR_INVALID (1 <= max_slots <= 64, n_max <= LSQ_MAX_N),
+ * LSQ_ERR_OOM, LSQ_ERR_CUDA. */
+lsq_status lsq_server_create(size_t arena_bytes, int max_slots, int64_t m_max, int64_t n_max,
+                             lsq_server *out);
+
+/* Submit one FOSSILS (method 0) or SPIR (method 1) solve; returns at once
+ * with a ticket.  opt: m <= m_max, n <= n_max, lda = n (or 0), zeta <= 8,
+ * FP64 precision, one right-hand side; the other options as for a plan.
+ * A (m x n row-major) and b (m) are host (on_device = 0) or device pointers;
+ * they are copied into the arena when the request is admitted (first come,
+ * first served, once a slot and its footprint 8(mn + m + n) bytes are free),
+ * so they must stay valid and unchanged until lsq_poll stops returning
+ * LSQ_PENDING.  Errors: LSQ_ERR_INVALID; LSQ_ERR_OOM when the footprint can
+ * never fit the arena (refused at admission time, nothing queued). */
+lsq_status lsq_submit(lsq_server srv, const lsq_options *opt, int method, const double *A,
+                      const double *b, int on_device, uint64_t *ticket);
+
+/* LSQ_PENDING while the request is queued or running.  Once done: copies x
+ * (n doubles) to the HOST buffer x (may be NULL), the solve's lsq_info to
+ * info (may be NULL) and the submit-to-completion time in seconds to
+ * latency_s (may be NULL), forgets the ticket and returns the solve's status. */
+lsq_status lsq_poll(lsq_server srv, uint64_t ticket, double *x, lsq_info *info,
+                    double *latency_s);
+
+/* Counters: out7 = {submitted, completed, queued, running, arena bytes,
+ * arena bytes in use, peak arena bytes in use}. */
+lsq_status lsq_server_stats(lsq_server srv, int64_t *out7);
+
+/* Stop the workers after their current solves and free everything; tickets
+ * not polled yet are dropped.  NULL is ignored. */
+void lsq_server_destroy(lsq_server srv);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char *lsq_last_error(void);
 

@@ -17,7 +17,8 @@ __all__ = [
     "lsq_plan_destroy", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir", "lsq_solve_host",
     "lsq_solve_fossils_multi",
     "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_R", "lsq_apply_normal", "lsq_residual",
-    "lsq_trsv", "lsq_apply_normal_noalloc", "lsq_last_error", "Plan", "library_path", "EXPORTED",
+    "lsq_trsv", "lsq_apply_normal_noalloc", "lsq_last_error", "Plan", "lsq_server_create",
+    "lsq_submit", "lsq_poll", "lsq_server_stats", "lsq_server_destroy", "library_path", "EXPORTED",
     "LSQ_PREC_AUTO", "LSQ_PREC_FP64", "LSQ_PREC_FP32_INNER",
 ]
 
@@ -98,6 +99,13 @@ EXPORTED = {
     "lsq_trsv": (_i32, [_vp, _i32, _vp, _vp]),
     "lsq_apply_normal_noalloc": (_i32, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                         _vp, _vp, _vp]),
+    "lsq_server_create": (_i32, [ctypes.c_size_t, _i32, ctypes.c_int64, ctypes.c_int64,
+                                 ctypes.POINTER(_vp)]),
+    "lsq_submit": (_i32, [_vp, ctypes.POINTER(LsqOptions), _i32, _vp, _vp, _i32,
+                          ctypes.POINTER(ctypes.c_uint64)]),
+    "lsq_poll": (_i32, [_vp, ctypes.c_uint64, _vp, ctypes.POINTER(LsqInfo), _dp]),
+    "lsq_server_stats": (_i32, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "lsq_server_destroy": (None, [_vp]),
     "lsq_last_error": (ctypes.c_char_p, []),
 }
 
@@ -234,6 +242,49 @@ def lsq_apply_normal_noalloc(A, m, n, lda, z, h, stream=None):
 
 def lsq_trsv(plan, trans, y, x):
     return _check(_lib().lsq_trsv(plan, int(trans), _ptr(y), _ptr(x)))
+
+
+def lsq_server_create(arena_bytes, max_slots, m_max, n_max):
+    h = _vp()
+    _check(_lib().lsq_server_create(int(arena_bytes), int(max_slots), int(m_max), int(n_max),
+                                    ctypes.byref(h)))
+    return h
+
+
+def lsq_submit(server, opts, method, A, b, on_device):
+    """A, b: device tensors (on_device=1) or host arrays/tensors (on_device=0)."""
+    def p(a):
+        if on_device:
+            return _ptr(a)
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+    t = ctypes.c_uint64()
+    _check(_lib().lsq_submit(server, ctypes.byref(opts), int(method), p(A), p(b), int(on_device),
+                             ctypes.byref(t)))
+    return t.value
+
+
+def lsq_poll(server, ticket, x=None, info=None):
+    """Returns (status, info, latency_s); status LSQ_PENDING (1) while not done.
+    x: host float64 array of length n (or None)."""
+    inf = info if info is not None else LsqInfo()
+    lat = ctypes.c_double()
+    xp = None if x is None else (x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data)
+    st = _lib().lsq_poll(server, ctypes.c_uint64(ticket), xp, ctypes.byref(inf), ctypes.byref(lat))
+    if st != LSQ_PENDING:
+        _check(st)
+    return st, inf, lat.value
+
+
+def lsq_server_stats(server):
+    out = (ctypes.c_int64 * 7)()
+    _check(_lib().lsq_server_stats(server, out))
+    keys = ("submitted", "completed", "queued", "running", "arena_bytes", "arena_used",
+            "arena_peak")
+    return dict(zip(keys, list(out)))
+
+
+def lsq_server_destroy(server):
+    _lib().lsq_server_destroy(server)
 
 
 class Plan:

@@ -131,6 +131,38 @@ __global__ void __launch_bounds__(kQrThreads, 1)
   }
 }
 
+// Non-cooperative form for concurrent solves (served requests): one launch
+// per column step, the kernel boundary acting as the grid barrier.  Same
+// column ownership (j mod G), same lookahead, columns in global memory.
+__global__ void __launch_bounds__(kQrThreads)
+    qr_step_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vbuf,
+                   int k) {
+  __shared__ double red[kQrThreads / 32 * kQrBatch];
+  __shared__ double wsh[kQrBatch];
+  const int G = gridDim.x, me = blockIdx.x;
+  const int nloc = (ncols - me + G - 1) / G;
+  auto colp = [&](int l) -> double * { return W + (size_t)(me + l * G) * d; };
+  if (k < 0) {  // prologue: v_0
+    if (me == 0) make_reflector(colp(0), 0, d, vbuf, red);
+    return;
+  }
+  const double *v = vbuf + (size_t)(k & 1) * d;
+  double *cols[kQrBatch];
+  const int l0 = (k + 1 > me) ? (k + 1 - me + G - 1) / G : 0;
+  int l = l0;
+  if (k + 1 < n && (k + 1) % G == me && l < nloc) {
+    cols[0] = colp(l);
+    apply_reflector(cols, 1, k, d, v, red, wsh);
+    make_reflector(colp(l), k + 1, d, vbuf + (size_t)((k + 1) & 1) * d, red);
+    l++;
+  }
+  while (l < nloc) {
+    int cnt = 0;
+    for (; cnt < kQrBatch && l < nloc; cnt++, l++) cols[cnt] = colp(l);
+    apply_reflector(cols, cnt, k, d, v, red, wsh);
+  }
+}
+
 __global__ void extract_r_kernel(const double *__restrict__ W, int d, int n, int nb, double *Rcm,
                                  double *Rrm, double *rinv, double *t) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -172,6 +204,16 @@ cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vbuf, unsigned
   }
   return cudaLaunchCooperativeKernel((const void *)qr_kernel<false>, dim3(grid), dim3(kQrThreads),
                                      args, 0, s);
+}
+
+cudaError_t launch_qr_stepwise(double *W, int d, int n, int ncols, double *vbuf, int grid,
+                               cudaStream_t s) {
+  for (int k = -1; k < n; k++) {
+    qr_step_kernel<<<grid, kQrThreads, 0, s>>>(W, d, n, ncols, vbuf, k);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_extract_r(const double *W, int d, int n, int nb, double *Rcm, double *Rrm,

@@ -57,6 +57,10 @@ struct lsq_plan_s {
   int dev = 0, nsm = 0;
   int64_t m = 0, n = 0, lda = 0;
   int d = 0, zeta = 0, npad = 0, gpass = 0, gqr = 0;
+  int64_t m_cap = 0, n_cap = 0;      // sizes the workspace was allocated for
+  int d_cap = 0, zeta_cap = 0;
+  bool stepwise_qr = false;          // one launch per QR column (concurrent solves)
+  uint64_t pat_key[4] = {0, 0, 0, 0};
   double eta = 0, alpha = 0, beta = 0;
   int32_t *pat_rows = nullptr;
   uint32_t *pat_sb = nullptr;
@@ -236,8 +240,11 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
                                 P->SAb, P->W, P->dcol, P->dinv, P->st, P->s));
   LSQ_CU(cudaEventRecord(P->ev[1], P->s));
   P->launches += 3 + 4;  // sketch, colnorm, transpose; qr, extract, condest, x0 solve
-  LSQ_CU(launch_qr(P->W, P->d, n, n + 1, P->vbuf, P->bar, P->st, qr_grid(n + 1, P->nsm),
-                   kBarrierTimeoutNs, P->s));
+  if (P->stepwise_qr)
+    LSQ_CU(launch_qr_stepwise(P->W, P->d, n, n + 1, P->vbuf, qr_grid(n + 1, P->nsm), P->s));
+  else
+    LSQ_CU(launch_qr(P->W, P->d, n, n + 1, P->vbuf, P->bar, P->st, qr_grid(n + 1, P->nsm),
+                     kBarrierTimeoutNs, P->s));
   LSQ_CU(launch_extract_r(P->W, P->d, n, 1, P->Rcm, P->Rrm, P->rinv, P->t, P->s));
   LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, n, kCondestIters, P->st, P->s));
   // sketch-and-solve x0 = R^{-1} t (scaled coordinates) and x0 / d (original)
@@ -533,6 +540,33 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
   return status;
 }
 
+// Derived per-problem fields of a plan (sizes within capacity, Polyak
+// coefficients, pass padding); invalidates the cached sketch pattern when its
+// key (m, d, zeta, seed) changes.
+void configure_fields(lsq_plan P, const lsq_options *opt) {
+  P->o = *opt;
+  P->m = opt->m;
+  P->n = opt->n;
+  P->lda = opt->lda ? opt->lda : opt->n;
+  P->d = opt->d ? opt->d : (int)(12 * opt->n);
+  P->zeta = opt->zeta ? opt->zeta : 8;
+  P->eta = opt->eta > 0 ? opt->eta : std::sqrt((double)P->n / (double)P->d);
+  P->beta = P->eta * P->eta;
+  P->alpha = (1.0 - P->beta) * (1.0 - P->beta);
+  if (P->o.max_inner == 0) P->o.max_inner = 100;
+  if (P->o.max_refine == 0) P->o.max_refine = 2;
+  P->npad = pass_npad((int)P->n);
+  P->ld32 = (P->n + 3) / 4 * 4;
+  P->want32 = (P->A32 != nullptr) &&
+              (opt->precision == LSQ_PREC_AUTO || opt->precision == LSQ_PREC_FP32_INNER);
+  const uint64_t key[4] = {(uint64_t)P->m, (uint64_t)P->d, (uint64_t)P->zeta, opt->seed};
+  if (std::memcmp(key, P->pat_key, sizeof(key)) != 0) {
+    std::memcpy(P->pat_key, key, sizeof(key));
+    P->pat_valid = false;
+  }
+  P->sketched = false;
+}
+
 void free_plan(lsq_plan P) {
   if (!P) return;
   void *bufs[] = {P->pat_rows, P->pat_sb, P->SAb, P->W, P->part, P->r2part, P->cpart, P->dcol, P->dinv,
@@ -575,18 +609,12 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   *out = nullptr;
   LSQ_TRY(validate(opt));
   lsq_plan P = new lsq_plan_s();
-  P->o = *opt;
   P->s = (cudaStream_t)cuda_stream;
-  P->m = opt->m;
-  P->n = opt->n;
-  P->lda = opt->lda ? opt->lda : opt->n;
-  P->d = opt->d ? opt->d : (int)(12 * opt->n);
-  P->zeta = opt->zeta ? opt->zeta : 8;
-  P->eta = opt->eta > 0 ? opt->eta : std::sqrt((double)P->n / (double)P->d);
-  P->beta = P->eta * P->eta;
-  P->alpha = (1.0 - P->beta) * (1.0 - P->beta);
-  if (P->o.max_inner == 0) P->o.max_inner = 100;
-  if (P->o.max_refine == 0) P->o.max_refine = 2;
+  P->m_cap = opt->m;
+  P->n_cap = opt->n;
+  P->d_cap = opt->d ? opt->d : (int)(12 * opt->n);
+  P->zeta_cap = opt->zeta ? opt->zeta : 8;
+  configure_fields(P, opt);
   const int n = (int)P->n;
   cudaError_t e = cudaGetDevice(&P->dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, P->dev);
@@ -594,13 +622,13 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
     free_plan(P);
     return fail(LSQ_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
   }
-  P->npad = pass_npad(n);
   P->gpass = P->nsm * kPassCtasPerSm;
-  P->gqr = qr_grid(n, P->nsm);
-  const size_t nn = (size_t)n * n, dn1 = (size_t)P->d * (n + 1);
+  P->gqr = qr_grid(n + 1, P->nsm);
+  // workspace sized for the capacity (equal to the first problem's sizes)
+  const size_t nn = (size_t)n * n, dn1 = (size_t)P->d_cap * (n + 1);
   e = cudaSuccess;
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-  A(dalloc(&P->pat_rows, (size_t)P->m * P->zeta));
+  A(dalloc(&P->pat_rows, (size_t)P->m_cap * P->zeta_cap));
   A(dalloc(&P->pat_sb, (size_t)P->m));
   P->k = opt->nrhs > 0 ? opt->nrhs : 0;
   A(dalloc(&P->SAb, dn1));
@@ -625,16 +653,17 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   A(dalloc(&P->Rrm, nn));
   A(dalloc(&P->rinv, n));
   A(dalloc(&P->t, n));
-  A(dalloc(&P->vbuf, 2 * (size_t)P->d));
+  A(dalloc(&P->vbuf, 2 * (size_t)P->d_cap));
   double **vecs[] = {&P->xs, &P->xo, &P->c, &P->g, &P->dy, &P->dyold, &P->z, &P->h, &P->w, &P->res, &P->p};
   for (double **v : vecs) A(dalloc(v, n));
   A(dalloc(&P->st, 1));
   A(dalloc(&P->bar, 2));
   A(cudaMallocHost((void **)&P->st_host, sizeof(DevState)));
   A(cudaMallocHost((void **)&P->dcol_host, sizeof(double) * n));
-  P->want32 = (P->o.precision == LSQ_PREC_AUTO || P->o.precision == LSQ_PREC_FP32_INNER);
-  P->ld32 = (n + 3) / 4 * 4;
-  if (P->want32) A(dalloc(&P->A32, (size_t)P->m * P->ld32));
+  if (P->o.precision == LSQ_PREC_AUTO || P->o.precision == LSQ_PREC_FP32_INNER) {
+    A(dalloc(&P->A32, (size_t)P->m_cap * ((n + 3) / 4 * 4)));
+    P->want32 = true;
+  }
   for (auto &ev : P->ev) A(cudaEventCreate(&ev));
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);
@@ -651,6 +680,36 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   *out = P;
   return LSQ_OK;
 }
+
+}  // extern "C"
+
+// Re-target a plan within its capacity (used by the request server).
+lsq_status lsq::plan_configure(lsq_plan P, const lsq_options *opt) {
+  if (!P) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  LSQ_TRY(validate(opt));
+  const int d = opt->d ? opt->d : (int)(12 * opt->n);
+  const int zeta = opt->zeta ? opt->zeta : 8;
+  if (opt->m > P->m_cap || opt->n > P->n_cap || d > P->d_cap || zeta > P->zeta_cap)
+    return fail(LSQ_ERR_INVALID, "problem exceeds the plan's capacity");
+  if ((opt->nrhs > 0) != (P->k > 0) || (P->k > 0 && opt->nrhs != P->k))
+    return fail(LSQ_ERR_INVALID, "nrhs differs from the plan's");
+  const bool want32 = (opt->precision == LSQ_PREC_AUTO || opt->precision == LSQ_PREC_FP32_INNER);
+  if (want32 && !P->A32) return fail(LSQ_ERR_INVALID, "plan has no FP32 copy of A");
+  configure_fields(P, opt);
+  return LSQ_OK;
+}
+
+lsq_status lsq::plan_solve(lsq_plan P, int method, const double *dA, const double *db,
+                           double *dx, lsq_info *info) {
+  if (!P) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  return run_solve(P, method, dA, db, dx, info);
+}
+
+void lsq::plan_set_stepwise_qr(lsq_plan P, int on) {
+  if (P) P->stepwise_qr = on != 0;
+}
+
+extern "C" {
 
 void lsq_plan_destroy(lsq_plan plan) { free_plan(plan); }
 

@@ -102,6 +102,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, volatile unsig
 // Message returned by lsq_last_error() on the calling thread (lsq_api.cu).
 void set_last_error(const char *msg);
 
+// Plan internals used by the request server (lsq_server.cu).
+// Point a plan at a new problem within the capacity it was created with.
+lsq_status plan_configure(lsq_plan P, const lsq_options *opt);
+// Run a FOSSILS (method 0) or SPIR (method 1) solve on the plan.
+lsq_status plan_solve(lsq_plan P, int method, const double *dA, const double *db, double *dx,
+                      lsq_info *info);
+// 1: factor the sketch with one launch per column (no cooperative launch).
+void plan_set_stepwise_qr(lsq_plan P, int on);
+
 // ---------------------------------------------------------------- launchers
 // Every launcher enqueues on `s` and returns the launch's cudaError_t.
 
@@ -124,6 +133,10 @@ cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad,
 cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vbuf, unsigned int *bar,
                       DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s);
 int qr_grid(int ncols, int nsm);
+// The same factorisation as n + 1 ordinary launches (no grid barrier): safe to
+// run concurrently with other solves' kernels.
+cudaError_t launch_qr_stepwise(double *W, int d, int n, int ncols, double *vbuf, int grid,
+                               cudaStream_t s);
 // R (upper n x n of W) to Rcm / Rrm, 1/R_ii, t = W[0:n, n:n+nb] (column-major n x nb).
 cudaError_t launch_extract_r(const double *W, int d, int n, int nb, double *Rcm, double *Rrm,
                              double *rinv, double *t, cudaStream_t s);
