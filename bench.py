@@ -296,6 +296,84 @@ def multi_compare(lsq, torch, dev, steps):
                           "peak_note": "measured bf16 x nominal fp64/bf16 (1.25/2250), " + kind}}
 
 
+def serve_compare(lsq, torch, dev, count=512, slots=8):
+    """Config 3: a stream of `count` independent problems (m log-uniform in
+    [2e4, 4e5], n in {32, 64, 128, 256}, kappa log-uniform in [1e2, 1e12],
+    b = A x + 1e-6 g), solved one at a time on one plan (plain), then through
+    the request server: closed loop (all submitted at once) for the capacity
+    C, and Poisson arrivals at 0.5 C and 0.9 C for p50 / p99 latency."""
+    import math
+    import numpy as np
+    from lsq_problems import problem_svd_torch
+    rng = np.random.default_rng(2026)
+    probs = []
+    for i in range(count):
+        m = int(math.exp(rng.uniform(math.log(2e4), math.log(4e5))))
+        n = int(rng.choice([32, 64, 128, 256]))
+        kappa = 10.0 ** rng.uniform(2, 12)
+        P = problem_svd_torch(m, n, kappa, 1e-6, seed=5000 + i, device=dev)
+        probs.append((m, n, P["A"], P["b"]))
+    torch.cuda.synchronize()
+    # plain: one plan of the largest size, re-targeted per problem (no
+    # allocation), one solve at a time on one stream (first 128 problems)
+    nplain = min(128, count)
+    x = torch.empty(256, dtype=torch.float64, device=dev)
+    plan = lsq.Plan(400000, 256, seed=1)
+    for (m, n, A, b) in probs[:4]:
+        lsq.lsq_plan_configure(plan.handle, lsq.lsq_options_default(m=m, n=n, seed=1))
+        lsq.lsq_solve_fossils(plan.handle, A, b, x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (m, n, A, b) in probs[:nplain]:
+        lsq.lsq_plan_configure(plan.handle, lsq.lsq_options_default(m=m, n=n, seed=1))
+        lsq.lsq_solve_fossils(plan.handle, A, b, x)
+    torch.cuda.synchronize()
+    plain_rate = nplain / (time.perf_counter() - t0)
+    plan.close()
+    foot = [8 * (m * n + m + n) + 768 for (m, n, _, _) in probs]
+    arena = int(min(sum(foot), 48 << 30))
+    srv = lsq.lsq_server_create(arena, slots, 400000, 256)
+
+    def run(gaps):
+        xb = np.empty(256)
+        t_start = time.perf_counter()
+        due = t_start + np.cumsum(gaps)
+        pending, lat, i = {}, [], 0
+        while i < count or pending:
+            now = time.perf_counter()
+            while i < count and due[i] <= now:
+                m, n, A, b = probs[i]
+                o = lsq.lsq_options_default(m=m, n=n, seed=1)
+                pending[lsq.lsq_submit(srv, o, 0, A, b, 1)] = i
+                i += 1
+            for t in list(pending):
+                st, info, l = lsq.lsq_poll(srv, t, xb)
+                if st != lsq.LSQ_PENDING:
+                    lat.append(l)
+                    del pending[t]
+            if not pending and i < count:
+                time.sleep(max(0.0, min(0.001, due[i] - time.perf_counter())))
+        el = time.perf_counter() - t_start
+        return count / el, float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+
+    run(np.zeros(count))  # warm-up
+    cap, _, _ = run(np.zeros(count))
+    out = {"workload": "served_stream_512_m2e4-4e5_n32-256_kappa1e2-1e12", "slots": slots,
+           "arena_gb": arena / 1e9, "plain_solves_per_s": plain_rate,
+           "capacity_solves_per_s": cap}
+    for frac in (0.5, 0.9):
+        rate = frac * cap
+        gaps = np.random.default_rng(7).exponential(1.0 / rate, count)
+        thr, p50, p99 = run(gaps)
+        out["rate_%.1fC" % frac] = {"offered_per_s": rate, "solves_per_s": thr,
+                                    "p50_ms": p50 * 1e3, "p99_ms": p99 * 1e3}
+    out["stats"] = lsq.lsq_server_stats(srv)
+    lsq.lsq_server_destroy(srv)
+    del probs
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -395,11 +473,13 @@ def run_ours(args):
 
     tier = None
     multi = None
+    served = None
     if not args.no_tier and not args.rows and not args.cols:
         del A
         torch.cuda.empty_cache()
         tier = tier_compare(lsq, torch, dev, max(2, args.steps // 3))
         multi = multi_compare(lsq, torch, dev, 2)
+        served = serve_compare(lsq, torch, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -420,7 +500,8 @@ def run_ours(args):
                                   "spir_solves_per_s": spir_rate,
                                   "spir_iters": spir_infos[-1]["iters"],
                                   "fp32_tier_1e6x1000": tier,
-                                  "multi_rhs_2e6x200_k64": multi}),
+                                  "multi_rhs_2e6x200_k64": multi,
+                                  "served_stream": served}),
                 "clocks": clocks, "e2e": e2e,
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "roofline": roof, "cpu_baseline": cpu}

@@ -120,6 +120,12 @@ void lsq_options_default(lsq_options *o);
  * Errors: LSQ_ERR_INVALID on bad options, LSQ_ERR_OOM, LSQ_ERR_CUDA. */
 lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *out);
 
+/* Point an existing plan at another problem without allocating: opt->m,
+ * opt->n, the sketch size d and zeta must not exceed the plan's (the sizes
+ * it was created with), nrhs must match, and AUTO / FP32_INNER precision
+ * needs a plan created with one of them.  Errors: LSQ_ERR_INVALID. */
+lsq_status lsq_plan_configure(lsq_plan plan, const lsq_options *opt);
+
 /* Free the plan and its workspace.  NULL is ignored. */
 void lsq_plan_destroy(lsq_plan plan);
 

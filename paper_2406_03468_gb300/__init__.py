@@ -14,7 +14,7 @@ from . import _build
 
 __all__ = [
     "LsqError", "LsqOptions", "LsqInfo", "lsq_options_default", "lsq_plan_create",
-    "lsq_plan_destroy", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir", "lsq_solve_host",
+    "lsq_plan_destroy", "lsq_plan_configure", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir", "lsq_solve_host",
     "lsq_solve_fossils_multi",
     "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_R", "lsq_apply_normal", "lsq_residual",
     "lsq_trsv", "lsq_apply_normal_noalloc", "lsq_last_error", "Plan", "lsq_server_create",
@@ -85,6 +85,7 @@ EXPORTED = {
     "lsq_options_default": (None, [ctypes.POINTER(LsqOptions)]),
     "lsq_plan_create": (_i32, [ctypes.POINTER(LsqOptions), _vp, ctypes.POINTER(_vp)]),
     "lsq_plan_destroy": (None, [_vp]),
+    "lsq_plan_configure": (_i32, [_vp, ctypes.POINTER(LsqOptions)]),
     "lsq_sketch": (_i32, [_vp, _vp, _vp]),
     "lsq_solve_fossils": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
     "lsq_solve_spir": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
@@ -167,6 +168,10 @@ def lsq_plan_create(opts, stream=None):
     s = getattr(stream, "cuda_stream", stream)
     _check(_lib().lsq_plan_create(ctypes.byref(opts), s, ctypes.byref(h)))
     return h
+
+
+def lsq_plan_configure(plan, opts):
+    return _check(_lib().lsq_plan_configure(plan, ctypes.byref(opts)))
 
 
 def lsq_plan_destroy(plan):

@@ -713,6 +713,10 @@ extern "C" {
 
 void lsq_plan_destroy(lsq_plan plan) { free_plan(plan); }
 
+lsq_status lsq_plan_configure(lsq_plan plan, const lsq_options *opt) {
+  return lsq::plan_configure(plan, opt);
+}
+
 lsq_status lsq_sketch(lsq_plan plan, const double *dA, const double *db) {
   if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
   return do_sketch(plan, dA, db);

@@ -180,3 +180,16 @@ def test_multi_rhs_rejects_unsupported():
         lsq.Plan(1000, 300, nrhs=8)       # n > 256
     with pytest.raises(lsq.LsqError):
         lsq.Plan(1000, 100, nrhs=12)      # not a multiple of 8
+
+
+def test_plan_configure_retargets_without_allocation():
+    plan = lsq.Plan(30000, 128, seed=1)
+    for (m, n) in ((30000, 128), (12000, 40), (20000, 128)):
+        P = problem_svd(m, n, 1e6, 1e-6, seed=m + n)
+        lsq.lsq_plan_configure(plan.handle, lsq.lsq_options_default(m=m, n=n, seed=2))
+        x = empty(n)
+        st, info = lsq.lsq_solve_fossils(plan.handle, T(P["A"]), T(P["b"]), x)
+        assert st == 0 and oracle.kw_relative(P["A"], P["b"], H(x)) <= 1e-13
+    with pytest.raises(lsq.LsqError):
+        lsq.lsq_plan_configure(plan.handle, lsq.lsq_options_default(m=40000, n=128))
+    plan.close()
