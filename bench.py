@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tier", action="store_true",
-                    help="skip the mixed-precision (FP32-inner) comparison on 1e6 x 1000")
+                    help="skip the tier / many-RHS / served comparisons")
+    ap.add_argument("--profile-case", default="", choices=["", "tier", "multi"],
+                    help="run small solves of one path for ncu captures (no bench line)")
     ap.add_argument("--rows", type=int, default=0,
                     help="override m (small cases for ncu captures; not a bench line)")
     ap.add_argument("--cols", type=int, default=0,
@@ -512,10 +514,42 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """Small cases for ncu captures: `tier` = FP32-inner FOSSILS on 2e5 x 1000
+    (kappa 1e4), `multi` = 64 right-hand sides on 2e5 x 200 (kappa 1e8)."""
+    import numpy as np
+    import torch
+    import paper_2406_03468_gb300 as lsq
+    from lsq_problems import problem_gaussian
+    dev = torch.device("cuda", 0)
+    if args.profile_case == "tier":
+        P = problem_gaussian(200000, 1000, 1e4, 1e-4, seed=31)
+        A, b = torch.from_numpy(P["A"]).to(dev), torch.from_numpy(P["b"]).to(dev)
+        plan = lsq.Plan(200000, 1000, seed=7, precision=lsq.LSQ_PREC_AUTO)
+        x = torch.empty(1000, dtype=torch.float64, device=dev)
+        for _ in range(max(1, args.steps)):
+            st, info = lsq.lsq_solve_fossils(plan.handle, A, b, x)
+    else:
+        P = problem_gaussian(200000, 200, 1e8, 1e-5, seed=41)
+        A = torch.from_numpy(P["A"]).to(dev)
+        Xt = torch.from_numpy(np.random.default_rng(3).standard_normal((200, 64))).to(dev)
+        B = (A @ Xt).contiguous()
+        plan = lsq.Plan(200000, 200, seed=6, nrhs=64)
+        X = torch.empty((200, 64), dtype=torch.float64, device=dev)
+        for _ in range(max(1, args.steps)):
+            st, info = lsq.lsq_solve_fossils_multi(plan.handle, A, B, 64, X)
+    torch.cuda.synchronize()
+    plan.close()
+    print(json.dumps({"profile_case": args.profile_case, "info": info.as_dict()}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args)
     return run_ours(args)
 
 
