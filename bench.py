@@ -185,7 +185,7 @@ def traffic_per_launch():
     """dram read+write bytes per launch of the inner pass from the committed
     ncu summary, or None when the kernel source changed since it was taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "atax_kernel_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "atax_df_kernel_traffic.txt")
     src = os.path.join(ROOT, "paper_2406_03468_gb300", "csrc", "k_pass.cu")
     try:
         rec = {}
@@ -435,7 +435,8 @@ def run_ours(args):
     achieved = bytes_pass / avg_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": traffic_per_launch(),
-            "kernel": ("atax_eft_kernel" if infos[-1]["inner_kernel"] else "atax_kernel")
+            "kernel": {0: "atax_kernel", 1: "atax_eft_kernel", 2: "atax32_kernel",
+                       3: "atax_df_kernel"}[infos[-1]["inner_kernel"]]
                       + " (fused A^T(A z) inner pass)", "launches_timed": n_in,
             "avg_launch_ms": avg_s * 1e3, "peak_kind": pk_kind}
     passes = statistics.mean(i["passes"] for i in infos)

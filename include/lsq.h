@@ -65,10 +65,9 @@ typedef struct {
   int32_t col_scale;     /* 1: scale columns of A to unit norm (Alg. 4), 0: off */
   int32_t max_inner;     /* cap on inner updates per refinement step (0 => 100) */
   int32_t max_refine;    /* refinement steps (0 => 2 on FP64; FP32 tier: up to 6) */
-  int32_t precision;     /* LSQ_PREC_* (default LSQ_PREC_FP64).  AUTO and FP32_INNER make
-                            the sketch pass also write an FP32 copy of A (4 m n bytes
-                            more device memory); the FP32 tier then runs its inner
-                            passes on it, the residual, A^T r, x update, QR and
+  int32_t precision;     /* LSQ_PREC_* (default LSQ_PREC_FP64).  With AUTO and
+                            FP32_INNER the FP32 tier runs its inner passes on the hi
+                            plane of A (A rounded to FP32), the residual, A^T r, x update, QR and
                             triangular solves staying FP64, and refines until ||c_i||
                             stops halving (at least 2, at most max(max_refine, 6) steps) */
   double fp32_cond_max;  /* FP32-inner gate on condest (0 => 1e5) */
@@ -76,9 +75,11 @@ typedef struct {
   double stop_rho;       /* step-1 stop constant rho (Alg. 4: 0.4; Sec. 4.2 text: 0.04) */
   int32_t fixed_inner;   /* > 0: every refinement step runs exactly this many updates */
   int32_t timing;        /* 1: time every streaming pass with CUDA events (lsq_info) */
-  int32_t inner_fp64_fma;/* 1: inner pass with two FP64 FMAs per element; 0 (default):
-                            row products on the FP32 pipe (exact splits, double-float
-                            sums) when every column norm is within 2^20 of the largest */
+  int32_t inner_fp64_fma;/* 1: inner pass with two FP64 FMAs per element on A itself.
+                            0 (default): the sketch pass also writes exact hi / lo FP32
+                            planes of A (8 m n bytes of device memory) and the inner
+                            passes run in double-float on the FP32 pipe when every
+                            column norm is in [2^-40, 2^40] */
   int32_t nrhs;          /* > 0: plan for lsq_solve_fossils_multi with this many
                             right-hand sides (multiple of 8, <= 64; n <= 256) */
   int32_t reserved[6];
@@ -105,8 +106,9 @@ typedef struct {
   int32_t n_resid_pass;           /* timing: residual passes */
   float ms_resid_pass;            /* timing: their summed device time */
   float ms_sketch_pass;           /* timing: the sketch pass */
-  int32_t inner_kernel;           /* 0: FP64-FMA inner pass, 1: FP32-pipe row products,
-                                     2: FP32 tier pass on the FP32 copy of A */
+  int32_t inner_kernel;           /* 0: FP64-FMA inner pass, 1: FP32-pipe row products on A,
+                                     2: FP32 tier pass (hi plane), 3: double-float pass on
+                                     the hi / lo planes */
   double bytes_a;                 /* bytes of A (and its FP32 copy) streamed by the solve */
   int32_t reserved[2];
 } lsq_info;

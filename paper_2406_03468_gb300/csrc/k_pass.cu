@@ -211,6 +211,141 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
 }
 
 // ---------------------------------------------------------------------------
+// Inner pass on the hi / lo FP32 planes of A (written by the sketch pass,
+// a = hi + lo to 2^-48 |a|), all arithmetic on the FP32 pipe:
+//   t_i = sum_j a_ij z_j : TwoProd of hi*z_hi, the cross terms hi*z_lo and
+//         lo*z_hi added to the error word, TwoSum accumulation, double-float
+//         warp reduction;
+//   h_j += a_ij t_i      : the same products against t = t_hi + t_lo, each
+//         column a double-float accumulator renormalised after every row
+//         (Fast2Sum) and flushed into an FP64 shared-memory accumulator every
+//         8 rows, so the double-float part never sums more than 8 terms.
+// The FP64 pipe only sees the flushes (1/8 of an add per element), so the
+// pass is no longer capped by GB300's FP64 rate.  z is scaled by a common
+// power of two 2^-Fz; h is scaled back.
+// ---------------------------------------------------------------------------
+constexpr int kDfFlush = 8;
+
+template <int NC>
+__global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
+    atax_df_kernel(const float *__restrict__ Ahi, const float *__restrict__ Alo, int64_t ld32,
+                   int64_t m, int n, const double *__restrict__ z, double *__restrict__ part,
+                   int npad, const DevState *gate) {
+  if (gate != nullptr && *(volatile const int *)&gate->done) return;
+  extern __shared__ double hacc[];  // [warps][NC * 64] FP64 flush accumulators
+  __shared__ double wmax[kPassThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = min(m, (int64_t)blockIdx.x * per), r1 = min(m, r0 + per);
+  double *hw = hacc + (size_t)warp * NC * 64;
+  for (int i = lane; i < NC * 64; i += 32) hw[i] = 0.0;
+  double zr[2 * NC];
+  load_vec<NC>(z, n, lane, zr);
+  double zmax = 0.0;
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) zmax = fmax(zmax, fabs(zr[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+  if (lane == 0) wmax[warp] = zmax;
+  __syncthreads();
+  zmax = 0.0;
+  for (int w = 0; w < nw; w++) zmax = fmax(zmax, wmax[w]);
+  int fz = 0;
+  if (zmax > 0.0) frexp(zmax, &fz);
+  const double down = ldexp(1.0, -fz), up = ldexp(1.0, fz);
+  float zh[2 * NC], zl[2 * NC], hh[2 * NC], hl[2 * NC];
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) {
+    const double v = zr[k] * down;
+    zh[k] = __double2float_rn(v);
+    zl[k] = __double2float_rn(v - (double)zh[k]);
+    hh[k] = 0.0f;
+    hl[k] = 0.0f;
+  }
+  int blk = 0;
+  for (int64_t i = r0 + warp; i < r1; i += nw) {
+    const float *rh = Ahi + i * ld32;
+    const float *rl = Alo + i * ld32;
+    float ah[2 * NC], al[2 * NC];
+#pragma unroll
+    for (int k = 0; k < NC; k++) {
+      const int col = 64 * k + 2 * lane;
+      if (col + 1 < n) {
+        const float2 vh = __ldcs(reinterpret_cast<const float2 *>(rh + col));
+        const float2 vl = __ldcs(reinterpret_cast<const float2 *>(rl + col));
+        ah[2 * k] = vh.x;
+        ah[2 * k + 1] = vh.y;
+        al[2 * k] = vl.x;
+        al[2 * k + 1] = vl.y;
+      } else {
+        ah[2 * k] = (col < n) ? __ldcs(rh + col) : 0.0f;
+        al[2 * k] = (col < n) ? __ldcs(rl + col) : 0.0f;
+        ah[2 * k + 1] = 0.0f;
+        al[2 * k + 1] = 0.0f;
+      }
+    }
+    float sh_ = 0.0f, sl_ = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 2 * NC; k++) {
+      const float p = __fmul_rn(ah[k], zh[k]);
+      const float e = __fmaf_rn(ah[k], zh[k], -p);
+      const float c = __fmaf_rn(ah[k], zl[k], __fmaf_rn(al[k], zh[k], e));
+      float s, err;
+      two_sum_f(sh_, p, s, err);
+      sh_ = s;
+      sl_ = __fadd_rn(sl_, __fadd_rn(err, c));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, sh_, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, sl_, o);
+      float s, err;
+      two_sum_f(sh_, oh, s, err);
+      sh_ = s;
+      sl_ = __fadd_rn(__fadd_rn(sl_, ol), err);
+    }
+    // renormalise t (Fast2Sum: |sh_| >= |sl_| after the sums above)
+    const float th = __fadd_rn(sh_, sl_);
+    const float tl = __fsub_rn(sl_, __fsub_rn(th, sh_));
+#pragma unroll
+    for (int k = 0; k < 2 * NC; k++) {
+      const float p = __fmul_rn(ah[k], th);
+      const float e = __fmaf_rn(ah[k], th, -p);
+      const float c = __fmaf_rn(ah[k], tl, __fmaf_rn(al[k], th, e));
+      float s, err;
+      two_sum_f(hh[k], p, s, err);
+      const float l = __fadd_rn(hl[k], __fadd_rn(err, c));
+      const float s2 = __fadd_rn(s, l);
+      hl[k] = __fsub_rn(l, __fsub_rn(s2, s));
+      hh[k] = s2;
+    }
+    if (++blk == kDfFlush) {
+      blk = 0;
+#pragma unroll
+      for (int k = 0; k < NC; k++) {
+        const int col = 64 * k + 2 * lane;
+        hw[col] += widen(hh[2 * k]) + widen(hl[2 * k]);
+        hw[col + 1] += widen(hh[2 * k + 1]) + widen(hl[2 * k + 1]);
+        hh[2 * k] = hl[2 * k] = hh[2 * k + 1] = hl[2 * k + 1] = 0.0f;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NC; k++) {
+    const int col = 64 * k + 2 * lane;
+    hw[col] += widen(hh[2 * k]) + widen(hl[2 * k]);
+    hw[col + 1] += widen(hh[2 * k + 1]) + widen(hl[2 * k + 1]);
+  }
+  __syncthreads();
+  // fixed-order sum over the warps of this CTA, scaled back by 2^Fz
+  for (int c = threadIdx.x; c < npad; c += blockDim.x) {
+    double sacc = 0.0;
+    for (int w = 0; w < nw; w++) sacc += hacc[(size_t)w * NC * 64 + c];
+    part[(size_t)blockIdx.x * npad + c] = sacc * up;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP32 inner pass of the mixed-precision tier (condest below the gate): reads
 // the FP32 copy of A (4 bytes per element), FP32 row products, FP32 column
 // sums flushed into FP64 accumulators every 32 rows (bounds the FP32
@@ -377,6 +512,21 @@ cudaError_t launch_pass_atax_eft(const double *A, int64_t lda, int64_t m, int n,
   LSQ_PASS_SWITCH(npad, {
     if (vec) atax_eft_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, z, ebias, zscale, part, npad, gate);
     else atax_eft_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, z, ebias, zscale, part, npad, gate);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_atax_df(const float *Ahi, const float *Alo, int64_t ld32, int64_t m, int n,
+                                const double *z, double *part, int grid, int npad,
+                                const DevState *gate, cudaStream_t s) {
+  const size_t smem = (size_t)(kPassThreads / 32) * npad * sizeof(double);
+  LSQ_PASS_SWITCH(npad, {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute((const void *)atax_df_kernel<NC>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    atax_df_kernel<NC><<<grid, kPassThreads, smem, s>>>(Ahi, Alo, ld32, m, n, z, part, npad, gate);
   });
   return cudaGetLastError();
 }

@@ -88,6 +88,25 @@ __device__ __forceinline__ void load_row(const double *__restrict__ row, int n, 
   }
 }
 
+// a = hi + lo exactly up to 2^-48 |a|, with integer operations only:
+// hi = a rounded to 24 significant bits (round half up, the carry going into
+// the exponent as in IEEE), lo = the signed 30-bit remainder scaled by
+// 2^(E-52) and rounded to FP32.  Entries outside FP32's normal range give 0
+// (the host takes this path only when every column norm is in [2^-40, 2^40]).
+__device__ __forceinline__ void split_rn(double a, float &hi, float &lo) {
+  const unsigned hw = (unsigned)__double2hiint(a), lw = (unsigned)__double2loint(a);
+  const int ef = (int)((hw >> 20) & 0x7ffu) - 896;
+  const unsigned sign = hw & 0x80000000u;
+  const unsigned up = (lw >> 28) & 1u;
+  const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
+  const unsigned hib = sign | (((unsigned)ef << 23) + m23 + up);
+  const int rem = (int)(lw & 0x1fffffffu) - (up ? (1 << 29) : 0);
+  const int lf = ef - 52;
+  const float l = __fmul_rn(__int2float_rn(rem), __int_as_float((lf > 0 ? lf : 1) << 23));
+  hi = (ef > 0 && ef < 254) ? __uint_as_float(hib) : 0.0f;
+  lo = (lf > 0 && ef < 254) ? __uint_as_float(__float_as_uint(l) ^ sign) : 0.0f;
+}
+
 __device__ __forceinline__ double flip_sign(double a, bool neg) {
   return __longlong_as_double(__double_as_longlong(a) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
 }
@@ -97,8 +116,8 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     sketch_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
                   const double *__restrict__ b, int d, int zeta, const int32_t *__restrict__ rows,
                   const uint32_t *__restrict__ signbits, double *__restrict__ SAb,
-                  double *__restrict__ colsq_part, int npad, float *__restrict__ A32,
-                  int64_t ld32) {
+                  double *__restrict__ colsq_part, int npad, float *__restrict__ Ahi,
+                  float *__restrict__ Alo, int64_t ld32) {
   __shared__ double acc[NC * 64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t per = (m + gridDim.x - 1) / gridDim.x;
@@ -113,16 +132,20 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     load_row<NC, VEC>(A + i * lda, n, lane, a);
     const int myh = (lane < zeta) ? rows[i * zeta + lane] : 0;
     const uint32_t sb = signbits[i];
-    if (A32 != nullptr) {  // FP32 copy of the row (rounded to nearest), written as it streams
+    if (Ahi != nullptr) {  // hi / lo FP32 planes of the row, written as it streams
 #pragma unroll
       for (int k = 0; k < NC; k++) {
         const int col = 64 * k + 2 * lane;
-        float *dst = A32 + i * ld32 + col;
-        if (col + 1 < n)
-          __stcs(reinterpret_cast<float2 *>(dst), make_float2(__double2float_rn(a[2 * k]),
-                                                               __double2float_rn(a[2 * k + 1])));
-        else if (col < n)
-          __stcs(dst, __double2float_rn(a[2 * k]));
+        float h0, l0, h1, l1;
+        split_rn(a[2 * k], h0, l0);
+        split_rn(a[2 * k + 1], h1, l1);
+        if (col + 1 < n) {
+          __stcs(reinterpret_cast<float2 *>(Ahi + i * ld32 + col), make_float2(h0, h1));
+          __stcs(reinterpret_cast<float2 *>(Alo + i * ld32 + col), make_float2(l0, l1));
+        } else if (col < n) {
+          __stcs(Ahi + i * ld32 + col, h0);
+          __stcs(Alo + i * ld32 + col, l0);
+        }
       }
     }
 #pragma unroll
@@ -219,26 +242,26 @@ template <int NC>
 static void sketch_dispatch(bool vec, int grid, cudaStream_t s, const double *A, int64_t lda,
                             int64_t m, int n, const double *b, int d, int zeta,
                             const int32_t *rows, const uint32_t *sb, double *SAb, double *part,
-                            int npad, float *A32, int64_t ld32) {
+                            int npad, float *Ahi, float *Alo, int64_t ld32) {
   if (vec)
     sketch_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, d, zeta, rows, sb, SAb,
-                                                          part, npad, A32, ld32);
+                                                          part, npad, Ahi, Alo, ld32);
   else
     sketch_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, d, zeta, rows, sb,
-                                                           SAb, part, npad, A32, ld32);
+                                                           SAb, part, npad, Ahi, Alo, ld32);
 }
 
 cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, const double *b, int d,
                           int zeta, const int32_t *rows, const uint32_t *signbits, double *SAb,
-                          double *colsq_part, int grid, int npad, float *A32, int64_t ld32,
-                          cudaStream_t s) {
+                          double *colsq_part, int grid, int npad, float *Ahi, float *Alo,
+                          int64_t ld32, cudaStream_t s) {
   const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 2 == 0);
   switch (npad / 64) {
-    case 1: sketch_dispatch<1>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, A32, ld32); break;
-    case 2: sketch_dispatch<2>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, A32, ld32); break;
-    case 4: sketch_dispatch<4>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, A32, ld32); break;
-    case 8: sketch_dispatch<8>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, A32, ld32); break;
-    case 16: sketch_dispatch<16>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, A32, ld32); break;
+    case 1: sketch_dispatch<1>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, Ahi, Alo, ld32); break;
+    case 2: sketch_dispatch<2>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, Ahi, Alo, ld32); break;
+    case 4: sketch_dispatch<4>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, Ahi, Alo, ld32); break;
+    case 8: sketch_dispatch<8>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, Ahi, Alo, ld32); break;
+    case 16: sketch_dispatch<16>(vec, grid, s, A, lda, m, n, b, d, zeta, rows, signbits, SAb, colsq_part, npad, Ahi, Alo, ld32); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -77,9 +77,10 @@ struct lsq_plan_s {
   double *stageA = nullptr, *stageb = nullptr, *stagex = nullptr;
   bool sketched = false;
   bool use_eft = false;              // inner pass on the FP32 pipe
-  bool want32 = false;               // keep an FP32 copy of A (tier)
-  float *A32 = nullptr;
+  bool want32 = false;               // the sketch pass writes the hi / lo planes of A
+  float *Ahi = nullptr, *Alo = nullptr;  // FP32 planes: hi = fl32(A), lo = A - hi
   int64_t ld32 = 0;
+  bool use_df = false;               // inner pass in double-float on the planes
   int col_exp = 0;                   // all |A_ij| < 2^col_exp
   double *dcol_host = nullptr;
   // many right-hand sides (nrhs > 0)
@@ -150,6 +151,8 @@ int tier_updates(double condest, double eta, int max_inner) {
   return q;
 }
 
+bool planes_ok(lsq_plan P);
+
 // FP32 tier gate: the FP32 copy exists, the precision option asks for it (or
 // AUTO and condest below the gate), and every column norm is in FP32 range.
 bool tier_ok(lsq_plan P) {
@@ -158,11 +161,7 @@ bool tier_ok(lsq_plan P) {
   if (prec == LSQ_PREC_FP64) return false;
   const double gate = P->o.fp32_cond_max > 0 ? P->o.fp32_cond_max : 1e5;
   if (prec == LSQ_PREC_AUTO && !(P->st_host->condest < gate)) return false;
-  for (int j = 0; j < (int)P->n; j++) {
-    const double v = P->dcol_host[j];
-    if (!(v >= std::ldexp(1.0, -100) && v <= std::ldexp(1.0, 100))) return false;
-  }
-  return true;
+  return planes_ok(P);
 }
 
 lsq_status read_state(lsq_plan P) {
@@ -190,12 +189,28 @@ float tev_ms(lsq_plan P, int idx) {
   return ms;
 }
 
+// The hi / lo planes hold every significant entry of A when each column
+// norm is in [2^-40, 2^40] (entries below 2^-60 of their column's norm may
+// lose their lo part, which is below 2^-84 of the column).
+bool planes_ok(lsq_plan P) {
+  for (int j = 0; j < (int)P->n; j++) {
+    const double v = P->dcol_host[j];
+    if (!(v >= std::ldexp(1.0, -40) && v <= std::ldexp(1.0, 40))) return false;
+  }
+  return true;
+}
+
 // The FP32-pipe inner pass needs every significant entry of A in FP32
 // range after one common power-of-two scaling: all column norms within 2^20
 // of the largest (column norms are the dcol of the column scaling).
 void choose_inner_kernel(lsq_plan P) {
   P->use_eft = false;
+  P->use_df = false;
   if (P->o.inner_fp64_fma) return;
+  if (P->want32 && planes_ok(P)) {
+    P->use_df = true;
+    return;
+  }
   double mx = 0.0, mn = INFINITY;
   for (int j = 0; j < (int)P->n; j++) {
     const double v = P->dcol_host[j];
@@ -233,8 +248,8 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
     LSQ_CU(cudaEventRecord(P->tev[2 * tk], P->s));
   }
   LSQ_CU(launch_sketch(dA, P->lda, P->m, n, db, P->d, P->zeta, P->pat_rows, P->pat_sb, P->SAb,
-                       P->cpart, P->gpass, P->npad, P->want32 ? P->A32 : nullptr, P->ld32,
-                       P->s));
+                       P->cpart, P->gpass, P->npad, P->want32 ? P->Ahi : nullptr,
+                       P->want32 ? P->Alo : nullptr, P->ld32, P->s));
   if (tk >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tk + 1], P->s));
   LSQ_CU(launch_sketch_finalize(P->cpart, P->gpass, P->npad, n, P->d, P->zeta, P->o.col_scale,
                                 P->SAb, P->W, P->dcol, P->dinv, P->st, P->s));
@@ -274,7 +289,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
   const int q32 = tier_updates(condest, P->eta, max_inner);
   const int nsteps_max = tier ? std::min(LSQ_MAX_REFINE, std::max(nref, 6)) : nref;
   const double mn8 = 8.0 * (double)P->m * (double)n;
-  double bytes_a = mn8 + (P->want32 ? mn8 / 2 : 0.0);  // sketch pass (+ FP32 copy)
+  double bytes_a = mn8 + (P->want32 ? mn8 : 0.0);  // sketch pass (+ hi / lo planes)
   int passes = 1;
   int iters[LSQ_MAX_REFINE] = {0};
   double resid0 = 0.0, cprev = INFINITY;
@@ -323,8 +338,11 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
         LSQ_CU(cudaEventRecord(P->tev[2 * tj], P->s));
       }
       if (tier)
-        LSQ_CU(launch_pass_atax32(P->A32, P->ld32, P->m, n, P->z, P->part, P->gpass, P->npad,
+        LSQ_CU(launch_pass_atax32(P->Ahi, P->ld32, P->m, n, P->z, P->part, P->gpass, P->npad,
                                   P->st, P->s));
+      else if (P->use_df)
+        LSQ_CU(launch_pass_atax_df(P->Ahi, P->Alo, P->ld32, P->m, n, P->z, P->part, P->gpass,
+                                   P->npad, P->st, P->s));
       else if (P->use_eft)
         LSQ_CU(launch_pass_atax_eft(dA, P->lda, P->m, n, P->z, P->col_exp, P->part, P->gpass,
                                     P->npad, P->st, P->s));
@@ -387,7 +405,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     cudaEventElapsedTime(&ms, P->ev[0], P->ev[3]);
     info->ms_total = ms;
     info->launches = P->launches;
-    info->inner_kernel = tier ? 2 : P->use_eft ? 1 : 0;
+    info->inner_kernel = tier ? 2 : P->use_df ? 3 : P->use_eft ? 1 : 0;
     if (P->o.timing) {
       for (int k : resid_ev) {
         info->ms_resid_pass += tev_ms(P, k);
@@ -431,9 +449,9 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
   LSQ_CU(cudaMemsetAsync(P->SAb, 0, sizeof(double) * (size_t)d * (n + 1), P->s));
   LSQ_CU(cudaMemsetAsync(P->SBb, 0, sizeof(double) * (size_t)d * (k + 1), P->s));
   LSQ_CU(launch_sketch(dA, P->lda, P->m, n, nullptr, d, P->zeta, P->pat_rows, P->pat_sb, P->SAb,
-                       P->cpart, P->gpass, P->npad, nullptr, 0, P->s));
+                       P->cpart, P->gpass, P->npad, nullptr, nullptr, 0, P->s));
   LSQ_CU(launch_sketch(dB, ldb, P->m, k, nullptr, d, P->zeta, P->pat_rows, P->pat_sb, P->SBb,
-                       P->cpartB, P->gpass, pass_npad(k), nullptr, 0, P->s));
+                       P->cpartB, P->gpass, pass_npad(k), nullptr, nullptr, 0, P->s));
   LSQ_CU(launch_sketch_finalize(P->cpart, P->gpass, P->npad, n, d, P->zeta, P->o.col_scale,
                                 P->SAb, P->W, P->dcol, P->dinv, P->st, P->s));
   LSQ_CU(launch_sketch_b_to_w(P->SBb, d, n, k, P->zeta, P->W, P->st, P->s));
@@ -557,8 +575,9 @@ void configure_fields(lsq_plan P, const lsq_options *opt) {
   if (P->o.max_refine == 0) P->o.max_refine = 2;
   P->npad = pass_npad((int)P->n);
   P->ld32 = (P->n + 3) / 4 * 4;
-  P->want32 = (P->A32 != nullptr) &&
-              (opt->precision == LSQ_PREC_AUTO || opt->precision == LSQ_PREC_FP32_INNER);
+  P->want32 = (P->Ahi != nullptr) &&
+              (!opt->inner_fp64_fma || opt->precision == LSQ_PREC_AUTO ||
+               opt->precision == LSQ_PREC_FP32_INNER);
   const uint64_t key[4] = {(uint64_t)P->m, (uint64_t)P->d, (uint64_t)P->zeta, opt->seed};
   if (std::memcmp(key, P->pat_key, sizeof(key)) != 0) {
     std::memcpy(P->pat_key, key, sizeof(key));
@@ -572,7 +591,7 @@ void free_plan(lsq_plan P) {
   void *bufs[] = {P->pat_rows, P->pat_sb, P->SAb, P->W, P->part, P->r2part, P->cpart, P->dcol, P->dinv,
                   P->Rcm, P->Rrm, P->rinv, P->t, P->vbuf, P->xs, P->xo, P->c, P->g, P->dy,
                   P->dyold, P->z, P->h, P->w, P->res, P->p, P->st, P->bar, P->stageA,
-                  P->stageb, P->stagex, P->A32, P->SBb, P->cpartB, P->mpart, P->mr2part,
+                  P->stageb, P->stagex, P->Ahi, P->Alo, P->SBb, P->cpartB, P->mpart, P->mr2part,
                   P->mT, P->mXs, P->mXo, P->mC, P->mG, P->mDY, P->mDYold, P->mZ, P->mH,
                   P->mW, P->mstate};
   for (void *b : bufs)
@@ -660,8 +679,11 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   A(dalloc(&P->bar, 2));
   A(cudaMallocHost((void **)&P->st_host, sizeof(DevState)));
   A(cudaMallocHost((void **)&P->dcol_host, sizeof(double) * n));
-  if (P->o.precision == LSQ_PREC_AUTO || P->o.precision == LSQ_PREC_FP32_INNER) {
-    A(dalloc(&P->A32, (size_t)P->m_cap * ((n + 3) / 4 * 4)));
+  // hi / lo FP32 planes of A: the double-float inner pass and the FP32 tier read them
+  if (!P->o.inner_fp64_fma || P->o.precision == LSQ_PREC_AUTO ||
+      P->o.precision == LSQ_PREC_FP32_INNER) {
+    A(dalloc(&P->Ahi, (size_t)P->m_cap * ((n + 3) / 4 * 4)));
+    A(dalloc(&P->Alo, (size_t)P->m_cap * ((n + 3) / 4 * 4)));
     P->want32 = true;
   }
   for (auto &ev : P->ev) A(cudaEventCreate(&ev));
@@ -694,7 +716,7 @@ lsq_status lsq::plan_configure(lsq_plan P, const lsq_options *opt) {
   if ((opt->nrhs > 0) != (P->k > 0) || (P->k > 0 && opt->nrhs != P->k))
     return fail(LSQ_ERR_INVALID, "nrhs differs from the plan's");
   const bool want32 = (opt->precision == LSQ_PREC_AUTO || opt->precision == LSQ_PREC_FP32_INNER);
-  if (want32 && !P->A32) return fail(LSQ_ERR_INVALID, "plan has no FP32 copy of A");
+  if (want32 && !P->Ahi) return fail(LSQ_ERR_INVALID, "plan has no FP32 planes of A");
   configure_fields(P, opt);
   return LSQ_OK;
 }
@@ -807,7 +829,10 @@ lsq_status lsq_get_R(lsq_plan P, double *dR, double *dt, double *dx0, double *co
 lsq_status lsq_apply_normal(lsq_plan P, const double *dA, const double *dz, double *dh) {
   if (!P || !dA || !dz || !dh) return fail(LSQ_ERR_INVALID, "NULL argument");
   const int n = (int)P->n;
-  if (P->sketched && P->use_eft)
+  if (P->sketched && P->use_df)
+    LSQ_CU(launch_pass_atax_df(P->Ahi, P->Alo, P->ld32, P->m, n, dz, P->part, P->gpass, P->npad,
+                               nullptr, P->s));
+  else if (P->sketched && P->use_eft)
     LSQ_CU(launch_pass_atax_eft(dA, P->lda, P->m, n, dz, P->col_exp, P->part, P->gpass, P->npad,
                                 nullptr, P->s));
   else

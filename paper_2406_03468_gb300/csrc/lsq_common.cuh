@@ -119,11 +119,12 @@ cudaError_t launch_sketch_pattern(int64_t m, int d, int zeta, uint64_t seed, int
                                   uint32_t *signbits, cudaStream_t s);
 // Unscaled +-1 sketch of [A b] into SAb (d x (n+1), row-major, must be
 // zeroed first) and column sums of squares partials (grid x npad).
-// A32 != NULL: also write fl32(A) (m x ld32 floats, ld32 even) as the rows stream.
+// Ahi != NULL: also write the hi / lo FP32 planes of A (m x ld32 floats each,
+// ld32 even; hi = A rounded to FP32, lo = the remainder) as the rows stream.
 cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, const double *b,
                           int d, int zeta, const int32_t *rows, const uint32_t *signbits,
-                          double *SAb, double *colsq_part, int grid, int npad, float *A32,
-                          int64_t ld32, cudaStream_t s);
+                          double *SAb, double *colsq_part, int grid, int npad, float *Ahi,
+                          float *Alo, int64_t ld32, cudaStream_t s);
 // Column norms from partials, scaling, transpose into column-major W (ld d).
 cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad, int n, int d,
                                    int zeta, int col_scale, const double *SAb, double *W,
@@ -170,6 +171,11 @@ cudaError_t launch_pass_atax_eft(const double *A, int64_t lda, int64_t m, int n,
 cudaError_t launch_pass_atax32(const float *A32, int64_t ld32, int64_t m, int n, const double *z,
                                double *part, int grid, int npad, const DevState *gate,
                                cudaStream_t s);
+// Inner pass on the hi / lo FP32 planes: row and column sums both in
+// double-float on the FP32 pipe (column sums flushed into FP64 every 8 rows).
+cudaError_t launch_pass_atax_df(const float *Ahi, const float *Alo, int64_t ld32, int64_t m, int n,
+                                const double *z, double *part, int grid, int npad,
+                                const DevState *gate, cudaStream_t s);
 cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, const double *b,
                               const double *x, double *part, double *r2_part, int grid, int npad,
                               cudaStream_t s);

@@ -185,14 +185,16 @@ def test_invalid_inputs():
     assert np.allclose(H(x), np.linalg.lstsq(A, b, rcond=None)[0], rtol=1e-12, atol=1e-13)
 
 
-@pytest.mark.parametrize("m,n", [(20011, 130), (20011, 37), (4097, 1000), (60000, 500)])
-def test_inner_pass_fp32_pipe(m, n):
-    """The FP32-pipe inner pass (exact hi/lo splits, double-float row sums,
-    FP64 column sums) against a compensated-arithmetic reference, on a z with
-    16 decades of dynamic range (as z = R^{-1} dy has on ill-conditioned
-    problems), with the same per-element bound as the FP64 pass."""
+@pytest.mark.parametrize("m,n,scale", [(20011, 130, 1.0), (20011, 37, 1.0), (4097, 1000, 1.0),
+                                       (60000, 500, 1.0), (20011, 130, 2.0 ** 50)])
+def test_inner_pass_fp32_pipe(m, n, scale):
+    """The FP32-pipe inner passes against a compensated-arithmetic reference,
+    on a z with 16 decades of dynamic range (as z = R^{-1} dy has on
+    ill-conditioned problems), with the same per-element bound as the FP64
+    pass.  scale 1: the double-float pass on the hi / lo planes; scale 2^50
+    (outside the planes' range): the pass that splits A on the fly."""
     rng = np.random.default_rng(m + 3 * n)
-    A = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-2, 2, n)
+    A = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-2, 2, n) * scale
     b = rng.standard_normal(m)
     z = rng.standard_normal(n) * 10.0 ** rng.uniform(-8, 8, n)
     out = {}
@@ -215,13 +217,17 @@ def test_inner_pass_fp32_pipe(m, n):
 
 
 def test_inner_kernel_choice_badly_scaled_columns():
-    """Column norms 2^30 apart: the FP32-pipe pass is not taken, the FP64 one
-    is, and the solve is still backward stable."""
+    """Which inner pass runs: the double-float pass on the planes (3) while
+    every column norm is in [2^-40, 2^40] (columns 2^30 apart included); the
+    on-the-fly split (1) for a uniform 2^50 scale; the FP64 pass (0) when
+    column norms are 2^50 apart.  Every solve is backward stable."""
     P = problem_svd(20000, 40, 1e6, 1e-5, seed=4)
-    A = P["A"].copy()
-    A[:, :20] *= 2.0 ** 30
     b = P["b"]
-    for Am, expect in ((P["A"], 1), (A, 0)):
+    A30 = P["A"].copy()
+    A30[:, :20] *= 2.0 ** 30
+    A50 = P["A"].copy()
+    A50[:, :20] *= 2.0 ** 50
+    for Am, expect in ((P["A"], 3), (A30, 3), (P["A"] * 2.0 ** 50, 1), (A50, 0)):
         plan = lsq.Plan(20000, 40, seed=2)
         x = empty(40)
         st, info = plan.solve(T(Am), T(b), x, "fossils")
