@@ -2,20 +2,25 @@
 // leading dimension d), giving R (the preconditioner, Sec. 2.1) in the upper
 // triangle and t = (Q^T Sb)[0:n] in the last column (the augmented column of
 // Alg. 1's sketch-and-solve start).  The paper's analysis assumes Householder
-// QR (Lemma 6.3), so this is plain column-by-column Householder:
-//   v = x + sign(x_1) ||x|| e_1,  v <- v / ||v||,  A <- A - 2 v (v^T A),
-// with ||v|| from the identity ||v||^2 = 2 ||x|| (||x|| + |x_1|) and v scaled
-// by the reciprocal 1/||v|| (one rounding more per entry than a division; the
-// FP64 divide runs on GB300's narrow FP64 pipe and dominated the step).
+// QR (Lemma 6.3), so this is plain column-by-column Householder: for the
+// trailing part x of column k,
+//   u = x + sign(x_1) ||x|| e_1,  beta = 2 / ||u||^2 = 1 / (||x|| (||x|| + |x_1|)),
+//   R_kk = -sign(x_1) ||x||,  and every later column c <- c - beta u (u^T c),
+// with ||u||^2 = 2 ||x|| (||x|| + |x_1|) from the identity, so no FP64
+// divide runs per entry.  Reflector k is published in place: rows k+1..d-1
+// of column k of W hold u (they are below R's triangle), and u_1, beta go to
+// a 2-per-column side array.
 //
 // GB300 design: one persistent cooperative launch, one CTA per SM.  Column
 // j belongs to CTA j mod G for the whole factorisation and, when the CTA's
 // columns fit (d = 12n up to n ~ 600), lives in that CTA's shared memory
-// from start to end.  Step k: every CTA applies H_k (v_k from one of two
-// global buffers, alternating with the parity of k) to its columns j > k;
-// the owner of column k+1 does that column first and then builds v_{k+1}
-// into the other buffer (lookahead), so no CTA waits for a serial reflector
-// step; one bounded grid barrier closes the step.
+// from start to end.  There is no grid-wide barrier: the owner of column k
+// publishes reflector k with a release store of a per-column flag, and a
+// CTA waits (bounded) only for the flag of the reflector it applies next.
+// The owner of column k+1 applies H_k to that column first and publishes
+// reflector k+1 at once (lookahead), then updates its other columns, so the
+// serial chain per step is one column update, one norm and one flag hand-off;
+// CTAs with no columns left leave early.
 #include "lsq_common.cuh"
 
 namespace lsq {
@@ -25,11 +30,22 @@ namespace {
 constexpr int kQrThreads = 512;
 constexpr int kQrBatch = 8;  // columns updated together by one CTA
 
-// Householder vector of column `col` at step k (col holds rows 0..d-1, the
-// entries below row k are the current trailing column): writes
-// v = (x + sign(x_k)||x|| e_k) / ||v|| to v[k..d-1] and R_kk = -sign(x_k)||x||
-// to col[k].  Whole CTA.
-__device__ void make_reflector(double *col, int k, int d, double *v, double *red) {
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Reflector of column `col` at step k (rows k..d-1 of col are the current
+// trailing column x).  Returns u_1 and beta to every thread, sets col[k] =
+// R_kk, and writes R_kk to W's column k row k, u_1 and beta to vhead[2k..];
+// with copy_u, also rows k+1..d-1 of col (= u) to W's column k.  Whole CTA.
+__device__ void make_reflector(double *col, int k, int d, double *Wk, double *vhead, bool copy_u,
+                               double *red, double &uk, double &beta) {
   const int tid = threadIdx.x, nt = blockDim.x;
   double s = 0.0;
   for (int i = k + tid; i < d; i += nt) s = fma(col[i], col[i], s);
@@ -37,25 +53,31 @@ __device__ void make_reflector(double *col, int k, int d, double *v, double *red
   const double nx = sqrt(s);
   const double x0 = col[k];
   const double sg = (x0 >= 0.0) ? 1.0 : -1.0;
-  const double v0 = x0 + sg * nx;
-  // ||v||^2 = ||x||^2 - x0^2 + (x0 + sign(x0) ||x||)^2 = 2 ||x|| (||x|| + |x0|)
-  const double nv = sqrt(2.0 * nx * (nx + fabs(x0)));
-  const double inv = (nv > 0.0) ? 1.0 / nv : 0.0;
-  for (int i = k + tid; i < d; i += nt) v[i] = ((i == k) ? v0 : col[i]) * inv;
-  __syncthreads();
-  if (tid == 0) col[k] = -sg * nx;
+  uk = x0 + sg * nx;
+  beta = (nx > 0.0) ? 1.0 / (nx * (nx + fabs(x0))) : 0.0;
+  if (copy_u)
+    for (int i = k + 1 + tid; i < d; i += nt) Wk[i] = col[i];
+  __syncthreads();  // every thread has read col[k]
+  if (tid == 0) {
+    col[k] = -sg * nx;
+    Wk[k] = -sg * nx;
+    vhead[2 * k] = uk;
+    vhead[2 * k + 1] = beta;
+  }
 }
 
-// Apply H_k = I - 2 v v^T (v from global memory, rows k..d-1) to `cnt` <= kQrBatch
-// columns cols[0..cnt).  Whole CTA.
-__device__ void apply_reflector(double *const *cols, int cnt, int k, int d, const double *v,
-                                double *red, double *wsh) {
+// c <- c - beta u (u^T c) for `cnt` <= kQrBatch columns cols[0..cnt), with u
+// = (uk, vsrc[k+1..d-1]); VG: vsrc is another CTA's published column (read
+// through L2).  Whole CTA.
+template <bool VG>
+__device__ void apply_reflector(double *const *cols, int cnt, int k, int d, const double *vsrc,
+                                double uk, double beta, double *red, double *wsh) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   double acc[kQrBatch];
 #pragma unroll
   for (int c = 0; c < kQrBatch; c++) acc[c] = 0.0;
-  for (int i = k + tid; i < d; i += nt) {
-    const double vi = __ldcg(v + i);
+  for (int i = k + 1 + tid; i < d; i += nt) {
+    const double vi = VG ? __ldcg(vsrc + i) : vsrc[i];
 #pragma unroll
     for (int c = 0; c < kQrBatch; c++)
       if (c < cnt) acc[c] = fma(vi, cols[c][i], acc[c]);
@@ -71,28 +93,56 @@ __device__ void apply_reflector(double *const *cols, int cnt, int k, int d, cons
   }
   __syncthreads();
   if (tid < cnt) {
-    double sacc = 0.0;
+    double sacc = uk * cols[tid][k];
     for (int w = 0; w < nw; w++) sacc += red[w * kQrBatch + tid];
-    wsh[tid] = 2.0 * sacc;
+    wsh[tid] = beta * sacc;
   }
   __syncthreads();
-  for (int i = k + tid; i < d; i += nt) {
-    const double vi = __ldcg(v + i);
+  for (int i = k + 1 + tid; i < d; i += nt) {
+    const double vi = VG ? __ldcg(vsrc + i) : vsrc[i];
 #pragma unroll
     for (int c = 0; c < kQrBatch; c++)
       if (c < cnt) cols[c][i] = fma(-wsh[c], vi, cols[c][i]);
   }
+  if (tid < cnt) cols[tid][k] = fma(-wsh[tid], uk, cols[tid][k]);
   __syncthreads();
+}
+
+// Bounded wait of the whole CTA for flag == epoch (thread 0 polls with
+// acquire loads).  false after timeout_ns (LSQ_ERR_TIMEOUT set) or when
+// another CTA has set an error.
+__device__ bool wait_flag(const int *flag, int epoch, int *err, uint64_t timeout_ns, int *s_ok) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (ld_acquire(flag) != epoch) {
+      const uint64_t t0 = global_ns();
+      while (ld_acquire(flag) != epoch) {
+        if (*(volatile int *)err != 0) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > timeout_ns) {
+          atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
 }
 
 // SMEM: the CTA's columns live in shared memory for the whole factorisation.
 template <bool SMEM>
 __global__ void __launch_bounds__(kQrThreads, 1)
-    qr_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vbuf,
-              unsigned int *bar, DevState *st, uint64_t timeout_ns) {
+    qr_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
+              int *flags, int epoch, DevState *st, uint64_t timeout_ns) {
   extern __shared__ double dsm[];
   __shared__ double red[kQrThreads / 32 * kQrBatch];
   __shared__ double wsh[kQrBatch];
+  __shared__ int s_ok;
   const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int nloc = (ncols - me + G - 1) / G;  // local columns j = me + l G
   auto colp = [&](int l) -> double * {
@@ -103,63 +153,100 @@ __global__ void __launch_bounds__(kQrThreads, 1)
       for (int i = tid; i < d; i += nt) dsm[(size_t)l * d + i] = W[(size_t)(me + l * G) * d + i];
     __syncthreads();
   }
-  if (me == 0) make_reflector(colp(0), 0, d, vbuf, red);
-  if (!grid_barrier(bar, bar + 1, &st->err, timeout_ns)) return;
   double *cols[kQrBatch];
+  int made = -1;  // reflector built ahead (lookahead) and its u_1, beta
+  double uk_ahead = 0.0, beta_ahead = 0.0;
   for (int k = 0; k < n; k++) {
-    const double *v = vbuf + (size_t)(k & 1) * d;
+    const bool own = (k % G == me);
+    double uk, beta;
+    if (own && made != k) {  // reflector 0, or any the lookahead did not build
+      make_reflector(colp((k - me) / G), k, d, W + (size_t)k * d, vhead, SMEM, red, uk, beta);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(flags + k, epoch);
+      }
+    } else if (own) {
+      uk = uk_ahead;
+      beta = beta_ahead;
+    }
     const int l0 = (k + 1 > me) ? (k + 1 - me + G - 1) / G : 0;  // first local column > k
+    if (l0 >= nloc) break;  // nothing left to update here
+    if (!own) {
+      if (!wait_flag(flags + k, epoch, &st->err, timeout_ns, &s_ok)) return;
+      uk = __ldcg(vhead + 2 * k);
+      beta = __ldcg(vhead + 2 * k + 1);
+    }
+    // u of reflector k: this CTA's own copy of column k, or the published one
+    const double *vk = own ? colp((k - me) / G) : W + (size_t)k * d;
     int l = l0;
-    // Lookahead: the owner of column k+1 applies H_k to it first and builds
-    // v_{k+1} into the other buffer while the rest of the grid is updating.
-    if (k + 1 < n && (k + 1) % G == me && l < nloc) {
+    if (k + 1 < n && (k + 1) % G == me) {  // lookahead: H_k on column k+1, then reflector k+1
       cols[0] = colp(l);
-      apply_reflector(cols, 1, k, d, v, red, wsh);
-      make_reflector(colp(l), k + 1, d, vbuf + (size_t)((k + 1) & 1) * d, red);
+      if (own) apply_reflector<false>(cols, 1, k, d, vk, uk, beta, red, wsh);
+      else apply_reflector<true>(cols, 1, k, d, vk, uk, beta, red, wsh);
+      make_reflector(colp(l), k + 1, d, W + (size_t)(k + 1) * d, vhead, SMEM, red, uk_ahead,
+                     beta_ahead);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(flags + k + 1, epoch);
+      }
+      made = k + 1;
       l++;
     }
     while (l < nloc) {
       int cnt = 0;
       for (; cnt < kQrBatch && l < nloc; cnt++, l++) cols[cnt] = colp(l);
-      apply_reflector(cols, cnt, k, d, v, red, wsh);
+      if (own) apply_reflector<false>(cols, cnt, k, d, vk, uk, beta, red, wsh);
+      else apply_reflector<true>(cols, cnt, k, d, vk, uk, beta, red, wsh);
     }
-    if (!grid_barrier(bar, bar + 1, &st->err, timeout_ns)) return;
   }
   if (SMEM) {
-    for (int l2 = 0; l2 < nloc; l2++)
-      for (int i = tid; i < d; i += nt) W[(size_t)(me + l2 * G) * d + i] = dsm[(size_t)l2 * d + i];
+    // R rows above the diagonal of the reflector columns, and the augmented
+    // columns whole (rows k..d-1 of reflector column k went out at publish).
+    __syncthreads();
+    for (int l2 = 0; l2 < nloc; l2++) {
+      const int j = me + l2 * G;
+      const int iend = (j < n) ? j : d;
+      for (int i = tid; i < iend; i += nt) W[(size_t)j * d + i] = dsm[(size_t)l2 * d + i];
+    }
   }
 }
 
 // Non-cooperative form for concurrent solves (served requests): one launch
-// per column step, the kernel boundary acting as the grid barrier.  Same
-// column ownership (j mod G), same lookahead, columns in global memory.
+// per column step, the kernel boundary standing in for the flags.  Same
+// column ownership (j mod G), same lookahead, same published reflectors,
+// columns in global memory.
 __global__ void __launch_bounds__(kQrThreads)
-    qr_step_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vbuf,
+    qr_step_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
                    int k) {
   __shared__ double red[kQrThreads / 32 * kQrBatch];
   __shared__ double wsh[kQrBatch];
   const int G = gridDim.x, me = blockIdx.x;
   const int nloc = (ncols - me + G - 1) / G;
   auto colp = [&](int l) -> double * { return W + (size_t)(me + l * G) * d; };
-  if (k < 0) {  // prologue: v_0
-    if (me == 0) make_reflector(colp(0), 0, d, vbuf, red);
+  double uk, beta;
+  if (k < 0) {  // prologue: reflector 0
+    if (me == 0) make_reflector(colp(0), 0, d, W, vhead, false, red, uk, beta);
     return;
   }
-  const double *v = vbuf + (size_t)(k & 1) * d;
+  uk = __ldcg(vhead + 2 * k);
+  beta = __ldcg(vhead + 2 * k + 1);
+  const double *vk = W + (size_t)k * d;
   double *cols[kQrBatch];
   const int l0 = (k + 1 > me) ? (k + 1 - me + G - 1) / G : 0;
   int l = l0;
   if (k + 1 < n && (k + 1) % G == me && l < nloc) {
     cols[0] = colp(l);
-    apply_reflector(cols, 1, k, d, v, red, wsh);
-    make_reflector(colp(l), k + 1, d, vbuf + (size_t)((k + 1) & 1) * d, red);
+    apply_reflector<true>(cols, 1, k, d, vk, uk, beta, red, wsh);
+    double u1, b1;
+    make_reflector(colp(l), k + 1, d, W + (size_t)(k + 1) * d, vhead, false, red, u1, b1);
     l++;
   }
   while (l < nloc) {
     int cnt = 0;
     for (; cnt < kQrBatch && l < nloc; cnt++, l++) cols[cnt] = colp(l);
-    apply_reflector(cols, cnt, k, d, v, red, wsh);
+    apply_reflector<true>(cols, cnt, k, d, vk, uk, beta, red, wsh);
   }
 }
 
@@ -188,16 +275,14 @@ int qr_grid(int ncols, int nsm) { return ncols < nsm ? ncols : nsm; }
 // Largest dynamic shared memory the columns may use (227 KB opt-in minus the static part).
 constexpr size_t kQrSmemMax = 225 * 1024;
 
-cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vbuf, unsigned int *bar,
+cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vhead, int *flags, int epoch,
                       DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s);
-  if (e != cudaSuccess) return e;
-  void *args[] = {&W, &d, &n, &ncols, &vbuf, &bar, &st, &timeout_ns};
+  void *args[] = {&W, &d, &n, &ncols, &vhead, &flags, &epoch, &st, &timeout_ns};
   const int nloc_max = (ncols + grid - 1) / grid;
   const size_t smem = (size_t)nloc_max * d * sizeof(double);
   if (smem <= kQrSmemMax) {
-    e = cudaFuncSetAttribute((const void *)qr_kernel<true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute((const void *)qr_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void *)qr_kernel<true>, dim3(grid),
                                        dim3(kQrThreads), args, smem, s);
@@ -206,10 +291,10 @@ cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vbuf, unsigned
                                      args, 0, s);
 }
 
-cudaError_t launch_qr_stepwise(double *W, int d, int n, int ncols, double *vbuf, int grid,
+cudaError_t launch_qr_stepwise(double *W, int d, int n, int ncols, double *vhead, int grid,
                                cudaStream_t s) {
   for (int k = -1; k < n; k++) {
-    qr_step_kernel<<<grid, kQrThreads, 0, s>>>(W, d, n, ncols, vbuf, k);
+    qr_step_kernel<<<grid, kQrThreads, 0, s>>>(W, d, n, ncols, vhead, k);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

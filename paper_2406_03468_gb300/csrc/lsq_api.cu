@@ -43,7 +43,7 @@ lsq_status fail(lsq_status st, const std::string &msg) {
     if (s_ < 0) return s_;            \
   } while (0)
 
-constexpr uint64_t kBarrierTimeoutNs = 5ull * 1000 * 1000 * 1000;  // 5 s per grid barrier
+constexpr uint64_t kBarrierTimeoutNs = 5ull * 1000 * 1000 * 1000;  // 5 s per inter-CTA wait
 constexpr int kCondestIters = 10;
 constexpr int kStopPollEvery = 4;  // step 1: read the device stop flag every 4 updates
 
@@ -72,7 +72,8 @@ struct lsq_plan_s {
   double *dyold = nullptr, *z = nullptr, *h = nullptr, *w = nullptr, *res = nullptr, *p = nullptr;
   DevState *st = nullptr;
   DevState *st_host = nullptr;
-  unsigned int *bar = nullptr;
+  int *qflag = nullptr;              // QR: per-column "reflector published" flags
+  int qr_epoch = 0;                  // value the flags take in the current QR launch
   cudaEvent_t ev[5] = {};
   double *stageA = nullptr, *stageb = nullptr, *stagex = nullptr;
   bool sketched = false;
@@ -162,6 +163,13 @@ bool tier_ok(lsq_plan P) {
   const double gate = P->o.fp32_cond_max > 0 ? P->o.fp32_cond_max : 1e5;
   if (prec == LSQ_PREC_AUTO && !(P->st_host->condest < gate)) return false;
   return planes_ok(P);
+}
+
+// Flag value of the next QR launch: never 0 (the flags' initial value) and
+// never the previous launch's.
+int next_epoch(lsq_plan P) {
+  P->qr_epoch = (P->qr_epoch >= (1 << 30)) ? 1 : P->qr_epoch + 1;
+  return P->qr_epoch;
 }
 
 lsq_status read_state(lsq_plan P) {
@@ -258,8 +266,8 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
   if (P->stepwise_qr)
     LSQ_CU(launch_qr_stepwise(P->W, P->d, n, n + 1, P->vbuf, qr_grid(n + 1, P->nsm), P->s));
   else
-    LSQ_CU(launch_qr(P->W, P->d, n, n + 1, P->vbuf, P->bar, P->st, qr_grid(n + 1, P->nsm),
-                     kBarrierTimeoutNs, P->s));
+    LSQ_CU(launch_qr(P->W, P->d, n, n + 1, P->vbuf, P->qflag, next_epoch(P), P->st,
+                     qr_grid(n + 1, P->nsm), kBarrierTimeoutNs, P->s));
   LSQ_CU(launch_extract_r(P->W, P->d, n, 1, P->Rcm, P->Rrm, P->rinv, P->t, P->s));
   LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, n, kCondestIters, P->st, P->s));
   // sketch-and-solve x0 = R^{-1} t (scaled coordinates) and x0 / d (original)
@@ -456,8 +464,8 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
                                 P->SAb, P->W, P->dcol, P->dinv, P->st, P->s));
   LSQ_CU(launch_sketch_b_to_w(P->SBb, d, n, k, P->zeta, P->W, P->st, P->s));
   LSQ_CU(cudaEventRecord(P->ev[1], P->s));
-  LSQ_CU(launch_qr(P->W, d, n, n + k, P->vbuf, P->bar, P->st, qr_grid(n + k, P->nsm),
-                   kBarrierTimeoutNs, P->s));
+  LSQ_CU(launch_qr(P->W, d, n, n + k, P->vbuf, P->qflag, next_epoch(P), P->st,
+                   qr_grid(n + k, P->nsm), kBarrierTimeoutNs, P->s));
   LSQ_CU(launch_extract_r(P->W, d, n, k, P->Rcm, P->Rrm, P->rinv, P->mT, P->s));
   LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, n, kCondestIters, P->st, P->s));
   LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->mT, nullptr, P->mXs, P->dinv, P->mXo,
@@ -590,7 +598,7 @@ void free_plan(lsq_plan P) {
   if (!P) return;
   void *bufs[] = {P->pat_rows, P->pat_sb, P->SAb, P->W, P->part, P->r2part, P->cpart, P->dcol, P->dinv,
                   P->Rcm, P->Rrm, P->rinv, P->t, P->vbuf, P->xs, P->xo, P->c, P->g, P->dy,
-                  P->dyold, P->z, P->h, P->w, P->res, P->p, P->st, P->bar, P->stageA,
+                  P->dyold, P->z, P->h, P->w, P->res, P->p, P->st, P->qflag, P->stageA,
                   P->stageb, P->stagex, P->Ahi, P->Alo, P->SBb, P->cpartB, P->mpart, P->mr2part,
                   P->mT, P->mXs, P->mXo, P->mC, P->mG, P->mDY, P->mDYold, P->mZ, P->mH,
                   P->mW, P->mstate};
@@ -676,7 +684,7 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   double **vecs[] = {&P->xs, &P->xo, &P->c, &P->g, &P->dy, &P->dyold, &P->z, &P->h, &P->w, &P->res, &P->p};
   for (double **v : vecs) A(dalloc(v, n));
   A(dalloc(&P->st, 1));
-  A(dalloc(&P->bar, 2));
+  A(dalloc(&P->qflag, n));
   A(cudaMallocHost((void **)&P->st_host, sizeof(DevState)));
   A(cudaMallocHost((void **)&P->dcol_host, sizeof(double) * n));
   // hi / lo FP32 planes of A: the double-float inner pass and the FP32 tier read them
@@ -693,6 +701,7 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
     return fail(oom ? LSQ_ERR_OOM : LSQ_ERR_CUDA, std::string("plan allocation: ") + cudaGetErrorString(e));
   }
   e = cudaMemsetAsync(P->st, 0, sizeof(DevState), P->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->qflag, 0, sizeof(int) * (size_t)P->n_cap, P->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
   if (e != cudaSuccess) {
     free_plan(P);

@@ -64,41 +64,6 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Bounded grid-wide barrier for cooperative launches.  count/gen live in
-// global memory (count == 0 at launch).  Returns false, after recording
-// LSQ_ERR_TIMEOUT in *err, when the other blocks did not arrive within
-// timeout_ns; every block then leaves the kernel.
-__device__ __forceinline__ bool grid_barrier(unsigned int *count, volatile unsigned int *gen,
-                                             int *err, uint64_t timeout_ns) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    unsigned int g = *gen;
-    __threadfence();
-    unsigned int arrived = atomicAdd(count, 1u);
-    if (arrived == gridDim.x - 1) {
-      *count = 0;
-      __threadfence();
-      atomicAdd((unsigned int *)gen, 1u);
-    } else {
-      uint64_t t0 = global_ns();
-      while (*gen == g) {
-        if (*(volatile int *)err != 0) { ok = 0; break; }
-        if (global_ns() - t0 > timeout_ns) {
-          atomicExch(err, (int)LSQ_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
 // Message returned by lsq_last_error() on the calling thread (lsq_api.cu).
 void set_last_error(const char *msg);
 
@@ -131,12 +96,16 @@ cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad,
                                    double *dcol, double *dinv, DevState *st, cudaStream_t s);
 // Householder QR of W (d x (n+1), column-major) in place (cooperative).
 // ncols = n + number of augmented columns (right-hand sides).
-cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vbuf, unsigned int *bar,
+// Cooperative Householder QR of W (d x ncols, column-major), reflectors for
+// columns 0..n-1.  vhead: 2 n doubles (u_1, beta per reflector); flags: n ints,
+// flag k set to epoch when reflector k is published (epoch != 0, different
+// from the previous launch's).  Waits are bounded by timeout_ns.
+cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vhead, int *flags, int epoch,
                       DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s);
 int qr_grid(int ncols, int nsm);
-// The same factorisation as n + 1 ordinary launches (no grid barrier): safe to
-// run concurrently with other solves' kernels.
-cudaError_t launch_qr_stepwise(double *W, int d, int n, int ncols, double *vbuf, int grid,
+// The same factorisation as n + 1 ordinary launches (no inter-CTA waits): safe
+// to run concurrently with other solves' kernels.
+cudaError_t launch_qr_stepwise(double *W, int d, int n, int ncols, double *vhead, int grid,
                                cudaStream_t s);
 // R (upper n x n of W) to Rcm / Rrm, 1/R_ii, t = W[0:n, n:n+nb] (column-major n x nb).
 cudaError_t launch_extract_r(const double *W, int d, int n, int nb, double *Rcm, double *Rrm,
