@@ -108,6 +108,54 @@ __device__ void apply_reflector(double *const *cols, int cnt, int k, int d, cons
   __syncthreads();
 }
 
+// The same update with u held in registers: vr[r] = u_i for i = tid + r nt
+// (0 outside k < i < d), loaded once per step for all of the CTA's columns.
+template <int VR>
+__device__ void apply_reflector_regs(double *const *cols, int cnt, int k, int d,
+                                     const double (&vr)[VR], double uk, double beta, double *red,
+                                     double *wsh) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  double acc[kQrBatch];
+#pragma unroll
+  for (int c = 0; c < kQrBatch; c++) acc[c] = 0.0;
+#pragma unroll
+  for (int r = 0; r < VR; r++) {
+    const int i = tid + r * nt;
+    if (i > k && i < d) {
+#pragma unroll
+      for (int c = 0; c < kQrBatch; c++)
+        if (c < cnt) acc[c] = fma(vr[r], cols[c][i], acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kQrBatch; c++)
+    if (c < cnt) acc[c] = warp_sum(acc[c]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < kQrBatch; c++)
+      if (c < cnt) red[warp * kQrBatch + c] = acc[c];
+  }
+  __syncthreads();
+  if (tid < cnt) {
+    double sacc = uk * cols[tid][k];
+    for (int w = 0; w < nw; w++) sacc += red[w * kQrBatch + tid];
+    wsh[tid] = beta * sacc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < VR; r++) {
+    const int i = tid + r * nt;
+    if (i > k && i < d) {
+#pragma unroll
+      for (int c = 0; c < kQrBatch; c++)
+        if (c < cnt) cols[c][i] = fma(-wsh[c], vr[r], cols[c][i]);
+    }
+  }
+  if (tid < cnt) cols[tid][k] = fma(-wsh[tid], uk, cols[tid][k]);
+  __syncthreads();
+}
+
 // Bounded wait of the whole CTA for flag == epoch (thread 0 polls with
 // acquire loads).  false after timeout_ns (LSQ_ERR_TIMEOUT set) or when
 // another CTA has set an error.
@@ -135,7 +183,10 @@ __device__ bool wait_flag(const int *flag, int epoch, int *err, uint64_t timeout
 }
 
 // SMEM: the CTA's columns live in shared memory for the whole factorisation.
-template <bool SMEM>
+// VR > 0 (d <= VR * kQrThreads): each thread holds its VR entries of the
+// current reflector in registers, so the L2 latency of reading it is paid
+// once per step instead of once per loop trip.
+template <bool SMEM, int VR>
 __global__ void __launch_bounds__(kQrThreads, 1)
     qr_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
               int *flags, int epoch, DevState *st, uint64_t timeout_ns) {
@@ -179,11 +230,23 @@ __global__ void __launch_bounds__(kQrThreads, 1)
     }
     // u of reflector k: this CTA's own copy of column k, or the published one
     const double *vk = own ? colp((k - me) / G) : W + (size_t)k * d;
+    double vr[VR > 0 ? VR : 1];
+    if (VR > 0) {
+#pragma unroll
+      for (int r = 0; r < (VR > 0 ? VR : 1); r++) {
+        const int i = tid + r * nt;
+        vr[r] = (i > k && i < d) ? (own ? vk[i] : __ldcg(vk + i)) : 0.0;
+      }
+    }
+    auto apply = [&](int cnt) {
+      if (VR > 0) apply_reflector_regs(cols, cnt, k, d, vr, uk, beta, red, wsh);
+      else if (own) apply_reflector<false>(cols, cnt, k, d, vk, uk, beta, red, wsh);
+      else apply_reflector<true>(cols, cnt, k, d, vk, uk, beta, red, wsh);
+    };
     int l = l0;
     if (k + 1 < n && (k + 1) % G == me) {  // lookahead: H_k on column k+1, then reflector k+1
       cols[0] = colp(l);
-      if (own) apply_reflector<false>(cols, 1, k, d, vk, uk, beta, red, wsh);
-      else apply_reflector<true>(cols, 1, k, d, vk, uk, beta, red, wsh);
+      apply(1);
       make_reflector(colp(l), k + 1, d, W + (size_t)(k + 1) * d, vhead, SMEM, red, uk_ahead,
                      beta_ahead);
       __syncthreads();
@@ -197,8 +260,7 @@ __global__ void __launch_bounds__(kQrThreads, 1)
     while (l < nloc) {
       int cnt = 0;
       for (; cnt < kQrBatch && l < nloc; cnt++, l++) cols[cnt] = colp(l);
-      if (own) apply_reflector<false>(cols, cnt, k, d, vk, uk, beta, red, wsh);
-      else apply_reflector<true>(cols, cnt, k, d, vk, uk, beta, red, wsh);
+      apply(cnt);
     }
   }
   if (SMEM) {
@@ -275,20 +337,32 @@ int qr_grid(int ncols, int nsm) { return ncols < nsm ? ncols : nsm; }
 // Largest dynamic shared memory the columns may use (227 KB opt-in minus the static part).
 constexpr size_t kQrSmemMax = 225 * 1024;
 
+template <bool SMEM, int VR>
+cudaError_t launch_qr_t(void **args, int grid, size_t smem, cudaStream_t s) {
+  const void *fn = (const void *)qr_kernel<SMEM, VR>;
+  if (SMEM) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kQrThreads), args, SMEM ? smem : 0, s);
+}
+
+template <bool SMEM>
+cudaError_t launch_qr_vr(void **args, int d, int grid, size_t smem, cudaStream_t s) {
+  if (d <= 8 * kQrThreads) return launch_qr_t<SMEM, 8>(args, grid, smem, s);
+  if (d <= 12 * kQrThreads) return launch_qr_t<SMEM, 12>(args, grid, smem, s);
+  if (d <= 16 * kQrThreads) return launch_qr_t<SMEM, 16>(args, grid, smem, s);
+  if (d <= 24 * kQrThreads) return launch_qr_t<SMEM, 24>(args, grid, smem, s);
+  return launch_qr_t<SMEM, 0>(args, grid, smem, s);
+}
+
 cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vhead, int *flags, int epoch,
                       DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s) {
   void *args[] = {&W, &d, &n, &ncols, &vhead, &flags, &epoch, &st, &timeout_ns};
   const int nloc_max = (ncols + grid - 1) / grid;
   const size_t smem = (size_t)nloc_max * d * sizeof(double);
-  if (smem <= kQrSmemMax) {
-    cudaError_t e = cudaFuncSetAttribute((const void *)qr_kernel<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel((const void *)qr_kernel<true>, dim3(grid),
-                                       dim3(kQrThreads), args, smem, s);
-  }
-  return cudaLaunchCooperativeKernel((const void *)qr_kernel<false>, dim3(grid), dim3(kQrThreads),
-                                     args, 0, s);
+  if (smem <= kQrSmemMax) return launch_qr_vr<true>(args, d, grid, smem, s);
+  return launch_qr_vr<false>(args, d, grid, 0, s);
 }
 
 cudaError_t launch_qr_stepwise(double *W, int d, int n, int ncols, double *vhead, int grid,

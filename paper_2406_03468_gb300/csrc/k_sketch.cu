@@ -222,6 +222,286 @@ __global__ void transpose_scale_kernel(const double *__restrict__ SAb, int n, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Gather form of the sketch pass.  The scatter above pays one L2 FP64 atomic
+// per element of A and target row (zeta per element); on GB300 those run at
+// ~0.6 G/s per ... SM slice and bound the pass.  The gather form inverts the
+// pattern once per plan into source lists (CSR by sketch row h: the rows i
+// of A with h among their zeta rows, sorted by i) and gives each sketch row
+// to one warp, which walks its list and sums the +-rows of A in registers.
+// The sums are 64-bit fixed point per column: every entry is rounded once to
+// a multiple of 2^F_j, F_j = E_j + L - 62 (|A_ij| < 2^E_j, L = bits of the
+// longest list), and added exactly, so the sketch is reproducible bit for
+// bit whatever the order, and each entry of S[A b] is the exact sum of the
+// rounded terms, rounded once to FP64 (error <= 2^-52 max_i |A_ij| per term
+// plus one final rounding).  All warps of one column chunk sweep A in row
+// order together, so the zeta reads of a row mostly hit L2.
+// ---------------------------------------------------------------------------
+
+constexpr int kGatherWarps = 8;      // warps per CTA of the gather kernel
+constexpr int kSortMax = 16384;      // longest source list sorted in shared memory
+
+__global__ void tgt_count_kernel(const int32_t *__restrict__ rows, int64_t mz, int d, int *cnt) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= mz) return;
+  const int h = rows[e];
+  if ((unsigned)h < (unsigned)d) atomicAdd(cnt + h, 1);
+}
+
+// Exclusive scan of cnt into ptr (d + 1 entries), longest list into *lmax,
+// cnt reset to 0 (it becomes the fill cursor).  One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024)
+    tgt_scan_kernel(int *cnt, int d, int64_t *ptr, int *lmax) {
+  __shared__ int64_t part[1024];
+  __shared__ int pmax[1024];
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int per = (d + nt - 1) / nt;
+  const int h0 = min(d, t * per), h1 = min(d, h0 + per);
+  int64_t sum = 0;
+  int mx = 0;
+  for (int h = h0; h < h1; h++) {
+    sum += cnt[h];
+    mx = max(mx, cnt[h]);
+  }
+  part[t] = sum;
+  pmax[t] = mx;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {  // inclusive Hillis-Steele scan
+    const int64_t v = (t >= off) ? part[t - off] : 0;
+    const int w = (t >= off) ? pmax[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    pmax[t] = max(pmax[t], w);
+    __syncthreads();
+  }
+  int64_t run = part[t] - sum;
+  for (int h = h0; h < h1; h++) {
+    ptr[h] = run;
+    run += cnt[h];
+    cnt[h] = 0;
+  }
+  if (t == nt - 1) {
+    ptr[d] = part[t];
+    *lmax = pmax[t];
+  }
+}
+
+__global__ void tgt_fill_kernel(const int32_t *__restrict__ rows, const uint32_t *__restrict__ sb,
+                                int64_t m, int zeta, int d, const int64_t *__restrict__ ptr,
+                                int *cursor, uint32_t *src) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m * zeta) return;
+  const int h = rows[e];
+  if ((unsigned)h >= (unsigned)d) return;
+  const int64_t i = e / zeta;
+  const int t = (int)(e - i * zeta);
+  const uint32_t neg = (sb[i] >> t) & 1u;
+  const int64_t pos = ptr[h] + atomicAdd(cursor + h, 1);
+  src[pos] = (uint32_t)i | (neg << 31);
+}
+
+// Sort each source list by row (bitonic, in shared memory); one CTA per list.
+__global__ void __launch_bounds__(512)
+    tgt_sort_kernel(const int64_t *__restrict__ ptr, uint32_t *src) {
+  extern __shared__ uint32_t keys[];
+  const int64_t p0 = ptr[blockIdx.x];
+  const int len = (int)(ptr[blockIdx.x + 1] - p0);
+  if (len <= 1 || len > kSortMax) return;
+  int P = 1;
+  while (P < len) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) keys[i] = (i < len) ? src[p0 + i] : 0x7fffffffu;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint32_t a = keys[i], c = keys[l];
+          const bool up = ((i & k) == 0);
+          const bool gt = (a & 0x7fffffffu) > (c & 0x7fffffffu);
+          if (gt == up) {
+            keys[i] = c;
+            keys[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < len; i += blockDim.x) src[p0 + i] = keys[i];
+}
+
+__device__ __forceinline__ int biased_exp(double a) {
+  return (int)(((unsigned)__double2hiint(a) >> 20) & 0x7ffu);
+}
+
+// One streaming pass over A (no sketch): column sums of squares (partials),
+// the largest biased exponent per column and of b (atomicMax into colexp[0..n)
+// and colexp[npad], zeroed first), and the hi / lo FP32 planes when Ahi != NULL.
+template <int NC, bool VEC>
+__global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
+    prep_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
+                const double *__restrict__ b, double *__restrict__ colsq_part, int npad,
+                int *colexp, float *__restrict__ Ahi, float *__restrict__ Alo, int64_t ld32) {
+  __shared__ double acc[NC * 64];
+  __shared__ int emax[NC * 64 + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = min(m, (int64_t)blockIdx.x * per), r1 = min(m, r0 + per);
+  for (int i = threadIdx.x; i <= NC * 64; i += blockDim.x) emax[i] = 0;
+  double sq[2 * NC];
+  int ex[2 * NC];
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) {
+    sq[k] = 0.0;
+    ex[k] = 0;
+  }
+  int bex = 0;
+  for (int64_t i = r0 + warp; i < r1; i += nw) {
+    double a[2 * NC];
+    load_row<NC, VEC>(A + i * lda, n, lane, a);
+    if (Ahi != nullptr) {
+#pragma unroll
+      for (int k = 0; k < NC; k++) {
+        const int col = 64 * k + 2 * lane;
+        float h0, l0, h1, l1;
+        split_rn(a[2 * k], h0, l0);
+        split_rn(a[2 * k + 1], h1, l1);
+        if (col + 1 < n) {
+          __stcs(reinterpret_cast<float2 *>(Ahi + i * ld32 + col), make_float2(h0, h1));
+          __stcs(reinterpret_cast<float2 *>(Alo + i * ld32 + col), make_float2(l0, l1));
+        } else if (col < n) {
+          __stcs(Ahi + i * ld32 + col, h0);
+          __stcs(Alo + i * ld32 + col, l0);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * NC; k++) {
+      sq[k] = fma(a[k], a[k], sq[k]);
+      ex[k] = max(ex[k], biased_exp(a[k]));
+    }
+    if (b != nullptr && lane == 0) bex = max(bex, biased_exp(b[i]));
+  }
+  for (int i = threadIdx.x; i < NC * 64; i += blockDim.x) acc[i] = 0.0;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NC; k++) {
+    const int col = 64 * k + 2 * lane;
+    atomicMax(emax + col, ex[2 * k]);
+    atomicMax(emax + col + 1, ex[2 * k + 1]);
+  }
+  if (lane == 0) atomicMax(emax + NC * 64, bex);
+  for (int w = 0; w < nw; w++) {
+    __syncthreads();
+    if (warp == w) {
+#pragma unroll
+      for (int k = 0; k < NC; k++) {
+        const int col = 64 * k + 2 * lane;
+        acc[col] += sq[2 * k];
+        acc[col + 1] += sq[2 * k + 1];
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+    colsq_part[(size_t)blockIdx.x * npad + i] = acc[i];
+    if (i < n && emax[i] > 0) atomicMax(colexp + i, emax[i]);
+  }
+  if (threadIdx.x == 0 && emax[NC * 64] > 0) atomicMax(colexp + npad, emax[NC * 64]);
+}
+
+// Fixed-point parameters per column (and b at index npad): with E = the
+// largest biased exponent (|a| < 2^(E - 1022)) and L = max(10, bits of the
+// longest list), F = (E - 1022) + L - 62, cshift = 1075 + F (the right shift
+// of a 53-bit significand with biased exponent e is cshift - e >= 1) and
+// cpow = 2^F.  A NaN or Inf (E = 2047) sets st->nonfinite.
+__global__ void fixed_params_kernel(const int *__restrict__ colexp, int n, int npad,
+                                    const int *__restrict__ lmax, int *cshift, double *cpow,
+                                    DevState *st) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > npad) return;
+  if (j >= n && j < npad) return;
+  const int E = max(colexp[j], 1);
+  if (colexp[j] == 2047) atomicExch(&st->nonfinite, 1);
+  int L = 10;
+  while (L < 40 && (1ll << L) <= (long long)*lmax) L++;
+  const int F = (E - 1022) + L - 62;
+  cshift[j] = 1075 + F;
+  cpow[j] = ldexp(1.0, F);
+}
+
+// Rounded a / 2^F as a signed 64-bit integer (round half away from zero),
+// negated when neg; C = 1075 + F.
+__device__ __forceinline__ long long to_fixed(double a, int C, unsigned neg) {
+  const unsigned hw = (unsigned)__double2hiint(a), lw = (unsigned)__double2loint(a);
+  const int e = (int)((hw >> 20) & 0x7ffu);
+  const unsigned mh = (hw & 0xfffffu) | (e != 0 ? 0x100000u : 0u);
+  const int s = C - (e != 0 ? e : 1);  // >= 1 by the choice of F
+  const unsigned long long mant = ((unsigned long long)mh << 32) | lw;
+  const unsigned long long t = (s <= 64) ? (mant >> (s - 1)) : 0ull;
+  const long long q = (long long)((t + 1ull) >> 1);
+  return ((hw >> 31) ^ neg) ? -q : q;
+}
+
+template <int CH>
+__global__ void __launch_bounds__(kGatherWarps * 32)
+    gather_kernel(const double *__restrict__ A, int64_t lda, int n, const double *__restrict__ b,
+                  int d, int npad, const int64_t *__restrict__ ptr,
+                  const uint32_t *__restrict__ src, const int *__restrict__ cshift,
+                  const double *__restrict__ cpow, double *__restrict__ SAb) {
+  __shared__ int sh[CH * 64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.y * CH * 64;
+  for (int i = threadIdx.x; i < CH * 64; i += blockDim.x)
+    sh[i] = (c0 + i < n) ? cshift[c0 + i] : 4096;
+  __syncthreads();
+  const int h = blockIdx.x * kGatherWarps + warp;
+  if (h >= d) return;
+  const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 2 == 0);
+  const bool dob = (b != nullptr && blockIdx.y == 0);
+  const int shb = dob ? cshift[npad] : 0;
+  long long acc[2 * CH];
+#pragma unroll
+  for (int k = 0; k < 2 * CH; k++) acc[k] = 0;
+  long long accb = 0;
+  const int64_t p1 = ptr[h + 1];
+  for (int64_t p = ptr[h]; p < p1; p++) {
+    const uint32_t e = __ldg(src + p);
+    const int64_t i = e & 0x7fffffffu;
+    const unsigned neg = e >> 31;
+    const double *row = A + i * lda + c0;
+    double a[2 * CH];
+#pragma unroll
+    for (int k = 0; k < CH; k++) {
+      const int col = 64 * k + 2 * lane;
+      if (vec && c0 + col + 1 < n) {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(row + col));
+        a[2 * k] = v.x;
+        a[2 * k + 1] = v.y;
+      } else {
+        a[2 * k] = (c0 + col < n) ? __ldg(row + col) : 0.0;
+        a[2 * k + 1] = (c0 + col + 1 < n) ? __ldg(row + col + 1) : 0.0;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CH; k++) {
+      const int col = 64 * k + 2 * lane;
+      acc[2 * k] += to_fixed(a[2 * k], sh[col], neg);
+      acc[2 * k + 1] += to_fixed(a[2 * k + 1], sh[col + 1], neg);
+    }
+    if (dob && lane == 0) accb += to_fixed(__ldg(b + i), shb, neg);
+  }
+  double *out = SAb + (size_t)h * (n + 1);
+#pragma unroll
+  for (int k = 0; k < CH; k++) {
+    const int col = c0 + 64 * k + 2 * lane;
+    if (col < n) out[col] = (double)acc[2 * k] * cpow[col];
+    if (col + 1 < n) out[col + 1] = (double)acc[2 * k + 1] * cpow[col + 1];
+  }
+  if (blockIdx.y == 0 && lane == 0) out[n] = dob ? (double)accb * cpow[npad] : 0.0;
+}
+
 }  // namespace
 
 int pass_npad(int n) {
@@ -276,6 +556,71 @@ cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad,
   if (e != cudaSuccess) return e;
   dim3 blk(32, 8), grd((n + 1 + 31) / 32, (d + 31) / 32);
   transpose_scale_kernel<<<grd, blk, 0, s>>>(SAb, n, d, dinv, 1.0 / sqrt((double)zeta), W, st);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_sketch_lists(const int32_t *rows, const uint32_t *signbits, int64_t m, int zeta,
+                                int d, int *cnt, int64_t *ptr, uint32_t *src, int *lmax,
+                                cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)d, s);
+  if (e != cudaSuccess) return e;
+  const int64_t mz = m * zeta;
+  const unsigned blocks = (unsigned)((mz + 255) / 256);
+  tgt_count_kernel<<<blocks, 256, 0, s>>>(rows, mz, d, cnt);
+  tgt_scan_kernel<<<1, 1024, 0, s>>>(cnt, d, ptr, lmax);
+  tgt_fill_kernel<<<blocks, 256, 0, s>>>(rows, signbits, m, zeta, d, ptr, cnt, src);
+  const size_t smem = sizeof(uint32_t) * kSortMax;
+  e = cudaFuncSetAttribute((const void *)tgt_sort_kernel,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  tgt_sort_kernel<<<d, 512, smem, s>>>(ptr, src);
+  return cudaGetLastError();
+}
+
+int sketch_list_max() { return kSortMax; }
+
+cudaError_t launch_sketch_prep(const double *A, int64_t lda, int64_t m, int n, const double *b,
+                               double *colsq_part, int grid, int npad, int *colexp, float *Ahi,
+                               float *Alo, int64_t ld32, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(colexp, 0, sizeof(int) * (size_t)(npad + 1), s);
+  if (e != cudaSuccess) return e;
+  const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 2 == 0);
+#define LSQ_PREP(NC)                                                                            \
+  (vec ? prep_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, colsq_part, npad, \
+                                                             colexp, Ahi, Alo, ld32)            \
+       : prep_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, colsq_part,     \
+                                                              npad, colexp, Ahi, Alo, ld32))
+  switch (npad / 64) {
+    case 1: LSQ_PREP(1); break;
+    case 2: LSQ_PREP(2); break;
+    case 4: LSQ_PREP(4); break;
+    case 8: LSQ_PREP(8); break;
+    case 16: LSQ_PREP(16); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef LSQ_PREP
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_gather(const double *A, int64_t lda, int n, const double *b, int d,
+                                 int npad, const int64_t *ptr, const uint32_t *src,
+                                 const int *colexp, const int *lmax, int *cshift, double *cpow,
+                                 double *SAb, DevState *st, cudaStream_t s) {
+  fixed_params_kernel<<<(npad + 1 + 255) / 256, 256, 0, s>>>(colexp, n, npad, lmax, cshift, cpow,
+                                                              st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int ch = npad >= 256 ? 4 : npad / 64;
+  const dim3 grid((unsigned)((d + kGatherWarps - 1) / kGatherWarps),
+                  (unsigned)((n + 64 * ch - 1) / (64 * ch)));
+  const int th = kGatherWarps * 32;
+  if (ch == 4)
+    gather_kernel<4><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb);
+  else if (ch == 2)
+    gather_kernel<2><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb);
+  else
+    gather_kernel<1><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb);
   return cudaGetLastError();
 }
 

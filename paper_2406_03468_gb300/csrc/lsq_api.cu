@@ -65,6 +65,13 @@ struct lsq_plan_s {
   int32_t *pat_rows = nullptr;
   uint32_t *pat_sb = nullptr;
   bool pat_valid = false;
+  // gather form of the sketch: source lists of the sketch rows (built with
+  // the pattern), fixed-point scratch
+  bool use_gather = false;
+  int *tcnt = nullptr, *tlmax = nullptr, *colexp = nullptr, *cshift = nullptr;
+  int64_t *tptr = nullptr;
+  uint32_t *tsrc = nullptr;
+  double *cpow = nullptr;
   double *SAb = nullptr, *W = nullptr, *part = nullptr, *r2part = nullptr, *cpart = nullptr;
   double *dcol = nullptr, *dinv = nullptr, *Rcm = nullptr, *Rrm = nullptr, *rinv = nullptr;
   double *t = nullptr, *vbuf = nullptr;
@@ -172,6 +179,35 @@ int next_epoch(lsq_plan P) {
   return P->qr_epoch;
 }
 
+// The gather form of the sketch pays a one-off list build per pattern and
+// wins on large problems; it needs row indices below 2^31.
+constexpr double kGatherMinElems = 16777216.0;  // m n >= 2^24 (A >= 128 MB)
+bool gather_size_ok(int64_t m, int64_t n) {
+  return m < ((int64_t)1 << 31) && (double)m * (double)n >= kGatherMinElems;
+}
+
+// The sparse sign pattern of the current (m, d, zeta, seed), built once and
+// cached, and for large problems the source lists of the gather sketch
+// (the sketch falls back to the scatter form when a list is too long to
+// sort in shared memory).
+lsq_status ensure_pattern(lsq_plan P) {
+  if (P->pat_valid) return LSQ_OK;
+  LSQ_CU(launch_sketch_pattern(P->m, P->d, P->zeta, P->o.seed, P->pat_rows, P->pat_sb, P->s));
+  P->launches++;
+  P->use_gather = false;
+  if (P->tsrc != nullptr && gather_size_ok(P->m, P->n)) {
+    LSQ_CU(launch_sketch_lists(P->pat_rows, P->pat_sb, P->m, P->zeta, P->d, P->tcnt, P->tptr,
+                               P->tsrc, P->tlmax, P->s));
+    P->launches += 4;
+    int lmax = 0;
+    LSQ_CU(cudaMemcpyAsync(&lmax, P->tlmax, sizeof(int), cudaMemcpyDeviceToHost, P->s));
+    LSQ_CU(cudaStreamSynchronize(P->s));
+    P->use_gather = lmax <= sketch_list_max();
+  }
+  P->pat_valid = true;
+  return LSQ_OK;
+}
+
 lsq_status read_state(lsq_plan P) {
   LSQ_CU(cudaMemcpyAsync(P->st_host, P->st, sizeof(DevState), cudaMemcpyDeviceToHost, P->s));
   LSQ_CU(cudaStreamSynchronize(P->s));
@@ -244,20 +280,25 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
   P->st_host->beta = P->beta;
   LSQ_CU(cudaMemcpyAsync(P->st, P->st_host, sizeof(DevState), cudaMemcpyHostToDevice, P->s));
   LSQ_CU(cudaEventRecord(P->ev[0], P->s));
-  if (!P->pat_valid) {
-    LSQ_CU(launch_sketch_pattern(P->m, P->d, P->zeta, P->o.seed, P->pat_rows, P->pat_sb, P->s));
-    P->pat_valid = true;
-    P->launches++;
-  }
-  LSQ_CU(cudaMemsetAsync(P->SAb, 0, sizeof(double) * (size_t)P->d * (n + 1), P->s));
+  LSQ_TRY(ensure_pattern(P));
   int tk = -1;
   if (P->o.timing) {
     LSQ_CU(tev_pair(P, &tk));
     LSQ_CU(cudaEventRecord(P->tev[2 * tk], P->s));
   }
-  LSQ_CU(launch_sketch(dA, P->lda, P->m, n, db, P->d, P->zeta, P->pat_rows, P->pat_sb, P->SAb,
-                       P->cpart, P->gpass, P->npad, P->want32 ? P->Ahi : nullptr,
-                       P->want32 ? P->Alo : nullptr, P->ld32, P->s));
+  if (P->use_gather) {
+    LSQ_CU(launch_sketch_prep(dA, P->lda, P->m, n, db, P->cpart, P->gpass, P->npad, P->colexp,
+                              P->want32 ? P->Ahi : nullptr, P->want32 ? P->Alo : nullptr, P->ld32,
+                              P->s));
+    LSQ_CU(launch_sketch_gather(dA, P->lda, n, db, P->d, P->npad, P->tptr, P->tsrc, P->colexp,
+                                P->tlmax, P->cshift, P->cpow, P->SAb, P->st, P->s));
+    P->launches += 2;
+  } else {
+    LSQ_CU(cudaMemsetAsync(P->SAb, 0, sizeof(double) * (size_t)P->d * (n + 1), P->s));
+    LSQ_CU(launch_sketch(dA, P->lda, P->m, n, db, P->d, P->zeta, P->pat_rows, P->pat_sb, P->SAb,
+                         P->cpart, P->gpass, P->npad, P->want32 ? P->Ahi : nullptr,
+                         P->want32 ? P->Alo : nullptr, P->ld32, P->s));
+  }
   if (tk >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tk + 1], P->s));
   LSQ_CU(launch_sketch_finalize(P->cpart, P->gpass, P->npad, n, P->d, P->zeta, P->o.col_scale,
                                 P->SAb, P->W, P->dcol, P->dinv, P->st, P->s));
@@ -449,10 +490,7 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
   P->st_host->beta = P->beta;
   LSQ_CU(cudaMemcpyAsync(P->st, P->st_host, sizeof(DevState), cudaMemcpyHostToDevice, P->s));
   LSQ_CU(cudaEventRecord(P->ev[0], P->s));
-  if (!P->pat_valid) {
-    LSQ_CU(launch_sketch_pattern(P->m, d, P->zeta, P->o.seed, P->pat_rows, P->pat_sb, P->s));
-    P->pat_valid = true;
-  }
+  LSQ_TRY(ensure_pattern(P));
   // one sketch S for [A B]: A's columns (with their norms), then B's
   LSQ_CU(cudaMemsetAsync(P->SAb, 0, sizeof(double) * (size_t)d * (n + 1), P->s));
   LSQ_CU(cudaMemsetAsync(P->SBb, 0, sizeof(double) * (size_t)d * (k + 1), P->s));
@@ -601,7 +639,8 @@ void free_plan(lsq_plan P) {
                   P->dyold, P->z, P->h, P->w, P->res, P->p, P->st, P->qflag, P->stageA,
                   P->stageb, P->stagex, P->Ahi, P->Alo, P->SBb, P->cpartB, P->mpart, P->mr2part,
                   P->mT, P->mXs, P->mXo, P->mC, P->mG, P->mDY, P->mDYold, P->mZ, P->mH,
-                  P->mW, P->mstate};
+                  P->mW, P->mstate, P->tcnt, P->tlmax, P->colexp, P->cshift,
+                  P->tptr, P->tsrc, P->cpow};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->st_host) cudaFreeHost(P->st_host);
@@ -657,6 +696,15 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(dalloc(&P->pat_rows, (size_t)P->m_cap * P->zeta_cap));
   A(dalloc(&P->pat_sb, (size_t)P->m));
+  if (gather_size_ok(P->m_cap, n)) {
+    A(dalloc(&P->tcnt, (size_t)P->d_cap));
+    A(dalloc(&P->tptr, (size_t)P->d_cap + 1));
+    A(dalloc(&P->tsrc, (size_t)P->m_cap * P->zeta_cap));
+    A(dalloc(&P->tlmax, 1));
+    A(dalloc(&P->colexp, (size_t)P->npad + 1));
+    A(dalloc(&P->cshift, (size_t)P->npad + 1));
+    A(dalloc(&P->cpow, (size_t)P->npad + 1));
+  }
   P->k = opt->nrhs > 0 ? opt->nrhs : 0;
   A(dalloc(&P->SAb, dn1));
   A(dalloc(&P->W, (size_t)P->d * (n + (P->k > 1 ? P->k : 1))));
@@ -794,10 +842,7 @@ lsq_status lsq_solve_host(lsq_plan P, int method, const double *hA, const double
 
 lsq_status lsq_sketch_pattern(lsq_plan P, int32_t *d_rows, uint32_t *d_signbits) {
   if (!P || !d_rows || !d_signbits) return fail(LSQ_ERR_INVALID, "NULL argument");
-  if (!P->pat_valid) {
-    LSQ_CU(launch_sketch_pattern(P->m, P->d, P->zeta, P->o.seed, P->pat_rows, P->pat_sb, P->s));
-    P->pat_valid = true;
-  }
+  LSQ_TRY(ensure_pattern(P));
   LSQ_CU(cudaMemcpyAsync(d_rows, P->pat_rows, sizeof(int32_t) * (size_t)P->m * P->zeta,
                          cudaMemcpyDeviceToDevice, P->s));
   LSQ_CU(cudaMemcpyAsync(d_signbits, P->pat_sb, sizeof(uint32_t) * (size_t)P->m,

@@ -90,6 +90,24 @@ cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, const 
                           int d, int zeta, const int32_t *rows, const uint32_t *signbits,
                           double *SAb, double *colsq_part, int grid, int npad, float *Ahi,
                           float *Alo, int64_t ld32, cudaStream_t s);
+// Gather form of the sketch.  Per plan: source lists of the sketch rows
+// (CSR by row h: ptr d + 1 entries, src m zeta entries i | sign << 31 sorted
+// by i when no list exceeds sketch_list_max(); cnt: d ints of scratch; *lmax
+// = longest list).  Per solve: launch_sketch_prep (column sums of squares,
+// largest exponents colexp[0..n) and of b at colexp[npad], FP32 planes),
+// then launch_sketch_gather (64-bit fixed-point sums into SAb, d x (n+1)
+// row-major, no zeroing needed; cshift / cpow: npad + 1 entries of scratch).
+cudaError_t launch_sketch_lists(const int32_t *rows, const uint32_t *signbits, int64_t m, int zeta,
+                                int d, int *cnt, int64_t *ptr, uint32_t *src, int *lmax,
+                                cudaStream_t s);
+int sketch_list_max();
+cudaError_t launch_sketch_prep(const double *A, int64_t lda, int64_t m, int n, const double *b,
+                               double *colsq_part, int grid, int npad, int *colexp, float *Ahi,
+                               float *Alo, int64_t ld32, cudaStream_t s);
+cudaError_t launch_sketch_gather(const double *A, int64_t lda, int n, const double *b, int d,
+                                 int npad, const int64_t *ptr, const uint32_t *src,
+                                 const int *colexp, const int *lmax, int *cshift, double *cpow,
+                                 double *SAb, DevState *st, cudaStream_t s);
 // Column norms from partials, scaling, transpose into column-major W (ld d).
 cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad, int n, int d,
                                    int zeta, int col_scale, const double *SAb, double *W,
