@@ -73,23 +73,15 @@ template <bool VG>
 __device__ void apply_reflector(double *const *cols, int cnt, int k, int d, const double *vsrc,
                                 double uk, double beta, double *red, double *wsh) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  double acc[kQrBatch];
-#pragma unroll
-  for (int c = 0; c < kQrBatch; c++) acc[c] = 0.0;
-  for (int i = k + 1 + tid; i < d; i += nt) {
-    const double vi = VG ? __ldcg(vsrc + i) : vsrc[i];
-#pragma unroll
-    for (int c = 0; c < kQrBatch; c++)
-      if (c < cnt) acc[c] = fma(vi, cols[c][i], acc[c]);
-  }
-#pragma unroll
-  for (int c = 0; c < kQrBatch; c++)
-    if (c < cnt) acc[c] = warp_sum(acc[c]);
-  __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int c = 0; c < kQrBatch; c++)
-      if (c < cnt) red[warp * kQrBatch + c] = acc[c];
+  for (int c = 0; c < cnt; c++) {
+    const double *col = cols[c];
+    double acc = 0.0;
+    for (int i = k + 1 + tid; i < d; i += nt) {
+      const double vi = VG ? __ldcg(vsrc + i) : vsrc[i];
+      acc = fma(vi, col[i], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) red[warp * kQrBatch + c] = acc;
   }
   __syncthreads();
   if (tid < cnt) {
@@ -98,11 +90,13 @@ __device__ void apply_reflector(double *const *cols, int cnt, int k, int d, cons
     wsh[tid] = beta * sacc;
   }
   __syncthreads();
-  for (int i = k + 1 + tid; i < d; i += nt) {
-    const double vi = VG ? __ldcg(vsrc + i) : vsrc[i];
-#pragma unroll
-    for (int c = 0; c < kQrBatch; c++)
-      if (c < cnt) cols[c][i] = fma(-wsh[c], vi, cols[c][i]);
+  for (int c = 0; c < cnt; c++) {
+    double *col = cols[c];
+    const double w = wsh[c];
+    for (int i = k + 1 + tid; i < d; i += nt) {
+      const double vi = VG ? __ldcg(vsrc + i) : vsrc[i];
+      col[i] = fma(-w, vi, col[i]);
+    }
   }
   if (tid < cnt) cols[tid][k] = fma(-wsh[tid], uk, cols[tid][k]);
   __syncthreads();
@@ -110,31 +104,25 @@ __device__ void apply_reflector(double *const *cols, int cnt, int k, int d, cons
 
 // The same update with u held in registers: vr[r] = u_i for i = tid + r nt
 // (0 outside k < i < d), loaded once per step for all of the CTA's columns.
+// The loops over columns run to cnt at run time: an unrolled loop to
+// kQrBatch with `c < cnt` guards would issue the guarded-off FP64 FMAs too,
+// and GB300's FP64 pipe is the unit that bounds this kernel.
 template <int VR>
 __device__ void apply_reflector_regs(double *const *cols, int cnt, int k, int d,
                                      const double (&vr)[VR], double uk, double beta, double *red,
                                      double *wsh) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  double acc[kQrBatch];
+  for (int c = 0; c < cnt; c++) {
+    const double *col = cols[c];
+    double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-  for (int c = 0; c < kQrBatch; c++) acc[c] = 0.0;
-#pragma unroll
-  for (int r = 0; r < VR; r++) {
-    const int i = tid + r * nt;
-    if (i > k && i < d) {
-#pragma unroll
-      for (int c = 0; c < kQrBatch; c++)
-        if (c < cnt) acc[c] = fma(vr[r], cols[c][i], acc[c]);
+    for (int r = 0; r < VR; r += 2) {
+      const int i0 = tid + r * nt, i1 = i0 + nt;
+      if (i0 > k && i0 < d) a0 = fma(vr[r], col[i0], a0);
+      if (r + 1 < VR && i1 > k && i1 < d) a1 = fma(vr[r + 1], col[i1], a1);
     }
-  }
-#pragma unroll
-  for (int c = 0; c < kQrBatch; c++)
-    if (c < cnt) acc[c] = warp_sum(acc[c]);
-  __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int c = 0; c < kQrBatch; c++)
-      if (c < cnt) red[warp * kQrBatch + c] = acc[c];
+    const double acc = warp_sum(a0 + a1);
+    if (lane == 0) red[warp * kQrBatch + c] = acc;
   }
   __syncthreads();
   if (tid < cnt) {
@@ -143,13 +131,13 @@ __device__ void apply_reflector_regs(double *const *cols, int cnt, int k, int d,
     wsh[tid] = beta * sacc;
   }
   __syncthreads();
+  for (int c = 0; c < cnt; c++) {
+    double *col = cols[c];
+    const double w = wsh[c];
 #pragma unroll
-  for (int r = 0; r < VR; r++) {
-    const int i = tid + r * nt;
-    if (i > k && i < d) {
-#pragma unroll
-      for (int c = 0; c < kQrBatch; c++)
-        if (c < cnt) cols[c][i] = fma(-wsh[c], vr[r], cols[c][i]);
+    for (int r = 0; r < VR; r++) {
+      const int i = tid + r * nt;
+      if (i > k && i < d) col[i] = fma(-w, vr[r], col[i]);
     }
   }
   if (tid < cnt) cols[tid][k] = fma(-wsh[tid], uk, cols[tid][k]);
