@@ -7,9 +7,9 @@
 // One CTA per solve: the vector lives in shared memory; R (n x n) is read
 // from L2 in both layouts so that every access is coalesced -- column j of R
 // (column-major copy) for R x = y, row j of R (row-major copy) for R^T x = y.
-// Blocked by 16: warp 0 solves each 16 x 16 diagonal block with shuffles,
-// then the whole CTA (one thread per row) subtracts the block's contribution
-// from the rest, so a solve costs 2 ceil(n/16) CTA barriers.  x_j = y_j * (1 / R_jj) with the
+// Blocked by 32: warp 0 solves each 32 x 32 diagonal block with shuffles,
+// then the whole CTA subtracts the block's contribution from the rest, so a
+// solve costs ceil(n/32) block barriers.  x_j = y_j * (1 / R_jj) with the
 // reciprocals computed once per factorisation; that perturbs each diagonal
 // entry by at most two roundings, so the solve stays backward stable.
 #include "lsq_common.cuh"
@@ -18,52 +18,22 @@ namespace lsq {
 
 namespace {
 
-constexpr int kTB = 16;  // diagonal block size
-static_assert(LSQ_MAX_N <= kVecThreads, "block_trsv takes one thread per row");
-
-// Entry (jj, l) of the diagonal block starting at j0 (len = its size): column
-// j0+jj of R for R x = y, row j0+jj for R^T x = y; 0 outside the block.
-__device__ __forceinline__ double diag_entry(const double *__restrict__ Rb, int n, int j0, int len,
-                                             int e) {
-  const int jj = e / kTB, l = e % kTB;
-  return (jj < len && l < len) ? Rb[(size_t)(j0 + jj) * n + j0 + l] : 0.0;
-}
-
-// Solve R x = y (trans 0, blocks last to first) or R^T x = y (trans 1) in
-// place on sy (n doubles of shared memory).  tile: 2 kTB (kTB + 1) doubles of
-// shared memory.  One thread per row (n <= blockDim.x).  Each round issues
-// the loads it will need next -- this round's kTB entries of R per row and
-// the next diagonal block -- before warp 0 runs the block's serial chain, so
-// their L2 latency overlaps the chain instead of following it.
+// tile: 32 x 33 doubles of shared memory for the diagonal block.
 __device__ void block_trsv(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
                            const double *__restrict__ rinv, int n, int trans, double *sy,
                            double *tile) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nb = (n + kTB - 1) / kTB;
-  const double *Rb = trans ? Rrm : Rcm;
-  constexpr int TS = kTB * (kTB + 1);
-  {
-    const int blk = trans ? 0 : nb - 1, j0 = blk * kTB, len = min(n, j0 + kTB) - j0;
-    if (tid < kTB * kTB) tile[(tid / kTB) * (kTB + 1) + tid % kTB] = diag_entry(Rb, n, j0, len, tid);
-  }
-  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nt = blockDim.x;
+  const int nb = (n + 31) / 32;
   for (int bb = 0; bb < nb; bb++) {
     const int blk = trans ? bb : nb - 1 - bb;
-    const int j0 = blk * kTB, j1 = min(n, j0 + kTB), len = j1 - j0;
-    const double *tcur = tile + (bb & 1) * TS;
-    double *tnext = tile + ((bb + 1) & 1) * TS;
-    double tv = 0.0;
-    if (bb + 1 < nb && tid < kTB * kTB) {
-      const int nblk = trans ? bb + 1 : nb - 2 - bb, nj0 = nblk * kTB;
-      tv = diag_entry(Rb, n, nj0, min(n, nj0 + kTB) - nj0, tid);
+    const int j0 = blk * 32, j1 = min(n, j0 + 32), len = j1 - j0;
+    // stage the diagonal block: tile[jj][l] = column jj (trans 0) / row jj (trans 1) entry l
+    const double *src = trans ? Rrm : Rcm;
+    for (int e = threadIdx.x; e < 32 * 32; e += nt) {
+      const int jj = e >> 5, l = e & 31;
+      tile[jj * 33 + l] = (jj < len && l < len) ? src[(size_t)(j0 + jj) * n + j0 + l] : 0.0;
     }
-    const int ib = trans ? j1 : 0, ie = trans ? n : j0;
-    const int i = ib + tid;
-    const bool upd = i < ie;
-    double rv[kTB];
-#pragma unroll
-    for (int jj = 0; jj < kTB; jj++)
-      rv[jj] = (upd && jj < len) ? Rb[(size_t)(j0 + jj) * n + i] : 0.0;
+    __syncthreads();
     if (warp == 0) {
       double yl = (lane < len) ? sy[j0 + lane] : 0.0;
       const double ri = (lane < len) ? rinv[j0 + lane] : 0.0;
@@ -71,32 +41,35 @@ __device__ void block_trsv(const double *__restrict__ Rcm, const double *__restr
         for (int jj = len - 1; jj >= 0; jj--) {
           const double xj = __shfl_sync(0xffffffffu, yl * ri, jj);
           if (lane == jj) yl = xj;
-          else if (lane < jj) yl = fma(-tcur[jj * (kTB + 1) + lane], xj, yl);
+          else if (lane < jj) yl = fma(-tile[jj * 33 + lane], xj, yl);
         }
       } else {
         for (int jj = 0; jj < len; jj++) {
           const double xj = __shfl_sync(0xffffffffu, yl * ri, jj);
           if (lane == jj) yl = xj;
-          else if (lane > jj && lane < len) yl = fma(-tcur[jj * (kTB + 1) + lane], xj, yl);
+          else if (lane > jj && lane < len) yl = fma(-tile[jj * 33 + lane], xj, yl);
         }
       }
       if (lane < len) sy[j0 + lane] = yl;
     }
     __syncthreads();
-    // subtract the block's contribution from the remaining rows; four
-    // independent accumulators keep the FP64 FMA chains short
-    if (upd) {
+    // Remaining rows: subtract this block's contribution.  Four independent
+    // accumulators per row keep the FP64 FMA chains short (the FP64 pipe's
+    // latency, not its throughput, bounds a one-CTA solve).
+    const double *Rb = trans ? Rrm : Rcm;
+    const int ib = trans ? j1 : 0, ie = trans ? n : j0;
+    for (int i = ib + threadIdx.x; i < ie; i += nt) {
       double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-#pragma unroll
-      for (int jj = 0; jj < kTB; jj += 4) {
-        a0 = fma(rv[jj], (jj < len) ? sy[j0 + jj] : 0.0, a0);
-        a1 = fma(rv[jj + 1], (jj + 1 < len) ? sy[j0 + jj + 1] : 0.0, a1);
-        a2 = fma(rv[jj + 2], (jj + 2 < len) ? sy[j0 + jj + 2] : 0.0, a2);
-        a3 = fma(rv[jj + 3], (jj + 3 < len) ? sy[j0 + jj + 3] : 0.0, a3);
+      int j = j0;
+      for (; j + 3 < j1; j += 4) {
+        a0 = fma(Rb[(size_t)j * n + i], sy[j], a0);
+        a1 = fma(Rb[(size_t)(j + 1) * n + i], sy[j + 1], a1);
+        a2 = fma(Rb[(size_t)(j + 2) * n + i], sy[j + 2], a2);
+        a3 = fma(Rb[(size_t)(j + 3) * n + i], sy[j + 3], a3);
       }
+      for (; j < j1; j++) a0 = fma(Rb[(size_t)j * n + i], sy[j], a0);
       sy[i] -= (a0 + a1) + (a2 + a3);
     }
-    if (bb + 1 < nb && tid < kTB * kTB) tnext[(tid / kTB) * (kTB + 1) + tid % kTB] = tv;
     __syncthreads();
   }
 }
