@@ -225,16 +225,17 @@ __global__ void transpose_scale_kernel(const double *__restrict__ SAb, int n, in
 // ---------------------------------------------------------------------------
 // Gather form of the sketch pass.  The scatter above pays one L2 FP64 atomic
 // per element of A and target row (zeta per element); on GB300 those run at
-// ~0.6 G/s per ... SM slice and bound the pass.  The gather form inverts the
+// about 0.6 G/s and bound the pass.  The gather form inverts the
 // pattern once per plan into source lists (CSR by sketch row h: the rows i
 // of A with h among their zeta rows, sorted by i) and gives each sketch row
 // to one warp, which walks its list and sums the +-rows of A in registers.
-// The sums are 64-bit fixed point per column: every entry is rounded once to
-// a multiple of 2^F_j, F_j = E_j + L - 62 (|A_ij| < 2^E_j, L = bits of the
+// The sums are 64-bit fixed point per column: every entry is truncated once
+// to a multiple of 2^F_j, F_j = E_j + L - 63 (|A_ij| < 2^E_j, L = bits of the
 // longest list), and added exactly, so the sketch is reproducible bit for
 // bit whatever the order, and each entry of S[A b] is the exact sum of the
-// rounded terms, rounded once to FP64 (error <= 2^-52 max_i |A_ij| per term
-// plus one final rounding).  All warps of one column chunk sweep A in row
+// truncated terms, rounded once to FP64 (error < 2^(L-62) max_i |A_ij| per
+// term, 2^-51 max_i |A_ij| for lists under 2^11 entries, plus one final
+// rounding).  All warps of one column chunk sweep A in row
 // order together, so the zeta reads of a row mostly hit L2.
 // ---------------------------------------------------------------------------
 
@@ -413,9 +414,12 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
 
 // Fixed-point parameters per column (and b at index npad): with E = the
 // largest biased exponent (|a| < 2^(E - 1022)) and L = max(10, bits of the
-// longest list), F = (E - 1022) + L - 62, cshift = 1075 + F (the right shift
-// of a 53-bit significand with biased exponent e is cshift - e >= 1) and
-// cpow = 2^F.  A NaN or Inf (E = 2047) sets st->nonfinite.
+// longest list), F = (E - 1022) + L - 63, cshift = 1075 + F (the right shift
+// of a 53-bit significand with biased exponent e is cshift - e >= 0) and
+// cpow = 2^F.  Each term is truncated to a multiple of 2^F, an error below
+// 2^F <= 2^(L-62) max |a| (2^-51 max |a| for lists under 2^11 entries), and
+// is below 2^(63-L) units in magnitude, so sums of up to 2^L - 1 terms fit in
+// 63 bits.  A NaN or Inf (E = 2047) sets st->nonfinite.
 __global__ void fixed_params_kernel(const int *__restrict__ colexp, int n, int npad,
                                     const int *__restrict__ lmax, int *cshift, double *cpow,
                                     DevState *st) {
@@ -426,22 +430,21 @@ __global__ void fixed_params_kernel(const int *__restrict__ colexp, int n, int n
   if (colexp[j] == 2047) atomicExch(&st->nonfinite, 1);
   int L = 10;
   while (L < 40 && (1ll << L) <= (long long)*lmax) L++;
-  const int F = (E - 1022) + L - 62;
+  const int F = (E - 1022) + L - 63;
   cshift[j] = 1075 + F;
   cpow[j] = ldexp(1.0, F);
 }
 
-// Rounded a / 2^F as a signed 64-bit integer (round half away from zero),
-// negated when neg; C = 1075 + F.
-__device__ __forceinline__ long long to_fixed(double a, int C, unsigned neg) {
+// acc += (+-) trunc(|a| / 2^F) with C = 1075 + F, the sign flipped when neg:
+// integer operations only.  Zeros and subnormals (exponent field 0) add 0.
+__device__ __forceinline__ void add_fixed(long long &acc, double a, int C, unsigned neg) {
   const unsigned hw = (unsigned)__double2hiint(a), lw = (unsigned)__double2loint(a);
-  const int e = (int)((hw >> 20) & 0x7ffu);
-  const unsigned mh = (hw & 0xfffffu) | (e != 0 ? 0x100000u : 0u);
-  const int s = C - (e != 0 ? e : 1);  // >= 1 by the choice of F
-  const unsigned long long mant = ((unsigned long long)mh << 32) | lw;
-  const unsigned long long t = (s <= 64) ? (mant >> (s - 1)) : 0ull;
-  const long long q = (long long)((t + 1ull) >> 1);
-  return ((hw >> 31) ^ neg) ? -q : q;
+  const unsigned e = (hw >> 20) & 0x7ffu;
+  const unsigned sh = e ? (unsigned)(C - (int)e) : 127u;
+  const unsigned long long mant = ((unsigned long long)((hw & 0xfffffu) | 0x100000u) << 32) | lw;
+  const unsigned long long t = (sh < 64u) ? (mant >> sh) : 0ull;
+  const unsigned long long m = 0ull - (unsigned long long)((hw >> 31) ^ neg);  // 0 or ~0
+  acc += (long long)((t ^ m) - m);
 }
 
 template <int CH>
@@ -454,43 +457,51 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c0 = blockIdx.y * CH * 64;
   for (int i = threadIdx.x; i < CH * 64; i += blockDim.x)
-    sh[i] = (c0 + i < n) ? cshift[c0 + i] : 4096;
+    sh[i] = (c0 + i < n) ? cshift[c0 + i] : 0;
   __syncthreads();
   const int h = blockIdx.x * kGatherWarps + warp;
   if (h >= d) return;
   const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 2 == 0);
   const bool dob = (b != nullptr && blockIdx.y == 0);
   const int shb = dob ? cshift[npad] : 0;
+  int shl[2 * CH];
+#pragma unroll
+  for (int k = 0; k < CH; k++) {
+    shl[2 * k] = sh[64 * k + 2 * lane];
+    shl[2 * k + 1] = sh[64 * k + 2 * lane + 1];
+  }
   long long acc[2 * CH];
 #pragma unroll
   for (int k = 0; k < 2 * CH; k++) acc[k] = 0;
   long long accb = 0;
-  const int64_t p1 = ptr[h + 1];
-  for (int64_t p = ptr[h]; p < p1; p++) {
-    const uint32_t e = __ldg(src + p);
-    const int64_t i = e & 0x7fffffffu;
-    const unsigned neg = e >> 31;
-    const double *row = A + i * lda + c0;
-    double a[2 * CH];
+  const int64_t pend = ptr[h + 1];
+  for (int64_t p0 = ptr[h]; p0 < pend; p0 += 32) {
+    // 32 list entries with one coalesced load, handed out by shuffles
+    const uint32_t mine = (p0 + lane < pend) ? __ldg(src + p0 + lane) : 0u;
+    const int cnt = (int)min((int64_t)32, pend - p0);
+#pragma unroll 1
+    for (int q = 0; q < cnt; q++) {
+      const uint32_t e = __shfl_sync(0xffffffffu, mine, q);
+      const int64_t i = e & 0x7fffffffu;
+      const unsigned neg = e >> 31;
+      const double *row = A + i * lda + c0;
+      double a[2 * CH];
 #pragma unroll
-    for (int k = 0; k < CH; k++) {
-      const int col = 64 * k + 2 * lane;
-      if (vec && c0 + col + 1 < n) {
-        const double2 v = __ldg(reinterpret_cast<const double2 *>(row + col));
-        a[2 * k] = v.x;
-        a[2 * k + 1] = v.y;
-      } else {
-        a[2 * k] = (c0 + col < n) ? __ldg(row + col) : 0.0;
-        a[2 * k + 1] = (c0 + col + 1 < n) ? __ldg(row + col + 1) : 0.0;
+      for (int k = 0; k < CH; k++) {
+        const int col = 64 * k + 2 * lane;
+        if (vec && c0 + col + 1 < n) {
+          const double2 v = __ldg(reinterpret_cast<const double2 *>(row + col));
+          a[2 * k] = v.x;
+          a[2 * k + 1] = v.y;
+        } else {
+          a[2 * k] = (c0 + col < n) ? __ldg(row + col) : 0.0;
+          a[2 * k + 1] = (c0 + col + 1 < n) ? __ldg(row + col + 1) : 0.0;
+        }
       }
-    }
 #pragma unroll
-    for (int k = 0; k < CH; k++) {
-      const int col = 64 * k + 2 * lane;
-      acc[2 * k] += to_fixed(a[2 * k], sh[col], neg);
-      acc[2 * k + 1] += to_fixed(a[2 * k + 1], sh[col + 1], neg);
+      for (int k = 0; k < 2 * CH; k++) add_fixed(acc[k], a[k], shl[k], neg);
+      if (dob && lane == 0) add_fixed(accb, __ldg(b + i), shb, neg);
     }
-    if (dob && lane == 0) accb += to_fixed(__ldg(b + i), shb, neg);
   }
   double *out = SAb + (size_t)h * (n + 1);
 #pragma unroll
@@ -611,13 +622,13 @@ cudaError_t launch_sketch_gather(const double *A, int64_t lda, int n, const doub
                                                               st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int ch = npad >= 256 ? 4 : npad / 64;
+  // 128 columns per warp (48 registers): a whole column chunk's d warps are
+  // resident at once on 152 SMs for d up to ~6000, so they sweep A together
+  const int ch = npad >= 128 ? 2 : 1;
   const dim3 grid((unsigned)((d + kGatherWarps - 1) / kGatherWarps),
                   (unsigned)((n + 64 * ch - 1) / (64 * ch)));
   const int th = kGatherWarps * 32;
-  if (ch == 4)
-    gather_kernel<4><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb);
-  else if (ch == 2)
+  if (ch == 2)
     gather_kernel<2><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb);
   else
     gather_kernel<1><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb);

@@ -7,9 +7,9 @@
 // One CTA per solve: the vector lives in shared memory; R (n x n) is read
 // from L2 in both layouts so that every access is coalesced -- column j of R
 // (column-major copy) for R x = y, row j of R (row-major copy) for R^T x = y.
-// Blocked by 32: warp 0 solves each 32 x 32 diagonal block with shuffles,
-// then the whole CTA subtracts the block's contribution from the rest, so a
-// solve costs ceil(n/32) block barriers.  x_j = y_j * (1 / R_jj) with the
+// Blocked by 32: warp 0 solves each 32 x 32 diagonal block with shuffles
+// while other warps subtract the previous block's contribution from the
+// remaining rows (see block_trsv).  x_j = y_j * (1 / R_jj) with the
 // reciprocals computed once per factorisation; that perturbs each diagonal
 // entry by at most two roundings, so the solve stays backward stable.
 #include "lsq_common.cuh"
@@ -18,60 +18,138 @@ namespace lsq {
 
 namespace {
 
-// tile: 32 x 33 doubles of shared memory for the diagonal block.
+static_assert(kVecThreads == 1024, "block_trsv's warp roles assume 32 warps");
+static_assert(LSQ_MAX_N <= 24 * 32 * 2, "bulk warps take at most two rows per round");
+
+constexpr int kSolveThreads = 32 + 24 * 32;  // the solver warp and the 24 bulk warps
+constexpr int kTile = 32 * 33;               // one 32 x 32 tile, padded rows
+
+__device__ __forceinline__ void bar_arrive(int id) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kSolveThreads) : "memory");
+}
+__device__ __forceinline__ void bar_wait(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kSolveThreads) : "memory");
+}
+__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Warp-level asynchronous copy of a 32 x 32 tile of R into shared memory:
+// dst[jj * 33 + l] = Rb[(c0 + jj) * n + r0 + l] for jj < ncol, l < nrow, else 0.
+__device__ __forceinline__ void tile_async(double *dst, const double *__restrict__ Rb, int n,
+                                           int c0, int ncol, int r0, int nrow, int lane) {
+  for (int jj = 0; jj < 32; jj++) {
+    if (jj < ncol && lane < nrow) cp_async8(dst + jj * 33 + lane, Rb + (size_t)(c0 + jj) * n + r0 + lane);
+    else dst[jj * 33 + lane] = 0.0;
+  }
+}
+
+// Solve R x = y (trans 0; blocks last to first) or R^T x = y (trans 1; first
+// to last) in place on sy (n doubles of shared memory); tile: 3 kTile
+// doubles of shared memory.  Blocks of 32.  Roles (1024 threads):
+//   * warp 0, the solver: for each block, the serial chain on the diagonal
+//     tile, then the "lookahead" update of the next block's rows with the
+//     block's x.  The diagonal and off-diagonal tiles it needs next are
+//     fetched with asynchronous copies while it works.
+//   * 24 bulk warps (warp % 4 != 0, so none shares warp 0's scheduler): the
+//     update of every row beyond the next block with the block's x.
+//   * the other 7 warps wait at the final barrier.
+// The solver hands x of round r to the bulk warps with a named barrier
+// (bar.arrive / bar.sync), and before its lookahead of round r waits for
+// the bulk update of round r-1 (the same rows).  Rounds alternate between
+// two barrier ids per direction, so an arrival for round r+2 can never fall
+// into round r's barrier.  The solver's chain therefore overlaps the bulk
+// update, whose FP64 work sets the pace only in the first rounds.
 __device__ void block_trsv(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
                            const double *__restrict__ rinv, int n, int trans, double *sy,
                            double *tile) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nt = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = (n + 31) / 32;
-  for (int bb = 0; bb < nb; bb++) {
-    const int blk = trans ? bb : nb - 1 - bb;
-    const int j0 = blk * 32, j1 = min(n, j0 + 32), len = j1 - j0;
-    // stage the diagonal block: tile[jj][l] = column jj (trans 0) / row jj (trans 1) entry l
-    const double *src = trans ? Rrm : Rcm;
-    for (int e = threadIdx.x; e < 32 * 32; e += nt) {
-      const int jj = e >> 5, l = e & 31;
-      tile[jj * 33 + l] = (jj < len && l < len) ? src[(size_t)(j0 + jj) * n + j0 + l] : 0.0;
-    }
-    __syncthreads();
-    if (warp == 0) {
+  const double *Rb = trans ? Rrm : Rcm;
+  double *otile = tile + 2 * kTile;
+  if (warp == 0) {
+    const int blk0 = trans ? 0 : nb - 1, j00 = blk0 * 32, len0 = min(n, j00 + 32) - j00;
+    tile_async(tile, Rb, n, j00, len0, j00, len0, lane);
+    cp_async_commit();
+    for (int r = 0; r < nb; r++) {
+      const int blk = trans ? r : nb - 1 - r;
+      const int j0 = blk * 32, len = min(n, j0 + 32) - j0;
+      const bool has_next = r + 1 < nb;
+      const int nblk = trans ? r + 1 : nb - 2 - r;
+      const int nj0 = nblk * 32, nlen = has_next ? min(n, nj0 + 32) - nj0 : 0;
+      const double *dt = tile + (r & 1) * kTile;
+      __syncwarp();
+      if (has_next) {
+        tile_async(tile + ((r + 1) & 1) * kTile, Rb, n, nj0, nlen, nj0, nlen, lane);
+        tile_async(otile, Rb, n, j0, len, nj0, nlen, lane);  // rows of the next block
+      }
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncwarp();
       double yl = (lane < len) ? sy[j0 + lane] : 0.0;
       const double ri = (lane < len) ? rinv[j0 + lane] : 0.0;
       if (!trans) {
         for (int jj = len - 1; jj >= 0; jj--) {
           const double xj = __shfl_sync(0xffffffffu, yl * ri, jj);
           if (lane == jj) yl = xj;
-          else if (lane < jj) yl = fma(-tile[jj * 33 + lane], xj, yl);
+          else if (lane < jj) yl = fma(-dt[jj * 33 + lane], xj, yl);
         }
       } else {
         for (int jj = 0; jj < len; jj++) {
           const double xj = __shfl_sync(0xffffffffu, yl * ri, jj);
           if (lane == jj) yl = xj;
-          else if (lane > jj && lane < len) yl = fma(-tile[jj * 33 + lane], xj, yl);
+          else if (lane > jj && lane < len) yl = fma(-dt[jj * 33 + lane], xj, yl);
         }
       }
       if (lane < len) sy[j0 + lane] = yl;
-    }
-    __syncthreads();
-    // Remaining rows: subtract this block's contribution.  Four independent
-    // accumulators per row keep the FP64 FMA chains short (the FP64 pipe's
-    // latency, not its throughput, bounds a one-CTA solve).
-    const double *Rb = trans ? Rrm : Rcm;
-    const int ib = trans ? j1 : 0, ie = trans ? n : j0;
-    for (int i = ib + threadIdx.x; i < ie; i += nt) {
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int j = j0;
-      for (; j + 3 < j1; j += 4) {
-        a0 = fma(Rb[(size_t)j * n + i], sy[j], a0);
-        a1 = fma(Rb[(size_t)(j + 1) * n + i], sy[j + 1], a1);
-        a2 = fma(Rb[(size_t)(j + 2) * n + i], sy[j + 2], a2);
-        a3 = fma(Rb[(size_t)(j + 3) * n + i], sy[j + 3], a3);
+      __syncwarp();
+      bar_arrive(1 + (r & 1));              // x of this block is in sy
+      if (r >= 1) bar_wait(3 + ((r - 1) & 1));  // bulk update of round r-1 done
+      if (has_next) {
+        cp_async_wait<0>();
+        __syncwarp();
+        if (lane < nlen) {
+          double a0 = 0.0, a1 = 0.0;
+          for (int jj = 0; jj + 1 < len; jj += 2) {
+            a0 = fma(otile[jj * 33 + lane], sy[j0 + jj], a0);
+            a1 = fma(otile[(jj + 1) * 33 + lane], sy[j0 + jj + 1], a1);
+          }
+          if (len & 1) a0 = fma(otile[(len - 1) * 33 + lane], sy[j0 + len - 1], a0);
+          sy[nj0 + lane] -= a0 + a1;
+        }
       }
-      for (; j < j1; j++) a0 = fma(Rb[(size_t)j * n + i], sy[j], a0);
-      sy[i] -= (a0 + a1) + (a2 + a3);
     }
-    __syncthreads();
+    bar_wait(3 + ((nb - 1) & 1));  // the bulk warps' last round
+  } else if (warp & 3) {
+    const int bt = (warp - 1 - (warp >> 2)) * 32 + lane;  // 0 .. 767
+    for (int r = 0; r < nb; r++) {
+      const int blk = trans ? r : nb - 1 - r;
+      const int j0 = blk * 32, j1 = min(n, j0 + 32), len = j1 - j0;
+      // rows beyond the next block
+      const int lo = trans ? min(n, j1 + 32) : 0, hi = trans ? n : max(0, j0 - 32);
+      bar_wait(1 + (r & 1));
+      for (int i = lo + bt; i < hi; i += 24 * 32) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int jj = 0;
+        for (; jj + 3 < len; jj += 4) {
+          a0 = fma(Rb[(size_t)(j0 + jj) * n + i], sy[j0 + jj], a0);
+          a1 = fma(Rb[(size_t)(j0 + jj + 1) * n + i], sy[j0 + jj + 1], a1);
+          a2 = fma(Rb[(size_t)(j0 + jj + 2) * n + i], sy[j0 + jj + 2], a2);
+          a3 = fma(Rb[(size_t)(j0 + jj + 3) * n + i], sy[j0 + jj + 3], a3);
+        }
+        for (; jj < len; jj++) a0 = fma(Rb[(size_t)(j0 + jj) * n + i], sy[j0 + jj], a0);
+        sy[i] -= (a0 + a1) + (a2 + a3);
+      }
+      bar_arrive(3 + (r & 1));
+    }
   }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kVecThreads)
@@ -180,7 +258,7 @@ cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv
                         const double *out_scale, double *out_scaled, double *accum,
                         double *norm2_out, const DevState *gate, cudaStream_t s, int batch,
                         int64_t bstride) {
-  const size_t smem = (size_t)(n + 32 + 32 * 33) * sizeof(double);
+  const size_t smem = (size_t)(n + 32 + 3 * kTile) * sizeof(double);
   trsv_kernel<<<batch, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, n, trans, y, in_scale, out,
                                                out_scale, out_scaled, accum, norm2_out, gate,
                                                bstride);
@@ -189,7 +267,7 @@ cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv
 
 cudaError_t launch_condest(const double *Rcm, const double *Rrm, const double *rinv, int n,
                            int iters, DevState *st, cudaStream_t s) {
-  const size_t smem = (size_t)(2 * n + 32 + 32 * 33) * sizeof(double);
+  const size_t smem = (size_t)(2 * n + 32 + 3 * kTile) * sizeof(double);
   condest_kernel<<<1, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, n, iters, st);
   return cudaGetLastError();
 }

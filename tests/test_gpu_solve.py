@@ -195,3 +195,21 @@ def test_plan_configure_retargets_without_allocation():
     with pytest.raises(lsq.LsqError):
         lsq.lsq_plan_configure(plan.handle, lsq.lsq_options_default(m=40000, n=128))
     plan.close()
+
+
+@pytest.mark.parametrize("method", ["fossils", "spir"])
+@pytest.mark.parametrize("kappa,resid", [(1e13, 1e-6), (1e14, 1e-2), (1e15, 1e-6)])
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_high_condition(method, kappa, resid, fp64):
+    """Fig. 1's construction (20000 x 100) up to kappa = 1e15, with the
+    default double-float inner pass and with the all-FP64 pass: the
+    backward error stays <= 1e-13.  At kappa = 1e15 the library flags the
+    problem as numerically rank deficient (status 2) and still returns the
+    answer."""
+    P = problem_svd(20000, 100, kappa, resid, seed=3)
+    A, b = P["A"], P["b"]
+    st, info, x = _gpu_solve(method, A, b, seed=9, inner_fp64_fma=fp64)
+    assert st in (0, lsq.LSQ_WARN_RANK_DEFICIENT)
+    assert info["inner_kernel"] == (0 if fp64 else 3)
+    _, R_A = oracle.qr_solve(A, b, return_R=True)
+    assert oracle.kw_relative(A, b, x, R_A=R_A) <= 1e-13, info
