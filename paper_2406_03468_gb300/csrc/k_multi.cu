@@ -262,8 +262,7 @@ static cudaError_t multi_dispatch(const double *A, int64_t lda, int64_t m, int n
 #define LSQ_MULTI_CASE(NT_)                                                                  \
   case NT_: {                                                                                \
     auto fn = multi_pass_kernel<NT_, RESID>;                                                 \
-    e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                             (int)smem);                                                     \
+    e = ensure_smem_attr((const void *)fn, (int)smem);                                       \
     if (e != cudaSuccess) return e;                                                          \
     fn<<<grid, kMultiThreads, smem, s>>>(A, lda, m, n, np8, Z, B, ldb, part, r2part, gate);   \
     break;                                                                                   \

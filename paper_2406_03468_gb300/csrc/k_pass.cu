@@ -223,20 +223,107 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
 // The FP64 pipe only sees the flushes (1/8 of an add per element), so the
 // pass is no longer capped by GB300's FP64 rate.  z is scaled by a common
 // power of two 2^-Fz; h is scaled back.
+//
+// Rows reach shared memory by TMA bulk copies (cp.async.bulk with mbarrier
+// completion), kDfStages rows per warp in flight: lane 0 of each warp issues
+// the copies of the rows its warp will process next while the warp computes
+// on the current one, so the bytes in flight no longer depend on registers.
+// Every mbarrier wait is bounded (kDfWaitNs); on a timeout the kernel
+// records LSQ_ERR_TIMEOUT, waits (bounded) for its copies in flight and
+// returns.
 // ---------------------------------------------------------------------------
 constexpr int kDfFlush = 8;
+constexpr int kDfStages = 2;
+constexpr uint64_t kDfWaitNs = 1000ull * 1000 * 1000;  // 1 s
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(bar)),
+               "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"((unsigned)__cvta_generic_to_shared(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase; false after kDfWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, phase))
+    if (global_ns() - t0 > kDfWaitNs) return false;
+  return true;
+}
+
+// L2 policy for data read once (the planes stream through L2 34 times per
+// solve and would otherwise evict R and the partial sums the small kernels
+// between passes read).
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                         uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+      "l"(src), "r"(bytes), "r"((unsigned)__cvta_generic_to_shared(bar)), "l"(pol)
+      : "memory");
+}
 
 template <int NC>
 __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     atax_df_kernel(const float *__restrict__ Ahi, const float *__restrict__ Alo, int64_t ld32,
                    int64_t m, int n, const double *__restrict__ z, double *__restrict__ part,
-                   int npad, const DevState *gate) {
+                   int npad, const DevState *gate, int *err) {
   if (gate != nullptr && *(volatile const int *)&gate->done) return;
-  extern __shared__ double hacc[];  // [warps][NC * 64] FP64 flush accumulators
+  // dynamic shared memory: [warps][NC*64] FP64 flush accumulators, then
+  // [warps][kDfStages][2][NC*64] FP32 row stages (hi, lo), then the mbarriers
+  extern __shared__ __align__(16) double hacc[];
   __shared__ double wmax[kPassThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float *stages = reinterpret_cast<float *>(hacc + (size_t)nw * NC * 64);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(stages + (size_t)nw * kDfStages * 2 * NC * 64);
+  float *wst = stages + (size_t)warp * kDfStages * 2 * NC * 64;
+  uint64_t *wbar = bars + warp * kDfStages;
   const int64_t per = (m + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = min(m, (int64_t)blockIdx.x * per), r1 = min(m, r0 + per);
+  const int64_t nrows = (r1 - r0 - warp + nw - 1) / nw > 0 ? (r1 - r0 - warp + nw - 1) / nw : 0;
+  const unsigned row_bytes = (unsigned)(ld32 * sizeof(float));
+  if (lane == 0) {
+    for (int st = 0; st < kDfStages; st++) mbar_init(wbar + st, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  // lane 0: bulk copies of the warp's q-th row (hi and lo) into stage q % kDfStages
+  const uint64_t pol = l2_evict_first();
+  auto issue = [&](int64_t q) {
+    if (lane == 0 && q < nrows) {
+      const int64_t i = r0 + warp + q * nw;
+      const int stg = (int)(q % kDfStages);
+      float *dh = wst + (size_t)stg * 2 * NC * 64;
+      mbar_expect_tx(wbar + stg, 2 * row_bytes);
+      bulk_g2s(dh, Ahi + i * ld32, row_bytes, wbar + stg, pol);
+      bulk_g2s(dh + NC * 64, Alo + i * ld32, row_bytes, wbar + stg, pol);
+    }
+  };
+  for (int64_t q = 0; q < kDfStages; q++) issue(q);
+
   double *hw = hacc + (size_t)warp * NC * 64;
   for (int i = lane; i < NC * 64; i += 32) hw[i] = 0.0;
   double zr[2 * NC];
@@ -263,46 +350,57 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     hl[k] = 0.0f;
   }
   int blk = 0;
-  for (int64_t i = r0 + warp; i < r1; i += nw) {
-    const float *rh = Ahi + i * ld32;
-    const float *rl = Alo + i * ld32;
+  bool ok = true;
+  for (int64_t q = 0; q < nrows; q++) {
+    const int stg = (int)(q % kDfStages);
+    if (!mbar_wait(wbar + stg, (unsigned)((q / kDfStages) & 1))) {
+      ok = false;
+      break;
+    }
+    const float *rh = wst + (size_t)stg * 2 * NC * 64;
+    const float *rl = rh + NC * 64;
     float ah[2 * NC], al[2 * NC];
 #pragma unroll
     for (int k = 0; k < NC; k++) {
       const int col = 64 * k + 2 * lane;
       if (col + 1 < n) {
-        const float2 vh = __ldcs(reinterpret_cast<const float2 *>(rh + col));
-        const float2 vl = __ldcs(reinterpret_cast<const float2 *>(rl + col));
+        const float2 vh = *reinterpret_cast<const float2 *>(rh + col);
+        const float2 vl = *reinterpret_cast<const float2 *>(rl + col);
         ah[2 * k] = vh.x;
         ah[2 * k + 1] = vh.y;
         al[2 * k] = vl.x;
         al[2 * k + 1] = vl.y;
       } else {
-        ah[2 * k] = (col < n) ? __ldcs(rh + col) : 0.0f;
-        al[2 * k] = (col < n) ? __ldcs(rl + col) : 0.0f;
+        ah[2 * k] = (col < n) ? rh[col] : 0.0f;
+        al[2 * k] = (col < n) ? rl[col] : 0.0f;
         ah[2 * k + 1] = 0.0f;
         al[2 * k + 1] = 0.0f;
       }
     }
+    // every lane has its values: the stage may be refilled (generic reads
+    // before the async-proxy writes of the next copy)
+    __syncwarp();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(q + kDfStages);
     float sh_ = 0.0f, sl_ = 0.0f;
 #pragma unroll
     for (int k = 0; k < 2 * NC; k++) {
       const float p = __fmul_rn(ah[k], zh[k]);
       const float e = __fmaf_rn(ah[k], zh[k], -p);
       const float c = __fmaf_rn(ah[k], zl[k], __fmaf_rn(al[k], zh[k], e));
-      float s, err;
-      two_sum_f(sh_, p, s, err);
+      float s, er;
+      two_sum_f(sh_, p, s, er);
       sh_ = s;
-      sl_ = __fadd_rn(sl_, __fadd_rn(err, c));
+      sl_ = __fadd_rn(sl_, __fadd_rn(er, c));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float oh = __shfl_xor_sync(0xffffffffu, sh_, o);
       const float ol = __shfl_xor_sync(0xffffffffu, sl_, o);
-      float s, err;
-      two_sum_f(sh_, oh, s, err);
+      float s, er;
+      two_sum_f(sh_, oh, s, er);
       sh_ = s;
-      sl_ = __fadd_rn(__fadd_rn(sl_, ol), err);
+      sl_ = __fadd_rn(__fadd_rn(sl_, ol), er);
     }
     // renormalise t (Fast2Sum: |sh_| >= |sl_| after the sums above)
     const float th = __fadd_rn(sh_, sl_);
@@ -312,9 +410,9 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
       const float p = __fmul_rn(ah[k], th);
       const float e = __fmaf_rn(ah[k], th, -p);
       const float c = __fmaf_rn(ah[k], tl, __fmaf_rn(al[k], th, e));
-      float s, err;
-      two_sum_f(hh[k], p, s, err);
-      const float l = __fadd_rn(hl[k], __fadd_rn(err, c));
+      float s, er;
+      two_sum_f(hh[k], p, s, er);
+      const float l = __fadd_rn(hl[k], __fadd_rn(er, c));
       const float s2 = __fadd_rn(s, l);
       hl[k] = __fsub_rn(l, __fsub_rn(s2, s));
       hh[k] = s2;
@@ -329,6 +427,12 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
         hh[2 * k] = hl[2 * k] = hh[2 * k + 1] = hl[2 * k + 1] = 0.0f;
       }
     }
+  }
+  if (!ok) {
+    // record the error; let the copies this warp has in flight land before
+    // the CTA's shared memory is released (bounded again)
+    if (lane == 0 && err != nullptr) atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
+    for (int st = 0; st < kDfStages; st++) mbar_wait(wbar + st, 0), mbar_wait(wbar + st, 1);
   }
 #pragma unroll
   for (int k = 0; k < NC; k++) {
@@ -518,15 +622,18 @@ cudaError_t launch_pass_atax_eft(const double *A, int64_t lda, int64_t m, int n,
 
 cudaError_t launch_pass_atax_df(const float *Ahi, const float *Alo, int64_t ld32, int64_t m, int n,
                                 const double *z, double *part, int grid, int npad,
-                                const DevState *gate, cudaStream_t s) {
-  const size_t smem = (size_t)(kPassThreads / 32) * npad * sizeof(double);
+                                const DevState *gate, int *err, cudaStream_t s) {
+  const int nw = kPassThreads / 32;
+  const size_t smem = (size_t)nw * npad * sizeof(double) +
+                      (size_t)nw * kDfStages * 2 * npad * sizeof(float) +
+                      (size_t)nw * kDfStages * sizeof(uint64_t);
   LSQ_PASS_SWITCH(npad, {
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute((const void *)atax_df_kernel<NC>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = ensure_smem_attr((const void *)atax_df_kernel<NC>, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    atax_df_kernel<NC><<<grid, kPassThreads, smem, s>>>(Ahi, Alo, ld32, m, n, z, part, npad, gate);
+    atax_df_kernel<NC><<<grid, kPassThreads, smem, s>>>(Ahi, Alo, ld32, m, n, z, part, npad, gate,
+                                                        err);
   });
   return cudaGetLastError();
 }

@@ -329,7 +329,7 @@ template <bool SMEM, int VR>
 cudaError_t launch_qr_t(void **args, int grid, size_t smem, cudaStream_t s) {
   const void *fn = (const void *)qr_kernel<SMEM, VR>;
   if (SMEM) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_attr(fn, (int)smem);
     if (e != cudaSuccess) return e;
   }
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kQrThreads), args, SMEM ? smem : 0, s);

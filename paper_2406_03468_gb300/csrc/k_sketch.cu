@@ -582,8 +582,7 @@ cudaError_t launch_sketch_lists(const int32_t *rows, const uint32_t *signbits, i
   tgt_scan_kernel<<<1, 1024, 0, s>>>(cnt, d, ptr, lmax);
   tgt_fill_kernel<<<blocks, 256, 0, s>>>(rows, signbits, m, zeta, d, ptr, cnt, src);
   const size_t smem = sizeof(uint32_t) * kSortMax;
-  e = cudaFuncSetAttribute((const void *)tgt_sort_kernel,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = ensure_smem_attr((const void *)tgt_sort_kernel, (int)smem);
   if (e != cudaSuccess) return e;
   tgt_sort_kernel<<<d, 512, smem, s>>>(ptr, src);
   return cudaGetLastError();

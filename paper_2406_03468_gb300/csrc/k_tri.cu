@@ -40,12 +40,12 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Warp-level asynchronous copy of a 32 x 32 tile of R into shared memory:
-// dst[jj * 33 + l] = Rb[(c0 + jj) * n + r0 + l] for jj < ncol, l < nrow, else 0.
-__device__ __forceinline__ void tile_async(double *dst, const double *__restrict__ Rb, int n,
+// Warp-level asynchronous copy of a 32 x 32 tile into shared memory:
+// dst[jj * 33 + l] = src[(c0 + jj) * ld + r0 + l] for jj < ncol, l < nrow, else 0.
+__device__ __forceinline__ void tile_async(double *dst, const double *__restrict__ src, int ld,
                                            int c0, int ncol, int r0, int nrow, int lane) {
   for (int jj = 0; jj < 32; jj++) {
-    if (jj < ncol && lane < nrow) cp_async8(dst + jj * 33 + lane, Rb + (size_t)(c0 + jj) * n + r0 + lane);
+    if (jj < ncol && lane < nrow) cp_async8(dst + jj * 33 + lane, src + (size_t)(c0 + jj) * ld + r0 + lane);
     else dst[jj * 33 + lane] = 0.0;
   }
 }
@@ -67,15 +67,16 @@ __device__ __forceinline__ void tile_async(double *dst, const double *__restrict
 // into round r's barrier.  The solver's chain therefore overlaps the bulk
 // update, whose FP64 work sets the pace only in the first rounds.
 __device__ void block_trsv(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
-                           const double *__restrict__ rinv, int n, int trans, double *sy,
-                           double *tile) {
+                           const double *__restrict__ rinv, const double *__restrict__ Dt, int n,
+                           int trans, double *sy, double *tile) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = (n + 31) / 32;
   const double *Rb = trans ? Rrm : Rcm;
+  const double *Db = Dt + (size_t)trans * nb * 1024;  // this direction's scaled diagonal blocks
   double *otile = tile + 2 * kTile;
   if (warp == 0) {
-    const int blk0 = trans ? 0 : nb - 1, j00 = blk0 * 32, len0 = min(n, j00 + 32) - j00;
-    tile_async(tile, Rb, n, j00, len0, j00, len0, lane);
+    const int blk0 = trans ? 0 : nb - 1;
+    tile_async(tile, Db + (size_t)blk0 * 1024, 32, 0, 32, 0, 32, lane);
     cp_async_commit();
     for (int r = 0; r < nb; r++) {
       const int blk = trans ? r : nb - 1 - r;
@@ -86,28 +87,27 @@ __device__ void block_trsv(const double *__restrict__ Rcm, const double *__restr
       const double *dt = tile + (r & 1) * kTile;
       __syncwarp();
       if (has_next) {
-        tile_async(tile + ((r + 1) & 1) * kTile, Rb, n, nj0, nlen, nj0, nlen, lane);
+        tile_async(tile + ((r + 1) & 1) * kTile, Db + (size_t)nblk * 1024, 32, 0, 32, 0, 32, lane);
         tile_async(otile, Rb, n, j0, len, nj0, nlen, lane);  // rows of the next block
       }
       cp_async_commit();
       cp_async_wait<1>();
       __syncwarp();
-      double yl = (lane < len) ? sy[j0 + lane] : 0.0;
-      const double ri = (lane < len) ? rinv[j0 + lane] : 0.0;
+      // the block's rows scaled by 1 / R_ll: with the tile pre-scaled the
+      // same way, each step of the chain is one shuffle and one FMA
+      double zl = (lane < len) ? sy[j0 + lane] * rinv[j0 + lane] : 0.0;
       if (!trans) {
         for (int jj = len - 1; jj >= 0; jj--) {
-          const double xj = __shfl_sync(0xffffffffu, yl * ri, jj);
-          if (lane == jj) yl = xj;
-          else if (lane < jj) yl = fma(-dt[jj * 33 + lane], xj, yl);
+          const double xj = __shfl_sync(0xffffffffu, zl, jj);
+          if (lane < jj) zl = fma(-dt[jj * 33 + lane], xj, zl);
         }
       } else {
         for (int jj = 0; jj < len; jj++) {
-          const double xj = __shfl_sync(0xffffffffu, yl * ri, jj);
-          if (lane == jj) yl = xj;
-          else if (lane > jj && lane < len) yl = fma(-dt[jj * 33 + lane], xj, yl);
+          const double xj = __shfl_sync(0xffffffffu, zl, jj);
+          if (lane > jj && lane < len) zl = fma(-dt[jj * 33 + lane], xj, zl);
         }
       }
-      if (lane < len) sy[j0 + lane] = yl;
+      if (lane < len) sy[j0 + lane] = zl;
       __syncwarp();
       bar_arrive(1 + (r & 1));              // x of this block is in sy
       if (r >= 1) bar_wait(3 + ((r - 1) & 1));  // bulk update of round r-1 done
@@ -154,7 +154,8 @@ __device__ void block_trsv(const double *__restrict__ Rcm, const double *__restr
 
 __global__ void __launch_bounds__(kVecThreads)
     trsv_kernel(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
-                const double *__restrict__ rinv, int n, int trans, const double *y,
+                const double *__restrict__ rinv, const double *__restrict__ Dt, int n, int trans,
+                const double *y,
                 const double *in_scale, double *out, const double *out_scale, double *out_scaled,
                 double *accum, double *norm2_out, const DevState *gate, int64_t bstride) {
   if (gate != nullptr && *(volatile const int *)&gate->done) return;
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kVecThreads)
   for (int i = threadIdx.x; i < n; i += blockDim.x)
     sy[i] = in_scale ? y[i] * in_scale[i] : y[i];
   __syncthreads();
-  block_trsv(Rcm, Rrm, rinv, n, trans, sy, tile);
+  block_trsv(Rcm, Rrm, rinv, Dt, n, trans, sy, tile);
   double nrm = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double x = sy[i];
@@ -218,7 +219,8 @@ __device__ double block_normalize(double *sv, int n, double *scratch) {
 // iteration on (R^T R)^{-1}, from a fixed start vector.
 __global__ void __launch_bounds__(kVecThreads)
     condest_kernel(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
-                   const double *__restrict__ rinv, int n, int iters, DevState *st) {
+                   const double *__restrict__ rinv, const double *__restrict__ Dt, int n, int iters,
+                   DevState *st) {
   extern __shared__ double sm[];
   double *v = sm, *y = sm + n, *scratch = sm + 2 * n, *tile = scratch + 32;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.0 + 0.25 * (double)((i * 7919) % 17);
@@ -238,10 +240,10 @@ __global__ void __launch_bounds__(kVecThreads)
   block_normalize(v, n, scratch);
   double winv = 0.0;
   for (int it = 0; it <= iters; it++) {
-    block_trsv(Rcm, Rrm, rinv, n, 1, v, tile);  // v <- R^{-T} v
+    block_trsv(Rcm, Rrm, rinv, Dt, n, 1, v, tile);  // v <- R^{-T} v
     winv = block_normalize(v, n, scratch);
     if (it == iters) break;
-    block_trsv(Rcm, Rrm, rinv, n, 0, v, tile);  // v <- R^{-1} v
+    block_trsv(Rcm, Rrm, rinv, Dt, n, 0, v, tile);  // v <- R^{-1} v
     block_normalize(v, n, scratch);
   }
   if (threadIdx.x == 0) {
@@ -251,24 +253,47 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
+// Dt[t][b][jj][l] = (t ? Rrm : Rcm)[(32b + jj) n + 32b + l] / R_(32b+l)(32b+l):
+// block b's diagonal tile for R x = y (t = 0) or R^T x = y (t = 1), each
+// entry scaled by the reciprocal diagonal of the row it updates; zero
+// outside the block.  One CTA of 1024 threads per (t, b).
+__global__ void __launch_bounds__(1024)
+    diag_tiles_kernel(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
+                      const double *__restrict__ rinv, int n, double *Dt) {
+  const int nb = (n + 31) / 32;
+  const int t = blockIdx.x / nb, b = blockIdx.x % nb;
+  const int jj = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int j0 = b * 32, len = min(n, j0 + 32) - j0;
+  const double *Rb = t ? Rrm : Rcm;
+  Dt[(size_t)blockIdx.x * 1024 + threadIdx.x] =
+      (jj < len && l < len) ? Rb[(size_t)(j0 + jj) * n + j0 + l] * rinv[j0 + l] : 0.0;
+}
+
 }  // namespace
 
-cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv, int n, int trans,
+cudaError_t launch_diag_tiles(const double *Rcm, const double *Rrm, const double *rinv, int n,
+                              double *Dt, cudaStream_t s) {
+  diag_tiles_kernel<<<2 * ((n + 31) / 32), 1024, 0, s>>>(Rcm, Rrm, rinv, n, Dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv, const double *Dt,
+                        int n, int trans,
                         const double *y, const double *in_scale, double *out,
                         const double *out_scale, double *out_scaled, double *accum,
                         double *norm2_out, const DevState *gate, cudaStream_t s, int batch,
                         int64_t bstride) {
   const size_t smem = (size_t)(n + 32 + 3 * kTile) * sizeof(double);
-  trsv_kernel<<<batch, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, n, trans, y, in_scale, out,
+  trsv_kernel<<<batch, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, Dt, n, trans, y, in_scale, out,
                                                out_scale, out_scaled, accum, norm2_out, gate,
                                                bstride);
   return cudaGetLastError();
 }
 
-cudaError_t launch_condest(const double *Rcm, const double *Rrm, const double *rinv, int n,
-                           int iters, DevState *st, cudaStream_t s) {
+cudaError_t launch_condest(const double *Rcm, const double *Rrm, const double *rinv,
+                           const double *Dt, int n, int iters, DevState *st, cudaStream_t s) {
   const size_t smem = (size_t)(2 * n + 32 + 3 * kTile) * sizeof(double);
-  condest_kernel<<<1, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, n, iters, st);
+  condest_kernel<<<1, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, Dt, n, iters, st);
   return cudaGetLastError();
 }
 

@@ -15,6 +15,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "lsq_common.cuh"
@@ -74,6 +76,7 @@ struct lsq_plan_s {
   double *cpow = nullptr;
   double *SAb = nullptr, *W = nullptr, *part = nullptr, *r2part = nullptr, *cpart = nullptr;
   double *dcol = nullptr, *dinv = nullptr, *Rcm = nullptr, *Rrm = nullptr, *rinv = nullptr;
+  double *Dt = nullptr;  // scaled diagonal blocks of R (launch_diag_tiles)
   double *t = nullptr, *vbuf = nullptr;
   double *xs = nullptr, *xo = nullptr, *c = nullptr, *g = nullptr, *dy = nullptr;
   double *dyold = nullptr, *z = nullptr, *h = nullptr, *w = nullptr, *res = nullptr, *p = nullptr;
@@ -100,6 +103,20 @@ struct lsq_plan_s {
   std::vector<cudaEvent_t> tev;     // timing: pass begin/end event pairs
   int tev_used = 0;
 };
+
+cudaError_t lsq::ensure_smem_attr(const void *fn, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, int> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  int &have = done[{dev, fn}];
+  if (have >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
 
 namespace {
 
@@ -303,16 +320,17 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
   LSQ_CU(launch_sketch_finalize(P->cpart, P->gpass, P->npad, n, P->d, P->zeta, P->o.col_scale,
                                 P->SAb, P->W, P->dcol, P->dinv, P->st, P->s));
   LSQ_CU(cudaEventRecord(P->ev[1], P->s));
-  P->launches += 3 + 4;  // sketch, colnorm, transpose; qr, extract, condest, x0 solve
+  P->launches += 3 + 5;  // sketch, colnorm, transpose; qr, extract, tiles, condest, x0 solve
   if (P->stepwise_qr)
     LSQ_CU(launch_qr_stepwise(P->W, P->d, n, n + 1, P->vbuf, qr_grid(n + 1, P->nsm), P->s));
   else
     LSQ_CU(launch_qr(P->W, P->d, n, n + 1, P->vbuf, P->qflag, next_epoch(P), P->st,
                      qr_grid(n + 1, P->nsm), kBarrierTimeoutNs, P->s));
   LSQ_CU(launch_extract_r(P->W, P->d, n, 1, P->Rcm, P->Rrm, P->rinv, P->t, P->s));
-  LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, n, kCondestIters, P->st, P->s));
+  LSQ_CU(launch_diag_tiles(P->Rcm, P->Rrm, P->rinv, n, P->Dt, P->s));
+  LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, P->Dt, n, kCondestIters, P->st, P->s));
   // sketch-and-solve x0 = R^{-1} t (scaled coordinates) and x0 / d (original)
-  LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->t, nullptr, P->xs, P->dinv, P->xo,
+  LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 0, P->t, nullptr, P->xs, P->dinv, P->xo,
                      nullptr, &P->st->x0norm2, nullptr, P->s));
   LSQ_CU(cudaEventRecord(P->ev[2], P->s));
   LSQ_CU(cudaMemcpyAsync(P->dcol_host, P->dcol, sizeof(double) * n, cudaMemcpyDeviceToHost, P->s));
@@ -358,7 +376,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->g, P->r2part, &P->st->r2,
                          nullptr, P->s));
     passes++;
-    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 1, P->g, nullptr, P->c, nullptr, nullptr,
+    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 1, P->g, nullptr, P->c, nullptr, nullptr,
                        nullptr, &P->st->cnorm2[i], nullptr, P->s));
     if (i == 0) LSQ_CU(launch_set_thresh(gam, rho, P->st, P->s));
     bytes_a += mn8;
@@ -378,7 +396,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     for (int it = 0; it < cap; it++) {
       const double *src = (method == 0) ? P->dy : P->p;
       // z = D^{-1} R^{-1} src;  h = D^{-1} A^T (A z);  w = R^{-T} h
-      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, src, nullptr, nullptr, P->dinv, P->z,
+      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 0, src, nullptr, nullptr, P->dinv, P->z,
                          nullptr, nullptr, P->st, P->s));
       int tj = -1;
       if (P->o.timing) {
@@ -391,7 +409,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
                                   P->st, P->s));
       else if (P->use_df)
         LSQ_CU(launch_pass_atax_df(P->Ahi, P->Alo, P->ld32, P->m, n, P->z, P->part, P->gpass,
-                                   P->npad, P->st, P->s));
+                                   P->npad, P->st, &P->st->err, P->s));
       else if (P->use_eft)
         LSQ_CU(launch_pass_atax_eft(dA, P->lda, P->m, n, P->z, P->col_exp, P->part, P->gpass,
                                     P->npad, P->st, P->s));
@@ -402,7 +420,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
       P->launches += 5;
       LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->h, nullptr, nullptr, P->st,
                            P->s));
-      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 1, P->h, nullptr, P->w, nullptr, nullptr,
+      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 1, P->h, nullptr, P->w, nullptr, nullptr,
                          nullptr, nullptr, P->st, P->s));
       if (method == 0)
         LSQ_CU(launch_polyak_update(n, P->c, P->w, P->dy, P->dyold, P->st, P->s));
@@ -414,7 +432,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
       }
     }
     // x_s += R^{-1} dy ; x_o = D^{-1} x_s
-    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->dy, nullptr, nullptr, P->dinv, P->xo,
+    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 0, P->dy, nullptr, nullptr, P->dinv, P->xo,
                        P->xs, nullptr, nullptr, P->s));
     P->launches++;
     LSQ_TRY(read_state(P));
@@ -505,11 +523,12 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
   LSQ_CU(launch_qr(P->W, d, n, n + k, P->vbuf, P->qflag, next_epoch(P), P->st,
                    qr_grid(n + k, P->nsm), kBarrierTimeoutNs, P->s));
   LSQ_CU(launch_extract_r(P->W, d, n, k, P->Rcm, P->Rrm, P->rinv, P->mT, P->s));
-  LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, n, kCondestIters, P->st, P->s));
-  LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->mT, nullptr, P->mXs, P->dinv, P->mXo,
+  LSQ_CU(launch_diag_tiles(P->Rcm, P->Rrm, P->rinv, n, P->Dt, P->s));
+  LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, P->Dt, n, kCondestIters, P->st, P->s));
+  LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 0, P->mT, nullptr, P->mXs, P->dinv, P->mXo,
                      nullptr, x0n2, nullptr, P->s, k, n));
   LSQ_CU(cudaEventRecord(P->ev[2], P->s));
-  P->launches += 11;
+  P->launches += 12;
   LSQ_TRY(read_state(P));
   if (P->st_host->nonfinite) return fail(LSQ_ERR_NONFINITE, "A or B holds NaN or Inf");
   if (P->st_host->zero_col) return fail(LSQ_ERR_INVALID, "A has a zero column (column scaling)");
@@ -525,7 +544,7 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
                               P->nsm, P->s));
     LSQ_CU(launch_multi_reduce(P->mpart, P->nsm, n, k, P->dinv, P->mG, P->mr2part, r2, nullptr,
                                P->s));
-    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 1, P->mG, nullptr, P->mC, nullptr, nullptr,
+    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 1, P->mG, nullptr, P->mC, nullptr, nullptr,
                        nullptr, cn2, nullptr, P->s, k, n));
     if (i == 0)
       LSQ_CU(launch_multi_thresh(k, P->o.stop_gamma, P->o.stop_rho, x0n2, r2, thr, P->st, P->s));
@@ -535,7 +554,7 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
     LSQ_CU(launch_multi_init(n, k, P->mC, P->mDY, P->mDYold, cap, use_thresh, P->st, P->s));
     P->launches += 5;
     for (int it = 0; it < cap; it++) {
-      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->mDY, nullptr, nullptr, P->dinv, P->mZ,
+      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 0, P->mDY, nullptr, nullptr, P->dinv, P->mZ,
                          nullptr, nullptr, P->st, P->s, k, n));
       int tj = -1;
       if (P->o.timing) {
@@ -547,7 +566,7 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
       if (tj >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tj + 1], P->s));
       LSQ_CU(launch_multi_reduce(P->mpart, P->nsm, n, k, P->dinv, P->mH, nullptr, nullptr, P->st,
                                  P->s));
-      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 1, P->mH, nullptr, P->mW, nullptr, nullptr,
+      LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 1, P->mH, nullptr, P->mW, nullptr, nullptr,
                          nullptr, nullptr, P->st, P->s, k, n));
       LSQ_CU(launch_multi_polyak(n, k, P->mC, P->mW, P->mDY, P->mDYold, dn2, thr, P->st, P->s));
       P->launches += 6;
@@ -556,7 +575,7 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
         if (P->st_host->done) break;
       }
     }
-    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, n, 0, P->mDY, nullptr, nullptr, P->dinv, P->mXo,
+    LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 0, P->mDY, nullptr, nullptr, P->dinv, P->mXo,
                        P->mXs, nullptr, nullptr, P->s, k, n));
     P->launches++;
     LSQ_CU(cudaMemcpyAsync(hc.data(), cn2, sizeof(double) * k, cudaMemcpyDeviceToHost, P->s));
@@ -635,7 +654,7 @@ void configure_fields(lsq_plan P, const lsq_options *opt) {
 void free_plan(lsq_plan P) {
   if (!P) return;
   void *bufs[] = {P->pat_rows, P->pat_sb, P->SAb, P->W, P->part, P->r2part, P->cpart, P->dcol, P->dinv,
-                  P->Rcm, P->Rrm, P->rinv, P->t, P->vbuf, P->xs, P->xo, P->c, P->g, P->dy,
+                  P->Rcm, P->Rrm, P->rinv, P->Dt, P->t, P->vbuf, P->xs, P->xo, P->c, P->g, P->dy,
                   P->dyold, P->z, P->h, P->w, P->res, P->p, P->st, P->qflag, P->stageA,
                   P->stageb, P->stagex, P->Ahi, P->Alo, P->SBb, P->cpartB, P->mpart, P->mr2part,
                   P->mT, P->mXs, P->mXo, P->mC, P->mG, P->mDY, P->mDYold, P->mZ, P->mH,
@@ -727,6 +746,7 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   A(dalloc(&P->Rcm, nn));
   A(dalloc(&P->Rrm, nn));
   A(dalloc(&P->rinv, n));
+  A(dalloc(&P->Dt, (size_t)2 * ((n + 31) / 32) * 1024));
   A(dalloc(&P->t, n));
   A(dalloc(&P->vbuf, 2 * (size_t)P->d_cap));
   double **vecs[] = {&P->xs, &P->xo, &P->c, &P->g, &P->dy, &P->dyold, &P->z, &P->h, &P->w, &P->res, &P->p};
@@ -885,14 +905,14 @@ lsq_status lsq_apply_normal(lsq_plan P, const double *dA, const double *dz, doub
   const int n = (int)P->n;
   if (P->sketched && P->use_df)
     LSQ_CU(launch_pass_atax_df(P->Ahi, P->Alo, P->ld32, P->m, n, dz, P->part, P->gpass, P->npad,
-                               nullptr, P->s));
+                               nullptr, &P->st->err, P->s));
   else if (P->sketched && P->use_eft)
     LSQ_CU(launch_pass_atax_eft(dA, P->lda, P->m, n, dz, P->col_exp, P->part, P->gpass, P->npad,
                                 nullptr, P->s));
   else
     LSQ_CU(launch_pass_atax(dA, P->lda, P->m, n, dz, P->part, P->gpass, P->npad, nullptr, P->s));
   LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, nullptr, dh, nullptr, nullptr, nullptr, P->s));
-  LSQ_CU(cudaStreamSynchronize(P->s));
+  LSQ_TRY(read_state(P));
   return LSQ_OK;
 }
 
@@ -910,7 +930,7 @@ lsq_status lsq_residual(lsq_plan P, const double *dA, const double *db, const do
 lsq_status lsq_trsv(lsq_plan P, int trans, const double *dy, double *dx) {
   if (!P || !dy || !dx) return fail(LSQ_ERR_INVALID, "NULL argument");
   if (!P->sketched) return fail(LSQ_ERR_INVALID, "call lsq_sketch first");
-  LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, (int)P->n, trans ? 1 : 0, dy, nullptr, dx, nullptr,
+  LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, (int)P->n, trans ? 1 : 0, dy, nullptr, dx, nullptr,
                      nullptr, nullptr, nullptr, nullptr, P->s));
   LSQ_CU(cudaStreamSynchronize(P->s));
   return LSQ_OK;

@@ -64,6 +64,11 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// cudaFuncSetAttribute(fn, MaxDynamicSharedMemorySize, bytes) once per
+// (device, kernel, size): the call costs host time, and the inner loop
+// launches its pass dozens of times per solve (lsq_api.cu).
+cudaError_t ensure_smem_attr(const void *fn, int bytes);
+
 // Message returned by lsq_last_error() on the calling thread (lsq_api.cu).
 void set_last_error(const char *msg);
 
@@ -129,8 +134,13 @@ cudaError_t launch_qr_stepwise(double *W, int d, int n, int ncols, double *vhead
 cudaError_t launch_extract_r(const double *W, int d, int n, int nb, double *Rcm, double *Rrm,
                              double *rinv, double *t, cudaStream_t s);
 // condest / normest of R by power and inverse power iteration.
-cudaError_t launch_condest(const double *Rcm, const double *Rrm, const double *rinv, int n,
-                           int iters, DevState *st, cudaStream_t s);
+cudaError_t launch_condest(const double *Rcm, const double *Rrm, const double *rinv,
+                           const double *Dt, int n, int iters, DevState *st, cudaStream_t s);
+// Dt (2 ceil(n/32) 1024 doubles): the diagonal 32 x 32 blocks of R for both
+// solve directions with each entry scaled by 1 / R_ll of the row it updates
+// (the triangular solves run the block chains on these).
+cudaError_t launch_diag_tiles(const double *Rcm, const double *Rrm, const double *rinv, int n,
+                              double *Dt, cudaStream_t s);
 // Triangular solve on one CTA.  trans 0: R x = y, 1: R^T x = y.
 //   y_eff = y (* in_scale if given); sol = solution;
 //   accum != NULL:   accum += sol, out = accum, out_scaled = out_scale * accum
@@ -138,7 +148,8 @@ cudaError_t launch_condest(const double *Rcm, const double *Rrm, const double *r
 //   norm2_out != NULL: *norm2_out = ||out||^2
 //   gate != NULL: return at once when gate->done.
 //   batch > 1: CTA b solves the vectors at offset b * bstride (norm2_out[b]).
-cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv, int n, int trans,
+cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv, const double *Dt,
+                        int n, int trans,
                         const double *y, const double *in_scale, double *out,
                         const double *out_scale, double *out_scaled, double *accum,
                         double *norm2_out, const DevState *gate, cudaStream_t s, int batch = 1,
@@ -159,10 +170,12 @@ cudaError_t launch_pass_atax32(const float *A32, int64_t ld32, int64_t m, int n,
                                double *part, int grid, int npad, const DevState *gate,
                                cudaStream_t s);
 // Inner pass on the hi / lo FP32 planes: row and column sums both in
-// double-float on the FP32 pipe (column sums flushed into FP64 every 8 rows).
+// double-float on the FP32 pipe (column sums flushed into FP64 every 8 rows);
+// rows staged by TMA bulk copies.  ld32: a multiple of 4 (16-byte rows);
+// Ahi / Alo 16-byte aligned.  err: LSQ_ERR_TIMEOUT if a copy never landed.
 cudaError_t launch_pass_atax_df(const float *Ahi, const float *Alo, int64_t ld32, int64_t m, int n,
                                 const double *z, double *part, int grid, int npad,
-                                const DevState *gate, cudaStream_t s);
+                                const DevState *gate, int *err, cudaStream_t s);
 cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, const double *b,
                               const double *x, double *part, double *r2_part, int grid, int npad,
                               cudaStream_t s);
