@@ -85,6 +85,11 @@ struct lsq_plan_s {
   int *qflag = nullptr;              // QR: per-column "reflector published" flags
   int qr_epoch = 0;                  // value the flags take in the current QR launch
   cudaEvent_t ev[5] = {};
+  // condest runs on a second stream, overlapping x0, the first residual and
+  // c0 on the main one; the main stream joins it before the step-1 threshold
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool condest_pending = false;
   double *stageA = nullptr, *stageb = nullptr, *stagex = nullptr;
   bool sketched = false;
   bool use_eft = false;              // inner pass on the FP32 pipe
@@ -225,6 +230,15 @@ lsq_status ensure_pattern(lsq_plan P) {
   return LSQ_OK;
 }
 
+// Order the main stream after the condest launched by do_sketch.
+lsq_status join_condest(lsq_plan P) {
+  if (P->condest_pending) {
+    LSQ_CU(cudaStreamWaitEvent(P->s, P->ev_join, 0));
+    P->condest_pending = false;
+  }
+  return LSQ_OK;
+}
+
 lsq_status read_state(lsq_plan P) {
   LSQ_CU(cudaMemcpyAsync(P->st_host, P->st, sizeof(DevState), cudaMemcpyDeviceToHost, P->s));
   LSQ_CU(cudaStreamSynchronize(P->s));
@@ -291,6 +305,7 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
   const int n = (int)P->n;
   P->launches = 0;
   P->tev_used = 0;
+  LSQ_TRY(join_condest(P));  // a previous call that failed early may have left one running
   // fresh device state with alpha, beta
   std::memset(P->st_host, 0, sizeof(DevState));
   P->st_host->alpha = P->alpha;
@@ -328,7 +343,11 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
                      qr_grid(n + 1, P->nsm), kBarrierTimeoutNs, P->s));
   LSQ_CU(launch_extract_r(P->W, P->d, n, 1, P->Rcm, P->Rrm, P->rinv, P->t, P->s));
   LSQ_CU(launch_diag_tiles(P->Rcm, P->Rrm, P->rinv, n, P->Dt, P->s));
-  LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, P->Dt, n, kCondestIters, P->st, P->s));
+  LSQ_CU(cudaEventRecord(P->ev_fork, P->s));
+  LSQ_CU(cudaStreamWaitEvent(P->s2, P->ev_fork, 0));
+  LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, P->Dt, n, kCondestIters, P->st, P->s2));
+  LSQ_CU(cudaEventRecord(P->ev_join, P->s2));
+  P->condest_pending = true;
   // sketch-and-solve x0 = R^{-1} t (scaled coordinates) and x0 / d (original)
   LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 0, P->t, nullptr, P->xs, P->dinv, P->xo,
                      nullptr, &P->st->x0norm2, nullptr, P->s));
@@ -347,13 +366,18 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
   if (!dx) return fail(LSQ_ERR_INVALID, "x is NULL");
   const int n = (int)P->n;
   LSQ_TRY(do_sketch(P, dA, db));
-  const double condest = P->st_host->condest;
   const int max_inner = P->o.max_inner ? P->o.max_inner : 100;
   const int nref = P->o.max_refine ? P->o.max_refine : 2;
-  const int q2 = step2_updates(condest, P->eta, max_inner);
   const double gam = P->o.stop_gamma, rho = P->o.stop_rho;
+  // the FP32 tier is chosen on condest up front; the FP64 path needs it only
+  // for the step-1 threshold (device) and the step-2 count (host, later)
+  if (P->o.precision == LSQ_PREC_AUTO || P->o.precision == LSQ_PREC_FP32_INNER) {
+    LSQ_TRY(join_condest(P));
+    LSQ_TRY(read_state(P));
+  }
   const bool tier = tier_ok(P);
-  const int q32 = tier_updates(condest, P->eta, max_inner);
+  const int q32 = tier ? tier_updates(P->st_host->condest, P->eta, max_inner) : 0;
+  int q2 = -1;  // set from condest once step 1 has read the device state
   const int nsteps_max = tier ? std::min(LSQ_MAX_REFINE, std::max(nref, 6)) : nref;
   const double mn8 = 8.0 * (double)P->m * (double)n;
   double bytes_a = mn8 + (P->want32 ? mn8 : 0.0);  // sketch pass (+ hi / lo planes)
@@ -378,7 +402,11 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     passes++;
     LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 1, P->g, nullptr, P->c, nullptr, nullptr,
                        nullptr, &P->st->cnorm2[i], nullptr, P->s));
-    if (i == 0) LSQ_CU(launch_set_thresh(gam, rho, P->st, P->s));
+    if (i == 0) {
+      LSQ_TRY(join_condest(P));
+      LSQ_CU(launch_set_thresh(gam, rho, P->st, P->s));
+    }
+    if (i == 1 && q2 < 0) q2 = step2_updates(P->st_host->condest, P->eta, max_inner);
     bytes_a += mn8;
     if (tier) {
       // refine until ||c_i|| stops halving (the FP64 residual's noise floor)
@@ -666,6 +694,9 @@ void free_plan(lsq_plan P) {
   if (P->dcol_host) cudaFreeHost(P->dcol_host);
   for (auto &e : P->ev)
     if (e) cudaEventDestroy(e);
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
+  if (P->s2) cudaStreamDestroy(P->s2);
   for (auto &e : P->tev) cudaEventDestroy(e);
   delete P;
 }
@@ -763,6 +794,9 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
     P->want32 = true;
   }
   for (auto &ev : P->ev) A(cudaEventCreate(&ev));
+  A(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+  A(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+  A(cudaStreamCreateWithFlags(&P->s2, cudaStreamNonBlocking));
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);
     free_plan(P);
@@ -818,7 +852,9 @@ lsq_status lsq_plan_configure(lsq_plan plan, const lsq_options *opt) {
 
 lsq_status lsq_sketch(lsq_plan plan, const double *dA, const double *db) {
   if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
-  return do_sketch(plan, dA, db);
+  LSQ_TRY(do_sketch(plan, dA, db));
+  LSQ_TRY(join_condest(plan));
+  return read_state(plan);
 }
 
 lsq_status lsq_solve_fossils(lsq_plan plan, const double *dA, const double *db, double *dx,
