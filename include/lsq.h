@@ -177,8 +177,11 @@ lsq_status lsq_solve_host(lsq_plan plan, int method, const double *hA, const dou
 
 /* Rows and signs of S: d_rows (m x zeta int32, device), d_signbits (m
  * uint32, device; bit k set => the k-th nonzero of column j is -1).  The
- * embedding is the Philox4x64-10 spec of Sec. 4.2's sparse sign embedding
- * described in the design doc. */
+ * pattern of Sec. 4.2's sparse sign embedding, drawn with Philox4x64-10
+ * (Salmon et al. 2011): for column j, key (seed, 0) and counters (j, t, 0,
+ * 0), t = 0, 1, ...; each block gives eight 32-bit words, low half first; the
+ * first word of block 0 is the sign word, every later word u is a candidate
+ * row floor(u d / 2^32), taken unless already drawn, until zeta rows. */
 lsq_status lsq_sketch_pattern(lsq_plan plan, int32_t *d_rows, uint32_t *d_signbits);
 
 /* After lsq_sketch: copy the scaled sketch [SA Sb] (d x (n+1), column-major,

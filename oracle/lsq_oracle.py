@@ -12,7 +12,7 @@ oracle/liboracle.c; matrix-vector products with A use numpy (a library
 matvec serving as a step); sums are never blocked, fused or reordered beyond
 what the definition states.
 
-Readings of the paper that this oracle takes (each is listed in the design doc):
+Readings of the paper that this oracle takes (the CUDA path takes the same ones):
   * u = 2^-53 (unit roundoff of IEEE double, the standard model of Sec. 1.4).
   * alpha, beta from eta = sqrt(n/d) (Sec. 4.2), i.e. beta = eta^2,
     alpha = (1 - beta)^2 (Sec. 2.3, optimal coefficients); Alg. 4's "beta <- d/n" is read as n/d.

@@ -217,9 +217,9 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
 //         lo*z_hi added to the error word, TwoSum accumulation, double-float
 //         warp reduction;
 //   h_j += a_ij t_i      : the same products against t = t_hi + t_lo, each
-//         column a double-float accumulator renormalised after every row
-//         (Fast2Sum) and flushed into an FP64 shared-memory accumulator every
-//         8 rows, so the double-float part never sums more than 8 terms.
+//         column a double-float accumulator (TwoSum into the high word, the
+//         error terms into the low word) flushed into an FP64 shared-memory
+//         accumulator every 8 rows, so it never sums more than 8 terms.
 // The FP64 pipe only sees the flushes (1/8 of an add per element), so the
 // pass is no longer capped by GB300's FP64 rate.  z is scaled by a common
 // power of two 2^-Fz; h is scaled back.
@@ -382,16 +382,29 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     __syncwarp();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     issue(q + kDfStages);
-    float sh_ = 0.0f, sl_ = 0.0f;
+    // two independent double-float accumulators (even / odd k) halve the
+    // dependent TwoSum chain of the row product
+    float sh0 = 0.0f, sl0 = 0.0f, sh1 = 0.0f, sl1 = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 2 * NC; k++) {
-      const float p = __fmul_rn(ah[k], zh[k]);
-      const float e = __fmaf_rn(ah[k], zh[k], -p);
-      const float c = __fmaf_rn(ah[k], zl[k], __fmaf_rn(al[k], zh[k], e));
+    for (int k = 0; k < 2 * NC; k += 2) {
+      const float p0 = __fmul_rn(ah[k], zh[k]);
+      const float c0 = __fmaf_rn(ah[k], zl[k], __fmaf_rn(al[k], zh[k], __fmaf_rn(ah[k], zh[k], -p0)));
+      const float p1 = __fmul_rn(ah[k + 1], zh[k + 1]);
+      const float c1 = __fmaf_rn(ah[k + 1], zl[k + 1],
+                                 __fmaf_rn(al[k + 1], zh[k + 1], __fmaf_rn(ah[k + 1], zh[k + 1], -p1)));
       float s, er;
-      two_sum_f(sh_, p, s, er);
-      sh_ = s;
-      sl_ = __fadd_rn(sl_, __fadd_rn(er, c));
+      two_sum_f(sh0, p0, s, er);
+      sh0 = s;
+      sl0 = __fadd_rn(sl0, __fadd_rn(er, c0));
+      two_sum_f(sh1, p1, s, er);
+      sh1 = s;
+      sl1 = __fadd_rn(sl1, __fadd_rn(er, c1));
+    }
+    float sh_, sl_;
+    {
+      float er;
+      two_sum_f(sh0, sh1, sh_, er);
+      sl_ = __fadd_rn(__fadd_rn(sl0, sl1), er);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -405,17 +418,17 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     // renormalise t (Fast2Sum: |sh_| >= |sl_| after the sums above)
     const float th = __fadd_rn(sh_, sl_);
     const float tl = __fsub_rn(sl_, __fsub_rn(th, sh_));
+    // column sums: TwoSum into the high word, error terms into the low word;
+    // the low word only gathers kDfFlush rows of small terms before the FP64
+    // flush, so it is not renormalised row by row
 #pragma unroll
     for (int k = 0; k < 2 * NC; k++) {
       const float p = __fmul_rn(ah[k], th);
-      const float e = __fmaf_rn(ah[k], th, -p);
-      const float c = __fmaf_rn(ah[k], tl, __fmaf_rn(al[k], th, e));
+      const float c = __fmaf_rn(ah[k], tl, __fmaf_rn(al[k], th, __fmaf_rn(ah[k], th, -p)));
       float s, er;
       two_sum_f(hh[k], p, s, er);
-      const float l = __fadd_rn(hl[k], __fadd_rn(er, c));
-      const float s2 = __fadd_rn(s, l);
-      hl[k] = __fsub_rn(l, __fsub_rn(s2, s));
-      hh[k] = s2;
+      hh[k] = s;
+      hl[k] = __fadd_rn(hl[k], __fadd_rn(er, c));
     }
     if (++blk == kDfFlush) {
       blk = 0;

@@ -16,11 +16,11 @@
 // columns fit (d = 12n up to n ~ 600), lives in that CTA's shared memory
 // from start to end.  There is no grid-wide barrier: the owner of column k
 // publishes reflector k with a release store of a per-column flag, and a
-// CTA waits (bounded) only for the flag of the reflector it applies next.
-// The owner of column k+1 applies H_k to that column first and publishes
-// reflector k+1 at once (lookahead), then updates its other columns, so the
-// serial chain per step is one column update, one norm and one flag hand-off;
-// CTAs with no columns left leave early.
+// CTA waits (bounded) only for a reflector it has nothing else to do
+// without.  Each CTA serves its lowest unfactored column first and catches
+// its other columns up while it would otherwise wait (see qr_kernel), so
+// the serial chain per column is one column update, one norm and one flag
+// hand-off.
 #include "lsq_common.cuh"
 
 namespace lsq {
@@ -144,36 +144,26 @@ __device__ void apply_reflector_regs(double *const *cols, int cnt, int k, int d,
   __syncthreads();
 }
 
-// Bounded wait of the whole CTA for flag == epoch (thread 0 polls with
-// acquire loads).  false after timeout_ns (LSQ_ERR_TIMEOUT set) or when
-// another CTA has set an error.
-__device__ bool wait_flag(const int *flag, int epoch, int *err, uint64_t timeout_ns, int *s_ok) {
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    if (ld_acquire(flag) != epoch) {
-      const uint64_t t0 = global_ns();
-      while (ld_acquire(flag) != epoch) {
-        if (*(volatile int *)err != 0) {
-          ok = 0;
-          break;
-        }
-        if (global_ns() - t0 > timeout_ns) {
-          atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
-}
-
 // SMEM: the CTA's columns live in shared memory for the whole factorisation.
 // VR > 0 (d <= VR * kQrThreads): each thread holds its VR entries of the
 // current reflector in registers, so the L2 latency of reading it is paid
-// once per step instead of once per loop trip.
+// once per update instead of once per loop trip.
+//
+// Scheduling inside a CTA (thread 0 decides, the CTA executes):
+//   * the pivot is the CTA's lowest column whose reflector is not yet built;
+//     when it has received H_0 .. H_{j-1} its reflector is built and
+//     published at once;
+//   * when the reflector the pivot needs next is out, it is applied to the
+//     pivot alone if the pivot is the next column to be factored (the
+//     critical chain), else to every column of the CTA waiting for it;
+//   * while the pivot waits, the CTA catches up its other columns with the
+//     reflectors they lack (all already published);
+//   * only with nothing else to do does thread 0 wait (bounded) for a flag.
+// So the serial chain per column is one column update, one norm and one
+// flag hand-off, and the rest of each CTA's FP64 work fills its waits.
+constexpr int kQrMaxLocal = 32;  // columns per CTA (bit mask)
+enum { kQrDone = 0, kQrBuild = 1, kQrApply = 2, kQrFail = 3 };
+
 template <bool SMEM, int VR>
 __global__ void __launch_bounds__(kQrThreads, 1)
     qr_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
@@ -181,7 +171,8 @@ __global__ void __launch_bounds__(kQrThreads, 1)
   extern __shared__ double dsm[];
   __shared__ double red[kQrThreads / 32 * kQrBatch];
   __shared__ double wsh[kQrBatch];
-  __shared__ int s_ok;
+  __shared__ int s_act, s_k;
+  __shared__ unsigned s_mask;
   const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int nloc = (ncols - me + G - 1) / G;  // local columns j = me + l G
   auto colp = [&](int l) -> double * {
@@ -192,31 +183,115 @@ __global__ void __launch_bounds__(kQrThreads, 1)
       for (int i = tid; i < d; i += nt) dsm[(size_t)l * d + i] = W[(size_t)(me + l * G) * d + i];
     __syncthreads();
   }
+  // thread 0's bookkeeping: reflectors applied per local column, the pivot
+  int applied[kQrMaxLocal];
+  int piv = 0;  // local index of the lowest unbuilt reflector column (nloc: none)
+  if (tid == 0) {
+    for (int l = 0; l < kQrMaxLocal; l++) applied[l] = 0;
+    while (piv < nloc && me + piv * G >= n) piv++;
+  }
   double *cols[kQrBatch];
-  int made = -1;  // reflector built ahead (lookahead) and its u_1, beta
-  double uk_ahead = 0.0, beta_ahead = 0.0;
-  for (int k = 0; k < n; k++) {
-    const bool own = (k % G == me);
-    double uk, beta;
-    if (own && made != k) {  // reflector 0, or any the lookahead did not build
+  for (;;) {
+    if (tid == 0) {
+      int act = kQrDone, k = 0;
+      unsigned mask = 0;
+      auto target = [&](int l) { return (me + l * G < n) ? me + l * G : n; };
+      for (;;) {
+        const int jpiv = me + piv * G;
+        const bool has_piv = piv < nloc && jpiv < n;
+        if (has_piv && applied[piv] == jpiv) {
+          act = kQrBuild;
+          k = jpiv;
+          break;
+        }
+        // the reflector this CTA needs first, and the columns waiting for it.
+        // Columns after the pivot never run ahead of it, so with a pivot
+        // every reflector below applied[piv] is already out.
+        int kneed = n;
+        unsigned mneed = 0;
+        if (has_piv) {
+          kneed = applied[piv];
+          if (jpiv == kneed + 1) {
+            mneed = 1u << piv;  // the critical chain: the pivot alone
+          } else {
+            for (int l = piv; l < nloc; l++)
+              if (applied[l] == kneed && applied[l] < target(l)) mneed |= 1u << l;
+          }
+        } else {
+          for (int l = 0; l < nloc; l++)
+            if (applied[l] < target(l)) kneed = min(kneed, applied[l]);
+          if (kneed >= n) {
+            act = kQrDone;
+            break;
+          }
+          for (int l = 0; l < nloc; l++)
+            if (applied[l] == kneed && applied[l] < target(l)) mneed |= 1u << l;
+        }
+        if ((kneed % G == me) || ld_acquire(flags + kneed) == epoch) {
+          act = kQrApply;
+          k = kneed;
+          mask = mneed;
+          break;
+        }
+        // while it is not out: catch up columns that lag further behind
+        int k2 = kneed;
+        for (int l = 0; l < nloc; l++)
+          if (l != piv && applied[l] < target(l)) k2 = min(k2, applied[l]);
+        if (k2 < kneed) {
+          act = kQrApply;
+          k = k2;
+          for (int l = 0; l < nloc; l++)
+            if (l != piv && applied[l] == k2 && applied[l] < target(l)) mask |= 1u << l;
+          break;
+        }
+        // nothing to do until reflector kneed is out: bounded wait
+        const uint64_t t0 = global_ns();
+        bool ok = true;
+        while (ld_acquire(flags + kneed) != epoch) {
+          if (*(volatile int *)&st->err != 0 || global_ns() - t0 > timeout_ns) {
+            atomicCAS(&st->err, 0, (int)LSQ_ERR_TIMEOUT);
+            ok = false;
+            break;
+          }
+        }
+        if (!ok) {
+          act = kQrFail;
+          break;
+        }
+      }
+      if (act == kQrBuild) {
+        // this column is done once its reflector is out
+        do piv++;
+        while (piv < nloc && me + piv * G >= n);
+      } else if (act == kQrApply) {
+        for (int l = 0; l < nloc; l++)
+          if (mask & (1u << l)) applied[l]++;
+      }
+      s_act = act;
+      s_k = k;
+      s_mask = mask;
+    }
+    __syncthreads();
+    const int act = s_act, k = s_k;
+    const unsigned mask = s_mask;
+    if (act == kQrDone || act == kQrFail) break;
+    if (act == kQrBuild) {
+      double uk, beta;
       make_reflector(colp((k - me) / G), k, d, W + (size_t)k * d, vhead, SMEM, red, uk, beta);
       __syncthreads();
       if (tid == 0) {
         __threadfence();
         st_release(flags + k, epoch);
       }
-    } else if (own) {
-      uk = uk_ahead;
-      beta = beta_ahead;
+      continue;
     }
-    const int l0 = (k + 1 > me) ? (k + 1 - me + G - 1) / G : 0;  // first local column > k
-    if (l0 >= nloc) break;  // nothing left to update here
-    if (!own) {
-      if (!wait_flag(flags + k, epoch, &st->err, timeout_ns, &s_ok)) return;
-      uk = __ldcg(vhead + 2 * k);
-      beta = __ldcg(vhead + 2 * k + 1);
+    if (mask == 0) {  // (not produced by the schedule above; keeps the barrier pattern safe)
+      __syncthreads();
+      continue;
     }
-    // u of reflector k: this CTA's own copy of column k, or the published one
+    // apply H_k to the columns in mask; u from this CTA's own copy or the published one
+    const bool own = (k % G == me);
+    const double uk = __ldcg(vhead + 2 * k), beta = __ldcg(vhead + 2 * k + 1);
     const double *vk = own ? colp((k - me) / G) : W + (size_t)k * d;
     double vr[VR > 0 ? VR : 1];
     if (VR > 0) {
@@ -226,35 +301,22 @@ __global__ void __launch_bounds__(kQrThreads, 1)
         vr[r] = (i > k && i < d) ? (own ? vk[i] : __ldcg(vk + i)) : 0.0;
       }
     }
-    auto apply = [&](int cnt) {
+    unsigned rest = mask;
+    while (rest) {
+      int cnt = 0;
+      while (rest && cnt < kQrBatch) {
+        const int l = __ffs(rest) - 1;
+        rest &= rest - 1;
+        cols[cnt++] = colp(l);
+      }
       if (VR > 0) apply_reflector_regs(cols, cnt, k, d, vr, uk, beta, red, wsh);
       else if (own) apply_reflector<false>(cols, cnt, k, d, vk, uk, beta, red, wsh);
       else apply_reflector<true>(cols, cnt, k, d, vk, uk, beta, red, wsh);
-    };
-    int l = l0;
-    if (k + 1 < n && (k + 1) % G == me) {  // lookahead: H_k on column k+1, then reflector k+1
-      cols[0] = colp(l);
-      apply(1);
-      make_reflector(colp(l), k + 1, d, W + (size_t)(k + 1) * d, vhead, SMEM, red, uk_ahead,
-                     beta_ahead);
-      __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        st_release(flags + k + 1, epoch);
-      }
-      made = k + 1;
-      l++;
-    }
-    while (l < nloc) {
-      int cnt = 0;
-      for (; cnt < kQrBatch && l < nloc; cnt++, l++) cols[cnt] = colp(l);
-      apply(cnt);
     }
   }
-  if (SMEM) {
+  if (SMEM && s_act == kQrDone) {
     // R rows above the diagonal of the reflector columns, and the augmented
     // columns whole (rows k..d-1 of reflector column k went out at publish).
-    __syncthreads();
     for (int l2 = 0; l2 < nloc; l2++) {
       const int j = me + l2 * G;
       const int iend = (j < n) ? j : d;
@@ -348,6 +410,7 @@ cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vhead, int *fl
                       DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s) {
   void *args[] = {&W, &d, &n, &ncols, &vhead, &flags, &epoch, &st, &timeout_ns};
   const int nloc_max = (ncols + grid - 1) / grid;
+  if (nloc_max > kQrMaxLocal) return cudaErrorInvalidConfiguration;
   const size_t smem = (size_t)nloc_max * d * sizeof(double);
   if (smem <= kQrSmemMax) return launch_qr_vr<true>(args, d, grid, smem, s);
   return launch_qr_vr<false>(args, d, grid, 0, s);

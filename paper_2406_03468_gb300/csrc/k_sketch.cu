@@ -192,7 +192,7 @@ __global__ void colnorm_kernel(const double *__restrict__ part, int grid, int np
   const double nrm = sqrt(s);
   if (!isfinite(nrm)) atomicExch(&st->nonfinite, 1);
   if (col_scale && nrm == 0.0) atomicExch(&st->zero_col, 1);
-  dcol[j] = col_scale ? nrm : 1.0;
+  dcol[j] = nrm;  // the column norm, also when the scaling is off
   dinv[j] = col_scale ? 1.0 / nrm : 1.0;
 }
 

@@ -176,6 +176,9 @@ cudaError_t launch_pass_atax32(const float *A32, int64_t ld32, int64_t m, int n,
 cudaError_t launch_pass_atax_df(const float *Ahi, const float *Alo, int64_t ld32, int64_t m, int n,
                                 const double *z, double *part, int grid, int npad,
                                 const DevState *gate, int *err, cudaStream_t s);
+// Residual pass r = b - A x, partials of A^T r and of ||r||^2, all FP64.
+// (A^T r is a sum with heavy cancellation -- r is nearly orthogonal to
+// range(A) -- and its rounding reaches x through kappa^2, so it stays FP64.)
 cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, const double *b,
                               const double *x, double *part, double *r2_part, int grid, int npad,
                               cudaStream_t s);

@@ -234,3 +234,23 @@ def test_inner_kernel_choice_badly_scaled_columns():
         assert info["inner_kernel"] == expect
         assert oracle.kw_relative(Am, b, H(x)) <= 1e-13
         plan.close()
+
+
+@pytest.mark.parametrize("m,n", [(20011, 130), (4097, 1000)])
+def test_residual_pass_after_sketch(m, n):
+    """The residual pass after lsq_sketch (the state a solve runs it in), on
+    columns of mixed scale: g within the FP64 componentwise bound of the
+    compensated oracle, ||r||^2 to 1e-12 relative."""
+    rng = np.random.default_rng(m * 3 + n)
+    A = rng.standard_normal((m, n)) * np.exp2(rng.integers(-8, 8, size=n))
+    b = rng.standard_normal(m)
+    x = rng.standard_normal(n)
+    plan = lsq.Plan(m, n, seed=2)
+    dA, db = T(A), T(b)
+    lsq.lsq_sketch(plan.handle, dA, db)
+    g = empty(n)
+    r2 = lsq.lsq_residual(plan.handle, dA, db, T(x), g)
+    r_hi, r_lo, g_ref = oracle.residual_dot2(A, b, x)
+    bound = 4 * (n + m) * u * (np.abs(A).T @ (np.abs(b) + np.abs(A) @ np.abs(x)))
+    assert (np.abs(H(g) - g_ref) <= bound).all()
+    assert abs(r2 - float(r_hi @ r_hi)) <= 1e-12 * float(r_hi @ r_hi)
