@@ -27,7 +27,8 @@ namespace lsq {
 
 namespace {
 
-constexpr int kQrThreads = 512;
+constexpr int kQrThreads = 256;
+constexpr int kQrCtasPerSm = 2;  // two CTAs per SM: one's barriers overlap the other's FP64 work
 constexpr int kQrBatch = 8;  // columns updated together by one CTA
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -165,7 +166,7 @@ constexpr int kQrMaxLocal = 32;  // columns per CTA (bit mask)
 enum { kQrDone = 0, kQrBuild = 1, kQrApply = 2, kQrFail = 3 };
 
 template <bool SMEM, int VR>
-__global__ void __launch_bounds__(kQrThreads, 1)
+__global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
     qr_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
               int *flags, int epoch, DevState *st, uint64_t timeout_ns) {
   extern __shared__ double dsm[];
@@ -382,7 +383,7 @@ __global__ void extract_r_kernel(const double *__restrict__ W, int d, int n, int
 
 }  // namespace
 
-int qr_grid(int ncols, int nsm) { return ncols < nsm ? ncols : nsm; }
+int qr_grid(int ncols, int nsm) { return ncols < kQrCtasPerSm * nsm ? ncols : kQrCtasPerSm * nsm; }
 
 // Largest dynamic shared memory the columns may use (227 KB opt-in minus the static part).
 constexpr size_t kQrSmemMax = 225 * 1024;
@@ -409,10 +410,16 @@ cudaError_t launch_qr_vr(void **args, int d, int grid, size_t smem, cudaStream_t
 cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vhead, int *flags, int epoch,
                       DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s) {
   void *args[] = {&W, &d, &n, &ncols, &vhead, &flags, &epoch, &st, &timeout_ns};
-  const int nloc_max = (ncols + grid - 1) / grid;
-  if (nloc_max > kQrMaxLocal) return cudaErrorInvalidConfiguration;
-  const size_t smem = (size_t)nloc_max * d * sizeof(double);
-  if (smem <= kQrSmemMax) return launch_qr_vr<true>(args, d, grid, smem, s);
+  // columns in shared memory at kQrCtasPerSm CTAs per SM if they fit, else
+  // at one CTA per SM, else in global memory (L2) at kQrCtasPerSm per SM
+  auto smem_for = [&](int g) { return (size_t)((ncols + g - 1) / g) * d * sizeof(double); };
+  if (kQrCtasPerSm * smem_for(grid) <= kQrSmemMax) return launch_qr_vr<true>(args, d, grid, smem_for(grid), s);
+  const int g1 = (grid + kQrCtasPerSm - 1) / kQrCtasPerSm;
+  if (smem_for(g1) <= kQrSmemMax && (ncols + g1 - 1) / g1 <= kQrMaxLocal) {
+    void *args1[] = {&W, &d, &n, &ncols, &vhead, &flags, &epoch, &st, &timeout_ns};
+    return launch_qr_vr<true>(args1, d, g1, smem_for(g1), s);
+  }
+  if ((ncols + grid - 1) / grid > kQrMaxLocal) return cudaErrorInvalidConfiguration;
   return launch_qr_vr<false>(args, d, grid, 0, s);
 }
 
