@@ -11,10 +11,10 @@
 // of column k of W hold u (they are below R's triangle), and u_1, beta go to
 // a 2-per-column side array.
 //
-// GB300 design: one persistent cooperative launch, one CTA per SM.  Column
-// j belongs to CTA j mod G for the whole factorisation and, when the CTA's
-// columns fit (d = 12n up to n ~ 600), lives in that CTA's shared memory
-// from start to end.  There is no grid-wide barrier: the owner of column k
+// GB300 design: one persistent cooperative launch, two CTAs per SM.  Each
+// column belongs to one CTA for the whole factorisation (snake order, see
+// qr_owner) and, when the CTA's columns fit (d = 12n up to n ~ 600), lives
+// in that CTA's shared memory from start to end.  There is no grid-wide barrier: the owner of column k
 // publishes reflector k with a release store of a per-column flag, and a
 // CTA waits (bounded) only for a reflector it has nothing else to do
 // without.  Each CTA serves its lowest unfactored column first and catches
@@ -163,6 +163,20 @@ __device__ void apply_reflector_regs(double *const *cols, int cnt, int k, int d,
 // So the serial chain per column is one column update, one norm and one
 // flag hand-off, and the rest of each CTA's FP64 work fills its waits.
 constexpr int kQrMaxLocal = 32;  // columns per CTA (bit mask)
+
+// Column ownership of the cooperative kernel: "snake" order.  Column j lies
+// in round r = j / G at offset o = j mod G and belongs to CTA o in even
+// rounds and to CTA G-1-o in odd ones, as its r-th (local) column.  A
+// column's work grows with j (it receives j reflectors), and pairing each
+// early column with a late one evens the CTAs' totals (the cyclic order
+// j mod G gives the last CTAs of round 0 both heavy columns).
+__device__ __forceinline__ int qr_owner(int j, int G) {
+  const int r = j / G, o = j - r * G;
+  return (r & 1) ? G - 1 - o : o;
+}
+__device__ __forceinline__ int qr_col(int me, int l, int G) {
+  return (l & 1) ? (l + 1) * G - 1 - me : l * G + me;
+}
 enum { kQrDone = 0, kQrBuild = 1, kQrApply = 2, kQrFail = 3 };
 
 template <bool SMEM, int VR>
@@ -175,13 +189,14 @@ __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
   __shared__ int s_act, s_k;
   __shared__ unsigned s_mask;
   const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  const int nloc = (ncols - me + G - 1) / G;  // local columns j = me + l G
+  int nloc = 0;  // local columns j = qr_col(me, l, G), increasing with l
+  while (qr_col(me, nloc, G) < ncols) nloc++;
   auto colp = [&](int l) -> double * {
-    return SMEM ? dsm + (size_t)l * d : W + (size_t)(me + l * G) * d;
+    return SMEM ? dsm + (size_t)l * d : W + (size_t)qr_col(me, l, G) * d;
   };
   if (SMEM) {
     for (int l = 0; l < nloc; l++)
-      for (int i = tid; i < d; i += nt) dsm[(size_t)l * d + i] = W[(size_t)(me + l * G) * d + i];
+      for (int i = tid; i < d; i += nt) dsm[(size_t)l * d + i] = W[(size_t)qr_col(me, l, G) * d + i];
     __syncthreads();
   }
   // thread 0's bookkeeping: reflectors applied per local column, the pivot
@@ -189,16 +204,16 @@ __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
   int piv = 0;  // local index of the lowest unbuilt reflector column (nloc: none)
   if (tid == 0) {
     for (int l = 0; l < kQrMaxLocal; l++) applied[l] = 0;
-    while (piv < nloc && me + piv * G >= n) piv++;
+    while (piv < nloc && qr_col(me, piv, G) >= n) piv++;
   }
   double *cols[kQrBatch];
   for (;;) {
     if (tid == 0) {
       int act = kQrDone, k = 0;
       unsigned mask = 0;
-      auto target = [&](int l) { return (me + l * G < n) ? me + l * G : n; };
+      auto target = [&](int l) { return min(qr_col(me, l, G), n); };
       for (;;) {
-        const int jpiv = me + piv * G;
+        const int jpiv = qr_col(me, piv, G);
         const bool has_piv = piv < nloc && jpiv < n;
         if (has_piv && applied[piv] == jpiv) {
           act = kQrBuild;
@@ -228,7 +243,7 @@ __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
           for (int l = 0; l < nloc; l++)
             if (applied[l] == kneed && applied[l] < target(l)) mneed |= 1u << l;
         }
-        if ((kneed % G == me) || ld_acquire(flags + kneed) == epoch) {
+        if (qr_owner(kneed, G) == me || ld_acquire(flags + kneed) == epoch) {
           act = kQrApply;
           k = kneed;
           mask = mneed;
@@ -263,7 +278,7 @@ __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
       if (act == kQrBuild) {
         // this column is done once its reflector is out
         do piv++;
-        while (piv < nloc && me + piv * G >= n);
+        while (piv < nloc && qr_col(me, piv, G) >= n);
       } else if (act == kQrApply) {
         for (int l = 0; l < nloc; l++)
           if (mask & (1u << l)) applied[l]++;
@@ -278,7 +293,7 @@ __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
     if (act == kQrDone || act == kQrFail) break;
     if (act == kQrBuild) {
       double uk, beta;
-      make_reflector(colp((k - me) / G), k, d, W + (size_t)k * d, vhead, SMEM, red, uk, beta);
+      make_reflector(colp(k / G), k, d, W + (size_t)k * d, vhead, SMEM, red, uk, beta);
       __syncthreads();
       if (tid == 0) {
         __threadfence();
@@ -291,9 +306,9 @@ __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
       continue;
     }
     // apply H_k to the columns in mask; u from this CTA's own copy or the published one
-    const bool own = (k % G == me);
+    const bool own = (qr_owner(k, G) == me);
     const double uk = __ldcg(vhead + 2 * k), beta = __ldcg(vhead + 2 * k + 1);
-    const double *vk = own ? colp((k - me) / G) : W + (size_t)k * d;
+    const double *vk = own ? colp(k / G) : W + (size_t)k * d;
     double vr[VR > 0 ? VR : 1];
     if (VR > 0) {
 #pragma unroll
@@ -319,7 +334,7 @@ __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
     // R rows above the diagonal of the reflector columns, and the augmented
     // columns whole (rows k..d-1 of reflector column k went out at publish).
     for (int l2 = 0; l2 < nloc; l2++) {
-      const int j = me + l2 * G;
+      const int j = qr_col(me, l2, G);
       const int iend = (j < n) ? j : d;
       for (int i = tid; i < iend; i += nt) W[(size_t)j * d + i] = dsm[(size_t)l2 * d + i];
     }
@@ -327,9 +342,10 @@ __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
 }
 
 // Non-cooperative form for concurrent solves (served requests): one launch
-// per column step, the kernel boundary standing in for the flags.  Same
-// column ownership (j mod G), same lookahead, same published reflectors,
-// columns in global memory.
+// per column step, the kernel boundary standing in for the flags.  Column j
+// belongs to CTA j mod G; the owner of column k+1 applies H_k to it and
+// publishes reflector k+1 within step k (lookahead); the reflectors are
+// published as in the cooperative kernel; columns stay in global memory.
 __global__ void __launch_bounds__(kQrThreads)
     qr_step_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
                    int k) {
