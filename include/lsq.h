@@ -108,7 +108,9 @@ typedef struct {
   float ms_sketch_pass;           /* timing: the sketch pass */
   int32_t inner_kernel;           /* 0: FP64-FMA inner pass, 1: FP32-pipe row products on A,
                                      2: FP32 tier pass (hi plane), 3: double-float pass on
-                                     the hi / lo planes */
+                                     the hi / lo planes (one batched launch for many
+                                     right-hand sides), 4: FP64 tensor-core (DMMA)
+                                     many-right-hand-side pass */
   double bytes_a;                 /* bytes of A (and its FP32 copy) streamed by the solve */
   int32_t reserved[2];
 } lsq_info;
@@ -157,9 +159,12 @@ lsq_status lsq_solve_spir(lsq_plan plan, const double *dA, const double *db, dou
 /* FOSSILS for k = opt.nrhs right-hand sides sharing one sketch S [A B] and
  * one QR (Alg. 1 with the augmented columns Q^T S B; Alg. 2 / Alg. 5 per
  * column, each column with its own Polyak vectors and step-1 threshold, the
- * step ending when every column meets its own).  The refinement passes
- * G = A^T (B - A X) and H = A^T (A Z) are FP64 tensor-core (DMMA)
- * contractions over row blocks of A.  dB: m x k row-major with leading
+ * step ending when every column meets its own).  The residual pass
+ * G = A^T (B - A X) is an FP64 tensor-core (DMMA) contraction over row
+ * blocks of A.  The inner pass H = A^T (A Z) runs all k vectors through the
+ * double-float pass on the hi / lo planes in one launch.  With
+ * inner_fp64_fma = 1, or column norms outside [2^-40, 2^40], it is also a
+ * DMMA contraction.  dB: m x k row-major with leading
  * dimension ldb >= k (0 => k); dX: n x k row-major (device).  Requires
  * n <= 256.  info (may be NULL) reports the largest ||c_i|| over columns. */
 lsq_status lsq_solve_fossils_multi(lsq_plan plan, const double *dA, const double *dB,

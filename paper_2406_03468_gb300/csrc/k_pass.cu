@@ -290,8 +290,12 @@ template <int NC>
 __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     atax_df_kernel(const float *__restrict__ Ahi, const float *__restrict__ Alo, int64_t ld32,
                    int64_t m, int n, const double *__restrict__ z, double *__restrict__ part,
-                   int npad, const DevState *gate, int *err) {
+                   int npad, const DevState *gate, int *err, int64_t zstride,
+                   int64_t pstride) {
   if (gate != nullptr && *(volatile const int *)&gate->done) return;
+  // many right-hand sides: grid row blockIdx.y works on vector z_(blockIdx.y)
+  z += (int64_t)blockIdx.y * zstride;
+  part += (int64_t)blockIdx.y * pstride;
   // dynamic shared memory: [warps][NC*64] FP64 flush accumulators, then
   // [warps][kDfStages][2][NC*64] FP32 row stages (hi, lo), then the mbarriers
   extern __shared__ __align__(16) double hacc[];
@@ -575,6 +579,21 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
   }
 }
 
+// out[c n + j] = scale[j] sum_g part[(c grid + g) npad + j] for c < batch
+// (the partials of a batched pass, one block of grid x npad per vector).
+__global__ void reduce_batched_kernel(const double *__restrict__ part, int grid, int npad, int n,
+                                      int batch, const double *__restrict__ scale,
+                                      double *__restrict__ out, const DevState *gate) {
+  if (gate != nullptr && *(volatile const int *)&gate->done) return;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * batch) return;
+  const int c = (int)(idx / n), j = (int)(idx % n);
+  const double *pc = part + (size_t)c * grid * npad + j;
+  double s = 0.0;
+  for (int g = 0; g < grid; g++) s += pc[(size_t)g * npad];
+  out[idx] = scale ? scale[j] * s : s;
+}
+
 __global__ void reduce_kernel(const double *__restrict__ part, int grid, int npad, int n,
                               const double *__restrict__ scale, double *__restrict__ out,
                               const double *__restrict__ r2_part, double *r2,
@@ -635,18 +654,20 @@ cudaError_t launch_pass_atax_eft(const double *A, int64_t lda, int64_t m, int n,
 
 cudaError_t launch_pass_atax_df(const float *Ahi, const float *Alo, int64_t ld32, int64_t m, int n,
                                 const double *z, double *part, int grid, int npad,
-                                const DevState *gate, int *err, cudaStream_t s) {
+                                const DevState *gate, int *err, cudaStream_t s, int batch,
+                                int64_t zstride, int64_t pstride) {
   const int nw = kPassThreads / 32;
   const size_t smem = (size_t)nw * npad * sizeof(double) +
                       (size_t)nw * kDfStages * 2 * npad * sizeof(float) +
                       (size_t)nw * kDfStages * sizeof(uint64_t);
+  const dim3 g(grid, batch);
   LSQ_PASS_SWITCH(npad, {
     if (smem > 48 * 1024) {
       cudaError_t e = ensure_smem_attr((const void *)atax_df_kernel<NC>, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    atax_df_kernel<NC><<<grid, kPassThreads, smem, s>>>(Ahi, Alo, ld32, m, n, z, part, npad, gate,
-                                                        err);
+    atax_df_kernel<NC><<<g, kPassThreads, smem, s>>>(Ahi, Alo, ld32, m, n, z, part, npad, gate,
+                                                     err, zstride, pstride);
   });
   return cudaGetLastError();
 }
@@ -668,6 +689,15 @@ cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, co
     if (vec) resid_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, x, part, r2_part, npad);
     else resid_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, x, part, r2_part, npad);
   });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_batched(const double *part, int grid, int npad, int n, int batch,
+                                  const double *scale, double *out, const DevState *gate,
+                                  cudaStream_t s) {
+  const int64_t cnt = (int64_t)n * batch;
+  reduce_batched_kernel<<<(unsigned)((cnt + 127) / 128), 128, 0, s>>>(part, grid, npad, n, batch,
+                                                                      scale, out, gate);
   return cudaGetLastError();
 }
 

@@ -102,6 +102,7 @@ struct lsq_plan_s {
   // many right-hand sides (nrhs > 0)
   int k = 0;
   double *SBb = nullptr, *cpartB = nullptr, *mpart = nullptr, *mr2part = nullptr, *mT = nullptr;
+  double *mpartdf = nullptr;  // partials of the batched double-float pass (k x gpass x npad)
   double *mXs = nullptr, *mXo = nullptr, *mC = nullptr, *mG = nullptr, *mDY = nullptr;
   double *mDYold = nullptr, *mZ = nullptr, *mH = nullptr, *mW = nullptr, *mstate = nullptr;
   int launches = 0;                 // kernels launched by the current call
@@ -541,7 +542,8 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
   LSQ_CU(cudaMemsetAsync(P->SAb, 0, sizeof(double) * (size_t)d * (n + 1), P->s));
   LSQ_CU(cudaMemsetAsync(P->SBb, 0, sizeof(double) * (size_t)d * (k + 1), P->s));
   LSQ_CU(launch_sketch(dA, P->lda, P->m, n, nullptr, d, P->zeta, P->pat_rows, P->pat_sb, P->SAb,
-                       P->cpart, P->gpass, P->npad, nullptr, nullptr, 0, P->s));
+                       P->cpart, P->gpass, P->npad, P->want32 ? P->Ahi : nullptr,
+                       P->want32 ? P->Alo : nullptr, P->ld32, P->s));
   LSQ_CU(launch_sketch(dB, ldb, P->m, k, nullptr, d, P->zeta, P->pat_rows, P->pat_sb, P->SBb,
                        P->cpartB, P->gpass, pass_npad(k), nullptr, nullptr, 0, P->s));
   LSQ_CU(launch_sketch_finalize(P->cpart, P->gpass, P->npad, n, d, P->zeta, P->o.col_scale,
@@ -557,7 +559,13 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
                      nullptr, x0n2, nullptr, P->s, k, n));
   LSQ_CU(cudaEventRecord(P->ev[2], P->s));
   P->launches += 12;
+  LSQ_CU(cudaMemcpyAsync(P->dcol_host, P->dcol, sizeof(double) * n, cudaMemcpyDeviceToHost, P->s));
   LSQ_TRY(read_state(P));
+  // the inner pass: all k vectors through the double-float pass on the planes
+  // (one batched launch) unless the planes are off or out of range, else the
+  // FP64 tensor-core contraction
+  choose_inner_kernel(P);
+  const bool multi_df = P->use_df;
   if (P->st_host->nonfinite) return fail(LSQ_ERR_NONFINITE, "A or B holds NaN or Inf");
   if (P->st_host->zero_col) return fail(LSQ_ERR_INVALID, "A has a zero column (column scaling)");
   const int max_inner = P->o.max_inner ? P->o.max_inner : 100;
@@ -590,10 +598,19 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
         inner_ev[i].push_back(tj);
         LSQ_CU(cudaEventRecord(P->tev[2 * tj], P->s));
       }
-      LSQ_CU(launch_multi_atax(dA, P->lda, P->m, n, k, P->mZ, P->mpart, P->nsm, P->st, P->s));
-      if (tj >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tj + 1], P->s));
-      LSQ_CU(launch_multi_reduce(P->mpart, P->nsm, n, k, P->dinv, P->mH, nullptr, nullptr, P->st,
-                                 P->s));
+      if (multi_df) {
+        const int64_t pstride = (int64_t)P->gpass * P->npad;
+        LSQ_CU(launch_pass_atax_df(P->Ahi, P->Alo, P->ld32, P->m, n, P->mZ, P->mpartdf, P->gpass,
+                                   P->npad, P->st, &P->st->err, P->s, k, n, pstride));
+        if (tj >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tj + 1], P->s));
+        LSQ_CU(launch_reduce_batched(P->mpartdf, P->gpass, P->npad, n, k, P->dinv, P->mH, P->st,
+                                     P->s));
+      } else {
+        LSQ_CU(launch_multi_atax(dA, P->lda, P->m, n, k, P->mZ, P->mpart, P->nsm, P->st, P->s));
+        if (tj >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tj + 1], P->s));
+        LSQ_CU(launch_multi_reduce(P->mpart, P->nsm, n, k, P->dinv, P->mH, nullptr, nullptr,
+                                   P->st, P->s));
+      }
       LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 1, P->mH, nullptr, P->mW, nullptr, nullptr,
                          nullptr, nullptr, P->st, P->s, k, n));
       LSQ_CU(launch_multi_polyak(n, k, P->mC, P->mW, P->mDY, P->mDYold, dn2, thr, P->st, P->s));
@@ -625,6 +642,7 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
     }
     info->refine_steps = nref;
     info->path = LSQ_PREC_FP64;
+    info->inner_kernel = multi_df ? 3 : 4;
     info->passes = 2 + nref + iters[0] + iters[1];
     info->status = status;
     info->condest = S.condest;
@@ -684,7 +702,7 @@ void free_plan(lsq_plan P) {
   void *bufs[] = {P->pat_rows, P->pat_sb, P->SAb, P->W, P->part, P->r2part, P->cpart, P->dcol, P->dinv,
                   P->Rcm, P->Rrm, P->rinv, P->Dt, P->t, P->vbuf, P->xs, P->xo, P->c, P->g, P->dy,
                   P->dyold, P->z, P->h, P->w, P->res, P->p, P->st, P->qflag, P->stageA,
-                  P->stageb, P->stagex, P->Ahi, P->Alo, P->SBb, P->cpartB, P->mpart, P->mr2part,
+                  P->stageb, P->stagex, P->Ahi, P->Alo, P->SBb, P->cpartB, P->mpart, P->mpartdf, P->mr2part,
                   P->mT, P->mXs, P->mXo, P->mC, P->mG, P->mDY, P->mDYold, P->mZ, P->mH,
                   P->mW, P->mstate, P->tcnt, P->tlmax, P->colexp, P->cshift,
                   P->tptr, P->tsrc, P->cpow};
@@ -763,6 +781,7 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
     A(dalloc(&P->SBb, (size_t)P->d * (P->k + 1)));
     A(dalloc(&P->cpartB, (size_t)P->gpass * pass_npad(P->k)));
     A(dalloc(&P->mpart, (size_t)P->nsm * np8k));
+    A(dalloc(&P->mpartdf, (size_t)P->k * P->gpass * P->npad));
     A(dalloc(&P->mr2part, (size_t)P->nsm * P->k));
     double **mv[] = {&P->mT, &P->mXs, &P->mXo, &P->mC, &P->mG, &P->mDY, &P->mDYold, &P->mZ,
                      &P->mH, &P->mW};

@@ -173,9 +173,15 @@ cudaError_t launch_pass_atax32(const float *A32, int64_t ld32, int64_t m, int n,
 // double-float on the FP32 pipe (column sums flushed into FP64 every 8 rows);
 // rows staged by TMA bulk copies.  ld32: a multiple of 4 (16-byte rows);
 // Ahi / Alo 16-byte aligned.  err: LSQ_ERR_TIMEOUT if a copy never landed.
+// batch > 1: grid rows c < batch work on z + c zstride into part + c pstride.
 cudaError_t launch_pass_atax_df(const float *Ahi, const float *Alo, int64_t ld32, int64_t m, int n,
                                 const double *z, double *part, int grid, int npad,
-                                const DevState *gate, int *err, cudaStream_t s);
+                                const DevState *gate, int *err, cudaStream_t s, int batch = 1,
+                                int64_t zstride = 0, int64_t pstride = 0);
+// out (n x batch, column-major) = scale .* the sums of a batched pass's partials.
+cudaError_t launch_reduce_batched(const double *part, int grid, int npad, int n, int batch,
+                                  const double *scale, double *out, const DevState *gate,
+                                  cudaStream_t s);
 // Residual pass r = b - A x, partials of A^T r and of ||r||^2, all FP64.
 // (A^T r is a sum with heavy cancellation -- r is nearly orthogonal to
 // range(A) -- and its rounding reaches x through kappa^2, so it stays FP64.)

@@ -147,20 +147,23 @@ def test_fp32_tier_forced_and_bytes():
     assert abs(info["bytes_a"] - expect) <= 1e-9 * expect, (info["bytes_a"], expect, info)
 
 
+@pytest.mark.parametrize("fp64", [0, 1])
 @pytest.mark.parametrize("m,n,k,kappa", [(40000, 200, 16, 1e8), (30011, 100, 8, 1e6),
                                          (20000, 200, 64, 1e8)])
-def test_multi_rhs_shared_sketch(m, n, k, kappa):
-    """k right-hand sides on one A (config-4 construction at reduced m):
-    every column of X is backward stable and within 10x of the oracle QR
-    solution's Wedin-bound yardstick; the same column solved alone on the
-    single-RHS path agrees to that level."""
+def test_multi_rhs_shared_sketch(m, n, k, kappa, fp64):
+    """k right-hand sides on one A (config-4 construction at reduced m), with
+    the batched double-float inner pass (default) and the DMMA one
+    (inner_fp64_fma = 1): every column of X is backward stable and within
+    10x of the oracle QR solution's Wedin-bound yardstick; the same column
+    solved alone on the single-RHS path agrees to that level."""
     from lsq_problems import problem_multi_rhs
     P = problem_multi_rhs(m, n, k, kappa, 1e-5, seed=41)
     A, B = P["A"], P["B"]
-    plan = lsq.Plan(m, n, seed=6, nrhs=k)
+    plan = lsq.Plan(m, n, seed=6, nrhs=k, inner_fp64_fma=fp64)
     X = torch.empty((n, k), dtype=torch.float64, device="cuda")
     st, info = lsq.lsq_solve_fossils_multi(plan.handle, T(A), T(B), k, X)
     assert st == 0
+    assert info.inner_kernel == (4 if fp64 else 3)
     Xh = H(X)
     R_A, V = oracle.householder_qr(A)
     for c in range(k):
