@@ -100,7 +100,9 @@ __device__ void apply_reflector(double *const *cols, int cnt, int k, int d, cons
     }
   }
   if (tid < cnt) cols[tid][k] = fma(-wsh[tid], uk, cols[tid][k]);
-  __syncthreads();
+  // no closing barrier: callers separate this update from the next reader of
+  // other threads' rows (the scheduling barrier of qr_kernel, or an explicit
+  // one); a following update of other columns is ordered by its own barriers
 }
 
 // The same update with u held in registers: vr[r] = u_i for i = tid + r nt
@@ -142,7 +144,9 @@ __device__ void apply_reflector_regs(double *const *cols, int cnt, int k, int d,
     }
   }
   if (tid < cnt) cols[tid][k] = fma(-wsh[tid], uk, cols[tid][k]);
-  __syncthreads();
+  // no closing barrier: callers separate this update from the next reader of
+  // other threads' rows (the scheduling barrier of qr_kernel, or an explicit
+  // one); a following update of other columns is ordered by its own barriers
 }
 
 // SMEM: the CTA's columns live in shared memory for the whole factorisation.
@@ -368,6 +372,7 @@ __global__ void __launch_bounds__(kQrThreads)
   if (k + 1 < n && (k + 1) % G == me && l < nloc) {
     cols[0] = colp(l);
     apply_reflector<true>(cols, 1, k, d, vk, uk, beta, red, wsh);
+    __syncthreads();  // the norm below reads rows other threads just updated
     double u1, b1;
     make_reflector(colp(l), k + 1, d, W + (size_t)(k + 1) * d, vhead, false, red, u1, b1);
     l++;
