@@ -478,10 +478,20 @@ def run_ours(args):
         hx = torch.empty(N, dtype=torch.float64).pin_memory()
         lsq.lsq_solve_host(h, 0, hA, hb, hx)
         torch.cuda.synchronize()
+        # the host link's own rate on these buffers (context for the e2e number)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record()
+        A.copy_(hA, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        link_gbs = 8 * M * N / (c0.elapsed_time(c1) * 1e-3) / 1e9
         k2 = max(1, args.steps // 2)
+        host_infos = []
         t0 = time.perf_counter()
         for _ in range(k2):
-            lsq.lsq_solve_host(h, 0, hA, hb, hx)
+            _, hinf = lsq.lsq_solve_host(h, 0, hA, hb, hx)
+            host_infos.append(hinf.as_dict())
         dt = time.perf_counter() - t0
         rate = k2 * world / dt
         if dist:
@@ -489,7 +499,9 @@ def run_ours(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             rate = k2 * world / float(t.item())
         e2e = {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 8 * M * N + 8 * M,
-               "d2h_bytes_per_step": 8 * N}
+               "d2h_bytes_per_step": 8 * N, "h2d_link_gbs": link_gbs,
+               "sketch_ms_incl_copy": statistics.median(i["ms_sketch"] for i in host_infos),
+               "device_ms_per_solve": statistics.median(i["ms_total"] for i in host_infos)}
 
     tier = None
     multi = None

@@ -170,10 +170,18 @@ lsq_status lsq_solve_spir(lsq_plan plan, const double *dA, const double *db, dou
 lsq_status lsq_solve_fossils_multi(lsq_plan plan, const double *dA, const double *dB,
                                    int64_t ldb, double *dX, lsq_info *info);
 
-/* As lsq_solve_fossils / lsq_solve_spir with HOST buffers hA (m x n, lda),
- * hb (m) and hx (n): copies A and b to plan-owned device memory (allocated
- * on first use, kept with the plan), solves, and copies x back.  method: 0 =
- * FOSSILS, 1 = SPIR. */
+/* As lsq_solve_fossils / lsq_solve_spir with HOST buffers hA (m x n, lda;
+ * (m - 1) lda + n doubles are read), hb (m) and hx (n): copies A and b to
+ * plan-owned device memory (allocated on first use, grown when a
+ * reconfigured plan needs more, kept with the plan), solves, and copies x
+ * back.  method: 0 = FOSSILS, 1 = SPIR.  When the sketch takes its gather
+ * form (m n >= 2^24), A is copied in row chunks of at least 128 MB (16 at
+ * most) on a copy stream and the sketch of each chunk (Sec. 4.2) runs as it
+ * lands, so the sketch overlaps the copy; each chunk's sums get their own
+ * fixed-point scale and are added in FP64 in row order, so the sketch, and
+ * x, can differ from the device entry's by rounding.  The overlap needs
+ * page-locked host memory (else each chunk's copy completes before the call
+ * goes on).  Returns after x is in hx. */
 lsq_status lsq_solve_host(lsq_plan plan, int method, const double *hA, const double *hb,
                           double *hx, lsq_info *info);
 

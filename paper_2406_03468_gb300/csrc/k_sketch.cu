@@ -339,11 +339,13 @@ __device__ __forceinline__ int biased_exp(double a) {
 // One streaming pass over A (no sketch): column sums of squares (partials),
 // the largest biased exponent per column and of b (atomicMax into colexp[0..n)
 // and colexp[npad], zeroed first), and the hi / lo FP32 planes when Ahi != NULL.
+// accumulate = 1 adds the partials to those of earlier rows (A in row chunks).
 template <int NC, bool VEC>
 __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     prep_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
                 const double *__restrict__ b, double *__restrict__ colsq_part, int npad,
-                int *colexp, float *__restrict__ Ahi, float *__restrict__ Alo, int64_t ld32) {
+                int *colexp, float *__restrict__ Ahi, float *__restrict__ Alo, int64_t ld32,
+                int accumulate) {
   __shared__ double acc[NC * 64];
   __shared__ int emax[NC * 64 + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -406,7 +408,8 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
   }
   __syncthreads();
   for (int i = threadIdx.x; i < npad; i += blockDim.x) {
-    colsq_part[(size_t)blockIdx.x * npad + i] = acc[i];
+    const size_t o = (size_t)blockIdx.x * npad + i;
+    colsq_part[o] = (accumulate ? colsq_part[o] : 0.0) + acc[i];
     if (i < n && emax[i] > 0) atomicMax(colexp + i, emax[i]);
   }
   if (threadIdx.x == 0 && emax[NC * 64] > 0) atomicMax(colexp + npad, emax[NC * 64]);
@@ -452,7 +455,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
     gather_kernel(const double *__restrict__ A, int64_t lda, int n, const double *__restrict__ b,
                   int d, int npad, const int64_t *__restrict__ ptr,
                   const uint32_t *__restrict__ src, const int *__restrict__ cshift,
-                  const double *__restrict__ cpow, double *__restrict__ SAb) {
+                  const double *__restrict__ cpow, double *__restrict__ SAb, int64_t row0,
+                  int64_t row1, int accumulate) {
   __shared__ int sh[CH * 64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c0 = blockIdx.y * CH * 64;
@@ -474,11 +478,24 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
 #pragma unroll
   for (int k = 0; k < 2 * CH; k++) acc[k] = 0;
   long long accb = 0;
-  const int64_t pend = ptr[h + 1];
-  for (int64_t p0 = ptr[h]; p0 < pend; p0 += 32) {
+  // this call's rows [row0, row1) of the sorted list: the first entry at or
+  // after row0 by binary search, then up to the first one at or after row1
+  int64_t pbeg = ptr[h], pend = ptr[h + 1];
+  if (row0 > 0) {
+    int64_t lo = pbeg, hi = pend;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)(__ldg(src + mid) & 0x7fffffffu) < row0) lo = mid + 1;
+      else hi = mid;
+    }
+    pbeg = lo;
+  }
+  for (int64_t p0 = pbeg; p0 < pend; p0 += 32) {
     // 32 list entries with one coalesced load, handed out by shuffles
-    const uint32_t mine = (p0 + lane < pend) ? __ldg(src + p0 + lane) : 0u;
-    const int cnt = (int)min((int64_t)32, pend - p0);
+    const uint32_t mine = (p0 + lane < pend) ? __ldg(src + p0 + lane) : 0x7fffffffu;
+    // entries are sorted by row: stop at the first one at or beyond row1
+    const unsigned beyond = __ballot_sync(0xffffffffu, (int64_t)(mine & 0x7fffffffu) >= row1);
+    const int cnt = beyond ? __ffs(beyond) - 1 : (int)min((int64_t)32, pend - p0);
 #pragma unroll 1
     for (int q = 0; q < cnt; q++) {
       const uint32_t e = __shfl_sync(0xffffffffu, mine, q);
@@ -502,15 +519,19 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
       for (int k = 0; k < 2 * CH; k++) add_fixed(acc[k], a[k], shl[k], neg);
       if (dob && lane == 0) add_fixed(accb, __ldg(b + i), shb, neg);
     }
+    if (beyond) break;
   }
+  // accumulate: add to the sums of earlier row ranges (one FP64 rounding each)
   double *out = SAb + (size_t)h * (n + 1);
 #pragma unroll
   for (int k = 0; k < CH; k++) {
     const int col = c0 + 64 * k + 2 * lane;
-    if (col < n) out[col] = (double)acc[2 * k] * cpow[col];
-    if (col + 1 < n) out[col + 1] = (double)acc[2 * k + 1] * cpow[col + 1];
+    if (col < n) out[col] = (accumulate ? out[col] : 0.0) + (double)acc[2 * k] * cpow[col];
+    if (col + 1 < n)
+      out[col + 1] = (accumulate ? out[col + 1] : 0.0) + (double)acc[2 * k + 1] * cpow[col + 1];
   }
-  if (blockIdx.y == 0 && lane == 0) out[n] = dob ? (double)accb * cpow[npad] : 0.0;
+  if (blockIdx.y == 0 && lane == 0)
+    out[n] = (accumulate ? out[n] : 0.0) + (dob ? (double)accb * cpow[npad] : 0.0);
 }
 
 }  // namespace
@@ -592,15 +613,17 @@ int sketch_list_max() { return kSortMax; }
 
 cudaError_t launch_sketch_prep(const double *A, int64_t lda, int64_t m, int n, const double *b,
                                double *colsq_part, int grid, int npad, int *colexp, float *Ahi,
-                               float *Alo, int64_t ld32, cudaStream_t s) {
+                               float *Alo, int64_t ld32, cudaStream_t s, int accumulate) {
   cudaError_t e = cudaMemsetAsync(colexp, 0, sizeof(int) * (size_t)(npad + 1), s);
   if (e != cudaSuccess) return e;
   const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 2 == 0);
 #define LSQ_PREP(NC)                                                                            \
   (vec ? prep_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, colsq_part, npad, \
-                                                             colexp, Ahi, Alo, ld32)            \
+                                                             colexp, Ahi, Alo, ld32,            \
+                                                             accumulate)                        \
        : prep_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, colsq_part,     \
-                                                              npad, colexp, Ahi, Alo, ld32))
+                                                              npad, colexp, Ahi, Alo, ld32,     \
+                                                              accumulate))
   switch (npad / 64) {
     case 1: LSQ_PREP(1); break;
     case 2: LSQ_PREP(2); break;
@@ -616,7 +639,8 @@ cudaError_t launch_sketch_prep(const double *A, int64_t lda, int64_t m, int n, c
 cudaError_t launch_sketch_gather(const double *A, int64_t lda, int n, const double *b, int d,
                                  int npad, const int64_t *ptr, const uint32_t *src,
                                  const int *colexp, const int *lmax, int *cshift, double *cpow,
-                                 double *SAb, DevState *st, cudaStream_t s) {
+                                 double *SAb, DevState *st, cudaStream_t s, int64_t row0,
+                                 int64_t row1, int accumulate) {
   fixed_params_kernel<<<(npad + 1 + 255) / 256, 256, 0, s>>>(colexp, n, npad, lmax, cshift, cpow,
                                                               st);
   cudaError_t e = cudaGetLastError();
@@ -628,9 +652,11 @@ cudaError_t launch_sketch_gather(const double *A, int64_t lda, int n, const doub
                   (unsigned)((n + 64 * ch - 1) / (64 * ch)));
   const int th = kGatherWarps * 32;
   if (ch == 2)
-    gather_kernel<2><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb);
+    gather_kernel<2><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb, row0,
+                                         row1, accumulate);
   else
-    gather_kernel<1><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb);
+    gather_kernel<1><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb, row0,
+                                         row1, accumulate);
   return cudaGetLastError();
 }
 

@@ -48,6 +48,8 @@ lsq_status fail(lsq_status st, const std::string &msg) {
 constexpr uint64_t kBarrierTimeoutNs = 5ull * 1000 * 1000 * 1000;  // 5 s per inter-CTA wait
 constexpr int kCondestIters = 10;
 constexpr int kStopPollEvery = 4;  // step 1: read the device stop flag every 4 updates
+constexpr int kHostChunksMax = 16;             // host entry: row chunks of A at most
+constexpr double kHostChunkBytes = 128.0e6;    // and at least this many bytes each
 
 }  // namespace
 
@@ -91,6 +93,14 @@ struct lsq_plan_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool condest_pending = false;
   double *stageA = nullptr, *stageb = nullptr, *stagex = nullptr;
+  size_t stage_cap = 0;              // doubles of stageA
+  // host entry: A copied in row chunks on a copy stream (one event per
+  // chunk), the sketch of each chunk run as it lands (gather form only)
+  cudaStream_t scopy = nullptr;
+  cudaEvent_t ev_stage = nullptr;
+  cudaEvent_t chunk_ev[kHostChunksMax] = {};
+  int64_t chunk_row[kHostChunksMax + 1] = {};
+  int host_chunks = 0;               // > 1: do_sketch waits per chunk
   bool sketched = false;
   bool use_eft = false;              // inner pass on the FP32 pipe
   bool want32 = false;               // the sketch pass writes the hi / lo planes of A
@@ -319,14 +329,25 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
     LSQ_CU(tev_pair(P, &tk));
     LSQ_CU(cudaEventRecord(P->tev[2 * tk], P->s));
   }
+  const int nch = P->host_chunks;
+  P->host_chunks = 0;
   if (P->use_gather) {
-    LSQ_CU(launch_sketch_prep(dA, P->lda, P->m, n, db, P->cpart, P->gpass, P->npad, P->colexp,
-                              P->want32 ? P->Ahi : nullptr, P->want32 ? P->Alo : nullptr, P->ld32,
-                              P->s));
-    LSQ_CU(launch_sketch_gather(dA, P->lda, n, db, P->d, P->npad, P->tptr, P->tsrc, P->colexp,
-                                P->tlmax, P->cshift, P->cpow, P->SAb, P->st, P->s));
-    P->launches += 2;
+    // one chunk, or the host entry's row chunks as their copies complete
+    for (int c = 0; c < std::max(nch, 1); c++) {
+      const int64_t r0 = nch > 1 ? P->chunk_row[c] : 0, r1 = nch > 1 ? P->chunk_row[c + 1] : P->m;
+      if (nch > 1) LSQ_CU(cudaStreamWaitEvent(P->s, P->chunk_ev[c], 0));
+      LSQ_CU(launch_sketch_prep(dA + r0 * P->lda, P->lda, r1 - r0, n, db + r0, P->cpart, P->gpass,
+                                P->npad, P->colexp, P->want32 ? P->Ahi + r0 * P->ld32 : nullptr,
+                                P->want32 ? P->Alo + r0 * P->ld32 : nullptr, P->ld32, P->s,
+                                c > 0));
+      LSQ_CU(launch_sketch_gather(dA, P->lda, n, db, P->d, P->npad, P->tptr, P->tsrc, P->colexp,
+                                  P->tlmax, P->cshift, P->cpow, P->SAb, P->st, P->s, r0, r1,
+                                  c > 0));
+      P->launches += 3;
+    }
+    P->launches -= 1;  // counted below with the finalize
   } else {
+    for (int c = 0; c < nch; c++) LSQ_CU(cudaStreamWaitEvent(P->s, P->chunk_ev[c], 0));
     LSQ_CU(cudaMemsetAsync(P->SAb, 0, sizeof(double) * (size_t)P->d * (n + 1), P->s));
     LSQ_CU(launch_sketch(dA, P->lda, P->m, n, db, P->d, P->zeta, P->pat_rows, P->pat_sb, P->SAb,
                          P->cpart, P->gpass, P->npad, P->want32 ? P->Ahi : nullptr,
@@ -713,6 +734,10 @@ void free_plan(lsq_plan P) {
   for (auto &e : P->ev)
     if (e) cudaEventDestroy(e);
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  for (auto &e : P->chunk_ev)
+    if (e) cudaEventDestroy(e);
+  if (P->ev_stage) cudaEventDestroy(P->ev_stage);
+  if (P->scopy) cudaStreamDestroy(P->scopy);
   if (P->ev_join) cudaEventDestroy(P->ev_join);
   if (P->s2) cudaStreamDestroy(P->s2);
   for (auto &e : P->tev) cudaEventDestroy(e);
@@ -899,17 +924,58 @@ lsq_status lsq_solve_host(lsq_plan P, int method, const double *hA, const double
   if (!P) return fail(LSQ_ERR_INVALID, "plan is NULL");
   if (!hA || !hb || !hx) return fail(LSQ_ERR_INVALID, "host buffer is NULL");
   if (method != 0 && method != 1) return fail(LSQ_ERR_INVALID, "method must be 0 or 1");
-  const size_t an = (size_t)P->m * P->lda;
-  if (!P->stageA) {
+  const size_t an = (size_t)(P->m - 1) * P->lda + P->n;  // doubles of A read from the host
+  if (an > P->stage_cap) {
+    if (P->stageA) cudaFree(P->stageA);
+    if (P->stageb) cudaFree(P->stageb);
+    if (P->stagex) cudaFree(P->stagex);
+    P->stageA = P->stageb = P->stagex = nullptr;
+    P->stage_cap = 0;
     cudaError_t e = dalloc(&P->stageA, an);
-    if (e == cudaSuccess) e = dalloc(&P->stageb, (size_t)P->m);
-    if (e == cudaSuccess) e = dalloc(&P->stagex, (size_t)P->n);
+    if (e == cudaSuccess) e = dalloc(&P->stageb, (size_t)P->m_cap);
+    if (e == cudaSuccess) e = dalloc(&P->stagex, (size_t)P->n_cap);
     if (e != cudaSuccess) return fail(LSQ_ERR_OOM, "staging allocation failed");
+    P->stage_cap = an;
   }
-  LSQ_CU(cudaMemcpyAsync(P->stageA, hA, an * sizeof(double), cudaMemcpyHostToDevice, P->s));
-  LSQ_CU(cudaMemcpyAsync(P->stageb, hb, (size_t)P->m * sizeof(double), cudaMemcpyHostToDevice, P->s));
+  if (!P->scopy) {
+    LSQ_CU(cudaStreamCreateWithFlags(&P->scopy, cudaStreamNonBlocking));
+    LSQ_CU(cudaEventCreateWithFlags(&P->ev_stage, cudaEventDisableTiming));
+    for (auto &e : P->chunk_ev) LSQ_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  LSQ_TRY(ensure_pattern(P));
+  // The gather-form sketch takes A in row chunks of at least kHostChunkBytes,
+  // each sketched on the main stream as soon as its copy lands, so the
+  // sketch runs under the host-to-device copy of the rest of A.
+  const double abytes = 8.0 * (double)an;
+  int nch = 1;
+  if (P->use_gather)
+    nch = (int)std::min<double>(kHostChunksMax, std::floor(abytes / kHostChunkBytes));
+  if (nch > 1) {
+    // the copies start once the main stream is done with the staging buffers
+    LSQ_CU(cudaEventRecord(P->ev_stage, P->s));
+    LSQ_CU(cudaStreamWaitEvent(P->scopy, P->ev_stage, 0));
+    LSQ_CU(cudaMemcpyAsync(P->stageb, hb, (size_t)P->m * sizeof(double), cudaMemcpyHostToDevice,
+                           P->scopy));
+    for (int c = 0; c <= nch; c++) P->chunk_row[c] = P->m * c / nch;
+    for (int c = 0; c < nch; c++) {
+      const int64_t r0 = P->chunk_row[c], r1 = P->chunk_row[c + 1];
+      const size_t cnt = (size_t)(r1 - r0 - 1) * P->lda + P->n;
+      LSQ_CU(cudaMemcpyAsync(P->stageA + r0 * P->lda, hA + r0 * P->lda, cnt * sizeof(double),
+                             cudaMemcpyHostToDevice, P->scopy));
+      LSQ_CU(cudaEventRecord(P->chunk_ev[c], P->scopy));
+    }
+    P->host_chunks = nch;
+  } else {
+    LSQ_CU(cudaMemcpyAsync(P->stageA, hA, an * sizeof(double), cudaMemcpyHostToDevice, P->s));
+    LSQ_CU(cudaMemcpyAsync(P->stageb, hb, (size_t)P->m * sizeof(double), cudaMemcpyHostToDevice,
+                           P->s));
+  }
   lsq_status st = run_solve(P, method, P->stageA, P->stageb, P->stagex, info);
-  if (st < 0) return st;
+  P->host_chunks = 0;
+  if (st < 0) {
+    cudaStreamSynchronize(P->scopy);  // no copy into the staging buffers outlives the call
+    return st;
+  }
   LSQ_CU(cudaMemcpyAsync(hx, P->stagex, (size_t)P->n * sizeof(double), cudaMemcpyDeviceToHost, P->s));
   LSQ_CU(cudaStreamSynchronize(P->s));
   return st;

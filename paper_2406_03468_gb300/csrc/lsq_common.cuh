@@ -102,17 +102,22 @@ cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, const 
 // largest exponents colexp[0..n) and of b at colexp[npad], FP32 planes),
 // then launch_sketch_gather (64-bit fixed-point sums into SAb, d x (n+1)
 // row-major, no zeroing needed; cshift / cpow: npad + 1 entries of scratch).
+// A may come in row chunks, each taken by a prep then a gather in row order,
+// accumulate = 0 for the first: the prep is given the chunk (A, b, Ahi, Alo
+// offset to its first row, m its rows), the gather all of A and b and the
+// chunk's row range; each chunk gets its own fixed-point scale.
 cudaError_t launch_sketch_lists(const int32_t *rows, const uint32_t *signbits, int64_t m, int zeta,
                                 int d, int *cnt, int64_t *ptr, uint32_t *src, int *lmax,
                                 cudaStream_t s);
 int sketch_list_max();
 cudaError_t launch_sketch_prep(const double *A, int64_t lda, int64_t m, int n, const double *b,
                                double *colsq_part, int grid, int npad, int *colexp, float *Ahi,
-                               float *Alo, int64_t ld32, cudaStream_t s);
+                               float *Alo, int64_t ld32, cudaStream_t s, int accumulate);
 cudaError_t launch_sketch_gather(const double *A, int64_t lda, int n, const double *b, int d,
                                  int npad, const int64_t *ptr, const uint32_t *src,
                                  const int *colexp, const int *lmax, int *cshift, double *cpow,
-                                 double *SAb, DevState *st, cudaStream_t s);
+                                 double *SAb, DevState *st, cudaStream_t s, int64_t row0,
+                                 int64_t row1, int accumulate);
 // Column norms from partials, scaling, transpose into column-major W (ld d).
 cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad, int n, int d,
                                    int zeta, int col_scale, const double *SAb, double *W,

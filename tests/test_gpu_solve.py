@@ -101,6 +101,28 @@ def test_host_entry_point_matches_device():
     assert oracle.kw_relative(A, b, xh) <= 1e-13
 
 
+@pytest.mark.parametrize("method", [0, 1])
+def test_host_entry_point_chunked(method):
+    """300007 x 256 (614 MB of A): the host entry copies A in 4 row chunks
+    and sketches each as it lands; the answer is backward stable and within
+    10x of the oracle QR's forward error, like the device entry's."""
+    m, n = 300007, 256
+    P = problem_svd(m, n, 1e10, 1e-4, seed=31)
+    A, b, xt = P["A"], P["b"], P["x_true"]
+    plan = lsq.Plan(m, n, seed=6)
+    xh = np.empty(n)
+    st, info = lsq.lsq_solve_host(plan.handle, method, A, b, xh)
+    assert st == 0
+    x = empty(n)
+    plan.solve(T(A), T(b), x, ("fossils", "spir")[method])
+    xd = H(x)
+    plan.close()
+    x_qr, R_A = oracle.qr_solve(A, b, return_R=True)
+    for xs in (xh, xd):
+        assert oracle.kw_relative(A, b, xs, R_A=R_A) <= 1e-13
+        assert oracle.forward_error(xs, xt) <= 10 * oracle.forward_error(x_qr, xt)
+
+
 @pytest.mark.parametrize("m,n", [(64, 64), (1000, 1), (513, 33)])
 def test_edge_shapes(m, n):
     rng = np.random.default_rng(m * 7 + n)

@@ -254,3 +254,45 @@ def test_residual_pass_after_sketch(m, n):
     bound = 4 * (n + m) * u * (np.abs(A).T @ (np.abs(b) + np.abs(A) @ np.abs(x)))
     assert (np.abs(H(g) - g_ref) <= bound).all()
     assert abs(r2 - float(r_hi @ r_hi)) <= 1e-12 * float(r_hi @ r_hi)
+
+
+@pytest.mark.parametrize("m,n,entry", [(200003, 100, "device"), (400003, 200, "host")])
+def test_gather_sketch_fixed_point(m, n, entry):
+    """The gather form of the sketch (m n >= 2^24): each list entry is
+    truncated to a multiple of 2^F with F = (E - 1022) + L - 63 (E the
+    largest biased exponent of the column in the rows summed, L = max(10,
+    bits of the longest list)), so an entry of S A is off by less than
+    cnt_h 2^(L-62) max|A_:j| plus FP64 roundings of the sums.  The host
+    entry copies A in row chunks (640 MB here: 5 chunks of >= 128 MB) and
+    sketches each as it lands, one fixed-point scale per chunk."""
+    P = problem_svd(m, n, 1e6, 1e-4, seed=13, keep_factors=False)
+    A, b = P["A"], P["b"]
+    zeta, d, seed = 8, 12 * n, 17
+    plan = lsq.Plan(m, n, seed=seed)
+    if entry == "device":
+        lsq.lsq_sketch(plan.handle, T(A), T(b))
+        nch = 1
+    else:
+        xh = np.empty(n)
+        st, _ = lsq.lsq_solve_host(plan.handle, 0, A, b, xh)
+        assert st == 0
+        nch = min(16, int(8.0 * A.size // 128e6))
+        assert nch == 5
+    SAb = empty(d * (n + 1))
+    cn = empty(n)
+    lsq.lsq_get_sketch(plan.handle, SAb, cn)
+    plan.close()
+    SAb = H(SAb).reshape(n + 1, d).T
+    SAg = SAb[:, :n] * H(cn)            # undo the column scaling (3 roundings)
+    SA, Sb = oracle.sketch(A, b, d, zeta, seed)
+    S = abs(sparse_sign_matrix(m, d, zeta, seed)).sign()
+    cnt = np.asarray(S.sum(axis=1)).ravel()
+    L = max(10, int(cnt.max()).bit_length())
+    c = 1.0 / math.sqrt(zeta)
+    k = (nch + 8) + int(cnt.max())
+    trunc_A = c * cnt[:, None] * 2.0 ** (L - 62) * np.abs(A).max(axis=0)[None, :]
+    trunc_b = c * cnt * 2.0 ** (L - 62) * np.abs(b).max()
+    bound_A = trunc_A + k * u * c * np.asarray(S @ np.abs(A)) + 1e-300
+    bound_b = trunc_b + k * u * c * np.asarray(S @ np.abs(b)).ravel() + 1e-300
+    assert (np.abs(SAg - SA) <= bound_A).all(), np.max(np.abs(SAg - SA) / bound_A)
+    assert (np.abs(SAb[:, n] - Sb) <= bound_b).all()
