@@ -149,6 +149,62 @@ __device__ void apply_reflector_regs(double *const *cols, int cnt, int k, int d,
   // one); a following update of other columns is ordered by its own barriers
 }
 
+// The step on the serial chain: H_k applied to column k+1 (the CTA's pivot)
+// fused with building reflector k+1 from it.  The update pass also sums the
+// squares of rows k+1.. of the updated column (the norm the reflector needs)
+// and writes rows k+2.. to W's column k+1 (the published u), so the chain
+// reads the column twice instead of four times.  Whole CTA; as
+// apply_reflector_regs then make_reflector(col, k + 1, ..., copy_u = true).
+template <int VR>
+__device__ void apply_build_regs(double *col, int k, int d, const double (&vr)[VR], double uk,
+                                 double beta, double *red, double *wsh, double *Wk1,
+                                 double *vhead) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+  for (int r = 0; r < VR; r += 2) {
+    const int i0 = tid + r * nt, i1 = i0 + nt;
+    if (i0 > k && i0 < d) a0 = fma(vr[r], col[i0], a0);
+    if (r + 1 < VR && i1 > k && i1 < d) a1 = fma(vr[r + 1], col[i1], a1);
+  }
+  const double acc = warp_sum(a0 + a1);
+  if (lane == 0) red[warp * kQrBatch] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double sacc = uk * col[k];
+    for (int w = 0; w < nw; w++) sacc += red[w * kQrBatch];
+    wsh[0] = beta * sacc;
+  }
+  __syncthreads();
+  const double w = wsh[0];
+  double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+  for (int r = 0; r < VR; r++) {
+    const int i = tid + r * nt;
+    if (i > k && i < d) {
+      const double c = fma(-w, vr[r], col[i]);
+      col[i] = c;
+      if (r & 1) s1 = fma(c, c, s1);
+      else s0 = fma(c, c, s0);
+      if (i > k + 1) Wk1[i] = c;
+    }
+  }
+  if (tid == 0) col[k] = fma(-w, uk, col[k]);
+  const double s = block_sum(s0 + s1, red);  // its barriers also publish col[k + 1]
+  const double nx = sqrt(s);
+  const double x0 = col[k + 1];
+  const double sg = (x0 >= 0.0) ? 1.0 : -1.0;
+  const double u1 = x0 + sg * nx;
+  const double b1 = (nx > 0.0) ? 1.0 / (nx * (nx + fabs(x0))) : 0.0;
+  __syncthreads();  // every thread has read col[k + 1]
+  if (tid == 0) {
+    col[k + 1] = -sg * nx;
+    Wk1[k + 1] = -sg * nx;
+    vhead[2 * (k + 1)] = u1;
+    vhead[2 * (k + 1) + 1] = b1;
+  }
+}
+
 // SMEM: the CTA's columns live in shared memory for the whole factorisation.
 // VR > 0 (d <= VR * kQrThreads): each thread holds its VR entries of the
 // current reflector in registers, so the L2 latency of reading it is paid
@@ -181,7 +237,7 @@ __device__ __forceinline__ int qr_owner(int j, int G) {
 __device__ __forceinline__ int qr_col(int me, int l, int G) {
   return (l & 1) ? (l + 1) * G - 1 - me : l * G + me;
 }
-enum { kQrDone = 0, kQrBuild = 1, kQrApply = 2, kQrFail = 3 };
+enum { kQrDone = 0, kQrBuild = 1, kQrApply = 2, kQrFail = 3, kQrApplyBuild = 4 };
 
 template <bool SMEM, int VR>
 __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
@@ -251,6 +307,10 @@ __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
           act = kQrApply;
           k = kneed;
           mask = mneed;
+          // the critical chain with the pivot in shared memory: update and
+          // build in one step (apply_build_regs)
+          if (SMEM && VR > 0 && has_piv && mneed == (1u << piv) && jpiv == kneed + 1)
+            act = kQrApplyBuild;
           break;
         }
         // while it is not out: catch up columns that lag further behind
@@ -279,7 +339,8 @@ __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
           break;
         }
       }
-      if (act == kQrBuild) {
+      if (act == kQrBuild || act == kQrApplyBuild) {
+        if (act == kQrApplyBuild) applied[piv]++;
         // this column is done once its reflector is out
         do piv++;
         while (piv < nloc && qr_col(me, piv, G) >= n);
@@ -311,6 +372,26 @@ __global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
     }
     // apply H_k to the columns in mask; u from this CTA's own copy or the published one
     const bool own = (qr_owner(k, G) == me);
+    if (act == kQrApplyBuild) {
+      if (VR > 0) {
+        const double uk = __ldcg(vhead + 2 * k), beta = __ldcg(vhead + 2 * k + 1);
+        const double *vk = own ? colp(k / G) : W + (size_t)k * d;
+        double vr[VR > 0 ? VR : 1];
+#pragma unroll
+        for (int r = 0; r < (VR > 0 ? VR : 1); r++) {
+          const int i = tid + r * nt;
+          vr[r] = (i > k && i < d) ? (own ? vk[i] : __ldcg(vk + i)) : 0.0;
+        }
+        apply_build_regs(colp((k + 1) / G), k, d, vr, uk, beta, red, wsh,
+                         W + (size_t)(k + 1) * d, vhead);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(flags + k + 1, epoch);
+      }
+      continue;
+    }
     const double uk = __ldcg(vhead + 2 * k), beta = __ldcg(vhead + 2 * k + 1);
     const double *vk = own ? colp(k / G) : W + (size_t)k * d;
     double vr[VR > 0 ? VR : 1];

@@ -253,6 +253,265 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster form of the substitution for one vector.  GB300 issues one FP64
+// warp instruction per 64 cycles per SM sub-partition (1.7 FMA per clock per
+// SM), so one CTA spends most of a solve on the n^2 / 2 updates of the rows
+// beyond the next block.  Here a cluster of kClusterCtas CTAs shares it:
+//   * CTA 0, the chain CTA: warp 0 solves each 32 x 32 diagonal block (one
+//     shuffle and one FMA per step, the tiles pre-scaled by 1 / R_ll);
+//     warps 1-3 (the other sub-partitions) apply the block's x to the next
+//     block's rows (the lookahead), a third of the columns each;
+//   * CTAs 1..7, the update CTAs: block k belongs to CTA 1 + k % 7, one warp
+//     per block with its running sums in registers.  Each x block that CTA 0
+//     broadcasts is applied to the owned blocks beyond the next one; once a
+//     block has its last such update (two rounds before it is solved) its
+//     sums go to CTA 0.
+// x travels CTA 0 -> CTAs 1..7 and the sums CTAs 1..7 -> CTA 0 by st.async
+// into the receiver's shared memory, each transfer completing an mbarrier of
+// the receiver that is used once.  The chain thus waits only on its own work
+// and on sums that were sent a round earlier.  Each inner product still runs
+// over the same terms, so the solve is backward stable as before.  Every
+// wait is bounded; a timeout records LSQ_ERR_TIMEOUT in *err.
+// ---------------------------------------------------------------------------
+constexpr int kClusterCtas = 8;
+constexpr int kClusterMinN = 97;  // four or more blocks: below, one CTA does as well
+constexpr int kUpdateCtas = kClusterCtas - 1;
+constexpr int kClusterThreads = 256;
+constexpr int kMaxBlocks = (LSQ_MAX_N + 31) / 32;
+constexpr uint64_t kClusterWaitNs = 1000ull * 1000 * 1000;  // 1 s
+static_assert(kMaxBlocks <= kUpdateCtas * (kClusterThreads / 32), "one warp per owned block");
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// the same shared-memory variable in CTA `rank` of the cluster
+__device__ __forceinline__ unsigned cluster_addr(const void *p, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_async_f64(unsigned raddr, double v, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(raddr),
+               "l"(__double_as_longlong(v)), "r"(rbar)
+               : "memory");
+}
+// An mbarrier for one transfer of `bytes`: its one arrival is made here, the
+// phase completes when the remote stores have delivered the bytes.
+__device__ __forceinline__ void xfer_bar_init(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool xfer_try(uint64_t *bar) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar))
+      : "memory");
+  return ok != 0;
+}
+__device__ bool xfer_wait(uint64_t *bar) {
+  if (xfer_try(bar)) return true;
+  const uint64_t t0 = global_ns();
+  while (!xfer_try(bar))
+    if (global_ns() - t0 > kClusterWaitNs) return false;
+  return true;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void nbar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// Round r solves block blk_of(r); the map is its own inverse (block k is
+// solved in round blk_of(k)).
+__device__ __forceinline__ int blk_of(int r, int nb, int trans) { return trans ? r : nb - 1 - r; }
+__device__ __forceinline__ int blk_len(int k, int n) { return min(n, 32 * k + 32) - 32 * k; }
+// the last round whose x update CTA `rank` (1..7) applies, plus 2
+__device__ __forceinline__ int update_last(int rank, int nb, int trans) {
+  int mp = -1;
+  for (int k = rank - 1; k < nb; k += kUpdateCtas) mp = max(mp, blk_of(k, nb, trans));
+  return mp;
+}
+
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads)
+    trsv_cluster_kernel(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
+                        const double *__restrict__ rinv, const double *__restrict__ Dt, int n,
+                        int trans, const double *y, const double *in_scale, double *out,
+                        const double *out_scale, double *out_scaled, double *accum,
+                        double *norm2_out, const DevState *gate, int *err) {
+  if (gate != nullptr && *(volatile const int *)&gate->done) return;
+  const int rank = (int)cluster_rank();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nb = (n + 31) / 32;
+  const double *Rb = trans ? Rrm : Rcm;
+  // shared: sx (x of the solved blocks, padded to 32 nb), ps (CTA 0: the
+  // shipped sums), lp (CTA 0: lookahead partials of warps 1-3), scratch,
+  // then one transfer mbarrier per block (CTA 0) or per round (CTAs 1..7)
+  extern __shared__ __align__(16) double csm[];
+  double *sx = csm, *ps = csm + 32 * nb, *lp = ps + 32 * nb, *scratch = lp + 96;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(scratch + 8);
+  for (int i = threadIdx.x; i < 32 * nb; i += blockDim.x) sx[i] = ps[i] = 0.0;
+  const int last = rank == 0 ? 0 : update_last(rank, nb, trans);
+  if (threadIdx.x == 0) {
+    if (rank == 0) {
+      for (int k = 0; k < nb; k++)
+        if (blk_of(k, nb, trans) >= 2) xfer_bar_init(bars + k, 8u * blk_len(k, n));
+    } else {
+      for (int r = 0; r <= last - 2; r++) xfer_bar_init(bars + r, 8u * blk_len(blk_of(r, nb, trans), n));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  cluster_sync_all();  // every barrier is armed before any remote store
+  bool ok = true;
+  if (rank == 0 && warp == 0) {
+    // the last round + 2 of update CTA lane + 1, for the broadcast
+    const int lastl = lane < kUpdateCtas ? update_last(lane + 1, nb, trans) : -1;
+    double dreg[32], rl = 0.0;  // the block's scaled diagonal tile and 1 / R_ll
+    auto load_diag = [&](int k) {
+      const double *D = Dt + ((size_t)trans * nb + k) * 1024;
+#pragma unroll
+      for (int jj = 0; jj < 32; jj++) dreg[jj] = D[jj * 32 + lane];
+      rl = lane < blk_len(k, n) ? rinv[32 * k + lane] : 0.0;
+    };
+    load_diag(blk_of(0, nb, trans));
+    for (int r = 0; r < nb; r++) {
+      const int l = blk_of(r, nb, trans), j0 = 32 * l, len = blk_len(l, n);
+      double zb;
+      if (r < 2) {
+        zb = (lane < len) ? (in_scale ? y[j0 + lane] * in_scale[j0 + lane] : y[j0 + lane]) : 0.0;
+      } else {
+        if (!xfer_wait(bars + l)) ok = false;
+        zb = ps[j0 + lane];
+      }
+      if (r >= 1) {
+        nbar_sync(3 + (r & 1), 128);  // lookahead of round r - 1 on this block
+        zb -= (lp[lane] + lp[32 + lane]) + lp[64 + lane];
+      }
+      double zl = zb * rl;
+      if (!trans) {
+#pragma unroll
+        for (int jj = 31; jj >= 0; jj--) {
+          if (jj < len) {
+            const double xj = __shfl_sync(0xffffffffu, zl, jj);
+            if (lane < jj) zl = fma(-dreg[jj], xj, zl);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 32; jj++) {
+          if (jj < len) {
+            const double xj = __shfl_sync(0xffffffffu, zl, jj);
+            if (lane > jj && lane < len) zl = fma(-dreg[jj], xj, zl);
+          }
+        }
+      }
+      if (lane < len) sx[j0 + lane] = zl;
+      __syncwarp();
+      if (r + 1 < nb) {
+        nbar_arrive(1 + (r & 1), 128);  // x of round r for the lookahead warps
+        load_diag(blk_of(r + 1, nb, trans));
+      }
+      for (int b = 1; b <= kUpdateCtas; b++) {
+        const int lb = __shfl_sync(0xffffffffu, lastl, b - 1);
+        if (lb >= r + 2 && lane < len)
+          st_async_f64(cluster_addr(sx + j0 + lane, b), zl, cluster_addr(bars + r, b));
+      }
+    }
+  } else if (rank == 0 && warp <= 3) {
+    // lookahead: columns [c0, c0 + 11) of the solved block on the next block's rows
+    const int c0 = 11 * (warp - 1);
+    for (int r = 0; r + 1 < nb; r++) {
+      const int l = blk_of(r, nb, trans), j0 = 32 * l, len = blk_len(l, n);
+      const int ln = blk_of(r + 1, nb, trans), i = 32 * ln + lane, lenn = blk_len(ln, n);
+      double rv[11];
+#pragma unroll
+      for (int q = 0; q < 11; q++) {
+        const int jj = c0 + q;
+        rv[q] = (jj < 32 && jj < len && lane < lenn) ? Rb[(size_t)(j0 + jj) * n + i] : 0.0;
+      }
+      nbar_sync(1 + (r & 1), 128);
+      double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+      for (int q = 0; q < 11; q++) {
+        const int jj = c0 + q;
+        const double xv = jj < 32 ? sx[j0 + jj] : 0.0;
+        if (q & 1) a1 = fma(rv[q], xv, a1);
+        else a0 = fma(rv[q], xv, a0);
+      }
+      lp[32 * (warp - 1) + lane] = a0 + a1;
+      nbar_arrive(3 + ((r + 1) & 1), 128);
+    }
+  } else if (rank > 0) {
+    const int k = rank - 1 + kUpdateCtas * warp;  // this warp's block
+    if (k < nb && blk_of(k, nb, trans) >= 2) {
+      const int pk = blk_of(k, nb, trans), i0 = 32 * k, lenk = blk_len(k, n), i = i0 + lane;
+      double S = (lane < lenk) ? (in_scale ? y[i] * in_scale[i] : y[i]) : 0.0;
+      for (int r = 0; r <= pk - 2; r++) {
+        const int l = blk_of(r, nb, trans), j0 = 32 * l, len = blk_len(l, n);
+        double rv[32];  // R does not depend on x: loaded before the wait
+#pragma unroll
+        for (int jj = 0; jj < 32; jj++)
+          rv[jj] = (jj < len && lane < lenk) ? Rb[(size_t)(j0 + jj) * n + i] : 0.0;
+        if (!xfer_wait(bars + r)) ok = false;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+        for (int jj = 0; jj < 32; jj += 4) {
+          a0 = fma(rv[jj], sx[j0 + jj], a0);
+          a1 = fma(rv[jj + 1], sx[j0 + jj + 1], a1);
+          a2 = fma(rv[jj + 2], sx[j0 + jj + 2], a2);
+          a3 = fma(rv[jj + 3], sx[j0 + jj + 3], a3);
+        }
+        S -= (a0 + a1) + (a2 + a3);
+      }
+      if (lane < lenk) st_async_f64(cluster_addr(ps + i0 + lane, 0), S, cluster_addr(bars + k, 0));
+    }
+  }
+  if (!ok) {
+    if (err != nullptr) atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
+    // let late transfers into this CTA land before it exits (bounded)
+    if (rank == 0) {
+      for (int k = 0; k < nb; k++)
+        if (blk_of(k, nb, trans) >= 2) xfer_wait(bars + k);
+    } else {
+      for (int r = 0; r <= last - 2; r++) xfer_wait(bars + r);
+    }
+  }
+  __syncthreads();
+  if (rank == 0) {
+    double nrm = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double x = sx[i];
+      if (accum) {
+        x = accum[i] + x;
+        accum[i] = x;
+      }
+      if (out) out[i] = x;
+      if (out_scaled) out_scaled[i] = out_scale[i] * x;
+      nrm = fma(x, x, nrm);
+    }
+    if (norm2_out) {
+      nrm = block_sum(nrm, scratch);
+      if (threadIdx.x == 0) *norm2_out = nrm;
+    }
+  }
+  cluster_sync_all();  // no CTA leaves while another may still address it
+}
+
 // Dt[t][b][jj][l] = (t ? Rrm : Rcm)[(32b + jj) n + 32b + l] / R_(32b+l)(32b+l):
 // block b's diagonal tile for R x = y (t = 0) or R^T x = y (t = 1), each
 // entry scaled by the reciprocal diagonal of the row it updates; zero
@@ -282,7 +541,15 @@ cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv
                         const double *y, const double *in_scale, double *out,
                         const double *out_scale, double *out_scaled, double *accum,
                         double *norm2_out, const DevState *gate, cudaStream_t s, int batch,
-                        int64_t bstride) {
+                        int64_t bstride, int *err) {
+  if (batch == 1 && n >= kClusterMinN) {
+    const int nb = (n + 31) / 32;
+    const size_t csmem = (size_t)(64 * nb + 96 + 8) * sizeof(double) + sizeof(uint64_t) * nb;
+    trsv_cluster_kernel<<<kClusterCtas, kClusterThreads, csmem, s>>>(
+        Rcm, Rrm, rinv, Dt, n, trans, y, in_scale, out, out_scale, out_scaled, accum, norm2_out,
+        gate, err);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)(n + 32 + 3 * kTile) * sizeof(double);
   trsv_kernel<<<batch, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, Dt, n, trans, y, in_scale, out,
                                                out_scale, out_scaled, accum, norm2_out, gate,

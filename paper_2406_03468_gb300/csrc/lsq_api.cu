@@ -372,7 +372,8 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
   P->condest_pending = true;
   // sketch-and-solve x0 = R^{-1} t (scaled coordinates) and x0 / d (original)
   LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 0, P->t, nullptr, P->xs, P->dinv, P->xo,
-                     nullptr, &P->st->x0norm2, nullptr, P->s));
+                     nullptr, &P->st->x0norm2, nullptr, P->s, 1, 0,
+                       &P->st->err));
   LSQ_CU(cudaEventRecord(P->ev[2], P->s));
   LSQ_CU(cudaMemcpyAsync(P->dcol_host, P->dcol, sizeof(double) * n, cudaMemcpyDeviceToHost, P->s));
   LSQ_TRY(read_state(P));
@@ -423,7 +424,8 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
                          nullptr, P->s));
     passes++;
     LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 1, P->g, nullptr, P->c, nullptr, nullptr,
-                       nullptr, &P->st->cnorm2[i], nullptr, P->s));
+                       nullptr, &P->st->cnorm2[i], nullptr, P->s, 1, 0,
+                       &P->st->err));
     if (i == 0) {
       LSQ_TRY(join_condest(P));
       LSQ_CU(launch_set_thresh(gam, rho, P->st, P->s));
@@ -447,7 +449,8 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
       const double *src = (method == 0) ? P->dy : P->p;
       // z = D^{-1} R^{-1} src;  h = D^{-1} A^T (A z);  w = R^{-T} h
       LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 0, src, nullptr, nullptr, P->dinv, P->z,
-                         nullptr, nullptr, P->st, P->s));
+                         nullptr, nullptr, P->st, P->s, 1, 0,
+                       &P->st->err));
       int tj = -1;
       if (P->o.timing) {
         LSQ_CU(tev_pair(P, &tj));
@@ -471,7 +474,8 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
       LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->h, nullptr, nullptr, P->st,
                            P->s));
       LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 1, P->h, nullptr, P->w, nullptr, nullptr,
-                         nullptr, nullptr, P->st, P->s));
+                         nullptr, nullptr, P->st, P->s, 1, 0,
+                       &P->st->err));
       if (method == 0)
         LSQ_CU(launch_polyak_update(n, P->c, P->w, P->dy, P->dyold, P->st, P->s));
       else
@@ -483,7 +487,8 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     }
     // x_s += R^{-1} dy ; x_o = D^{-1} x_s
     LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 0, P->dy, nullptr, nullptr, P->dinv, P->xo,
-                       P->xs, nullptr, nullptr, P->s));
+                       P->xs, nullptr, nullptr, P->s, 1, 0,
+                       &P->st->err));
     P->launches++;
     LSQ_TRY(read_state(P));
     iters[i] = P->st_host->iters;
@@ -1052,7 +1057,8 @@ lsq_status lsq_trsv(lsq_plan P, int trans, const double *dy, double *dx) {
   if (!P || !dy || !dx) return fail(LSQ_ERR_INVALID, "NULL argument");
   if (!P->sketched) return fail(LSQ_ERR_INVALID, "call lsq_sketch first");
   LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, (int)P->n, trans ? 1 : 0, dy, nullptr, dx, nullptr,
-                     nullptr, nullptr, nullptr, nullptr, P->s));
+                     nullptr, nullptr, nullptr, nullptr, P->s, 1, 0,
+                       &P->st->err));
   LSQ_CU(cudaStreamSynchronize(P->s));
   return LSQ_OK;
 }

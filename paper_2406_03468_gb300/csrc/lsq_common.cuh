@@ -153,12 +153,14 @@ cudaError_t launch_diag_tiles(const double *Rcm, const double *Rrm, const double
 //   norm2_out != NULL: *norm2_out = ||out||^2
 //   gate != NULL: return at once when gate->done.
 //   batch > 1: CTA b solves the vectors at offset b * bstride (norm2_out[b]).
+//   batch == 1 (n > 96): a cluster of 8 CTAs; a wait that times out sets
+//   *err (if given) to LSQ_ERR_TIMEOUT.
 cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv, const double *Dt,
                         int n, int trans,
                         const double *y, const double *in_scale, double *out,
                         const double *out_scale, double *out_scaled, double *accum,
                         double *norm2_out, const DevState *gate, cudaStream_t s, int batch = 1,
-                        int64_t bstride = 0);
+                        int64_t bstride = 0, int *err = nullptr);
 // Fused passes (partials: grid x npad doubles, r2_part: grid doubles).
 cudaError_t launch_pass_atax(const double *A, int64_t lda, int64_t m, int n, const double *z,
                              double *part, int grid, int npad, const DevState *gate,
