@@ -543,11 +543,16 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
   cta_store_partial<NC>(hd, sh, part, npad);
 }
 
+// With Ahi != NULL the pass also writes the hi / lo FP32 planes of A: this
+// pass is bound by the FP64 pipe with HBM to spare, so the plane stores cost
+// almost nothing here (the large-problem sketch leaves them to the first
+// residual pass of a solve).
 template <int NC, bool VEC>
 __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     resid_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
                  const double *__restrict__ b, const double *__restrict__ x,
-                 double *__restrict__ part, double *__restrict__ r2_part, int npad) {
+                 double *__restrict__ part, double *__restrict__ r2_part, int npad,
+                 float *__restrict__ Ahi, float *__restrict__ Alo, int64_t ld32) {
   __shared__ double sh[NC * 64];
   __shared__ double r2sh[kPassThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -561,6 +566,22 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
   for (int64_t i = r0 + warp; i < r1; i += nw) {
     double a[2 * NC];
     load_row<NC, VEC>(A + i * lda, n, lane, a);
+    if (Ahi != nullptr) {
+#pragma unroll
+      for (int k = 0; k < NC; k++) {
+        const int col = 64 * k + 2 * lane;
+        float h0, l0, h1, l1;
+        split_rn(a[2 * k], h0, l0);
+        split_rn(a[2 * k + 1], h1, l1);
+        if (col + 1 < n) {
+          __stcs(reinterpret_cast<float2 *>(Ahi + i * ld32 + col), make_float2(h0, h1));
+          __stcs(reinterpret_cast<float2 *>(Alo + i * ld32 + col), make_float2(l0, l1));
+        } else if (col < n) {
+          __stcs(Ahi + i * ld32 + col, h0);
+          __stcs(Alo + i * ld32 + col, l0);
+        }
+      }
+    }
     double s = 0.0;
 #pragma unroll
     for (int k = 0; k < 2 * NC; k++) s = fma(a[k], xr[k], s);
@@ -683,11 +704,15 @@ cudaError_t launch_pass_atax32(const float *A32, int64_t ld32, int64_t m, int n,
 
 cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, const double *b,
                               const double *x, double *part, double *r2_part, int grid, int npad,
-                              cudaStream_t s) {
+                              cudaStream_t s, float *Ahi, float *Alo, int64_t ld32) {
   const bool vec = vec_ok(A, lda);
   LSQ_PASS_SWITCH(npad, {
-    if (vec) resid_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, x, part, r2_part, npad);
-    else resid_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, x, part, r2_part, npad);
+    if (vec)
+      resid_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, x, part, r2_part,
+                                                           npad, Ahi, Alo, ld32);
+    else
+      resid_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, x, part, r2_part,
+                                                            npad, Ahi, Alo, ld32);
   });
   return cudaGetLastError();
 }

@@ -88,24 +88,6 @@ __device__ __forceinline__ void load_row(const double *__restrict__ row, int n, 
   }
 }
 
-// a = hi + lo exactly up to 2^-48 |a|, with integer operations only:
-// hi = a rounded to 24 significant bits (round half up, the carry going into
-// the exponent as in IEEE), lo = the signed 30-bit remainder scaled by
-// 2^(E-52) and rounded to FP32.  Entries outside FP32's normal range give 0
-// (the host takes this path only when every column norm is in [2^-40, 2^40]).
-__device__ __forceinline__ void split_rn(double a, float &hi, float &lo) {
-  const unsigned hw = (unsigned)__double2hiint(a), lw = (unsigned)__double2loint(a);
-  const int ef = (int)((hw >> 20) & 0x7ffu) - 896;
-  const unsigned sign = hw & 0x80000000u;
-  const unsigned up = (lw >> 28) & 1u;
-  const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
-  const unsigned hib = sign | (((unsigned)ef << 23) + m23 + up);
-  const int rem = (int)(lw & 0x1fffffffu) - (up ? (1 << 29) : 0);
-  const int lf = ef - 52;
-  const float l = __fmul_rn(__int2float_rn(rem), __int_as_float((lf > 0 ? lf : 1) << 23));
-  hi = (ef > 0 && ef < 254) ? __uint_as_float(hib) : 0.0f;
-  lo = (lf > 0 && ef < 254) ? __uint_as_float(__float_as_uint(l) ^ sign) : 0.0f;
-}
 
 __device__ __forceinline__ double flip_sign(double a, bool neg) {
   return __longlong_as_double(__double_as_longlong(a) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
@@ -439,13 +421,16 @@ __global__ void fixed_params_kernel(const int *__restrict__ colexp, int n, int n
 }
 
 // acc += (+-) trunc(|a| / 2^F) with C = 1075 + F, the sign flipped when neg:
-// integer operations only.  Zeros and subnormals (exponent field 0) add 0.
+// integer operations only.  The shift is PTX shr.b64, which gives 0 for
+// shift amounts of 64 or more, so zeros and subnormals (exponent field 0,
+// shift 64) and terms below 2^F add 0 with no compare.
 __device__ __forceinline__ void add_fixed(long long &acc, double a, int C, unsigned neg) {
   const unsigned hw = (unsigned)__double2hiint(a), lw = (unsigned)__double2loint(a);
   const unsigned e = (hw >> 20) & 0x7ffu;
-  const unsigned sh = e ? (unsigned)(C - (int)e) : 127u;
+  const unsigned sh = e ? (unsigned)(C - (int)e) : 64u;
   const unsigned long long mant = ((unsigned long long)((hw & 0xfffffu) | 0x100000u) << 32) | lw;
-  const unsigned long long t = (sh < 64u) ? (mant >> sh) : 0ull;
+  unsigned long long t;
+  asm("shr.b64 %0, %1, %2;" : "=l"(t) : "l"(mant), "r"(sh));
   const unsigned long long m = 0ull - (unsigned long long)((hw >> 31) ^ neg);  // 0 or ~0
   acc += (long long)((t ^ m) - m);
 }

@@ -104,6 +104,7 @@ struct lsq_plan_s {
   bool sketched = false;
   bool use_eft = false;              // inner pass on the FP32 pipe
   bool want32 = false;               // the sketch pass writes the hi / lo planes of A
+  bool planes_pending = false;       // the first residual pass of the solve writes them
   float *Ahi = nullptr, *Alo = nullptr;  // FP32 planes: hi = fl32(A), lo = A - hi
   int64_t ld32 = 0;
   bool use_df = false;               // inner pass in double-float on the planes
@@ -311,7 +312,9 @@ void choose_inner_kernel(lsq_plan P) {
   P->use_eft = true;
 }
 
-lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
+// defer_planes: on the gather path the prep pass leaves the hi / lo planes to
+// the solve's first residual pass (planes_pending), which reads A anyway.
+lsq_status do_sketch(lsq_plan P, const double *dA, const double *db, bool defer_planes) {
   if (!dA || !db) return fail(LSQ_ERR_INVALID, "A or b is NULL");
   const int n = (int)P->n;
   P->launches = 0;
@@ -331,15 +334,17 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db) {
   }
   const int nch = P->host_chunks;
   P->host_chunks = 0;
+  P->planes_pending = false;
   if (P->use_gather) {
+    const bool planes = P->want32 && !defer_planes;
+    P->planes_pending = P->want32 && defer_planes;
     // one chunk, or the host entry's row chunks as their copies complete
     for (int c = 0; c < std::max(nch, 1); c++) {
       const int64_t r0 = nch > 1 ? P->chunk_row[c] : 0, r1 = nch > 1 ? P->chunk_row[c + 1] : P->m;
       if (nch > 1) LSQ_CU(cudaStreamWaitEvent(P->s, P->chunk_ev[c], 0));
       LSQ_CU(launch_sketch_prep(dA + r0 * P->lda, P->lda, r1 - r0, n, db + r0, P->cpart, P->gpass,
-                                P->npad, P->colexp, P->want32 ? P->Ahi + r0 * P->ld32 : nullptr,
-                                P->want32 ? P->Alo + r0 * P->ld32 : nullptr, P->ld32, P->s,
-                                c > 0));
+                                P->npad, P->colexp, planes ? P->Ahi + r0 * P->ld32 : nullptr,
+                                planes ? P->Alo + r0 * P->ld32 : nullptr, P->ld32, P->s, c > 0));
       LSQ_CU(launch_sketch_gather(dA, P->lda, n, db, P->d, P->npad, P->tptr, P->tsrc, P->colexp,
                                   P->tlmax, P->cshift, P->cpow, P->SAb, P->st, P->s, r0, r1,
                                   c > 0));
@@ -388,7 +393,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
                      lsq_info *info) {
   if (!dx) return fail(LSQ_ERR_INVALID, "x is NULL");
   const int n = (int)P->n;
-  LSQ_TRY(do_sketch(P, dA, db));
+  LSQ_TRY(do_sketch(P, dA, db, true));
   const int max_inner = P->o.max_inner ? P->o.max_inner : 100;
   const int nref = P->o.max_refine ? P->o.max_refine : 2;
   const double gam = P->o.stop_gamma, rho = P->o.stop_rho;
@@ -416,8 +421,11 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
       resid_ev.push_back(tk);
       LSQ_CU(cudaEventRecord(P->tev[2 * tk], P->s));
     }
+    const bool planes = P->planes_pending;
+    P->planes_pending = false;
     LSQ_CU(launch_pass_resid(dA, P->lda, P->m, n, db, P->xo, P->part, P->r2part, P->gpass,
-                             P->npad, P->s));
+                             P->npad, P->s, planes ? P->Ahi : nullptr, planes ? P->Alo : nullptr,
+                             P->ld32));
     if (tk >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tk + 1], P->s));
     P->launches += 3 + (i == 0 ? 1 : 0) + 1;  // resid, reduce, trsv, [thresh], init
     LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->g, P->r2part, &P->st->r2,
@@ -901,7 +909,7 @@ lsq_status lsq_plan_configure(lsq_plan plan, const lsq_options *opt) {
 
 lsq_status lsq_sketch(lsq_plan plan, const double *dA, const double *db) {
   if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
-  LSQ_TRY(do_sketch(plan, dA, db));
+  LSQ_TRY(do_sketch(plan, dA, db, false));
   LSQ_TRY(join_condest(plan));
   return read_state(plan);
 }
@@ -1029,7 +1037,7 @@ lsq_status lsq_get_R(lsq_plan P, double *dR, double *dt, double *dx0, double *co
 lsq_status lsq_apply_normal(lsq_plan P, const double *dA, const double *dz, double *dh) {
   if (!P || !dA || !dz || !dh) return fail(LSQ_ERR_INVALID, "NULL argument");
   const int n = (int)P->n;
-  if (P->sketched && P->use_df)
+  if (P->sketched && P->use_df && !P->planes_pending)
     LSQ_CU(launch_pass_atax_df(P->Ahi, P->Alo, P->ld32, P->m, n, dz, P->part, P->gpass, P->npad,
                                nullptr, &P->st->err, P->s));
   else if (P->sketched && P->use_eft)

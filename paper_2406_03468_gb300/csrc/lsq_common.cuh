@@ -64,6 +64,27 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// Split for the hi / lo FP32 planes of A (written by the sketch pass or by
+// the first residual pass).
+// a = hi + lo exactly up to 2^-48 |a|, with integer operations only:
+// hi = a rounded to 24 significant bits (round half up, the carry going into
+// the exponent as in IEEE), lo = the signed 30-bit remainder scaled by
+// 2^(E-52) and rounded to FP32.  Entries outside FP32's normal range give 0
+// (the host takes this path only when every column norm is in [2^-40, 2^40]).
+__device__ __forceinline__ void split_rn(double a, float &hi, float &lo) {
+  const unsigned hw = (unsigned)__double2hiint(a), lw = (unsigned)__double2loint(a);
+  const int ef = (int)((hw >> 20) & 0x7ffu) - 896;
+  const unsigned sign = hw & 0x80000000u;
+  const unsigned up = (lw >> 28) & 1u;
+  const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
+  const unsigned hib = sign | (((unsigned)ef << 23) + m23 + up);
+  const int rem = (int)(lw & 0x1fffffffu) - (up ? (1 << 29) : 0);
+  const int lf = ef - 52;
+  const float l = __fmul_rn(__int2float_rn(rem), __int_as_float((lf > 0 ? lf : 1) << 23));
+  hi = (ef > 0 && ef < 254) ? __uint_as_float(hib) : 0.0f;
+  lo = (lf > 0 && ef < 254) ? __uint_as_float(__float_as_uint(l) ^ sign) : 0.0f;
+}
+
 // cudaFuncSetAttribute(fn, MaxDynamicSharedMemorySize, bytes) once per
 // (device, kernel, size): the call costs host time, and the inner loop
 // launches its pass dozens of times per solve (lsq_api.cu).
@@ -192,9 +213,11 @@ cudaError_t launch_reduce_batched(const double *part, int grid, int npad, int n,
 // Residual pass r = b - A x, partials of A^T r and of ||r||^2, all FP64.
 // (A^T r is a sum with heavy cancellation -- r is nearly orthogonal to
 // range(A) -- and its rounding reaches x through kappa^2, so it stays FP64.)
+// Ahi != NULL: also write the hi / lo FP32 planes of A (as launch_sketch).
 cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, const double *b,
                               const double *x, double *part, double *r2_part, int grid, int npad,
-                              cudaStream_t s);
+                              cudaStream_t s, float *Ahi = nullptr, float *Alo = nullptr,
+                              int64_t ld32 = 0);
 // out[j] = scale[j] * sum_g part[g][j] (scale may be NULL); r2 (if non-NULL)
 // = sum_g r2_part[g]; gated.
 cudaError_t launch_reduce(const double *part, int grid, int npad, int n, const double *scale,

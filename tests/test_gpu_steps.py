@@ -106,8 +106,10 @@ def test_qr_of_sketch(m, n):
     assert 0.8 * smax / smin <= ce <= 1.0001 * smax / smin
 
 
-@pytest.mark.parametrize("n", [130, 37])
+@pytest.mark.parametrize("n", [37, 96, 97, 130, 500, 1024])
 def test_triangular_solves(n):
+    """n <= 96: one CTA; n > 96: the 8-CTA cluster form (n = 97: a last
+    block of one row; n = 1024: 32 blocks, the most the update CTAs hold)."""
     P, A = _problem(20011, n, 1e6, seed=3)
     plan = lsq.Plan(20011, n, seed=5)
     lsq.lsq_sketch(plan.handle, T(A), T(P["b"]))
