@@ -286,6 +286,50 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
       : "memory");
 }
 
+// Packed FP32 pairs (two columns per 64-bit register, the lower one in the
+// low word): sm_100-class add / sub / mul / fma .rn.f32x2 round each half as
+// the scalar instruction would, at one issue slot per two elements.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+  return ((f2_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ float f2_lo(f2_t v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float f2_hi(f2_t v) { return __uint_as_float((unsigned)(v >> 32)); }
+// One double-float accumulation step on a pair: (s, l) += (a * b exactly,
+// with the cross terms a * bl + al * b), given bn = -b.  The product's
+// rounding error comes from fma(a, b, -p) with -p = a * bn; the TwoSum adds p
+// as s - (-p).  Every operation is the scalar algorithm's, per half.
+__device__ __forceinline__ void f2_dd_step(f2_t &s, f2_t &l, f2_t a, f2_t al, f2_t b, f2_t bl,
+                                           f2_t bn) {
+  const f2_t pn = f2_mul(a, bn);
+  const f2_t c = f2_fma(a, bl, f2_fma(al, b, f2_fma(a, b, pn)));
+  const f2_t s1 = f2_sub(s, pn);
+  const f2_t bb = f2_sub(s1, s);
+  const f2_t er = f2_sub(f2_sub(s, f2_sub(s1, bb)), f2_add(pn, bb));
+  s = s1;
+  l = f2_add(l, f2_add(er, c));
+}
+
 template <int NC>
 __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     atax_df_kernel(const float *__restrict__ Ahi, const float *__restrict__ Alo, int64_t ld32,
@@ -344,14 +388,17 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
   int fz = 0;
   if (zmax > 0.0) frexp(zmax, &fz);
   const double down = ldexp(1.0, -fz), up = ldexp(1.0, fz);
-  float zh[2 * NC], zl[2 * NC], hh[2 * NC], hl[2 * NC];
+  // column pairs (2k, 2k + 1) of this lane: z hi / lo / -hi and the
+  // double-float column sums, packed
+  f2_t zh[NC], zl[NC], zn[NC], hh[NC], hl[NC];
 #pragma unroll
-  for (int k = 0; k < 2 * NC; k++) {
-    const double v = zr[k] * down;
-    zh[k] = __double2float_rn(v);
-    zl[k] = __double2float_rn(v - (double)zh[k]);
-    hh[k] = 0.0f;
-    hl[k] = 0.0f;
+  for (int k = 0; k < NC; k++) {
+    const double v0 = zr[2 * k] * down, v1 = zr[2 * k + 1] * down;
+    const float h0 = __double2float_rn(v0), h1 = __double2float_rn(v1);
+    zh[k] = f2_pack(h0, h1);
+    zl[k] = f2_pack(__double2float_rn(v0 - (double)h0), __double2float_rn(v1 - (double)h1));
+    zn[k] = f2_pack(-h0, -h1);
+    hh[k] = hl[k] = 0ull;
   }
   int blk = 0;
   bool ok = true;
@@ -363,22 +410,16 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     }
     const float *rh = wst + (size_t)stg * 2 * NC * 64;
     const float *rl = rh + NC * 64;
-    float ah[2 * NC], al[2 * NC];
+    f2_t ah[NC], al[NC];
 #pragma unroll
     for (int k = 0; k < NC; k++) {
       const int col = 64 * k + 2 * lane;
       if (col + 1 < n) {
-        const float2 vh = *reinterpret_cast<const float2 *>(rh + col);
-        const float2 vl = *reinterpret_cast<const float2 *>(rl + col);
-        ah[2 * k] = vh.x;
-        ah[2 * k + 1] = vh.y;
-        al[2 * k] = vl.x;
-        al[2 * k + 1] = vl.y;
+        ah[k] = *reinterpret_cast<const f2_t *>(rh + col);
+        al[k] = *reinterpret_cast<const f2_t *>(rl + col);
       } else {
-        ah[2 * k] = (col < n) ? rh[col] : 0.0f;
-        al[2 * k] = (col < n) ? rl[col] : 0.0f;
-        ah[2 * k + 1] = 0.0f;
-        al[2 * k + 1] = 0.0f;
+        ah[k] = (col < n) ? f2_pack(rh[col], 0.0f) : 0ull;
+        al[k] = (col < n) ? f2_pack(rl[col], 0.0f) : 0ull;
       }
     }
     // every lane has its values: the stage may be refilled (generic reads
@@ -386,29 +427,16 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     __syncwarp();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     issue(q + kDfStages);
-    // two independent double-float accumulators (even / odd k) halve the
-    // dependent TwoSum chain of the row product
-    float sh0 = 0.0f, sl0 = 0.0f, sh1 = 0.0f, sl1 = 0.0f;
+    // two independent double-float accumulators (even / odd column, the
+    // halves of one packed pair) halve the dependent TwoSum chain
+    f2_t shp = 0ull, slp = 0ull;
 #pragma unroll
-    for (int k = 0; k < 2 * NC; k += 2) {
-      const float p0 = __fmul_rn(ah[k], zh[k]);
-      const float c0 = __fmaf_rn(ah[k], zl[k], __fmaf_rn(al[k], zh[k], __fmaf_rn(ah[k], zh[k], -p0)));
-      const float p1 = __fmul_rn(ah[k + 1], zh[k + 1]);
-      const float c1 = __fmaf_rn(ah[k + 1], zl[k + 1],
-                                 __fmaf_rn(al[k + 1], zh[k + 1], __fmaf_rn(ah[k + 1], zh[k + 1], -p1)));
-      float s, er;
-      two_sum_f(sh0, p0, s, er);
-      sh0 = s;
-      sl0 = __fadd_rn(sl0, __fadd_rn(er, c0));
-      two_sum_f(sh1, p1, s, er);
-      sh1 = s;
-      sl1 = __fadd_rn(sl1, __fadd_rn(er, c1));
-    }
+    for (int k = 0; k < NC; k++) f2_dd_step(shp, slp, ah[k], al[k], zh[k], zl[k], zn[k]);
     float sh_, sl_;
     {
       float er;
-      two_sum_f(sh0, sh1, sh_, er);
-      sl_ = __fadd_rn(__fadd_rn(sl0, sl1), er);
+      two_sum_f(f2_lo(shp), f2_hi(shp), sh_, er);
+      sl_ = __fadd_rn(__fadd_rn(f2_lo(slp), f2_hi(slp)), er);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -425,23 +453,17 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     // column sums: TwoSum into the high word, error terms into the low word;
     // the low word only gathers kDfFlush rows of small terms before the FP64
     // flush, so it is not renormalised row by row
+    const f2_t th2 = f2_pack(th, th), tl2 = f2_pack(tl, tl), tn2 = f2_pack(-th, -th);
 #pragma unroll
-    for (int k = 0; k < 2 * NC; k++) {
-      const float p = __fmul_rn(ah[k], th);
-      const float c = __fmaf_rn(ah[k], tl, __fmaf_rn(al[k], th, __fmaf_rn(ah[k], th, -p)));
-      float s, er;
-      two_sum_f(hh[k], p, s, er);
-      hh[k] = s;
-      hl[k] = __fadd_rn(hl[k], __fadd_rn(er, c));
-    }
+    for (int k = 0; k < NC; k++) f2_dd_step(hh[k], hl[k], ah[k], al[k], th2, tl2, tn2);
     if (++blk == kDfFlush) {
       blk = 0;
 #pragma unroll
       for (int k = 0; k < NC; k++) {
         const int col = 64 * k + 2 * lane;
-        hw[col] += widen(hh[2 * k]) + widen(hl[2 * k]);
-        hw[col + 1] += widen(hh[2 * k + 1]) + widen(hl[2 * k + 1]);
-        hh[2 * k] = hl[2 * k] = hh[2 * k + 1] = hl[2 * k + 1] = 0.0f;
+        hw[col] += widen(f2_lo(hh[k])) + widen(f2_lo(hl[k]));
+        hw[col + 1] += widen(f2_hi(hh[k])) + widen(f2_hi(hl[k]));
+        hh[k] = hl[k] = 0ull;
       }
     }
   }
@@ -454,8 +476,8 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
 #pragma unroll
   for (int k = 0; k < NC; k++) {
     const int col = 64 * k + 2 * lane;
-    hw[col] += widen(hh[2 * k]) + widen(hl[2 * k]);
-    hw[col + 1] += widen(hh[2 * k + 1]) + widen(hl[2 * k + 1]);
+    hw[col] += widen(f2_lo(hh[k])) + widen(f2_lo(hl[k]));
+    hw[col + 1] += widen(f2_hi(hh[k])) + widen(f2_hi(hl[k]));
   }
   __syncthreads();
   // fixed-order sum over the warps of this CTA, scaled back by 2^Fz
