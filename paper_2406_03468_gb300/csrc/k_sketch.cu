@@ -519,6 +519,124 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
     out[n] = (accumulate ? out[n] : 0.0) + (dob ? (double)accb * cpow[npad] : 0.0);
 }
 
+// Fixed-point copy of rows [row0, row1): Q[i ldq + j] = (+-) trunc(|A_ij| /
+// 2^F_j) and Qb[i] for b (F from fixed_params_kernel, the terms add_fixed
+// forms), so the zeta reads of each entry by the gather are plain 64-bit
+// additions.  One warp per row, 64 NC columns per row.
+template <int NC, bool VEC>
+__global__ void __launch_bounds__(kPassThreads)
+    fixed_copy_kernel(const double *__restrict__ A, int64_t lda, int n, const double *__restrict__ b,
+                      int npad, const int *__restrict__ cshift, int64_t row0, int64_t row1,
+                      long long *__restrict__ Q, int64_t ldq, long long *__restrict__ Qb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int sh[2 * NC];
+#pragma unroll
+  for (int k = 0; k < NC; k++) {
+    const int col = 64 * k + 2 * lane;
+    sh[2 * k] = col < n ? cshift[col] : 0;
+    sh[2 * k + 1] = col + 1 < n ? cshift[col + 1] : 0;
+  }
+  const int shb = b != nullptr ? cshift[npad] : 0;
+  const int64_t rows = row1 - row0, per = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = row0 + min(rows, (int64_t)blockIdx.x * per), r1 = min(row1, r0 + per);
+  for (int64_t i = r0 + warp; i < r1; i += nw) {
+    double a[2 * NC];
+    load_row<NC, VEC>(A + i * lda, n, lane, a);
+    long long q[2 * NC];
+#pragma unroll
+    for (int k = 0; k < 2 * NC; k++) {
+      q[k] = 0;
+      add_fixed(q[k], a[k], sh[k], 0u);
+    }
+    long long *row = Q + i * ldq;
+#pragma unroll
+    for (int k = 0; k < NC; k++) {
+      const int col = 64 * k + 2 * lane;
+      if (col + 1 < n) __stcs(reinterpret_cast<longlong2 *>(row + col), make_longlong2(q[2 * k], q[2 * k + 1]));
+      else if (col < n) row[col] = q[2 * k];
+    }
+    if (b != nullptr && lane == 0) {
+      long long qb = 0;
+      add_fixed(qb, b[i], shb, 0u);
+      Qb[i] = qb;
+    }
+  }
+}
+
+// The gather on the fixed-point copy: the same integer sums as gather_kernel.
+template <int CH>
+__global__ void __launch_bounds__(kGatherWarps * 32)
+    gather_q_kernel(const long long *__restrict__ Q, int64_t ldq, int n,
+                    const long long *__restrict__ Qb, int d, int npad,
+                    const int64_t *__restrict__ ptr, const uint32_t *__restrict__ src,
+                    const double *__restrict__ cpow, double *__restrict__ SAb, int64_t row0,
+                    int64_t row1, int accumulate) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.y * CH * 64;
+  const int h = blockIdx.x * kGatherWarps + warp;
+  if (h >= d) return;
+  const bool dob = (Qb != nullptr && blockIdx.y == 0);
+  long long acc[2 * CH];
+#pragma unroll
+  for (int k = 0; k < 2 * CH; k++) acc[k] = 0;
+  long long accb = 0;
+  int64_t pbeg = ptr[h], pend = ptr[h + 1];
+  if (row0 > 0) {
+    int64_t lo = pbeg, hi = pend;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)(__ldg(src + mid) & 0x7fffffffu) < row0) lo = mid + 1;
+      else hi = mid;
+    }
+    pbeg = lo;
+  }
+  for (int64_t p0 = pbeg; p0 < pend; p0 += 32) {
+    const uint32_t mine = (p0 + lane < pend) ? __ldg(src + p0 + lane) : 0x7fffffffu;
+    const unsigned beyond = __ballot_sync(0xffffffffu, (int64_t)(mine & 0x7fffffffu) >= row1);
+    const int cnt = beyond ? __ffs(beyond) - 1 : (int)min((int64_t)32, pend - p0);
+#pragma unroll 1
+    for (int q = 0; q < cnt; q++) {
+      const uint32_t e = __shfl_sync(0xffffffffu, mine, q);
+      const int64_t i = e & 0x7fffffffu;
+      const long long *row = Q + i * ldq + c0;
+      long long v[2 * CH];
+#pragma unroll
+      for (int k = 0; k < CH; k++) {
+        const int col = 64 * k + 2 * lane;
+        if (c0 + col + 1 < n) {
+          const longlong2 t = __ldg(reinterpret_cast<const longlong2 *>(row + col));
+          v[2 * k] = t.x;
+          v[2 * k + 1] = t.y;
+        } else {
+          v[2 * k] = (c0 + col < n) ? __ldg(row + col) : 0;
+          v[2 * k + 1] = 0;
+        }
+      }
+      const long long vb = (dob && lane == 0) ? __ldg(Qb + i) : 0;
+      if (e >> 31) {  // the sign of the entry: the same for the whole warp
+#pragma unroll
+        for (int k = 0; k < 2 * CH; k++) acc[k] -= v[k];
+        accb -= vb;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 2 * CH; k++) acc[k] += v[k];
+        accb += vb;
+      }
+    }
+    if (beyond) break;
+  }
+  double *out = SAb + (size_t)h * (n + 1);
+#pragma unroll
+  for (int k = 0; k < CH; k++) {
+    const int col = c0 + 64 * k + 2 * lane;
+    if (col < n) out[col] = (accumulate ? out[col] : 0.0) + (double)acc[2 * k] * cpow[col];
+    if (col + 1 < n)
+      out[col + 1] = (accumulate ? out[col + 1] : 0.0) + (double)acc[2 * k + 1] * cpow[col + 1];
+  }
+  if (blockIdx.y == 0 && lane == 0)
+    out[n] = (accumulate ? out[n] : 0.0) + (dob ? (double)accb * cpow[npad] : 0.0);
+}
+
 }  // namespace
 
 int pass_npad(int n) {
@@ -625,23 +743,50 @@ cudaError_t launch_sketch_gather(const double *A, int64_t lda, int n, const doub
                                  int npad, const int64_t *ptr, const uint32_t *src,
                                  const int *colexp, const int *lmax, int *cshift, double *cpow,
                                  double *SAb, DevState *st, cudaStream_t s, int64_t row0,
-                                 int64_t row1, int accumulate) {
+                                 int64_t row1, int accumulate, long long *Q, long long *Qb,
+                                 int64_t ldq, int grid) {
   fixed_params_kernel<<<(npad + 1 + 255) / 256, 256, 0, s>>>(colexp, n, npad, lmax, cshift, cpow,
                                                               st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // 128 columns per warp (48 registers): a whole column chunk's d warps are
-  // resident at once on 152 SMs for d up to ~6000, so they sweep A together
+  // 128 columns per warp: a whole column chunk's d warps are resident at
+  // once on 152 SMs for d up to ~6000, so they sweep the rows together
   const int ch = npad >= 128 ? 2 : 1;
-  const dim3 grid((unsigned)((d + kGatherWarps - 1) / kGatherWarps),
-                  (unsigned)((n + 64 * ch - 1) / (64 * ch)));
+  const dim3 ggrid((unsigned)((d + kGatherWarps - 1) / kGatherWarps),
+                   (unsigned)((n + 64 * ch - 1) / (64 * ch)));
   const int th = kGatherWarps * 32;
+  if (Q != nullptr) {
+    const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 2 == 0);
+#define LSQ_FIXED_COPY(NC)                                                                       \
+  (vec ? fixed_copy_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, n, b, npad, cshift,   \
+                                                                  row0, row1, Q, ldq, Qb)        \
+       : fixed_copy_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, n, b, npad, cshift,  \
+                                                                   row0, row1, Q, ldq, Qb))
+    switch (npad / 64) {
+      case 1: LSQ_FIXED_COPY(1); break;
+      case 2: LSQ_FIXED_COPY(2); break;
+      case 4: LSQ_FIXED_COPY(4); break;
+      case 8: LSQ_FIXED_COPY(8); break;
+      case 16: LSQ_FIXED_COPY(16); break;
+      default: return cudaErrorInvalidValue;
+    }
+#undef LSQ_FIXED_COPY
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ch == 2)
+      gather_q_kernel<2><<<ggrid, th, 0, s>>>(Q, ldq, n, b ? Qb : nullptr, d, npad, ptr, src, cpow,
+                                              SAb, row0, row1, accumulate);
+    else
+      gather_q_kernel<1><<<ggrid, th, 0, s>>>(Q, ldq, n, b ? Qb : nullptr, d, npad, ptr, src, cpow,
+                                              SAb, row0, row1, accumulate);
+    return cudaGetLastError();
+  }
   if (ch == 2)
-    gather_kernel<2><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb, row0,
-                                         row1, accumulate);
+    gather_kernel<2><<<ggrid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb, row0,
+                                          row1, accumulate);
   else
-    gather_kernel<1><<<grid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb, row0,
-                                         row1, accumulate);
+    gather_kernel<1><<<ggrid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb, row0,
+                                          row1, accumulate);
   return cudaGetLastError();
 }
 

@@ -76,6 +76,7 @@ struct lsq_plan_s {
   int64_t *tptr = nullptr;
   uint32_t *tsrc = nullptr;
   double *cpow = nullptr;
+  long long *Qfix = nullptr, *Qbfix = nullptr;  // fixed-point copy of A and b (gather)
   double *SAb = nullptr, *W = nullptr, *part = nullptr, *r2part = nullptr, *cpart = nullptr;
   double *dcol = nullptr, *dinv = nullptr, *Rcm = nullptr, *Rrm = nullptr, *rinv = nullptr;
   double *Dt = nullptr;  // scaled diagonal blocks of R (launch_diag_tiles)
@@ -347,8 +348,8 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db, bool defer_
                                 planes ? P->Alo + r0 * P->ld32 : nullptr, P->ld32, P->s, c > 0));
       LSQ_CU(launch_sketch_gather(dA, P->lda, n, db, P->d, P->npad, P->tptr, P->tsrc, P->colexp,
                                   P->tlmax, P->cshift, P->cpow, P->SAb, P->st, P->s, r0, r1,
-                                  c > 0));
-      P->launches += 3;
+                                  c > 0, P->Qfix, P->Qbfix, (n + 1) & ~1, P->gpass));
+      P->launches += 4;  // prep, fixed parameters, fixed-point copy, gather
     }
     P->launches -= 1;  // counted below with the finalize
   } else {
@@ -739,7 +740,7 @@ void free_plan(lsq_plan P) {
                   P->stageb, P->stagex, P->Ahi, P->Alo, P->SBb, P->cpartB, P->mpart, P->mpartdf, P->mr2part,
                   P->mT, P->mXs, P->mXo, P->mC, P->mG, P->mDY, P->mDYold, P->mZ, P->mH,
                   P->mW, P->mstate, P->tcnt, P->tlmax, P->colexp, P->cshift,
-                  P->tptr, P->tsrc, P->cpow};
+                  P->tptr, P->tsrc, P->cpow, P->Qfix, P->Qbfix};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->st_host) cudaFreeHost(P->st_host);
@@ -810,6 +811,8 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
     A(dalloc(&P->colexp, (size_t)P->npad + 1));
     A(dalloc(&P->cshift, (size_t)P->npad + 1));
     A(dalloc(&P->cpow, (size_t)P->npad + 1));
+    A(dalloc(&P->Qfix, (size_t)P->m_cap * (size_t)((n + 1) & ~1)));
+    A(dalloc(&P->Qbfix, (size_t)P->m_cap));
   }
   P->k = opt->nrhs > 0 ? opt->nrhs : 0;
   A(dalloc(&P->SAb, dn1));
