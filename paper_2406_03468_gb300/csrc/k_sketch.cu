@@ -435,90 +435,6 @@ __device__ __forceinline__ void add_fixed(long long &acc, double a, int C, unsig
   acc += (long long)((t ^ m) - m);
 }
 
-template <int CH>
-__global__ void __launch_bounds__(kGatherWarps * 32)
-    gather_kernel(const double *__restrict__ A, int64_t lda, int n, const double *__restrict__ b,
-                  int d, int npad, const int64_t *__restrict__ ptr,
-                  const uint32_t *__restrict__ src, const int *__restrict__ cshift,
-                  const double *__restrict__ cpow, double *__restrict__ SAb, int64_t row0,
-                  int64_t row1, int accumulate) {
-  __shared__ int sh[CH * 64];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c0 = blockIdx.y * CH * 64;
-  for (int i = threadIdx.x; i < CH * 64; i += blockDim.x)
-    sh[i] = (c0 + i < n) ? cshift[c0 + i] : 0;
-  __syncthreads();
-  const int h = blockIdx.x * kGatherWarps + warp;
-  if (h >= d) return;
-  const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 2 == 0);
-  const bool dob = (b != nullptr && blockIdx.y == 0);
-  const int shb = dob ? cshift[npad] : 0;
-  int shl[2 * CH];
-#pragma unroll
-  for (int k = 0; k < CH; k++) {
-    shl[2 * k] = sh[64 * k + 2 * lane];
-    shl[2 * k + 1] = sh[64 * k + 2 * lane + 1];
-  }
-  long long acc[2 * CH];
-#pragma unroll
-  for (int k = 0; k < 2 * CH; k++) acc[k] = 0;
-  long long accb = 0;
-  // this call's rows [row0, row1) of the sorted list: the first entry at or
-  // after row0 by binary search, then up to the first one at or after row1
-  int64_t pbeg = ptr[h], pend = ptr[h + 1];
-  if (row0 > 0) {
-    int64_t lo = pbeg, hi = pend;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if ((int64_t)(__ldg(src + mid) & 0x7fffffffu) < row0) lo = mid + 1;
-      else hi = mid;
-    }
-    pbeg = lo;
-  }
-  for (int64_t p0 = pbeg; p0 < pend; p0 += 32) {
-    // 32 list entries with one coalesced load, handed out by shuffles
-    const uint32_t mine = (p0 + lane < pend) ? __ldg(src + p0 + lane) : 0x7fffffffu;
-    // entries are sorted by row: stop at the first one at or beyond row1
-    const unsigned beyond = __ballot_sync(0xffffffffu, (int64_t)(mine & 0x7fffffffu) >= row1);
-    const int cnt = beyond ? __ffs(beyond) - 1 : (int)min((int64_t)32, pend - p0);
-#pragma unroll 1
-    for (int q = 0; q < cnt; q++) {
-      const uint32_t e = __shfl_sync(0xffffffffu, mine, q);
-      const int64_t i = e & 0x7fffffffu;
-      const unsigned neg = e >> 31;
-      const double *row = A + i * lda + c0;
-      double a[2 * CH];
-#pragma unroll
-      for (int k = 0; k < CH; k++) {
-        const int col = 64 * k + 2 * lane;
-        if (vec && c0 + col + 1 < n) {
-          const double2 v = __ldg(reinterpret_cast<const double2 *>(row + col));
-          a[2 * k] = v.x;
-          a[2 * k + 1] = v.y;
-        } else {
-          a[2 * k] = (c0 + col < n) ? __ldg(row + col) : 0.0;
-          a[2 * k + 1] = (c0 + col + 1 < n) ? __ldg(row + col + 1) : 0.0;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 2 * CH; k++) add_fixed(acc[k], a[k], shl[k], neg);
-      if (dob && lane == 0) add_fixed(accb, __ldg(b + i), shb, neg);
-    }
-    if (beyond) break;
-  }
-  // accumulate: add to the sums of earlier row ranges (one FP64 rounding each)
-  double *out = SAb + (size_t)h * (n + 1);
-#pragma unroll
-  for (int k = 0; k < CH; k++) {
-    const int col = c0 + 64 * k + 2 * lane;
-    if (col < n) out[col] = (accumulate ? out[col] : 0.0) + (double)acc[2 * k] * cpow[col];
-    if (col + 1 < n)
-      out[col + 1] = (accumulate ? out[col + 1] : 0.0) + (double)acc[2 * k + 1] * cpow[col + 1];
-  }
-  if (blockIdx.y == 0 && lane == 0)
-    out[n] = (accumulate ? out[n] : 0.0) + (dob ? (double)accb * cpow[npad] : 0.0);
-}
-
 // Fixed-point copy of rows [row0, row1): Q[i ldq + j] = (+-) trunc(|A_ij| /
 // 2^F_j) and Qb[i] for b (F from fixed_params_kernel, the terms add_fixed
 // forms), so the zeta reads of each entry by the gather are plain 64-bit
@@ -563,7 +479,11 @@ __global__ void __launch_bounds__(kPassThreads)
   }
 }
 
-// The gather on the fixed-point copy: the same integer sums as gather_kernel.
+// The gather: one warp per (sketch row h, chunk of 64 CH columns) walks h's
+// sorted source list and adds or subtracts (the entry's sign, the same for
+// the whole warp) the rows' fixed-point values: exact 64-bit integer sums,
+// each rounded once to FP64 (times 2^F_j) at the end; accumulate = 1 adds
+// them to SAb (rows in chunks).
 template <int CH>
 __global__ void __launch_bounds__(kGatherWarps * 32)
     gather_q_kernel(const long long *__restrict__ Q, int64_t ldq, int n,
@@ -755,7 +675,8 @@ cudaError_t launch_sketch_gather(const double *A, int64_t lda, int n, const doub
   const dim3 ggrid((unsigned)((d + kGatherWarps - 1) / kGatherWarps),
                    (unsigned)((n + 64 * ch - 1) / (64 * ch)));
   const int th = kGatherWarps * 32;
-  if (Q != nullptr) {
+  if (Q == nullptr) return cudaErrorInvalidValue;
+  {
     const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 2 == 0);
 #define LSQ_FIXED_COPY(NC)                                                                       \
   (vec ? fixed_copy_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, n, b, npad, cshift,   \
@@ -781,13 +702,6 @@ cudaError_t launch_sketch_gather(const double *A, int64_t lda, int n, const doub
                                               SAb, row0, row1, accumulate);
     return cudaGetLastError();
   }
-  if (ch == 2)
-    gather_kernel<2><<<ggrid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb, row0,
-                                          row1, accumulate);
-  else
-    gather_kernel<1><<<ggrid, th, 0, s>>>(A, lda, n, b, d, npad, ptr, src, cshift, cpow, SAb, row0,
-                                          row1, accumulate);
-  return cudaGetLastError();
 }
 
 }  // namespace lsq

@@ -126,10 +126,10 @@ cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, const 
 // A may come in row chunks, each taken by a prep then a gather in row order,
 // accumulate = 0 for the first: the prep is given the chunk (A, b, Ahi, Alo
 // offset to its first row, m its rows), the gather all of A and b and the
-// chunk's row range; each chunk gets its own fixed-point scale.  With Q
-// (>= row1 rows of ldq int64, ldq even) and Qb (b's, when b is given) the
-// rows' fixed-point values are written there first (grid CTAs), once per
-// entry, and the gather adds those: the same integer sums.
+// chunk's row range; each chunk gets its own fixed-point scale.  The rows'
+// fixed-point values go to Q (>= row1 rows of ldq int64, ldq even; required)
+// and Qb (b's, when b is given) first (grid CTAs), once per entry, and the
+// gather adds those.
 cudaError_t launch_sketch_lists(const int32_t *rows, const uint32_t *signbits, int64_t m, int zeta,
                                 int d, int *cnt, int64_t *ptr, uint32_t *src, int *lmax,
                                 cudaStream_t s);
@@ -141,8 +141,8 @@ cudaError_t launch_sketch_gather(const double *A, int64_t lda, int n, const doub
                                  int npad, const int64_t *ptr, const uint32_t *src,
                                  const int *colexp, const int *lmax, int *cshift, double *cpow,
                                  double *SAb, DevState *st, cudaStream_t s, int64_t row0,
-                                 int64_t row1, int accumulate, long long *Q = nullptr,
-                                 long long *Qb = nullptr, int64_t ldq = 0, int grid = 0);
+                                 int64_t row1, int accumulate, long long *Q, long long *Qb,
+                                 int64_t ldq, int grid);
 // Column norms from partials, scaling, transpose into column-major W (ld d).
 cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad, int n, int d,
                                    int zeta, int col_scale, const double *SAb, double *W,
