@@ -11,7 +11,7 @@
 // of column k of W hold u (they are below R's triangle), and u_1, beta go to
 // a 2-per-column side array.
 //
-// GB300 design: one persistent cooperative launch, two CTAs per SM.  Each
+// GB300 design: one persistent cooperative launch, one CTA per SM.  Each
 // column belongs to one CTA for the whole factorisation (snake order, see
 // qr_owner) and, when the CTA's columns fit (d = 12n up to n ~ 600), lives
 // in that CTA's shared memory from start to end.  There is no grid-wide barrier: the owner of column k
@@ -28,7 +28,14 @@ namespace lsq {
 namespace {
 
 constexpr int kQrThreads = 256;
-constexpr int kQrCtasPerSm = 2;  // two CTAs per SM: one's barriers overlap the other's FP64 work
+// CTAs per SM.  Columns in shared memory: one, since with the serial
+// chain's step fused (apply_build_regs) a second CTA's catch-up FP64 work on
+// the same SM slows the chain more than its barrier overlap gains (6.64 vs
+// 6.96 ms at d = 6000, n = 500).  Columns in global memory: two, whose
+// overlap hides L2 latency (72 vs 106 ms at d = 12000, n = 1000).
+constexpr int kQrSmemCtasPerSm = 1;
+constexpr int kQrGlobalCtasPerSm = 2;
+constexpr int kQrStepCtasPerSm = 2;  // the one-launch-per-column form
 constexpr int kQrBatch = 8;  // columns updated together by one CTA
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -240,7 +247,7 @@ __device__ __forceinline__ int qr_col(int me, int l, int G) {
 enum { kQrDone = 0, kQrBuild = 1, kQrApply = 2, kQrFail = 3, kQrApplyBuild = 4 };
 
 template <bool SMEM, int VR>
-__global__ void __launch_bounds__(kQrThreads, kQrCtasPerSm)
+__global__ void __launch_bounds__(kQrThreads, SMEM ? kQrSmemCtasPerSm : kQrGlobalCtasPerSm)
     qr_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
               int *flags, int epoch, DevState *st, uint64_t timeout_ns) {
   extern __shared__ double dsm[];
@@ -485,7 +492,12 @@ __global__ void extract_r_kernel(const double *__restrict__ W, int d, int n, int
 
 }  // namespace
 
-int qr_grid(int ncols, int nsm) { return ncols < kQrCtasPerSm * nsm ? ncols : kQrCtasPerSm * nsm; }
+int qr_grid(int ncols, int nsm) {
+  return ncols < kQrGlobalCtasPerSm * nsm ? ncols : kQrGlobalCtasPerSm * nsm;
+}
+int qr_step_grid(int ncols, int nsm) {
+  return ncols < kQrStepCtasPerSm * nsm ? ncols : kQrStepCtasPerSm * nsm;
+}
 
 // Largest dynamic shared memory the columns may use (227 KB opt-in minus the static part).
 constexpr size_t kQrSmemMax = 225 * 1024;
@@ -512,12 +524,16 @@ cudaError_t launch_qr_vr(void **args, int d, int grid, size_t smem, cudaStream_t
 cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vhead, int *flags, int epoch,
                       DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s) {
   void *args[] = {&W, &d, &n, &ncols, &vhead, &flags, &epoch, &st, &timeout_ns};
-  // columns in shared memory at kQrCtasPerSm CTAs per SM if they fit, else
-  // at one CTA per SM, else in global memory (L2) at kQrCtasPerSm per SM
+  // grid: CTAs at kQrGlobalCtasPerSm per SM (qr_grid).  Columns in shared
+  // memory at kQrSmemCtasPerSm CTAs per SM if they fit, else in global
+  // memory (L2) at kQrGlobalCtasPerSm per SM.
   auto smem_for = [&](int g) { return (size_t)((ncols + g - 1) / g) * d * sizeof(double); };
-  if (kQrCtasPerSm * smem_for(grid) <= kQrSmemMax) return launch_qr_vr<true>(args, d, grid, smem_for(grid), s);
-  const int g1 = (grid + kQrCtasPerSm - 1) / kQrCtasPerSm;
-  if (smem_for(g1) <= kQrSmemMax && (ncols + g1 - 1) / g1 <= kQrMaxLocal) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int g1 = ncols < kQrSmemCtasPerSm * nsm ? ncols : kQrSmemCtasPerSm * nsm;
+  if (kQrSmemCtasPerSm * smem_for(g1) <= kQrSmemMax && (ncols + g1 - 1) / g1 <= kQrMaxLocal) {
     void *args1[] = {&W, &d, &n, &ncols, &vhead, &flags, &epoch, &st, &timeout_ns};
     return launch_qr_vr<true>(args1, d, g1, smem_for(g1), s);
   }

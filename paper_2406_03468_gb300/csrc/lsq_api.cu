@@ -365,7 +365,7 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db, bool defer_
   LSQ_CU(cudaEventRecord(P->ev[1], P->s));
   P->launches += 3 + 5;  // sketch, colnorm, transpose; qr, extract, tiles, condest, x0 solve
   if (P->stepwise_qr)
-    LSQ_CU(launch_qr_stepwise(P->W, P->d, n, n + 1, P->vbuf, qr_grid(n + 1, P->nsm), P->s));
+    LSQ_CU(launch_qr_stepwise(P->W, P->d, n, n + 1, P->vbuf, qr_step_grid(n + 1, P->nsm), P->s));
   else
     LSQ_CU(launch_qr(P->W, P->d, n, n + 1, P->vbuf, P->qflag, next_epoch(P), P->st,
                      qr_grid(n + 1, P->nsm), kBarrierTimeoutNs, P->s));

@@ -155,7 +155,8 @@ cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad,
 // from the previous launch's).  Waits are bounded by timeout_ns.
 cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vhead, int *flags, int epoch,
                       DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s);
-int qr_grid(int ncols, int nsm);
+int qr_grid(int ncols, int nsm);       // CTAs of launch_qr
+int qr_step_grid(int ncols, int nsm);  // CTAs of launch_qr_stepwise
 // The same factorisation as n + 1 ordinary launches (no inter-CTA waits): safe
 // to run concurrently with other solves' kernels.
 cudaError_t launch_qr_stepwise(double *W, int d, int n, int ncols, double *vhead, int grid,
