@@ -637,21 +637,49 @@ __global__ void reduce_batched_kernel(const double *__restrict__ part, int grid,
   out[idx] = scale ? scale[j] * s : s;
 }
 
-__global__ void reduce_kernel(const double *__restrict__ part, int grid, int npad, int n,
-                              const double *__restrict__ scale, double *__restrict__ out,
-                              const double *__restrict__ r2_part, double *r2,
-                              const DevState *gate) {
+// out[j] = scale[j] sum_g part[g npad + j]; *r2 = sum_g r2_part[g] (CTA 0).
+// One CTA per 32 columns: warp w sums the partials g = w, w + 8, ... of the
+// lane's column, then warp 0 adds the 8 warp sums in order (a fixed order,
+// so the result is deterministic).  A sub-partition issues one FP64 warp
+// instruction per 64 cycles, so the partials of a column are spread over
+// all four sub-partitions rather than summed by one thread.
+constexpr int kReduceThreads = 256;
+__global__ void __launch_bounds__(kReduceThreads)
+    reduce_kernel(const double *__restrict__ part, int grid, int npad, int n,
+                  const double *__restrict__ scale, double *__restrict__ out,
+                  const double *__restrict__ r2_part, double *r2, const DevState *gate) {
   if (gate != nullptr && *(volatile const int *)&gate->done) return;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double red[kReduceThreads / 32][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kReduceThreads / 32;
+  const int j = blockIdx.x * 32 + lane;
+  double s0 = 0.0, s1 = 0.0;
   if (j < n) {
+    int g = warp;
+    for (; g + nw < grid; g += 2 * nw) {
+      s0 += part[(size_t)g * npad + j];
+      s1 += part[(size_t)(g + nw) * npad + j];
+    }
+    if (g < grid) s0 += part[(size_t)g * npad + j];
+  }
+  red[warp][lane] = s0 + s1;
+  __syncthreads();
+  if (warp == 0 && j < n) {
     double s = 0.0;
-    for (int g = 0; g < grid; g++) s += part[(size_t)g * npad + j];
+    for (int w = 0; w < nw; w++) s += red[w][lane];
     out[j] = scale ? scale[j] * s : s;
   }
-  if (r2 != nullptr && j == 0) {
-    double s = 0.0;
-    for (int g = 0; g < grid; g++) s += r2_part[g];
-    *r2 = s;
+  if (r2 != nullptr && blockIdx.x == 0) {
+    __syncthreads();
+    double t = 0.0;
+    for (int g = threadIdx.x; g < grid; g += kReduceThreads) t += r2_part[g];
+    t = warp_sum(t);
+    if (lane == 0) red[warp][32] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double u = 0.0;
+      for (int w = 0; w < nw; w++) u += red[w][32];
+      *r2 = u;
+    }
   }
 }
 
@@ -751,9 +779,8 @@ cudaError_t launch_reduce_batched(const double *part, int grid, int npad, int n,
 cudaError_t launch_reduce(const double *part, int grid, int npad, int n, const double *scale,
                           double *out, const double *r2_part, double *r2, const DevState *gate,
                           cudaStream_t s) {
-  const int th = 128;
-  const int blocks = (n + th - 1) / th;
-  reduce_kernel<<<blocks, th, 0, s>>>(part, grid, npad, n, scale, out, r2_part, r2, gate);
+  reduce_kernel<<<(n + 31) / 32, kReduceThreads, 0, s>>>(part, grid, npad, n, scale, out, r2_part,
+                                                       r2, gate);
   return cudaGetLastError();
 }
 
