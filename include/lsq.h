@@ -201,6 +201,15 @@ lsq_status lsq_sketch_pattern(lsq_plan plan, int32_t *d_rows, uint32_t *d_signbi
  * leading dimension d) and the column norms d_j (n) to device buffers. */
 lsq_status lsq_get_sketch(lsq_plan plan, double *dSAb, double *dcolnorm);
 
+/* After lsq_sketch or a solve on the plan: copy the sums of the unscaled
+ * sketch, S' [A b] with S' the +-1 pattern of Sec. 4.2's embedding (no
+ * zeta^{-1/2}, no column scaling), to dSAb (d x (n+1) FP64, row-major,
+ * device).  For m n >= 2^24 these are the 64-bit fixed-point sums, each
+ * rounded once to FP64 (for lsq_solve_host: per row chunk, the chunks added
+ * in order); below that, FP64 atomic sums whose order is not fixed.
+ * Errors: LSQ_ERR_INVALID for NULL arguments or before any sketch. */
+lsq_status lsq_get_sketch_raw(lsq_plan plan, double *dSAb);
+
 /* After lsq_sketch: copy R (n x n, row-major, zeros below the diagonal),
  * t = (Q^T Sb)[0:n] and x0 (scaled coordinates) to device buffers (any may
  * be NULL), and the condest / normest estimates to host doubles (may be NULL). */

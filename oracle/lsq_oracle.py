@@ -152,6 +152,58 @@ def sketch(A, b, d, zeta, seed):
     return SA, Sb
 
 
+def fixed_point_sketch(A, b, d, zeta, seed, row_chunks=None):
+    """Unscaled S [A b] (the +-1 pattern of Sec. 4.2's sparse sign embedding,
+    without the zeta^{-1/2} factor) summed in 64-bit fixed point per column,
+    the summation order this build takes for large problems (the paper fixes
+    none).  Every term a_ij is truncated toward zero to a multiple of 2^F_j,
+    F_j = (E_j - 1022) + L - 63, where E_j is the largest biased exponent in
+    column j over the rows summed (at least 1) and L the bit length of the
+    longest source list (the most nonzeros in one row of S; at least 10).  The
+    truncated terms are added exactly in integers, and each sum is rounded
+    once to FP64 and scaled by 2^F_j.
+
+    row_chunks: row boundaries [0, r_1, ..., m]; each chunk has its own E_j,
+    and the chunk results are added in FP64 in chunk order.  Returns the
+    (d, n + 1) array whose last column is S b.  Plain numpy and scipy integer
+    arithmetic; the sparse product is a library step on exact integers.
+    """
+    import scipy.sparse as sp
+    from .philox import sparse_sign_pattern
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    rows, signs = sparse_sign_pattern(m, d, zeta, seed)
+    lmax = int(np.bincount(rows[rows >= 0].ravel(), minlength=d).max())
+    L = 10
+    while L < 40 and (1 << L) <= lmax:
+        L += 1
+    Ab = np.ascontiguousarray(np.concatenate([A, np.asarray(b, dtype=np.float64)[:, None]], axis=1))
+    bounds = list(row_chunks) if row_chunks is not None else [0, m]
+    out = None
+    for c in range(len(bounds) - 1):
+        r0, r1 = int(bounds[c]), int(bounds[c + 1])
+        bits = Ab[r0:r1].view(np.uint64)
+        e = ((bits >> np.uint64(52)) & np.uint64(0x7FF)).astype(np.int64)
+        E = np.maximum(e.max(axis=0), 1)
+        F = (E - 1022) + L - 63
+        shift = (1075 + F)[None, :] - e              # >= L - 10 >= 0 where e >= 1
+        mant = (bits & np.uint64((1 << 52) - 1)) | np.uint64(1 << 52)
+        keep = (e > 0) & (shift < 64)
+        t = np.where(keep, mant >> np.minimum(shift, 63).astype(np.uint64), np.uint64(0))
+        t = t.astype(np.int64)
+        t = np.where((bits >> np.uint64(63)) == 1, -t, t)
+        # sum over each row of S: the +-1 entries of S times the integer terms
+        rr, ss = rows[r0:r1], signs[r0:r1]
+        ok = rr >= 0
+        cols = np.repeat(np.arange(r1 - r0, dtype=np.int64)[:, None], rr.shape[1], axis=1)
+        S = sp.csr_matrix((ss[ok].astype(np.int64), (rr[ok], cols[ok])), shape=(d, r1 - r0),
+                          dtype=np.int64)
+        sums = np.asarray(S @ t, dtype=np.int64)
+        part = sums.astype(np.float64) * np.ldexp(1.0, F)[None, :]
+        out = part if out is None else out + part
+    return out
+
+
 def sigma_extremes(R):
     """(sigma_max, sigma_min) of R via the LAPACK SVD (a library step)."""
     s = np.linalg.svd(R, compute_uv=False)

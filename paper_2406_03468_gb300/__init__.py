@@ -16,7 +16,7 @@ __all__ = [
     "LsqError", "LsqOptions", "LsqInfo", "lsq_options_default", "lsq_plan_create",
     "lsq_plan_destroy", "lsq_plan_configure", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir", "lsq_solve_host",
     "lsq_solve_fossils_multi",
-    "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_R", "lsq_apply_normal", "lsq_residual",
+    "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_sketch_raw", "lsq_get_R", "lsq_apply_normal", "lsq_residual",
     "lsq_trsv", "lsq_apply_normal_noalloc", "lsq_last_error", "Plan", "lsq_server_create",
     "lsq_submit", "lsq_poll", "lsq_server_stats", "lsq_server_destroy", "library_path", "EXPORTED",
     "LSQ_PREC_AUTO", "LSQ_PREC_FP64", "LSQ_PREC_FP32_INNER",
@@ -94,6 +94,7 @@ EXPORTED = {
                                        ctypes.POINTER(LsqInfo)]),
     "lsq_sketch_pattern": (_i32, [_vp, _vp, _vp]),
     "lsq_get_sketch": (_i32, [_vp, _vp, _vp]),
+    "lsq_get_sketch_raw": (_i32, [_vp, _vp]),
     "lsq_get_R": (_i32, [_vp, _vp, _vp, _vp, _dp, _dp]),
     "lsq_apply_normal": (_i32, [_vp, _vp, _vp, _vp]),
     "lsq_residual": (_i32, [_vp, _vp, _vp, _vp, _vp, _dp]),
@@ -219,6 +220,10 @@ def lsq_sketch_pattern(plan, rows, signbits):
 
 def lsq_get_sketch(plan, SAb, colnorm):
     return _check(_lib().lsq_get_sketch(plan, _ptr(SAb), _ptr(colnorm)))
+
+
+def lsq_get_sketch_raw(plan, SAb):
+    return _check(_lib().lsq_get_sketch_raw(plan, _ptr(SAb)))
 
 
 def lsq_get_R(plan, R=None, t=None, x0=None):

@@ -1023,6 +1023,15 @@ lsq_status lsq_get_sketch(lsq_plan P, double *dSAb, double *dcolnorm) {
   return LSQ_OK;
 }
 
+lsq_status lsq_get_sketch_raw(lsq_plan P, double *dSAb) {
+  if (!P || !dSAb) return fail(LSQ_ERR_INVALID, "NULL argument");
+  if (!P->sketched) return fail(LSQ_ERR_INVALID, "call lsq_sketch first");
+  LSQ_CU(cudaMemcpyAsync(dSAb, P->SAb, sizeof(double) * (size_t)P->d * (P->n + 1),
+                         cudaMemcpyDeviceToDevice, P->s));
+  LSQ_CU(cudaStreamSynchronize(P->s));
+  return LSQ_OK;
+}
+
 lsq_status lsq_get_R(lsq_plan P, double *dR, double *dt, double *dx0, double *condest,
                      double *normest) {
   if (!P) return fail(LSQ_ERR_INVALID, "plan is NULL");

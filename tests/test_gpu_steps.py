@@ -260,7 +260,8 @@ def test_residual_pass_after_sketch(m, n):
 
 @pytest.mark.parametrize("m,n,entry", [(200003, 100, "device"), (400003, 200, "host")])
 def test_gather_sketch_fixed_point(m, n, entry):
-    """The gather form of the sketch (m n >= 2^24): each list entry is
+    """The gather form of the sketch (m n >= 2^24).  Its raw sums are integer
+    work and must equal oracle.fixed_point_sketch bit for bit.  Each list entry is
     truncated to a multiple of 2^F with F = (E - 1022) + L - 63 (E the
     largest biased exponent of the column in the rows summed, L = max(10,
     bits of the longest list)), so an entry of S A is off by less than
@@ -283,7 +284,16 @@ def test_gather_sketch_fixed_point(m, n, entry):
     SAb = empty(d * (n + 1))
     cn = empty(n)
     lsq.lsq_get_sketch(plan.handle, SAb, cn)
+    raw = empty(d * (n + 1))
+    lsq.lsq_get_sketch_raw(plan.handle, raw)
     plan.close()
+    # integer work: the fixed-point sums, rounded once to FP64 per row chunk,
+    # equal the oracle's bit for bit
+    bounds = [m * c // nch for c in range(nch + 1)]
+    ref_raw = oracle.fixed_point_sketch(A, b, d, zeta, seed, row_chunks=bounds)
+    got_raw = H(raw).reshape(d, n + 1)
+    assert np.array_equal(got_raw.view(np.uint64), ref_raw.view(np.uint64)), \
+        int((got_raw != ref_raw).sum())
     SAb = H(SAb).reshape(n + 1, d).T
     SAg = SAb[:, :n] * H(cn)            # undo the column scaling (3 roundings)
     SA, Sb = oracle.sketch(A, b, d, zeta, seed)

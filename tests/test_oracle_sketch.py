@@ -109,3 +109,81 @@ def test_embedding_whitens(m, n, d):
     eta = 1.25 * math.sqrt(n / d)
     assert s.min() >= 1 / (1 + eta)
     assert s.max() <= 1 / (1 - eta)
+
+
+def _brute_fixed_point(A, b, d, zeta, seed, bounds):
+    """The fixed-point sketch from its definition with exact rationals: each
+    term floor(|a| / 2^F_j) (signed), E_j from math.frexp, L the smallest
+    L >= 10 with 2^L above the longest source list, integer sums rounded once
+    to FP64 (Python float of an int), chunk results added in order."""
+    from fractions import Fraction
+    m, n = A.shape
+    rows, signs = sparse_sign_pattern(m, d, zeta, seed)
+    counts = [0] * d
+    for i in range(m):
+        for z in range(zeta):
+            if rows[i, z] >= 0:
+                counts[int(rows[i, z])] += 1
+    L = 10
+    while (1 << L) <= max(counts):
+        L += 1
+    cols = [A[:, j] for j in range(n)] + [b]
+    out = [[None] * (n + 1) for _ in range(d)]
+    for c in range(len(bounds) - 1):
+        r0, r1 = bounds[c], bounds[c + 1]
+        for j, col in enumerate(cols):
+            E = 1
+            for i in range(r0, r1):
+                x = float(col[i])
+                if x != 0.0:
+                    E = max(E, math.frexp(x)[1] + 1022)
+            F = (E - 1022) + L - 63
+            q = Fraction(2) ** F
+            sums = [0] * d
+            for i in range(r0, r1):
+                x = float(col[i])
+                t = int(Fraction(abs(x)) / q)      # floor of a non-negative rational
+                t = -t if x < 0 else t
+                for z in range(zeta):
+                    h = int(rows[i, z])
+                    if h >= 0:
+                        sums[h] += t if signs[i, z] > 0 else -t
+            for h in range(d):
+                v = math.ldexp(float(sums[h]), F)
+                out[h][j] = v if out[h][j] is None else out[h][j] + v
+    return np.array(out, dtype=np.float64)
+
+
+@pytest.mark.parametrize("bounds", [[0, 300], [0, 101, 300], [0, 7, 150, 299, 300]])
+def test_fixed_point_sketch_brute_force(bounds):
+    """oracle.fixed_point_sketch equals the exact-rational brute force bit for
+    bit, chunked or not, with signs, zeros and terms far below 2^F_j."""
+    rng = np.random.default_rng(17)
+    m, n, d, zeta, seed = 300, 5, 12, 3, 23
+    A = rng.standard_normal((m, n)) * np.array([1.0, 1e-3, 1e5, 1.0, 3.0])
+    A[::7, 0] = 0.0
+    A[::11, 3] = 1e-30                       # below 2^F_3: truncated to 0
+    b = rng.standard_normal(m) * 1e2
+    got = O.fixed_point_sketch(A, b, d, zeta, seed, row_chunks=bounds)
+    ref = _brute_fixed_point(A, b, d, zeta, seed, bounds)
+    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+
+
+def test_fixed_point_sketch_close_to_exact_sum():
+    """Each entry differs from the exact sum of S [A b] by less than the
+    truncation of its terms (one 2^F_j per term) plus one rounding."""
+    rng = np.random.default_rng(3)
+    m, n, d, zeta, seed = 3000, 20, 60, 8, 5
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal(m)
+    got = O.fixed_point_sketch(A, b, d, zeta, seed)
+    S = sparse_sign_matrix(m, d, zeta, seed).sign()
+    ref = np.asarray(S @ np.concatenate([A, b[:, None]], axis=1))
+    cnt = np.asarray(abs(S).sum(axis=1)).ravel()
+    L = max(10, int(cnt.max()).bit_length())
+    absmax = np.abs(np.concatenate([A, b[:, None]], axis=1)).max(axis=0)
+    E = np.frexp(absmax)[1] + 1022
+    step = np.ldexp(1.0, (E - 1022) + L - 63)
+    absref = np.asarray(abs(S) @ np.abs(np.concatenate([A, b[:, None]], axis=1)))
+    bound = cnt[:, None] * step[None, :] + 2.0 ** -52 * np.abs(ref) + 2 * cnt[:, None] * 2.0 ** -53 * absref
+    assert (np.abs(got - ref) <= bound).all()
