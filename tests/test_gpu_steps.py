@@ -4,7 +4,8 @@ the C ABI (paper_2406_03468_gb300 is a ctypes binding of liblsq.so).
 Sizes span several CTAs and row blocks with ragged tails (m = 20011 rows,
 n = 130 or 37 columns, lda > n).  Bars:
   * sketch pattern: bit-exact (index work);
-  * sums (sketch, passes): within the standard summation error bound
+  * fixed-point sketch sums (m n >= 2^24): bit-exact (integer work);
+  * other sums (scatter sketch, passes): within the standard summation error bound
     gamma_k sum |terms| with k the number of terms, written per element;
   * QR / triangular solves: normwise backward-error level, kappa(R) u.
 """
