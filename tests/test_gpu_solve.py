@@ -223,6 +223,24 @@ def test_plan_configure_retargets_without_allocation():
 
 
 @pytest.mark.parametrize("method", ["fossils", "spir"])
+@pytest.mark.parametrize("kappa", [1e0, 1e4, 1e8, 1e12])
+@pytest.mark.parametrize("resid", [1e-12, 1e-6, 1e-1])
+def test_difficulty_grid(method, kappa, resid):
+    """The (kappa, ||r||) grid of the paper's stability experiments (Sec. 5,
+    Fig. 1's construction at 4000 x 50): backward error <= 1e-13 at every
+    point, and the forward error within 10x of the larger of the oracle QR
+    solve's and the first-order Wedin bound (Fact 2.4)."""
+    P = problem_svd(4000, 50, kappa, resid, seed=41)
+    A, b, xt = P["A"], P["b"], P["x_true"]
+    st, info, x = _gpu_solve(method, A, b, seed=12)
+    assert st in (0, lsq.LSQ_WARN_RANK_DEFICIENT)
+    x_qr, R_A = oracle.qr_solve(A, b, return_R=True)
+    assert oracle.kw_relative(A, b, x, R_A=R_A) <= 1e-13, info
+    wed = oracle.wedin_bound(kappa, 1.0, xt, resid)
+    assert oracle.forward_error(x, xt) <= 10 * max(oracle.forward_error(x_qr, xt), wed)
+
+
+@pytest.mark.parametrize("method", ["fossils", "spir"])
 @pytest.mark.parametrize("kappa,resid", [(1e13, 1e-6), (1e14, 1e-2), (1e15, 1e-6)])
 @pytest.mark.parametrize("fp64", [0, 1])
 def test_high_condition(method, kappa, resid, fp64):
