@@ -31,6 +31,9 @@ Readings of the paper that this oracle takes (the CUDA path takes the same ones)
     so step 2 runs ceil(q0) - 1 updates (capped at 100).
   * SPIR's CG starts from dy = 0 and uses the same two stopping rules, with
     Delta = gamma_k p_k the CG update of dy.
+  * LSQR-based SPIR solves each step's least-squares problem
+    min ||r_i - A D^{-1} R^{-1} dy|| by LSQR from dy = 0, with the same two
+    stopping rules applied to the LSQR update (phi_k / rho_k) w_k.
   * Column scaling (Alg. 4, first line) is on by default and is applied
     explicitly, A <- A diag(d)^{-1}; x is unscaled at the end (Alg. 4, last
     line).
@@ -309,6 +312,58 @@ def _cg(P, c, max_updates, thresh):
     return dy, k
 
 
+def _lsqr(P, r, max_updates, thresh):
+    """LSQR (Paige and Saunders) on min ||r - B dy||, B = A R^{-1} (the step's
+    least-squares problem, eq. (ls-itref), right-preconditioned by R; Sec.
+    "SPIR: Conjugate gradient or LSQR?"), from dy = 0.  Golub-Kahan
+    bidiagonalisation of B started from r, plane rotations on the bidiagonal,
+    and the update dy += (phi_k / rho_k) w_k, whose norm the stopping rule
+    reads as SPIR reads CG's step."""
+    def B(v):
+        return P.As @ backsub(P.R, v)
+
+    def BT(u):
+        return backsub_t(P.R, P.As.T @ u)
+
+    dy = np.zeros(P.n)
+    beta = float(np.linalg.norm(r))
+    if beta == 0.0:
+        return dy, 0
+    u = r / beta
+    v = BT(u)
+    alpha = float(np.linalg.norm(v))
+    if alpha == 0.0:
+        return dy, 0
+    v = v / alpha
+    w = v.copy()
+    phibar, rhobar = beta, alpha
+    k = 0
+    for _ in range(max_updates):
+        u = B(v) - alpha * u
+        beta = float(np.linalg.norm(u))
+        if beta > 0.0:
+            u = u / beta
+        v = BT(u) - beta * v
+        alpha = float(np.linalg.norm(v))
+        if alpha > 0.0:
+            v = v / alpha
+        rho = math.hypot(rhobar, beta)
+        cs, sn = rhobar / rho, beta / rho
+        theta = sn * alpha
+        rhobar = -cs * alpha
+        phi = cs * phibar
+        phibar = sn * phibar
+        step = (phi / rho) * w
+        dy = dy + step
+        w = v - (theta / rho) * w
+        k += 1
+        if thresh is not None and np.linalg.norm(step) <= thresh:
+            break
+        if alpha == 0.0 or phibar == 0.0:
+            break
+    return dy, k
+
+
 def _solve(method, A, b, d, zeta, seed, eta, col_scale, max_inner, stop_gamma,
            stop_rho, n_refine, fixed_updates):
     P = _Problem(A, b, d, zeta, seed, eta, col_scale)
@@ -321,7 +376,7 @@ def _solve(method, A, b, d, zeta, seed, eta, col_scale, max_inner, stop_gamma,
     cnorms = []
     iters = []
     for i in range(n_refine):
-        c, _ = P.rhs(x)
+        c, r = P.rhs(x)
         cnorms.append(float(np.linalg.norm(c)))
         if fixed_updates is not None:
             nmax, th = fixed_updates, None
@@ -331,6 +386,8 @@ def _solve(method, A, b, d, zeta, seed, eta, col_scale, max_inner, stop_gamma,
             nmax, th = q2, None
         if method == "fossils":
             dy, k = _polyak(P, c, P.alpha, P.beta, nmax, th)
+        elif method == "spir_lsqr":
+            dy, k = _lsqr(P, r, nmax, th)
         else:
             dy, k = _cg(P, c, nmax, th)
         iters.append(k)
@@ -366,6 +423,16 @@ def spir(A, b, d=None, zeta=8, seed=0, eta=None, col_scale=True, max_inner=100,
          stop_gamma=10.0, stop_rho=0.4, n_refine=2, fixed_updates=None):
     """SPIR (Alg. 3): as FOSSILS with conjugate gradient as inner solver."""
     return _solve("spir", A, b, d, zeta, seed, eta, col_scale, max_inner,
+                  stop_gamma, stop_rho, n_refine, fixed_updates)
+
+
+def spir_lsqr(A, b, d=None, zeta=8, seed=0, eta=None, col_scale=True, max_inner=100,
+              stop_gamma=10.0, stop_rho=0.4, n_refine=2, fixed_updates=None):
+    """LSQR-based SPIR (Sec. "SPIR: Conjugate gradient or LSQR?"): as SPIR,
+    with each refinement step's least-squares problem solved by LSQR with
+    preconditioner R instead of CG on its normal equations; the same two
+    stopping rules, applied to the LSQR step."""
+    return _solve("spir_lsqr", A, b, d, zeta, seed, eta, col_scale, max_inner,
                   stop_gamma, stop_rho, n_refine, fixed_updates)
 
 

@@ -6,6 +6,9 @@
   the eta = 0 special case (identity preconditioned operator: exact after one
   update).
 * CG against finite termination on a small SPD system.
+* LSQR (the inner solver of LSQR-based SPIR) against CG's iterates on the
+  same preconditioned problem (identical in exact arithmetic) and against
+  LAPACK lstsq after convergence; LSQR-based SPIR on constructed problems.
 * FOSSILS / SPIR on constructed problems with known solution: backward error
   <= 1e-13 (Karlson-Walden, Sec. 4.1), forward error within 10x of the
   Householder QR solve, two refinement steps needed (Sec. 5.1), and the
@@ -165,3 +168,61 @@ def test_kw_below_perturbation():
     est = O.kw_estimate(A, b, x, theta=1e8)
     assert est <= 1.05 * np.linalg.norm(dA)
     assert est >= 1e-3 * np.linalg.norm(dA)
+
+
+def _preconditioned_problem(kappa, resid, seed, m=3000, n=30):
+    """The preconditioned operator B = A D^{-1} R^{-1} of a constructed
+    problem and a generic right-hand side r (a refinement residual is nearly
+    orthogonal to range(A), so B^T r cancels heavily and its rounding would
+    swamp the comparison), with c = B^T r."""
+    P = problem_svd(m, n, kappa, resid, seed=seed)
+    prob = O._Problem(P["A"], P["b"], None, 8, seed, None, True)
+    r = np.random.default_rng(seed + 100).standard_normal(m)
+    c = O.backsub_t(prob.R, prob.As.T @ r)
+    return prob, c, r
+
+
+@pytest.mark.parametrize("steps", [1, 3, 6])
+def test_lsqr_iterates_match_cg(steps):
+    """LSQR on min ||r - B dy|| and CG on B^T B dy = B^T r (B = A R^{-1}) give
+    the same iterates in exact arithmetic.  With kappa(A) = 10 the triangular
+    solves with R are accurate to rounding (their forward error grows with
+    kappa(R)), so the two oracle solvers must agree to rounding."""
+    prob, c, r = _preconditioned_problem(10.0, 1e-4, 3)
+    dy_l, k_l = O._lsqr(prob, r, steps, None)
+    dy_c, k_c = O._cg(prob, c, steps, None)
+    assert k_l == k_c == steps
+    assert np.linalg.norm(dy_l - dy_c) <= 1e-11 * np.linalg.norm(dy_c)
+
+
+def test_lsqr_converges_to_least_squares_solution():
+    """After enough steps LSQR's dy solves min ||r - B dy|| (LAPACK lstsq on
+    the explicitly formed B as the reference)."""
+    prob, c, r = _preconditioned_problem(1e4, 1e-2, 5, m=2000, n=20)
+    dy, _ = O._lsqr(prob, r, 60, None)
+    B = prob.As @ np.linalg.inv(prob.R)
+    ref = np.linalg.lstsq(B, r, rcond=None)[0]
+    assert np.linalg.norm(dy - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_spir_lsqr_backward_stable_config1(seed):
+    """LSQR-based SPIR on Fig. 1's construction: backward stable after two
+    steps, forward error within 10x of Householder QR, one step not enough;
+    and (Sec. "SPIR: Conjugate gradient or LSQR?") its backward error is at
+    the CG-based SPIR's level.  (The forward errors here are of order one for
+    every solver, QR included, kappa = 1e12, so they are compared with QR's,
+    not with each other's.)"""
+    P = problem_svd(4000, 50, 1e12, 1e-6, seed=seed)
+    A, b, xt = P["A"], P["b"], P["x_true"]
+    x_qr, R_A = O.qr_solve(A, b, return_R=True)
+    res = O.spir_lsqr(A, b, seed=seed)
+    be = O.kw_relative(A, b, res["x"], R_A=R_A)
+    assert be <= 1e-13
+    fe = O.forward_error(res["x"], xt)
+    assert fe <= 10 * O.forward_error(x_qr, xt)
+    assert O.kw_relative(A, b, res["iterates"][1], R_A=R_A) > 10 * be
+    cg = O.spir(A, b, seed=seed)
+    be_cg = O.kw_relative(A, b, cg["x"], R_A=R_A)
+    assert be <= max(10 * be_cg, 1e-15) and be_cg <= max(10 * be, 1e-15)
+    assert res["iters"] == cg["iters"]   # the same stopping decisions
