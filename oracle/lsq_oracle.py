@@ -31,6 +31,9 @@ Readings of the paper that this oracle takes (the CUDA path takes the same ones)
     so step 2 runs ceil(q0) - 1 updates (capped at 100).
   * SPIR's CG starts from dy = 0 and uses the same two stopping rules, with
     Delta = gamma_k p_k the CG update of dy.
+  * Alg. 4's step-2 test reads "Mod(i, 5)" with i the refinement index, which
+    is 1 throughout step 2; it is read as the inner index j: the sketched
+    KW estimate is checked after updates 1, 6, 11, ... of the second solve.
   * LSQR-based SPIR solves each step's least-squares problem
     min ||r_i - A D^{-1} R^{-1} dy|| by LSQR from dy = 0, with the same two
     stopping rules applied to the LSQR update (phi_k / rho_k) w_k.
@@ -270,11 +273,12 @@ class _Problem:
         return backsub_t(self.R, self.As.T @ r), r
 
 
-def _polyak(P, c, alpha, beta, max_updates, thresh):
+def _polyak(P, c, alpha, beta, max_updates, thresh, check=None):
     """Polyak heavy ball on (R^{-T}A^T A R^{-1}) dy = c (Alg. 5 / Alg. 4 loop):
     dy = dy_old = c; Delta = alpha (c - M dy) + beta (dy - dy_old);
     (dy, dy_old) <- (dy + Delta, dy).  Stops after an update with
-    ||Delta|| <= thresh when thresh is given."""
+    ||Delta|| <= thresh when thresh is given, or when check(dy, k) (k updates
+    done) returns True."""
     dy = c.copy()
     dy_old = c.copy()
     k = 0
@@ -284,6 +288,8 @@ def _polyak(P, c, alpha, beta, max_updates, thresh):
         dy = dy + delta
         k += 1
         if thresh is not None and np.linalg.norm(delta) <= thresh:
+            break
+        if check is not None and check(dy, k):
             break
     return dy, k
 
@@ -365,7 +371,7 @@ def _lsqr(P, r, max_updates, thresh):
 
 
 def _solve(method, A, b, d, zeta, seed, eta, col_scale, max_inner, stop_gamma,
-           stop_rho, n_refine, fixed_updates):
+           stop_rho, n_refine, fixed_updates, kw_stop=False):
     P = _Problem(A, b, d, zeta, seed, eta, col_scale)
     x = backsub(P.R, P.t)  # sketch-and-solve x0 (Sec. 2.3)
     r0 = P.b - P.As @ x
@@ -384,8 +390,22 @@ def _solve(method, A, b, d, zeta, seed, eta, col_scale, max_inner, stop_gamma,
             nmax, th = max_inner, thresh1
         else:
             nmax, th = q2, None
+        check = None
+        if kw_stop and i >= 1 and fixed_updates is None:
+            # Alg. 4, second inner solve: every five updates (after updates
+            # 1, 6, 11, ...) estimate the backward error of x + R^{-1} dy with
+            # the sketched KW estimate (theta = ||A||_F / ||b||, on the column-
+            # normalised A) and stop once it is below u ||A||_F.
+            nmax = max_inner
+            fro = float(np.linalg.norm(P.As))
+
+            def check(dy_, k_, x_=x):
+                if (k_ - 1) % 5 != 0:
+                    return False
+                xh = x_ + backsub(P.R, dy_)
+                return sketched_kw(P.SA, P.As, P.b, xh) < U_ROUNDOFF * fro
         if method == "fossils":
-            dy, k = _polyak(P, c, P.alpha, P.beta, nmax, th)
+            dy, k = _polyak(P, c, P.alpha, P.beta, nmax, th, check)
         elif method == "spir_lsqr":
             dy, k = _lsqr(P, r, nmax, th)
         else:
@@ -411,12 +431,15 @@ def _solve(method, A, b, d, zeta, seed, eta, col_scale, max_inner, stop_gamma,
 
 
 def fossils(A, b, d=None, zeta=8, seed=0, eta=None, col_scale=True, max_inner=100,
-            stop_gamma=10.0, stop_rho=0.4, n_refine=2, fixed_updates=None):
+            stop_gamma=10.0, stop_rho=0.4, n_refine=2, fixed_updates=None, kw_stop=False):
     """FOSSILS (Alg. 2 with the practical rules of Sec. 4.2 / Alg. 4, QR
     preconditioner): sketch, Householder QR, sketch-and-solve x0, then
-    n_refine (default 2) refinement steps with the Polyak inner solver."""
+    n_refine (default 2) refinement steps with the Polyak inner solver.
+    kw_stop: end the second inner solve with Alg. 4's sketched
+    Karlson-Walden test (every five updates, cap max_inner) instead of
+    Theorem 7.1's count."""
     return _solve("fossils", A, b, d, zeta, seed, eta, col_scale, max_inner,
-                  stop_gamma, stop_rho, n_refine, fixed_updates)
+                  stop_gamma, stop_rho, n_refine, fixed_updates, kw_stop)
 
 
 def spir(A, b, d=None, zeta=8, seed=0, eta=None, col_scale=True, max_inner=100,
@@ -481,6 +504,31 @@ def kw_estimate(A, b, xhat, theta=None, R_A=None):
     stacked = np.vstack([R_A, math.sqrt(lam) * np.eye(n)])
     R_lam, _ = householder_qr(stacked)
     y = backsub_t(R_lam, g)
+    return theta / math.sqrt(1.0 + theta ** 2 * nx ** 2) * float(np.linalg.norm(y))
+
+
+def sketched_kw(SA, A, b, xhat, theta=None):
+    """Sketched Karlson-Walden estimate (Sec. 4.1, eq. (sketched-kw)):
+
+        theta / sqrt(1 + theta^2 ||x||^2) *
+            || ((SA)^T (SA) + lam I)^{-1/2} A^T r ||,
+        lam = theta^2 ||r||^2 / (1 + theta^2 ||x||^2),  r = b - A x,
+
+    evaluated as Alg. 4 does, through the SVD SA = U Sigma V^T:
+    || (Sigma^2 + lam I)^{-1/2} V^T (A^T r) ||.  theta defaults to
+    ||A||_F / ||b||.  r and A^T r use compensated dot products; the SVD is
+    LAPACK's (a library step).  Returns the absolute estimate."""
+    A = _c64(A)
+    b = _c64(b)
+    xhat = _c64(xhat)
+    if theta is None:
+        theta = np.linalg.norm(A) / np.linalg.norm(b)
+    _, sig, Vt = np.linalg.svd(np.asarray(SA, dtype=np.float64), full_matrices=False)
+    r_hi, _, g = residual_dot2(A, b, xhat)
+    nr = np.linalg.norm(r_hi)
+    nx = np.linalg.norm(xhat)
+    lam = theta ** 2 * nr ** 2 / (1.0 + theta ** 2 * nx ** 2)
+    y = (Vt @ g) / np.sqrt(sig ** 2 + lam)
     return theta / math.sqrt(1.0 + theta ** 2 * nx ** 2) * float(np.linalg.norm(y))
 
 

@@ -9,6 +9,9 @@
 * LSQR (the inner solver of LSQR-based SPIR) against CG's iterates on the
   same preconditioned problem (identical in exact arithmetic) and against
   LAPACK lstsq after convergence; LSQR-based SPIR on constructed problems.
+* The sketched Karlson-Walden estimate (eq. (sketched-kw)) against the KW
+  estimate when the "sketch" is A itself, against the Proposition's bounds
+  for a sparse sign sketch, and Alg. 4's step-2 test built on it.
 * FOSSILS / SPIR on constructed problems with known solution: backward error
   <= 1e-13 (Karlson-Walden, Sec. 4.1), forward error within 10x of the
   Householder QR solve, two refinement steps needed (Sec. 5.1), and the
@@ -226,3 +229,52 @@ def test_spir_lsqr_backward_stable_config1(seed):
     be_cg = O.kw_relative(A, b, cg["x"], R_A=R_A)
     assert be <= max(10 * be_cg, 1e-15) and be_cg <= max(10 * be, 1e-15)
     assert res["iters"] == cg["iters"]   # the same stopping decisions
+
+
+def test_sketched_kw_without_sketch_is_kw():
+    """With SA replaced by A itself (no sketch, distortion 0) the sketched
+    estimate (eq. (sketched-kw), through the SVD) is the Karlson-Walden
+    estimate (through a QR), so the two routes agree to rounding."""
+    P = problem_svd(2000, 30, 1e6, 1e-3, seed=8)
+    A, b = P["A"], P["b"]
+    x = O.qr_solve(A, b) + 1e-9 * np.random.default_rng(1).standard_normal(30)
+    kw = O.kw_estimate(A, b, x)
+    sk = O.sketched_kw(A, A, b, x)
+    assert abs(sk - kw) <= 1e-10 * kw
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_sketched_kw_within_proposition_bounds(seed):
+    """Proposition (sketched KW) with Fact (KW estimate): for an embedding of
+    distortion eta, KW / (sqrt(2)(1 + eta)) <= BE_sk <= sqrt(2) KW / (1 - eta);
+    checked with eta = 1/2 (d = 12n, zeta = 8 sparse sign) at perturbed
+    solutions of several quality levels."""
+    P = problem_svd(3000, 40, 1e8, 1e-4, seed=seed)
+    A, b = P["A"], P["b"]
+    SA, _ = O.sketch(A, b, 480, 8, seed)
+    eta = 0.5
+    x_qr = O.qr_solve(A, b)
+    rng = np.random.default_rng(seed)
+    for scale in (0.0, 1e-12, 1e-6):
+        x = x_qr + scale * rng.standard_normal(40)
+        kw = O.kw_estimate(A, b, x)
+        sk = O.sketched_kw(SA, A, b, x)
+        assert kw / (math.sqrt(2) * (1 + eta)) <= sk <= math.sqrt(2) * kw / (1 - eta)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fossils_sketched_kw_stop(seed):
+    """Alg. 4's step-2 test: checks after updates 1, 6, 11, ...; where it
+    stops, the estimate is below u ||A||_F and the solution is backward
+    stable."""
+    P = problem_svd(4000, 50, 1e12, 1e-6, seed=seed)
+    A, b = P["A"], P["b"]
+    _, R_A = O.qr_solve(A, b, return_R=True)
+    res = O.fossils(A, b, seed=seed, kw_stop=True)
+    k2 = res["iters"][1]
+    assert k2 < 100 and (k2 - 1) % 5 == 0
+    assert O.kw_relative(A, b, res["x"], R_A=R_A) <= 1e-13
+    As = A / O.column_norms(A)
+    SA, _ = O.sketch(As, b, 600, 8, seed)
+    xs = res["x"] * O.column_norms(A)   # (x / d) d: a rounding away from the x tested
+    assert O.sketched_kw(SA, As, b, xs) < 1.1 * 2.0 ** -53 * np.linalg.norm(As)
