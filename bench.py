@@ -3,10 +3,16 @@
 
 One step = one complete FOSSILS solve (sketch S[A b], Householder QR of the
 sketch, sketch-and-solve start, two refinement steps with the Polyak inner
-solver) of the 1,000,000 x 500 FP64 problem A = (G/sqrt(m)) diag(sigma) V^T,
+solver) of the 1,000,000 x 500 problem A = (G/sqrt(m)) diag(sigma) V^T,
 sigma log-spaced 1..1e-10, b = A x + 1e-4 g, d = 12n, zeta = 8, with A and b
 resident in HBM.  A (4 GB) is larger than the 129 MB L2, so no flush is
-needed between steps.
+needed between steps.  Arithmetic: the residual b - A x, A^T r, the x
+updates, the QR and the triangular solves in FP64; the inner passes
+A^T (A z) in double-float on the FP32 pipe over an exact-to-2^-48 hi / lo
+FP32 split of A (an FP64-class evaluation); the same solve with strict-FP64
+inner passes is timed beside it.  Every timed result is checked against
+the CPU oracle after the timed region (Karlson-Walden backward error and
+forward error).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -15,8 +21,8 @@ own replica of the problem on its own GPU ("replicas only": the solve has no
 cross-GPU exchange); only the step timer is reduced (max over ranks).
 
 --impl reference times the CPU oracle (oracle/, plain FP64 loops and numpy
-BLAS) on the host cores, on a bounded row sample of the same problem, scaled
-to the full problem's solves/s.
+BLAS) on the host cores, each step one oracle FOSSILS solve of the whole
+1,000,000 x 500 problem.
 """
 import argparse
 import json
@@ -35,8 +41,12 @@ UNIT = "solves/s"
 M, N, KAPPA, NOISE, SEED = 1_000_000, 500, 1e10, 1e-4, 5
 SKETCH_SEED = 9
 WORKLOAD = "fossils_fp64_m1000000_n500_kappa1e10_d6000_zeta8"
-REF_SAMPLE_ROWS = 100_000      # oracle sample per reference step
-CPU_BASELINE_ROWS = 250_000    # oracle sample for the cpu_baseline object
+DTYPE = "f64+df32"
+DTYPE_NOTE = ("FP64 residual, A^T r, x updates, QR and triangular solves; inner passes "
+              "A^T(A z) in double-float (FP32 pipe) on an exact-to-2^-48 hi/lo FP32 split of A")
+CPU_1T_ROWS = 200_000          # single-thread oracle sample (the O(mn) part is scaled)
+WARM_ROWS = 50_000             # rows of a reference-arm warm-up step
+BE_MAX = 1e-13
 
 
 def parse():
@@ -90,51 +100,122 @@ def make_problem(rows=None):
 # oracle (CPU) timing: the cpu_baseline object and the reference arm
 # --------------------------------------------------------------------------
 
-def oracle_time(P, rows, reps=1):
-    """Seconds per oracle FOSSILS solve on the first `rows` rows of P."""
+def oracle_seconds(A, b):
+    """Seconds of one oracle FOSSILS solve of (A, b)."""
     import oracle
-    A = P["A"][:rows]
-    b = P["b"][:rows]
-    ts = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        oracle.fossils(A, b, seed=SKETCH_SEED)
-        ts.append(time.perf_counter() - t0)
-    return ts
+    t0 = time.perf_counter()
+    oracle.fossils(A, b, seed=SKETCH_SEED)
+    return time.perf_counter() - t0
 
 
-def cpu_baseline_obj(P, rows):
-    ts = oracle_time(P, rows, reps=1)
-    per_solve_full = ts[0] * (M / rows)
-    return {"value": 1.0 / per_solve_full, "unit": UNIT, "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": "oracle FOSSILS (numpy BLAS + plain C, FP64) on the first %d of %d rows "
-                      "of the same A, b; %.2f s, time scaled by m/rows (passes are O(mn))"
-                      % (rows, M, ts[0])}
+_ONE_THREAD = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, %(root)r)
+import oracle
+from lsq_problems import problem_gaussian
+rows, n, d = %(rows)d, %(n)d, %(d)d
+X = np.random.default_rng(0).standard_normal((d, n))
+t0 = time.perf_counter()
+R, V = oracle.householder_qr(X)
+oracle.apply_qt(V, X[:, 0])
+oracle.sigma_extremes(R)
+t_fixed = time.perf_counter() - t0
+P = problem_gaussian(rows, n, %(kappa)r, %(noise)r, seed=%(seed)d)
+t0 = time.perf_counter()
+oracle.fossils(P["A"], P["b"], seed=%(sseed)d)
+t_sample = time.perf_counter() - t0
+print(json.dumps({"t_fixed": t_fixed, "t_sample": t_sample}))
+"""
+
+
+def oracle_one_thread():
+    """The oracle on one host core (a child process with one OpenMP and one
+    BLAS thread): the m-independent part (QR of the d x n sketch and its
+    singular values) timed once, FOSSILS on the first CPU_1T_ROWS rows, and
+    the full problem's time as fixed + (sample - fixed) m / rows."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _ONE_THREAD % {"root": ROOT, "rows": CPU_1T_ROWS, "n": N, "d": 12 * N,
+                          "kappa": KAPPA, "noise": NOISE, "seed": SEED, "sseed": SKETCH_SEED}
+    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True,
+                         text=True, timeout=900)
+    if out.returncode != 0:
+        return {"error": out.stderr[-500:]}
+    t = json.loads(out.stdout.strip().splitlines()[-1])
+    full = t["t_fixed"] + (t["t_sample"] - t["t_fixed"]) * (M / CPU_1T_ROWS)
+    return {"value": 1.0 / full, "unit": UNIT, "cores": 1, "seconds_per_solve": full,
+            "sample": "oracle FOSSILS on the first %d rows (%.2f s) and the m-independent "
+                      "QR + SVD of the %d x %d sketch alone (%.2f s); the full solve is "
+                      "fixed + (sample - fixed) m / rows"
+                      % (CPU_1T_ROWS, t["t_sample"], 12 * N, N, t["t_fixed"])}
+
+
+def cpu_baseline_obj(P):
+    """The oracle on all host cores, one solve of the whole problem (no
+    extrapolation), with the single-core figure beside it."""
+    t = oracle_seconds(P["A"], P["b"])
+    return {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "seconds_per_solve": t,
+            "sample": "one oracle FOSSILS solve (numpy BLAS + plain C with OpenMP, FP64) of "
+                      "the whole %d x %d problem on all %d host cores: %.2f s"
+                      % (M, N, os.cpu_count(), t),
+            "single_thread": oracle_one_thread()}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    P = make_problem(REF_SAMPLE_ROWS)
-    oracle_time(P, REF_SAMPLE_ROWS, reps=max(0, args.warmup))
-    ts = oracle_time(P, REF_SAMPLE_ROWS, reps=args.steps)
-    per_full = statistics.mean(ts) * (M / REF_SAMPLE_ROWS)
-    value = 1.0 / per_full
+    P = make_problem()
+    # warm-up steps load the oracle's libraries and touch their code paths
+    # on a small slice (the oracle has no caches to fill); every timed step
+    # solves the whole problem
+    for _ in range(max(0, args.warmup)):
+        oracle_seconds(P["A"][:WARM_ROWS], P["b"][:WARM_ROWS])
+    ts = [oracle_seconds(P["A"], P["b"]) for _ in range(args.steps)]
+    per = statistics.mean(ts)
+    value = 1.0 / per
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": per_full * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config({"sample_rows": REF_SAMPLE_ROWS}),
+            "config": config(),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
                              "kind": "oracle",
-                             "sample": "each step: oracle FOSSILS on %d of %d rows, time "
-                                       "scaled by m/rows" % (REF_SAMPLE_ROWS, M)},
+                             "sample": "each step: one oracle FOSSILS solve of the whole "
+                                       "%d x %d problem on all host cores (mean of %d; "
+                                       "warm-up steps on the first %d rows)"
+                                       % (M, N, len(ts), WARM_ROWS)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# --------------------------------------------------------------------------
+# accuracy of the timed results against the oracle
+# --------------------------------------------------------------------------
+
+def check_x(A, b, x, x_qr, R_A, x_true=None, condest=None):
+    """Karlson-Walden backward error (Sec. 4.1, relative to ||A||_F) of x and
+    its forward error: against x_true when the problem's solution is known
+    (r orthogonal to range(A)), with the oracle QR solve's beside it, else
+    against the oracle QR solve with the first-order Wedin bound (Fact 2.4)
+    at the GPU's condest as the yardstick."""
+    import numpy as np
+    import oracle
+    be = oracle.kw_relative(A, b, x, R_A=R_A)
+    out = {"be_rel": be}
+    if x_true is not None:
+        out["fwd_err"] = oracle.forward_error(x, x_true)
+        out["fwd_err_oracle_qr"] = oracle.forward_error(x_qr, x_true)
+        out["ok"] = bool(be <= BE_MAX and out["fwd_err"] <= 10 * out["fwd_err_oracle_qr"])
+    else:
+        out["fwd_err_vs_oracle_qr"] = oracle.forward_error(x, x_qr)
+        rn = float(np.linalg.norm(b - A @ x_qr))
+        out["wedin_bound"] = oracle.wedin_bound(condest, 1.0, x_qr, rn)
+        out["ok"] = bool(be <= BE_MAX and out["fwd_err_vs_oracle_qr"] <= 10 * out["wedin_bound"])
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -210,15 +291,22 @@ def peaks():
 
 def tier_compare(lsq, torch, dev, steps):
     """Config 5: 1e6 x 1000, A built as for the Fig. 1 problems at kappa = 1e4,
-    solved by FOSSILS on the all-FP64 path and on the FP32-inner tier (AUTO),
-    and the automatic FP64 fallback at kappa = 1e10."""
+    solved by FOSSILS on the FP64 path (double-float inner passes, and strict
+    FP64 inner passes) and with precision AUTO (the FP32-inner tier); then the
+    same shape at kappa = 1e10, where AUTO falls back to the FP64 path.  Every
+    result is checked against the oracle's QR solve of the same problem."""
+    import oracle
     from lsq_problems import problem_svd_torch
     m, n = 1_000_000, 1000
     out = {"workload": "fossils_m1000000_n1000_kappa1e4_d12000_zeta8", "steps": steps}
     P = problem_svd_torch(m, n, 1e4, 1e-4, seed=31, device=dev)
     x = torch.empty(n, dtype=torch.float64, device=dev)
-    for name, prec in (("fp64", lsq.LSQ_PREC_FP64), ("auto", lsq.LSQ_PREC_AUTO)):
-        plan = lsq.Plan(m, n, seed=7, precision=prec, timing=1)
+    xs = {}
+    runs = (("fp64_df", dict(precision=lsq.LSQ_PREC_FP64)),
+            ("fp64_strict", dict(precision=lsq.LSQ_PREC_FP64, inner_fp64_fma=1)),
+            ("auto", dict(precision=lsq.LSQ_PREC_AUTO)))
+    for name, opts in runs:
+        plan = lsq.Plan(m, n, seed=7, timing=1, **opts)
         lsq.lsq_solve_fossils(plan.handle, P["A"], P["b"], x)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -229,33 +317,53 @@ def tier_compare(lsq, torch, dev, steps):
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / steps
         last = infos[-1]
+        xs[name] = x.cpu().numpy().copy()
         out[name] = {"solves_per_s": 1.0 / dt, "ms_per_solve": dt * 1e3, "path": last["path"],
+                     "inner_kernel": last["inner_kernel"],
                      "refine_steps": last["refine_steps"], "iters": last["iters"],
                      "bytes_a_gb": last["bytes_a"] / 1e9,
                      "phase_ms": {"sketch": last["ms_sketch"], "qr": last["ms_qr"],
                                   "refine": last["ms_refine"]},
                      "inner_pass_ms": (last["ms_inner_pass"] / max(1, last["n_inner_pass"]))}
         plan.close()
+    out["auto_vs_fp64_df"] = out["auto"]["solves_per_s"] / out["fp64_df"]["solves_per_s"]
+    out["auto_vs_fp64_strict"] = out["auto"]["solves_per_s"] / out["fp64_strict"]["solves_per_s"]
+    t0 = time.perf_counter()
+    A, b, xt = P["A"].cpu().numpy(), P["b"].cpu().numpy(), P["x_true"].cpu().numpy()
     del P
     torch.cuda.empty_cache()
+    x_qr, R_A = oracle.qr_solve_lapack(A, b, return_R=True)
+    for name in xs:
+        out[name]["check"] = check_x(A, b, xs[name], x_qr, R_A, x_true=xt)
+    del A, b, R_A
     P = problem_svd_torch(m, n, 1e10, 1e-4, seed=32, device=dev)
     plan = lsq.Plan(m, n, seed=7, precision=lsq.LSQ_PREC_AUTO)
     st, inf = lsq.lsq_solve_fossils(plan.handle, P["A"], P["b"], x)
-    out["auto_kappa1e10_path"] = inf.as_dict()["path"]
-    out["auto_kappa1e10_condest"] = inf.as_dict()["condest"]
+    fb = inf.as_dict()
     plan.close()
+    out["auto_kappa1e10"] = {"path": fb["path"], "inner_kernel": fb["inner_kernel"],
+                             "condest": fb["condest"], "iters": fb["iters"]}
+    A, b, xt = P["A"].cpu().numpy(), P["b"].cpu().numpy(), P["x_true"].cpu().numpy()
+    xf = x.cpu().numpy().copy()
     del P
     torch.cuda.empty_cache()
+    x_qr, R_A = oracle.qr_solve_lapack(A, b, return_R=True)
+    out["auto_kappa1e10"]["check"] = check_x(A, b, xf, x_qr, R_A, x_true=xt)
+    out["check_seconds"] = time.perf_counter() - t0
+    del A, b, R_A
     return out
 
 
 def multi_compare(lsq, torch, dev, steps):
     """Config 4: 2e6 x 200, k = 64 right-hand sides sharing one sketch and QR.
-    The default plan runs the inner pass for all k vectors as one batched
-    double-float launch on the hi / lo planes (HBM roofline over k 8mn
-    bytes per pass); a strict-FP64 plan (inner_fp64_fma = 1) runs it as the
-    FP64 tensor-core (DMMA) contraction (tensor roofline); both against the
-    single-RHS path solving one column."""
+    The default plan runs the inner pass for all k vectors in one launch of
+    the double-float pass on the hi / lo planes (HBM roofline over the 8mn
+    bytes of the planes); a strict-FP64 plan (inner_fp64_fma = 1) runs it as
+    the FP64 tensor-core (DMMA) contraction (tensor roofline), timed over the
+    same number of solves; both against the single-RHS path solving one
+    column.  Four columns of X are checked against the oracle."""
+    import numpy as np
+    import oracle
     from lsq_problems import problem_multi_rhs_torch
     m, n, k = 2_000_000, 200, 64
     P = problem_multi_rhs_torch(m, n, k, 1e8, 1e-5, seed=41, device=dev)
@@ -275,12 +383,12 @@ def multi_compare(lsq, torch, dev, steps):
         dt = (time.perf_counter() - t0) / nsteps
         plan.close()
         last = infos[-1]
-        return dt, last, last["ms_inner_pass"] / max(1, last["n_inner_pass"])
+        return dt, last, last["ms_inner_pass"] / max(1, last["n_inner_pass"]), X.cpu().numpy().copy()
 
-    dt, last, pass_ms = run({}, steps)
-    hbm_bytes = 8.0 * m * n * k
-    achieved = hbm_bytes / (pass_ms / 1e3) / 1e9
-    dt64, last64, pass64_ms = run({"inner_fp64_fma": 1}, 1)
+    dt, last, pass_ms, Xd = run({}, steps)
+    plane_bytes = 8.0 * m * n
+    achieved = plane_bytes / (pass_ms / 1e3) / 1e9
+    dt64, last64, pass64_ms, X64 = run({"inner_fp64_fma": 1}, steps)
     flops = 4.0 * m * n * k
     # FP64 tensor peak: the measured BF16 peak times the nominal FP64 / BF16 ratio (1.25 / 2250)
     fp64_peak = pk.get("bf16_tflops", 1900.0) * 1.25 / 2250.0
@@ -296,23 +404,45 @@ def multi_compare(lsq, torch, dev, steps):
     torch.cuda.synchronize()
     dt1 = (time.perf_counter() - t0) / steps
     plan1.close()
+    out = {"workload": "fossils_multi_m2000000_n200_k64_kappa1e8_d2400_zeta8", "steps": steps,
+           "solves_per_s": 1.0 / dt, "rhs_solves_per_s": k / dt, "ms_per_solve": dt * 1e3,
+           "path": "default: inner pass double-float on the hi/lo planes, all k vectors per "
+                   "launch; residual pass FP64 DMMA",
+           "inner_kernel": last["inner_kernel"],
+           "iters": last["iters"], "phase_ms": {"sketch": last["ms_sketch"], "qr": last["ms_qr"],
+                                                "refine": last["ms_refine"]},
+           "single_rhs_solves_per_s": 1.0 / dt1,
+           "inner_pass": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                          "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "ms": pass_ms,
+                          "bytes": plane_bytes,
+                          "bytes_note": "the hi/lo planes read once per pass (8mn)",
+                          "peak_kind": kind},
+           "fp64_dmma": {"rhs_solves_per_s": k / dt64, "steps": steps,
+                         "inner_kernel": last64["inner_kernel"],
+                         "pass": {"bound": "tensor", "achieved": achieved64, "peak": fp64_peak,
+                                  "unit": "TFLOP/s", "frac": achieved64 / fp64_peak,
+                                  "ms": pass64_ms, "flops": flops,
+                                  "peak_note": "measured bf16 x nominal fp64/bf16 (1.25/2250), "
+                                  + kind}}}
+    t0 = time.perf_counter()
+    A, B = P["A"].cpu().numpy(), P["B"].cpu().numpy()
     del P
     torch.cuda.empty_cache()
-    return {"workload": "fossils_multi_m2000000_n200_k64_kappa1e8_d2400_zeta8",
-            "solves_per_s": 1.0 / dt, "rhs_solves_per_s": k / dt, "ms_per_solve": dt * 1e3,
-            "inner_kernel": last["inner_kernel"],
-            "iters": last["iters"], "phase_ms": {"sketch": last["ms_sketch"], "qr": last["ms_qr"],
-                                                 "refine": last["ms_refine"]},
-            "single_rhs_solves_per_s": 1.0 / dt1,
-            "inner_pass": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-                           "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "ms": pass_ms,
-                           "bytes": hbm_bytes, "peak_kind": kind},
-            "fp64_dmma": {"rhs_solves_per_s": k / dt64, "inner_kernel": last64["inner_kernel"],
-                          "pass": {"bound": "tensor", "achieved": achieved64, "peak": fp64_peak,
-                                   "unit": "TFLOP/s", "frac": achieved64 / fp64_peak,
-                                   "ms": pass64_ms, "flops": flops,
-                                   "peak_note": "measured bf16 x nominal fp64/bf16 (1.25/2250), "
-                                   + kind}}}
+    import scipy.linalg as sl
+    cols = [0, 21, 42, 63]
+    qtb, R_A = sl.qr_multiply(A, np.ascontiguousarray(B[:, cols].T), mode="right")
+    R_A = np.ascontiguousarray(np.triu(R_A[:n, :n]))
+    checks = []
+    for j, c in enumerate(cols):
+        x_qr = oracle.backsub(R_A, np.ascontiguousarray(qtb[j, :n]))
+        b = np.ascontiguousarray(B[:, c])
+        for name, Xh in (("default", Xd), ("fp64_dmma", X64)):
+            ck = check_x(A, b, np.ascontiguousarray(Xh[:, c]), x_qr, R_A, condest=1e8)
+            ck.update({"column": c, "plan": name})
+            checks.append(ck)
+    out["checks"] = checks
+    out["check_seconds"] = time.perf_counter() - t0
+    return out
 
 
 def serve_compare(lsq, torch, dev, count=512, slots=8):
@@ -325,13 +455,15 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
     import numpy as np
     from lsq_problems import problem_svd_torch
     rng = np.random.default_rng(2026)
-    probs = []
+    probs, xtrue, kappas = [], [], []
     for i in range(count):
         m = int(math.exp(rng.uniform(math.log(2e4), math.log(4e5))))
         n = int(rng.choice([32, 64, 128, 256]))
         kappa = 10.0 ** rng.uniform(2, 12)
         P = problem_svd_torch(m, n, kappa, 1e-6, seed=5000 + i, device=dev)
         probs.append((m, n, P["A"], P["b"]))
+        xtrue.append(P["x_true"].cpu().numpy())
+        kappas.append(kappa)
     torch.cuda.synchronize()
     # plain: one plan of the largest size, re-targeted per problem (no
     # allocation), one solve at a time on one stream (first 128 problems)
@@ -353,7 +485,10 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
     arena = int(min(sum(foot), 48 << 30))
     srv = lsq.lsq_server_create(arena, slots, 400000, 256)
 
-    def run(gaps):
+    sample = list(range(0, count, max(1, count // 8)))[:8]
+    kept = {}
+
+    def run(gaps, keep=False):
         xb = np.empty(256)
         t_start = time.perf_counter()
         due = t_start + np.cumsum(gaps)
@@ -369,6 +504,9 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
                 st, info, l = lsq.lsq_poll(srv, t, xb)
                 if st != lsq.LSQ_PENDING:
                     lat.append(l)
+                    j = pending[t]
+                    if keep and j in sample:
+                        kept[j] = xb[:probs[j][1]].copy()
                     del pending[t]
             if not pending and i < count:
                 time.sleep(max(0.0, min(0.001, due[i] - time.perf_counter())))
@@ -376,7 +514,7 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
         return count / el, float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
 
     run(np.zeros(count))  # warm-up
-    cap, _, _ = run(np.zeros(count))
+    cap, _, _ = run(np.zeros(count), keep=True)
     out = {"workload": "served_stream_512_m2e4-4e5_n32-256_kappa1e2-1e12", "slots": slots,
            "arena_gb": arena / 1e9, "plain_solves_per_s": plain_rate,
            "capacity_solves_per_s": cap}
@@ -388,9 +526,51 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
                                     "p50_ms": p50 * 1e3, "p99_ms": p99 * 1e3}
     out["stats"] = lsq.lsq_server_stats(srv)
     lsq.lsq_server_destroy(srv)
+    # a sample of the served results against the oracle's QR solve (the
+    # problems' construction has r orthogonal to range(A), so x is known)
+    import oracle
+    checks = []
+    for j in sample:
+        m, n, A, b = probs[j]
+        Ah, bh = A.cpu().numpy(), b.cpu().numpy()
+        x_qr, R_A = oracle.qr_solve_lapack(Ah, bh, return_R=True)
+        ck = check_x(Ah, bh, kept[j], x_qr, R_A, x_true=xtrue[j])
+        ck.update({"problem": j, "m": m, "n": n, "kappa": kappas[j]})
+        checks.append(ck)
+    out["checks"] = checks
     del probs
     torch.cuda.empty_cache()
     return out
+
+
+def timed_solves(lsq, torch, plan, A, b, x, steps, method=0):
+    """steps solves bracketed by CUDA events on the plan's (default) stream;
+    returns (ms, [info dicts])."""
+    fn = lsq.lsq_solve_fossils if method == 0 else lsq.lsq_solve_spir
+    infos = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        st, inf = fn(plan.handle, A, b, x)
+        infos.append(inf.as_dict())
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), infos
+
+
+def pass_roofline(infos, kernel, pk, pk_kind, traffic):
+    """HBM roofline of the inner pass: 8mn algorithmic bytes per launch (the
+    hi / lo planes, or A itself) over the average CUDA-event duration of the
+    launches that did work."""
+    n_in = sum(i["n_inner_pass"] for i in infos)
+    ms_in = sum(i["ms_inner_pass"] for i in infos)
+    avg_s = (ms_in / n_in) / 1e3
+    achieved = 8.0 * M * N / avg_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": kernel,
+            "launches_timed": n_in, "avg_launch_ms": avg_s * 1e3, "peak_kind": pk_kind,
+            "bytes_per_launch": 8.0 * M * N}
 
 
 def run_ours(args):
@@ -424,51 +604,43 @@ def run_ours(args):
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    infos = []
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        st, inf = lsq.lsq_solve_fossils(h, A, b, x)
-        infos.append(inf.as_dict())
-    e1.record()
-    torch.cuda.synchronize()
+    ms, infos = timed_solves(lsq, torch, plan, A, b, x, args.steps)
     clocks = sampler.stop() if sampler else None
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
     if dist:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = args.steps * world / (ms / 1e3)
+    x_fossils = x.cpu().numpy().copy()
 
-    # roofline of the dominant kernel: the fused A^T(A z) pass
-    n_in = sum(i["n_inner_pass"] for i in infos)
-    ms_in = sum(i["ms_inner_pass"] for i in infos)
+    # roofline of the dominant kernel: the fused A^T(A z) inner pass
     pk, pk_kind = peaks()
-    bytes_pass = 8.0 * M * N
-    avg_s = (ms_in / n_in) / 1e3
-    achieved = bytes_pass / avg_s / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": traffic_per_launch(),
-            "kernel": {0: "atax_kernel", 1: "atax_eft_kernel", 2: "atax32_kernel",
-                       3: "atax_df_kernel"}[infos[-1]["inner_kernel"]]
-                      + " (fused A^T(A z) inner pass)", "launches_timed": n_in,
-            "avg_launch_ms": avg_s * 1e3, "peak_kind": pk_kind}
+    kname = {0: "atax_kernel", 1: "atax_eft_kernel", 2: "atax32_kernel",
+             3: "atax_df_kernel"}[infos[-1]["inner_kernel"]]
+    roof = pass_roofline(infos, kname + " (fused A^T(A z) inner pass)", pk, pk_kind,
+                         traffic_per_launch())
     passes = statistics.mean(i["passes"] for i in infos)
-    hbm_solve = passes * bytes_pass / (ms / args.steps / 1e3) / 1e9
+    hbm_solve = passes * 8.0 * M * N / (ms / args.steps / 1e3) / 1e9
 
     # SPIR on the same plan (context)
     xs = torch.empty_like(x)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    spir_infos = []
-    for _ in range(max(1, args.steps // 2)):
-        st, inf = lsq.lsq_solve_spir(h, A, b, xs)
-        spir_infos.append(inf.as_dict())
-    torch.cuda.synchronize()
-    spir_rate = len(spir_infos) / (time.perf_counter() - t0)
+    ms_spir, spir_infos = timed_solves(lsq, torch, plan, A, b, xs, max(2, args.steps // 2), 1)
+    spir_rate = len(spir_infos) / (ms_spir / 1e3)
+    x_spir = xs.cpu().numpy().copy()
+
+    # the same solve with strict-FP64 inner passes (two FP64 FMAs per element)
+    plan64 = lsq.Plan(M, N, seed=SKETCH_SEED, timing=1, inner_fp64_fma=1)
+    x64 = torch.empty_like(x)
+    lsq.lsq_solve_fossils(plan64.handle, A, b, x64)
+    ms64, infos64 = timed_solves(lsq, torch, plan64, A, b, x64, max(2, args.steps // 2))
+    plan64.close()
+    strict = {"solves_per_s": len(infos64) / (ms64 / 1e3), "ms_per_solve": ms64 / len(infos64),
+              "steps": len(infos64), "iters": infos64[-1]["iters"],
+              "roofline": pass_roofline(infos64, "atax_kernel (strict FP64 inner pass)", pk,
+                                        pk_kind, None)}
+    x_strict = x64.cpu().numpy().copy()
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
@@ -502,27 +674,64 @@ def run_ours(args):
                "d2h_bytes_per_step": 8 * N, "h2d_link_gbs": link_gbs,
                "sketch_ms_incl_copy": statistics.median(i["ms_sketch"] for i in host_infos),
                "device_ms_per_solve": statistics.median(i["ms_total"] for i in host_infos)}
+        x_host = hx.numpy().copy()
+        del hA, hb
+    plan.close()
 
     tier = None
     multi = None
     served = None
     if not args.no_tier and not args.rows and not args.cols:
-        del A
+        del A, b
         torch.cuda.empty_cache()
         tier = tier_compare(lsq, torch, dev, max(2, args.steps // 3))
         multi = multi_compare(lsq, torch, dev, 2)
         served = serve_compare(lsq, torch, dev)
 
+    # every timed result against the oracle (after the timed regions)
+    accuracy = None
+    checks_ok = True
+    if rank == 0:
+        import oracle
+        t0 = time.perf_counter()
+        x_qr, R_A = oracle.qr_solve_lapack(P["A"], P["b"], return_R=True)
+        cond = infos[-1]["condest"]
+        accuracy = {"fossils": check_x(P["A"], P["b"], x_fossils, x_qr, R_A, condest=cond),
+                    "spir": check_x(P["A"], P["b"], x_spir, x_qr, R_A, condest=cond),
+                    "fossils_strict_fp64": check_x(P["A"], P["b"], x_strict, x_qr, R_A,
+                                                   condest=cond)}
+        if e2e is not None:
+            accuracy["fossils_host_entry"] = check_x(P["A"], P["b"], x_host, x_qr, R_A,
+                                                     condest=cond)
+        accuracy["oracle"] = "x_ref: LAPACK Householder QR solve (oracle.qr_solve_lapack); BE: " \
+                             "Karlson-Walden estimate with compensated residuals (oracle.kw_relative)"
+        accuracy["check_seconds"] = time.perf_counter() - t0
+        del R_A
+        oks = [v["ok"] for v in accuracy.values() if isinstance(v, dict)]
+        for part in (tier, multi, served):
+            if not part:
+                continue
+            for v in part.values():
+                if isinstance(v, dict) and isinstance(v.get("check"), dict):
+                    oks.append(v["check"]["ok"])
+            for ck in part.get("checks", []):
+                oks.append(ck["ok"])
+            if isinstance(part.get("auto_kappa1e10"), dict):
+                oks.append(part["auto_kappa1e10"]["check"]["ok"])
+        checks_ok = all(oks)
+        accuracy["results_checked"] = len(oks)
+        accuracy["all_ok"] = checks_ok
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_obj(P, CPU_BASELINE_ROWS)
+        cpu = cpu_baseline_obj(P)
 
     if rank == 0:
         last = infos[-1]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic",
+                "dtype": DTYPE, "dtype_note": DTYPE_NOTE, "data": "synthetic",
                 "config": config({"hbm_gbs_per_solve": hbm_solve,
                                   "passes_per_solve": passes,
                                   "iters": last["iters"], "condest": last["condest"],
@@ -531,17 +740,22 @@ def run_ours(args):
                                   "sketch_pass_ms": last["ms_sketch_pass"],
                                   "spir_solves_per_s": spir_rate,
                                   "spir_iters": spir_infos[-1]["iters"],
+                                  "strict_fp64_inner": strict,
                                   "fp32_tier_1e6x1000": tier,
                                   "multi_rhs_2e6x200_k64": multi,
                                   "served_stream": served}),
+                "accuracy": accuracy, "checks_passed": checks_ok,
                 "clocks": clocks, "e2e": e2e,
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "roofline": roof, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
-    plan.close()
+        if not checks_ok:
+            print("bench: a timed result failed its accuracy check (BE <= 1e-13 and the "
+                  "forward-error yardstick); see the 'accuracy' and 'check' entries",
+                  file=sys.stderr)
     if dist:
         dist.destroy_process_group()
-    return 0
+    return 0 if checks_ok else 1
 
 
 def run_profile_case(args):

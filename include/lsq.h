@@ -46,11 +46,17 @@ typedef enum {
   LSQ_ERR_NONFINITE = -6         /* A or b holds NaN or Inf */
 } lsq_status;
 
-/* Arithmetic of the inner iterations (north of the residual, which is FP64). */
+/* Arithmetic of the inner iterations.  On every path the residual b - A x,
+ * A^T r, the update of x, the QR of the sketch and the triangular solves with
+ * R are FP64.  The inner passes h = A^T (A z) of the FP64 path run, by
+ * default, in double-float on the FP32 pipe over an exact-to-2^-48 split of A
+ * into FP32 hi / lo planes (an FP64-class evaluation, within the per-element
+ * error bound of an FP64 pass); inner_fp64_fma = 1 makes them strict FP64
+ * (two FP64 FMAs per element of A). */
 enum {
-  LSQ_PREC_AUTO = 0,        /* FP32 inner passes when condest < fp32_cond_max, else FP64 */
-  LSQ_PREC_FP64 = 1,        /* every step in FP64 */
-  LSQ_PREC_FP32_INNER = 2   /* sketch and inner passes read an FP32 copy of A */
+  LSQ_PREC_AUTO = 0,        /* FP32 inner passes when condest < fp32_cond_max, else the FP64 path */
+  LSQ_PREC_FP64 = 1,        /* the FP64 path (inner passes as inner_fp64_fma selects) */
+  LSQ_PREC_FP32_INNER = 2   /* inner passes read the FP32 hi plane of A (FP32 arithmetic) */
 };
 
 typedef struct lsq_plan_s *lsq_plan;
@@ -82,7 +88,12 @@ typedef struct {
                             column norm is in [2^-40, 2^40] */
   int32_t nrhs;          /* > 0: plan for lsq_solve_fossils_multi with this many
                             right-hand sides (multiple of 8, <= 64; n <= 256) */
-  int32_t reserved[6];
+  int32_t qr_wait_us;    /* > 0: each inter-CTA wait of the QR of the sketch gives up
+                            after this many microseconds (0 => 5 s); the solve then
+                            returns LSQ_ERR_TIMEOUT and the plan stays usable.  The
+                            other device waits (TMA copies, cluster transfers) keep
+                            their own limits, so no copy can outlive its CTA */
+  int32_t reserved[5];
 } lsq_options;
 
 #define LSQ_MAX_N 1024
@@ -241,7 +252,7 @@ lsq_status lsq_trsv(lsq_plan plan, int trans, const double *dy, double *dx);
  * has no counterpart; it is a packaging of lsq_apply_normal's FP64 pass.
  * No plan is needed.  dA: m x n row-major (lda, 0 => n), dz, dh: n, all
  * device pointers owned by the caller; cuda_stream: cudaStream_t (NULL =
- * default stream); returns after the stream has finished the call.
+ * default stream).  Every call synchronizes that stream before it returns.
  * Scratch: a fixed 2 MiB device array inside the library (held by every GPU
  * that loads it until the process exits).  The first call on a device looks
  * up the array's device address and must come before any stream capture.
@@ -272,7 +283,9 @@ lsq_status lsq_server_create(size_t arena_bytes, int max_slots, int64_t m_max, i
  * they are copied into the arena when the request is admitted (first come,
  * first served, once a slot and its footprint 8(mn + m + n) bytes are free),
  * so they must stay valid and unchanged until lsq_poll stops returning
- * LSQ_PENDING.  Errors: LSQ_ERR_INVALID; LSQ_ERR_OOM when the footprint can
+ * LSQ_PENDING.  Device inputs are copied on the server's own streams, which
+ * are not ordered after any stream of the caller: the work that produced A
+ * and b must be complete (its stream synchronized) before lsq_submit.  Errors: LSQ_ERR_INVALID; LSQ_ERR_OOM when the footprint can
  * never fit the arena (refused at admission time, nothing queued). */
 lsq_status lsq_submit(lsq_server srv, const lsq_options *opt, int method, const double *A,
                       const double *b, int on_device, uint64_t *ticket);

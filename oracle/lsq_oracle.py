@@ -140,6 +140,23 @@ def qr_solve(A, b, return_R=False):
     return (x, R) if return_R else x
 
 
+def qr_solve_lapack(A, b, return_R=False):
+    """The least-squares solve of qr_solve, x = R^{-1} (Q^T b)[:n], with the
+    factorisation and Q^T b taken from LAPACK's blocked Householder QR
+    (dgeqrf / dormqr through scipy.linalg.qr_multiply: a library step) and
+    the back substitution from this oracle.  For problems where the plain
+    loops of householder_qr take minutes (m n^2 above ~1e11).  R may differ
+    from householder_qr's by row signs; R^T R = A^T A either way, which is
+    all kw_estimate needs of it."""
+    import scipy.linalg as sl
+    A = _c64(A)
+    n = A.shape[1]
+    qtb, R = sl.qr_multiply(A, _c64(b)[None, :], mode="right")
+    R = np.ascontiguousarray(np.triu(R[:n, :n]))
+    x = backsub(R, np.ascontiguousarray(qtb.ravel()[:n]))
+    return (x, R) if return_R else x
+
+
 def column_norms(A):
     """d_j = ||A[:, j]||_2 (Alg. 4, ColumnNorms)."""
     return np.sqrt(np.einsum("ij,ij->j", A, A))
@@ -161,7 +178,7 @@ def sketch(A, b, d, zeta, seed):
 def fixed_point_sketch(A, b, d, zeta, seed, row_chunks=None):
     """Unscaled S [A b] (the +-1 pattern of Sec. 4.2's sparse sign embedding,
     without the zeta^{-1/2} factor) summed in 64-bit fixed point per column,
-    the summation order this build takes for large problems (the paper fixes
+    the summation order the CUDA library takes for large problems (the paper fixes
     none).  Every term a_ij is truncated toward zero to a multiple of 2^F_j,
     F_j = (E_j - 1022) + L - 63, where E_j is the largest biased exponent in
     column j over the rows summed (at least 1) and L the bit length of the

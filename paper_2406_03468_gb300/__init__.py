@@ -48,7 +48,7 @@ class LsqOptions(ctypes.Structure):
                 ("stop_gamma", ctypes.c_double), ("stop_rho", ctypes.c_double),
                 ("fixed_inner", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("inner_fp64_fma", ctypes.c_int32), ("nrhs", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("qr_wait_us", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class LsqInfo(ctypes.Structure):

@@ -157,6 +157,7 @@ lsq_status validate(const lsq_options *o) {
   if (o->eta < 0 || o->eta >= 1) return fail(LSQ_ERR_INVALID, "eta must be in [0, 1)");
   if (o->precision < LSQ_PREC_AUTO || o->precision > LSQ_PREC_FP32_INNER)
     return fail(LSQ_ERR_INVALID, "unknown precision");
+  if (o->qr_wait_us < 0) return fail(LSQ_ERR_INVALID, "qr_wait_us must be >= 0");
   if (o->nrhs < 0 || (o->nrhs > 0 && !multi_supported((int)o->n, o->nrhs)))
     return fail(LSQ_ERR_INVALID, "nrhs must be a multiple of 8 in [8, 64] with n <= 256");
   return LSQ_OK;
@@ -205,6 +206,11 @@ bool tier_ok(lsq_plan P) {
   const double gate = P->o.fp32_cond_max > 0 ? P->o.fp32_cond_max : 1e5;
   if (prec == LSQ_PREC_AUTO && !(P->st_host->condest < gate)) return false;
   return planes_ok(P);
+}
+
+// Limit of each inter-CTA wait of the cooperative QR.
+uint64_t qr_timeout_ns(lsq_plan P) {
+  return P->o.qr_wait_us > 0 ? (uint64_t)P->o.qr_wait_us * 1000ull : kBarrierTimeoutNs;
 }
 
 // Flag value of the next QR launch: never 0 (the flags' initial value) and
@@ -368,7 +374,7 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db, bool defer_
     LSQ_CU(launch_qr_stepwise(P->W, P->d, n, n + 1, P->vbuf, qr_step_grid(n + 1, P->nsm), P->s));
   else
     LSQ_CU(launch_qr(P->W, P->d, n, n + 1, P->vbuf, P->qflag, next_epoch(P), P->st,
-                     qr_grid(n + 1, P->nsm), kBarrierTimeoutNs, P->s));
+                     qr_grid(n + 1, P->nsm), qr_timeout_ns(P), P->s));
   LSQ_CU(launch_extract_r(P->W, P->d, n, 1, P->Rcm, P->Rrm, P->rinv, P->t, P->s));
   LSQ_CU(launch_diag_tiles(P->Rcm, P->Rrm, P->rinv, n, P->Dt, P->s));
   LSQ_CU(cudaEventRecord(P->ev_fork, P->s));
@@ -586,7 +592,7 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
   LSQ_CU(launch_sketch_b_to_w(P->SBb, d, n, k, P->zeta, P->W, P->st, P->s));
   LSQ_CU(cudaEventRecord(P->ev[1], P->s));
   LSQ_CU(launch_qr(P->W, d, n, n + k, P->vbuf, P->qflag, next_epoch(P), P->st,
-                   qr_grid(n + k, P->nsm), kBarrierTimeoutNs, P->s));
+                   qr_grid(n + k, P->nsm), qr_timeout_ns(P), P->s));
   LSQ_CU(launch_extract_r(P->W, d, n, k, P->Rcm, P->Rrm, P->rinv, P->mT, P->s));
   LSQ_CU(launch_diag_tiles(P->Rcm, P->Rrm, P->rinv, n, P->Dt, P->s));
   LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, P->Dt, n, kCondestIters, P->st, P->s));

@@ -129,7 +129,10 @@ size_t footprint(const lsq_options &o) {
          align_up(sizeof(double) * o.n);
 }
 
-void run_request(lsq_server S, lsq_server_s::Slot &slot, Request *r) {
+// Runs one request on the slot.  Returns false when the slot's stream could
+// not be drained: the arena region may then still be read or written by work
+// in flight, so the caller must not hand it to another request.
+bool run_request(lsq_server S, lsq_server_s::Slot &slot, Request *r) {
   double *base = reinterpret_cast<double *>(S->arena_base + r->off);
   const size_t mn = (size_t)r->opt.m * r->opt.n;
   double *dA = base;
@@ -153,13 +156,21 @@ void run_request(lsq_server S, lsq_server_s::Slot &slot, Request *r) {
   if (st >= 0) {
     r->x.resize(r->opt.n);
     e = cudaMemcpyAsync(r->x.data(), dx, sizeof(double) * r->opt.n, cudaMemcpyDeviceToHost, slot.s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(slot.s);
     if (e != cudaSuccess) {
       st = LSQ_ERR_CUDA;
       r->err = cudaGetErrorString(e);
     }
   }
+  // Whatever the status, nothing queued on the slot's stream may outlive the
+  // request: an error can leave copies or kernels that read the region
+  // behind it.
+  e = cudaStreamSynchronize(slot.s);
+  if (e != cudaSuccess && st >= 0) {
+    st = LSQ_ERR_CUDA;
+    r->err = cudaGetErrorString(e);
+  }
   r->status = st;
+  return e == cudaSuccess;
 }
 
 void worker(lsq_server S, int idx) {
@@ -181,10 +192,12 @@ void worker(lsq_server S, int idx) {
       }
     }
     r->t_start = now_s();
-    run_request(S, slot, r);
+    const bool drained = run_request(S, slot, r);
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      S->arena->release(r->off, r->bytes);
+      // a region whose stream could not be drained stays allocated (leaked
+      // for the server's lifetime) rather than being handed out again
+      if (drained) S->arena->release(r->off, r->bytes);
       r->t_end = now_s();
       r->done = true;
       S->running--;

@@ -14,7 +14,7 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # A GPU test collected on a machine without CUDA (a plain `pytest` here)
-    # is skipped; on the GPU machine it runs.
+    # is skipped; where a GPU is present it runs.
     try:
         import torch
         has_gpu = torch.cuda.is_available()

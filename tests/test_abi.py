@@ -32,9 +32,10 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layout_matches_c(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include "lsq.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                    'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(lsq_options), '
+                    'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(lsq_options), '
                     'sizeof(lsq_info), offsetof(lsq_options, fixed_inner), '
-                    'offsetof(lsq_info, ms_total)); return 0;}\n')
+                    'offsetof(lsq_info, ms_total), offsetof(lsq_options, qr_wait_us)); '
+                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
@@ -42,6 +43,7 @@ def test_struct_layout_matches_c(tmp_path):
     assert int(out[1]) == ctypes.sizeof(lsq.LsqInfo)
     assert int(out[2]) == lsq.LsqOptions.fixed_inner.offset
     assert int(out[3]) == lsq.LsqInfo.ms_total.offset
+    assert int(out[4]) == lsq.LsqOptions.qr_wait_us.offset
 
 
 def test_defaults_and_validation_without_gpu():

@@ -43,12 +43,11 @@ def test_config1_fig1_problem(method, seed):
     assert be <= 1e-13, (be, info)
     assert oracle.forward_error(x, xt) <= 10 * oracle.forward_error(x_qr, xt)
     ref = getattr(oracle, method)(A, b, seed=seed)
-    # Step 1 ends once ||Delta|| reaches the rounding-noise floor, where the
-    # exact update that crosses the threshold depends on summation order
-    # (it differs between this oracle on x86 and on Arm), so only "before
-    # the cap" is compared; step 2 runs q0 - 1 updates on both sides (condest
-    # is estimated on the GPU, exact in the oracle).
-    assert info["iters"][0] < 100
+    # Step 1 stops at the first update below Alg. 4's threshold; which update
+    # crosses it first depends on rounding order by a step or two.  Step 2
+    # runs q0 - 1 updates on both sides (condest is estimated on the GPU,
+    # exact in the oracle).
+    assert abs(info["iters"][0] - ref["iters"][0]) <= 2, (info["iters"], ref["iters"])
     assert abs(info["iters"][1] - ref["iters"][1]) <= 1
     # ||c|| at x0 (Table 2: 3.0e-7) and at x1 (Table 2: 1.9e-11; rounding noise)
     assert ref["cnorms"][0] / 5 <= info["cnorm"][0] <= ref["cnorms"][0] * 5
@@ -169,6 +168,39 @@ def test_fp32_tier_forced_and_bytes():
     assert abs(info["bytes_a"] - expect) <= 1e-9 * expect, (info["bytes_a"], expect, info)
 
 
+_C5 = {}
+
+
+def _config5_width_problem(kappa):
+    """The 150000 x 1000 problem at this kappa and the oracle's QR solve of
+    it, built once per kappa for both methods."""
+    if kappa not in _C5:
+        _C5.clear()
+        P = problem_svd(150000, 1000, kappa, 1e-4, seed=51, keep_factors=False)
+        x_qr, R_A = oracle.qr_solve(P["A"], P["b"], return_R=True)
+        _C5[kappa] = (P, x_qr, R_A)
+    return _C5[kappa]
+
+
+@pytest.mark.parametrize("method", ["fossils", "spir"])
+@pytest.mark.parametrize("kappa,path", [(1e4, lsq.LSQ_PREC_FP32_INNER), (1e10, lsq.LSQ_PREC_FP64)])
+def test_fp32_tier_config5_width(method, kappa, path):
+    """Config 5's width, n = 1000 (150000 x 1000, the widest pass and QR
+    instantiations): AUTO takes the FP32 tier at kappa = 1e4 and the FP64
+    path at kappa = 1e10; both results are backward stable and within 10x of
+    the oracle QR's forward error."""
+    P, x_qr, R_A = _config5_width_problem(kappa)
+    A, b, xt = P["A"], P["b"], P["x_true"]
+    st, info, x = _gpu_solve(method, A, b, seed=8, precision=lsq.LSQ_PREC_AUTO)
+    assert st == 0
+    assert info["path"] == path, info
+    if path == lsq.LSQ_PREC_FP32_INNER:
+        assert info["inner_kernel"] == 2 and 2 <= info["refine_steps"] <= 6
+    be = oracle.kw_relative(A, b, x, R_A=R_A)
+    assert be <= 1e-13, (be, info)
+    assert oracle.forward_error(x, xt) <= 10 * oracle.forward_error(x_qr, xt)
+
+
 @pytest.mark.parametrize("fp64", [0, 1])
 @pytest.mark.parametrize("m,n,k,kappa", [(40000, 200, 16, 1e8), (30011, 100, 8, 1e6),
                                          (20000, 200, 64, 1e8)])
@@ -256,3 +288,24 @@ def test_high_condition(method, kappa, resid, fp64):
     assert info["inner_kernel"] == (0 if fp64 else 3)
     _, R_A = oracle.qr_solve(A, b, return_R=True)
     assert oracle.kw_relative(A, b, x, R_A=R_A) <= 1e-13, info
+
+
+def test_qr_wait_runs_out_and_plan_recovers():
+    """A bounded device wait that runs out.  With qr_wait_us = 1 every CTA of
+    the QR but the owner of column 0 waits for reflector 0, which takes the
+    owner several microseconds to build; the waits give up, the solve
+    returns LSQ_ERR_TIMEOUT (no hang, no fault), and the same plan,
+    re-targeted with the default limit, solves the problem backward stably."""
+    m, n = 60000, 500
+    P = problem_svd(m, n, 1e6, 1e-4, seed=2, keep_factors=False)
+    A, b = T(P["A"]), T(P["b"])
+    plan = lsq.Plan(m, n, seed=3, qr_wait_us=1)
+    x = empty(n)
+    with pytest.raises(lsq.LsqError) as e:
+        plan.solve(A, b, x, "fossils")
+    assert e.value.status == -5, str(e.value)
+    lsq.lsq_plan_configure(plan.handle, lsq.lsq_options_default(m=m, n=n, seed=3))
+    st, info = plan.solve(A, b, x, "fossils")
+    assert st == 0
+    assert oracle.kw_relative(P["A"], P["b"], H(x)) <= 1e-13
+    plan.close()

@@ -97,9 +97,11 @@ def test_qr_of_sketch(m, n):
     assert np.allclose(np.tril(R, -1), 0.0)
     assert np.linalg.norm(R - R_or, 2) <= 1e3 * n * u * nR
     assert np.linalg.norm(H(t) - t_or) <= 1e3 * n * u * np.linalg.norm(SAb[:, n])
-    # sketch-and-solve x0 = R^{-1} t
+    # sketch-and-solve x0 = R^{-1} t: both R and t agree to rounding, so x0
+    # agrees to kappa(R) times that (10 kappa(R) n u)
     x0_or = oracle.backsub(R_or, t_or)
-    assert np.linalg.norm(H(x0) - x0_or) <= 1e-9 * np.linalg.norm(x0_or)
+    kR = np.linalg.cond(R_or)
+    assert np.linalg.norm(H(x0) - x0_or) <= 10 * kR * n * u * np.linalg.norm(x0_or)
     # condest / normest against the exact singular values of R
     smax, smin = oracle.sigma_extremes(R_or)
     assert 0.7 * smax <= ne <= 1.0001 * smax

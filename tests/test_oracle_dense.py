@@ -7,6 +7,7 @@
   digits) normal-equations solve on tiny inputs, and against LAPACK lstsq.
 * Compensated residual against an exact rational evaluation.
 """
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -96,3 +97,72 @@ def test_residual_dot2_exact():
     g_ex_f = np.array([float(v) for v in g_ex])
     assert np.allclose(r_hi, r_ex_f, rtol=4e-16, atol=0)
     assert np.allclose(g, g_ex_f, rtol=1e-14, atol=1e-16 * np.abs(g_ex_f).max())
+
+
+def test_wedin_bound_hand_values():
+    """Fact 2.4's forward-error bound, relative to ||x||, at points evaluated
+    by hand: 2.23 kappa (||x|| + kappa ||r|| / ||A||) u / ||x||."""
+    u = 2.0 ** -53
+    x = np.array([3.0, 4.0])                      # ||x|| = 5
+    # kappa 1e6, ||A|| 2, ||r|| 1e-3: 2.23e6 (5 + 500) / 5 = 2.2523e8
+    assert abs(O.wedin_bound(1e6, 2.0, x, 1e-3) / (2.2523e8 * u) - 1) < 1e-12
+    # kappa 1e8, ||A|| 1, ||r|| 1e-2: 2.23e8 (5 + 1e6) / 5 = 4.46002230e13
+    assert abs(O.wedin_bound(1e8, 1.0, x, 1e-2) / (4.4600223e13 * u) - 1) < 1e-12
+    # zero residual: 2.23 kappa
+    assert abs(O.wedin_bound(1e10, 1.0, x, 0.0) / (2.23e10 * u) - 1) < 1e-12
+    # eps other than u enters linearly
+    assert abs(O.wedin_bound(1e3, 1.0, x, 0.0, u=1e-8) / (2.23e-5) - 1) < 1e-12
+
+
+def _exact_ls_orthogonal_columns(cols, b):
+    """Exact least-squares solution when the columns are mutually
+    orthogonal: x_j = a_j^T b / ||a_j||^2 (rational arithmetic)."""
+    return [sum(a * bi for a, bi in zip(c, b)) / sum(a * a for a in c) for c in cols]
+
+
+@pytest.mark.parametrize("term", ["kappa_x", "kappa2_r"])
+def test_wedin_bound_is_attained(term):
+    """Fact 2.4 is tight to its constant: on A = [e1, delta e2] (3 x 2,
+    ||A|| = 1, kappa = 1/delta) a perturbation with ||Delta A|| = eps moves x
+    by eps kappa ||x|| (zero residual; Delta A scales the second column) or
+    by eps kappa^2 ||r|| (residual r = rho e3; Delta A tilts the second column
+    towards r).  The exact perturbed solutions (rational arithmetic) must lie
+    below the bound and above 0.4 of it (the first-order error is 1 / 2.23 of
+    the bound), so a dropped term or a wrong constant fails."""
+    F = Fraction
+    delta, eps = F(1, 10 ** 4), F(1, 10 ** 12)
+    kappa = 1 / delta
+    if term == "kappa_x":
+        x = [F(0), F(1)]
+        rho = F(0)
+        cols_p = [[F(1), F(0), F(0)], [F(0), delta + eps, F(0)]]
+    else:
+        x = [F(1), F(1)]
+        rho = F(1)
+        cols_p = [[F(1), F(0), F(0)], [F(0), delta, eps]]
+    b = [x[0], delta * x[1], rho]                 # A x + rho e3, r = rho e3 orthogonal to range(A)
+    xp = _exact_ls_orthogonal_columns(cols_p, b)
+    err = math.sqrt(float(sum((p - q) ** 2 for p, q in zip(xp, x))))
+    nx = math.sqrt(float(sum(v * v for v in x)))
+    bound = O.wedin_bound(float(kappa), 1.0, np.array([float(v) for v in x]), float(rho),
+                          u=float(eps)) * nx
+    assert err <= bound, (err, bound)
+    assert err >= 0.4 * bound, (err, bound)
+
+
+def test_qr_solve_lapack_matches_plain_loops():
+    """The LAPACK-backed solve (for the large bench problems) against the
+    oracle's plain Householder loops: R equal up to row signs, x within the
+    Wedin bound of the known solution and of the plain solve."""
+    P = problem_svd(3000, 40, 1e8, 1e-4, seed=12)
+    x, R = O.qr_solve(P["A"], P["b"], return_R=True)
+    xl, Rl = O.qr_solve_lapack(P["A"], P["b"], return_R=True)
+    s = np.sign(np.diag(R)) * np.sign(np.diag(Rl))
+    assert np.allclose(Rl * s[:, None], R, rtol=0, atol=1e-12 * np.abs(R).max())
+    wb = O.wedin_bound(1e8, 1.0, P["x_true"], 1e-4)
+    assert O.forward_error(xl, P["x_true"]) < wb
+    assert O.forward_error(xl, x) < 2 * wb
+    # the KW estimate is the same whichever R it is given
+    be = O.kw_relative(P["A"], P["b"], xl, R_A=R)
+    bel = O.kw_relative(P["A"], P["b"], xl, R_A=Rl)
+    assert abs(be - bel) <= 1e-6 * be

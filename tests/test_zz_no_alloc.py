@@ -1,5 +1,6 @@
 """The allocation-free fused pass (lsq_apply_normal_noalloc) against the
-plan-based lsq_apply_normal, both through the C ABI.
+plan-based lsq_apply_normal, both through the C ABI, and against the
+oracle's compensated A^T (A z).
 
 Callers that cannot allocate device memory (a framework that owns all GPU
 memory through its own pool, a latency-critical loop that cannot afford
@@ -12,6 +13,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2406_03468_gb300 as lsq
 
 pytestmark = pytest.mark.gpu
@@ -36,10 +38,13 @@ def test_noalloc_matches_plan_pass_twice(m, n, lda):
         torch.cuda.synchronize()
         hp = h_plan.cpu().numpy()
         hf = h_free.cpu().numpy()
-        # the same per-element bound the pass tests use
+        # the same per-element bound the pass tests use, against the plan
+        # pass and against the oracle's compensated A^T (A z)
         bound = 4 * (n + m) * u * (np.abs(An).T @ (np.abs(An) @ np.abs(z)))
+        _, _, h_ref = oracle.residual_dot2(An, np.zeros(m), -z)
         assert np.isfinite(hf).all(), call
         assert (np.abs(hf - hp) <= bound).all(), call
+        assert (np.abs(hf - h_ref) <= bound).all(), call
     plan.close()
 
 
