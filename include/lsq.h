@@ -121,7 +121,9 @@ typedef struct {
                                      2: FP32 tier pass (hi plane), 3: double-float pass on
                                      the hi / lo planes (one batched launch for many
                                      right-hand sides), 4: FP64 tensor-core (DMMA)
-                                     many-right-hand-side pass */
+                                     many-right-hand-side pass, 5: the double-float
+                                     pass for many right-hand sides that applies each
+                                     row block of A to all k vectors (A read once) */
   double bytes_a;                 /* bytes of A (and its FP32 copy) streamed by the solve */
   int32_t reserved[2];
 } lsq_info;
@@ -172,10 +174,10 @@ lsq_status lsq_solve_spir(lsq_plan plan, const double *dA, const double *db, dou
  * column, each column with its own Polyak vectors and step-1 threshold, the
  * step ending when every column meets its own).  The residual pass
  * G = A^T (B - A X) is an FP64 tensor-core (DMMA) contraction over row
- * blocks of A.  The inner pass H = A^T (A Z) runs all k vectors through the
- * double-float pass on the hi / lo planes in one launch.  With
- * inner_fp64_fma = 1, or column norms outside [2^-40, 2^40], it is also a
- * DMMA contraction.  dB: m x k row-major with leading
+ * blocks of A.  The inner pass H = A^T (A Z) runs in double-float on the
+ * hi / lo planes, each row block of A applied to all k vectors in one read
+ * of A.  With inner_fp64_fma = 1, or column norms outside [2^-40, 2^40], it
+ * is also a DMMA contraction.  dB: m x k row-major with leading
  * dimension ldb >= k (0 => k); dX: n x k row-major (device).  Requires
  * n <= 256.  info (may be NULL) reports the largest ||c_i|| over columns. */
 lsq_status lsq_solve_fossils_multi(lsq_plan plan, const double *dA, const double *dB,
@@ -234,6 +236,17 @@ lsq_status lsq_get_R(lsq_plan plan, double *dR, double *dt, double *dx0, double 
  * column norms allow it; otherwise two FP64 FMAs per element.  dz, dh: n,
  * device.  No scaling is applied. */
 lsq_status lsq_apply_normal(lsq_plan plan, const double *dA, const double *dz, double *dh);
+
+/* Many right-hand sides, one pass: dH = A^T (A dZ) for the plan's k = nrhs
+ * vectors (Alg. 1's Apply for each right-hand side of
+ * lsq_solve_fossils_multi), with the inner-pass kernel that solve uses.
+ * After lsq_solve_fossils_multi on the same A (it writes the hi / lo FP32
+ * planes) and unless inner_fp64_fma is set: double-float on the planes,
+ * every row block of A applied to all k vectors while it is in shared
+ * memory; otherwise the FP64 tensor-core (DMMA) contraction on dA.  dZ, dH:
+ * n x k column-major (vector c at offset c n), device.  No scaling is
+ * applied.  Errors: LSQ_ERR_INVALID (NULL argument, nrhs = 0 plan). */
+lsq_status lsq_apply_normal_multi(lsq_plan plan, const double *dA, const double *dZ, double *dH);
 
 /* One fused streaming pass over A: dg = A^T (db - A dx) and *r2 = ||b - A x||^2
  * (Alg. 1, the refinement right-hand side before the R^{-T} solve).  r2 is a

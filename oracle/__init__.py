@@ -30,5 +30,5 @@ formula is not in the paper.
 from . import lsq_oracle, philox  # noqa: F401
 from .lsq_oracle import (  # noqa: F401
     U_ROUNDOFF, apply_qt, backsub, backsub_t, column_norms, fixed_point_sketch, forward_error, fossils,
-    householder_qr, kw_estimate, kw_relative, q0_count, qr_solve, residual_dot2,
+    householder_qr, kw_estimate, kw_relative, q0_count, qr_solve, qr_solve_lapack, residual_dot2,
     sigma_extremes, sketch, sketched_kw, spir, spir_lsqr, step2_updates, wedin_bound)

@@ -16,7 +16,8 @@ __all__ = [
     "LsqError", "LsqOptions", "LsqInfo", "lsq_options_default", "lsq_plan_create",
     "lsq_plan_destroy", "lsq_plan_configure", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir", "lsq_solve_host",
     "lsq_solve_fossils_multi",
-    "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_sketch_raw", "lsq_get_R", "lsq_apply_normal", "lsq_residual",
+    "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_sketch_raw", "lsq_get_R", "lsq_apply_normal",
+    "lsq_apply_normal_multi", "lsq_residual",
     "lsq_trsv", "lsq_apply_normal_noalloc", "lsq_last_error", "Plan", "lsq_server_create",
     "lsq_submit", "lsq_poll", "lsq_server_stats", "lsq_server_destroy", "library_path", "EXPORTED",
     "LSQ_PREC_AUTO", "LSQ_PREC_FP64", "LSQ_PREC_FP32_INNER",
@@ -97,6 +98,7 @@ EXPORTED = {
     "lsq_get_sketch_raw": (_i32, [_vp, _vp]),
     "lsq_get_R": (_i32, [_vp, _vp, _vp, _vp, _dp, _dp]),
     "lsq_apply_normal": (_i32, [_vp, _vp, _vp, _vp]),
+    "lsq_apply_normal_multi": (_i32, [_vp, _vp, _vp, _vp]),
     "lsq_residual": (_i32, [_vp, _vp, _vp, _vp, _vp, _dp]),
     "lsq_trsv": (_i32, [_vp, _i32, _vp, _vp]),
     "lsq_apply_normal_noalloc": (_i32, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
@@ -235,6 +237,11 @@ def lsq_get_R(plan, R=None, t=None, x0=None):
 
 def lsq_apply_normal(plan, A, z, h):
     return _check(_lib().lsq_apply_normal(plan, _ptr(A), _ptr(z), _ptr(h)))
+
+
+def lsq_apply_normal_multi(plan, A, Z, H):
+    """H = A^T (A Z) for the plan's nrhs vectors (Z, H: n x k column-major)."""
+    return _check(_lib().lsq_apply_normal_multi(plan, _ptr(A), _ptr(Z), _ptr(H)))
 
 
 def lsq_residual(plan, A, b, x, g):

@@ -9,6 +9,7 @@
 // partial n-vector and a separate kernel sums the partials in a fixed order,
 // so the result does not depend on scheduling.
 #include "lsq_common.cuh"
+#include "lsq_dev.cuh"
 
 namespace lsq {
 
@@ -110,12 +111,6 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
 // the largest, which keeps every significant entry of A in FP32 range.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
 // a * 2^-Eg split into hi + lo (ebias = 896 + Eg).
 __device__ __forceinline__ void split_f64(double a, int ebias, float &hi, float &lo) {
   const unsigned hw = (unsigned)__double2hiint(a), lw = (unsigned)__double2loint(a);
@@ -126,15 +121,6 @@ __device__ __forceinline__ void split_f64(double a, int ebias, float &hi, float 
   const float l = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), __int_as_float((lf > 0 ? lf : 1) << 23));
   hi = (ef > 0) ? __uint_as_float(hib) : 0.0f;
   lo = (lf > 0) ? __uint_as_float(__float_as_uint(l) | sign) : 0.0f;
-}
-
-// Exact FP32 -> FP64 widening with integer operations (normal and zero inputs).
-__device__ __forceinline__ double widen(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned e = (b >> 23) & 0xffu;
-  if (e == 0) return 0.0;
-  const unsigned hw = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-  return __hiloint2double((int)hw, (int)(b << 29));
 }
 
 template <int NC, bool VEC>
@@ -241,100 +227,6 @@ constexpr int kDfFlush = 32;
 constexpr int kDfStages = 2;
 constexpr uint64_t kDfWaitNs = 1000ull * 1000 * 1000;  // 1 s
 
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(bar)),
-               "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                   (unsigned)__cvta_generic_to_shared(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"((unsigned)__cvta_generic_to_shared(bar)), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase; false after kDfWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
-  if (mbar_try_wait(bar, phase)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, phase))
-    if (global_ns() - t0 > kDfWaitNs) return false;
-  return true;
-}
-
-// L2 policy for data read once (the planes stream through L2 34 times per
-// solve and would otherwise evict R and the partial sums the small kernels
-// between passes read).
-__device__ __forceinline__ uint64_t l2_evict_first() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar,
-                                         uint64_t pol) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-      " [%0], [%1], %2, [%3], %4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-      "l"(src), "r"(bytes), "r"((unsigned)__cvta_generic_to_shared(bar)), "l"(pol)
-      : "memory");
-}
-
-// Packed FP32 pairs (two columns per 64-bit register, the lower one in the
-// low word): sm_100-class add / sub / mul / fma .rn.f32x2 round each half as
-// the scalar instruction would, at one issue slot per two elements.
-typedef unsigned long long f2_t;
-__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
-  f2_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
-  f2_t d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
-  f2_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
-  f2_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
-  return ((f2_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
-}
-__device__ __forceinline__ float f2_lo(f2_t v) { return __uint_as_float((unsigned)v); }
-__device__ __forceinline__ float f2_hi(f2_t v) { return __uint_as_float((unsigned)(v >> 32)); }
-// One double-float accumulation step on a pair: (s, l) += (a * b exactly,
-// with the cross terms a * bl + al * b), given bn = -b.  The product's
-// rounding error comes from fma(a, b, -p) with -p = a * bn; the TwoSum adds p
-// as s - (-p).  Every operation is the scalar algorithm's, per half.
-__device__ __forceinline__ void f2_dd_step(f2_t &s, f2_t &l, f2_t a, f2_t al, f2_t b, f2_t bl,
-                                           f2_t bn) {
-  const f2_t pn = f2_mul(a, bn);
-  const f2_t c = f2_fma(a, bl, f2_fma(al, b, f2_fma(a, b, pn)));
-  const f2_t s1 = f2_sub(s, pn);
-  const f2_t bb = f2_sub(s1, s);
-  const f2_t er = f2_sub(f2_sub(s, f2_sub(s1, bb)), f2_add(pn, bb));
-  s = s1;
-  l = f2_add(l, f2_add(er, c));
-}
-
 template <int NC>
 __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     atax_df_kernel(const float *__restrict__ Ahi, const float *__restrict__ Alo, int64_t ld32,
@@ -406,11 +298,13 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     hh[k] = hl[k] = 0ull;
   }
   int blk = 0;
-  bool ok = true;
+  int64_t qfail = -1;
   for (int64_t q = 0; q < nrows; q++) {
     const int stg = (int)(q % kDfStages);
-    if (!mbar_wait(wbar + stg, (unsigned)((q / kDfStages) & 1))) {
-      ok = false;
+    // one decision per warp: a lane whose wait ran out takes the whole warp
+    // to the drain below
+    if (!__all_sync(0xffffffffu, mbar_wait(wbar + stg, (unsigned)((q / kDfStages) & 1), kDfWaitNs))) {
+      qfail = q;
       break;
     }
     const float *rh = wst + (size_t)stg * 2 * NC * 64;
@@ -472,11 +366,16 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
       }
     }
   }
-  if (!ok) {
-    // record the error; let the copies this warp has in flight land before
-    // the CTA's shared memory is released (bounded again)
-    if (lane == 0 && err != nullptr) atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
-    for (int st = 0; st < kDfStages; st++) mbar_wait(wbar + st, 0), mbar_wait(wbar + st, 1);
+  if (qfail >= 0) {
+    // record the error; let the copies this warp has in flight (rows qfail
+    // .. qfail + kDfStages - 1, one per stage) land before the CTA's shared
+    // memory is released (bounded again)
+    if (lane == 0) {
+      if (err != nullptr) atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
+      for (int64_t r = qfail; r < qfail + kDfStages && r < nrows; r++)
+        mbar_wait(wbar + (r % kDfStages), (unsigned)((r / kDfStages) & 1), kDfWaitNs);
+    }
+    __syncwarp();
   }
 #pragma unroll
   for (int k = 0; k < NC; k++) {
@@ -495,22 +394,51 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
 
 // ---------------------------------------------------------------------------
 // FP32 inner pass of the mixed-precision tier (condest below the gate): reads
-// the FP32 copy of A (4 bytes per element), FP32 row products, FP32 column
-// sums flushed into FP64 accumulators every 32 rows (bounds the FP32
-// accumulation error at about 32 u_32 per block).  z is scaled by a common
-// power of two so that it sits in FP32 range; h is scaled back.
+// the hi plane of A (A rounded to FP32, 4 bytes per element), FP32 row
+// products, FP32 column sums flushed into FP64 accumulators every 32 rows
+// (bounds the FP32 accumulation error at about 32 u_32 per block).  z is
+// scaled by a common power of two so that it sits in FP32 range; h is scaled
+// back.  Rows reach shared memory by TMA bulk copies, k32Stages rows per
+// warp in flight (lane 0 issues the copies of the rows its warp will take
+// next while the warp works on the current one), with the same bounded
+// mbarrier waits and drain as the double-float pass.
 // ---------------------------------------------------------------------------
+constexpr int k32Stages = 4;
+
 template <int NC>
 __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     atax32_kernel(const float *__restrict__ A32, int64_t ld32, int64_t m, int n,
                   const double *__restrict__ z, double *__restrict__ part, int npad,
-                  const DevState *gate) {
+                  const DevState *gate, int *err) {
   if (gate != nullptr && *(volatile const int *)&gate->done) return;
+  // dynamic shared memory: [warps][k32Stages][NC*64] FP32 row stages, then
+  // the mbarriers
+  extern __shared__ __align__(16) float rst[];
   __shared__ double sh[NC * 64];
   __shared__ double wmax[kPassThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float *wst = rst + (size_t)warp * k32Stages * NC * 64;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(rst + (size_t)nw * k32Stages * NC * 64);
+  uint64_t *wbar = bars + warp * k32Stages;
   const int64_t per = (m + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = min(m, (int64_t)blockIdx.x * per), r1 = min(m, r0 + per);
+  const int64_t nrows = (r1 - r0 - warp + nw - 1) / nw > 0 ? (r1 - r0 - warp + nw - 1) / nw : 0;
+  const unsigned row_bytes = (unsigned)(ld32 * sizeof(float));
+  if (lane == 0) {
+    for (int st = 0; st < k32Stages; st++) mbar_init(wbar + st, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const uint64_t pol = l2_evict_first();
+  auto issue = [&](int64_t q) {
+    if (lane == 0 && q < nrows) {
+      const int64_t i = r0 + warp + q * nw;
+      const int stg = (int)(q % k32Stages);
+      mbar_expect_tx(wbar + stg, row_bytes);
+      bulk_g2s(wst + (size_t)stg * NC * 64, A32 + i * ld32, row_bytes, wbar + stg, pol);
+    }
+  };
+  for (int64_t q = 0; q < k32Stages; q++) issue(q);
   double zr[2 * NC];
   load_vec<NC>(z, n, lane, zr);
   double zmax = 0.0;
@@ -534,24 +462,40 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     hd[k] = 0.0;
   }
   int blk = 0;
-  for (int64_t i = r0 + warp; i < r1; i += nw) {
-    const float *row = A32 + i * ld32;
+  int64_t qfail = -1;
+  for (int64_t q = 0; q < nrows; q++) {
+    const int stg = (int)(q % k32Stages);
+    // one decision per warp: a lane whose wait ran out takes the whole warp
+    // to the drain below
+    if (!__all_sync(0xffffffffu, mbar_wait(wbar + stg, (unsigned)((q / k32Stages) & 1), kDfWaitNs))) {
+      qfail = q;
+      break;
+    }
+    const float *row = wst + (size_t)stg * NC * 64;
     float a[2 * NC];
 #pragma unroll
     for (int k = 0; k < NC; k++) {
       const int col = 64 * k + 2 * lane;
       if (col + 1 < n) {
-        const float2 v = __ldcs(reinterpret_cast<const float2 *>(row + col));
+        const float2 v = *reinterpret_cast<const float2 *>(row + col);
         a[2 * k] = v.x;
         a[2 * k + 1] = v.y;
       } else {
-        a[2 * k] = (col < n) ? __ldcs(row + col) : 0.0f;
+        a[2 * k] = (col < n) ? row[col] : 0.0f;
         a[2 * k + 1] = 0.0f;
       }
     }
-    float t = 0.0f;
+    // every lane has its values: the stage may be refilled
+    __syncwarp();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(q + k32Stages);
+    float t0 = 0.0f, t1 = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 2 * NC; k++) t = __fmaf_rn(a[k], zf[k], t);
+    for (int k = 0; k < NC; k++) {
+      t0 = __fmaf_rn(a[2 * k], zf[2 * k], t0);
+      t1 = __fmaf_rn(a[2 * k + 1], zf[2 * k + 1], t1);
+    }
+    float t = t0 + t1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
 #pragma unroll
@@ -564,6 +508,17 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
         hf[k] = 0.0f;
       }
     }
+  }
+  if (qfail >= 0) {
+    // record the error; let the copies this warp has in flight (rows qfail
+    // .. qfail + k32Stages - 1, one per stage) land before the CTA's shared
+    // memory is released
+    if (lane == 0) {
+      if (err != nullptr) atomicCAS(err, 0, (int)LSQ_ERR_TIMEOUT);
+      for (int64_t r = qfail; r < qfail + k32Stages && r < nrows; r++)
+        mbar_wait(wbar + (r % k32Stages), (unsigned)((r / k32Stages) & 1), kDfWaitNs);
+    }
+    __syncwarp();
   }
 #pragma unroll
   for (int k = 0; k < 2 * NC; k++) hd[k] = (hd[k] + (double)hf[k]) * up;
@@ -749,10 +704,17 @@ cudaError_t launch_pass_atax_df(const float *Ahi, const float *Alo, int64_t ld32
 }
 
 cudaError_t launch_pass_atax32(const float *A32, int64_t ld32, int64_t m, int n, const double *z,
-                               double *part, int grid, int npad, const DevState *gate,
+                               double *part, int grid, int npad, const DevState *gate, int *err,
                                cudaStream_t s) {
+  const int nw = kPassThreads / 32;
+  const size_t smem = (size_t)nw * k32Stages * npad * sizeof(float) +
+                      (size_t)nw * k32Stages * sizeof(uint64_t);
   LSQ_PASS_SWITCH(npad, {
-    atax32_kernel<NC><<<grid, kPassThreads, 0, s>>>(A32, ld32, m, n, z, part, npad, gate);
+    if (smem > 48 * 1024) {
+      cudaError_t e = ensure_smem_attr((const void *)atax32_kernel<NC>, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    atax32_kernel<NC><<<grid, kPassThreads, smem, s>>>(A32, ld32, m, n, z, part, npad, gate, err);
   });
   return cudaGetLastError();
 }

@@ -113,6 +113,7 @@ struct lsq_plan_s {
   double *dcol_host = nullptr;
   // many right-hand sides (nrhs > 0)
   int k = 0;
+  bool multi_planes = false;        // the planes hold the A of the last multi solve
   double *SBb = nullptr, *cpartB = nullptr, *mpart = nullptr, *mr2part = nullptr, *mT = nullptr;
   double *mpartdf = nullptr;  // partials of the batched double-float pass (k x gpass x npad)
   double *mXs = nullptr, *mXo = nullptr, *mC = nullptr, *mG = nullptr, *mDY = nullptr;
@@ -327,6 +328,7 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db, bool defer_
   P->launches = 0;
   P->tev_used = 0;
   LSQ_TRY(join_condest(P));  // a previous call that failed early may have left one running
+  P->multi_planes = false;
   // fresh device state with alpha, beta
   std::memset(P->st_host, 0, sizeof(DevState));
   P->st_host->alpha = P->alpha;
@@ -474,7 +476,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
       }
       if (tier)
         LSQ_CU(launch_pass_atax32(P->Ahi, P->ld32, P->m, n, P->z, P->part, P->gpass, P->npad,
-                                  P->st, P->s));
+                                  P->st, &P->st->err, P->s));
       else if (P->use_df)
         LSQ_CU(launch_pass_atax_df(P->Ahi, P->Alo, P->ld32, P->m, n, P->z, P->part, P->gpass,
                                    P->npad, P->st, &P->st->err, P->s));
@@ -561,6 +563,27 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
   return status;
 }
 
+// Many right-hand sides, inner pass in double-float on the planes: the
+// k-tiled pass (every row block of A applied to all k vectors while it is in
+// shared memory) when its tiles fit, else one launch of the single-vector
+// pass over k grid rows (each vector re-reads A).  H (n x k column-major) =
+// scale .* A^T (A Z).
+cudaError_t launch_multi_df_pass(lsq_plan P, const double *Z, double *H, const double *scale,
+                                 const DevState *gate) {
+  const int n = (int)P->n, k = P->k;
+  if (multi_df_supported(n, k, P->ld32)) {
+    cudaError_t e = launch_pass_atax_df_multi(P->Ahi, P->Alo, P->ld32, P->m, n, Z, k, P->mpartdf,
+                                              P->nsm, P->npad, gate, &P->st->err, P->s);
+    if (e != cudaSuccess) return e;
+    return launch_reduce_batched(P->mpartdf, P->nsm, P->npad, n, k, scale, H, gate, P->s);
+  }
+  const int64_t pstride = (int64_t)P->gpass * P->npad;
+  cudaError_t e = launch_pass_atax_df(P->Ahi, P->Alo, P->ld32, P->m, n, Z, P->mpartdf, P->gpass,
+                                      P->npad, gate, &P->st->err, P->s, k, n, pstride);
+  if (e != cudaSuccess) return e;
+  return launch_reduce_batched(P->mpartdf, P->gpass, P->npad, n, k, scale, H, gate, P->s);
+}
+
 // FOSSILS for k right-hand sides sharing one sketch and one QR.
 lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64_t ldb,
                            double *dX, lsq_info *info) {
@@ -607,6 +630,7 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
   // FP64 tensor-core contraction
   choose_inner_kernel(P);
   const bool multi_df = P->use_df;
+  P->multi_planes = P->want32;  // the sketch above wrote the planes of this A
   if (P->st_host->nonfinite) return fail(LSQ_ERR_NONFINITE, "A or B holds NaN or Inf");
   if (P->st_host->zero_col) return fail(LSQ_ERR_INVALID, "A has a zero column (column scaling)");
   const int max_inner = P->o.max_inner ? P->o.max_inner : 100;
@@ -640,12 +664,8 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
         LSQ_CU(cudaEventRecord(P->tev[2 * tj], P->s));
       }
       if (multi_df) {
-        const int64_t pstride = (int64_t)P->gpass * P->npad;
-        LSQ_CU(launch_pass_atax_df(P->Ahi, P->Alo, P->ld32, P->m, n, P->mZ, P->mpartdf, P->gpass,
-                                   P->npad, P->st, &P->st->err, P->s, k, n, pstride));
+        LSQ_CU(launch_multi_df_pass(P, P->mZ, P->mH, P->dinv, P->st));
         if (tj >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tj + 1], P->s));
-        LSQ_CU(launch_reduce_batched(P->mpartdf, P->gpass, P->npad, n, k, P->dinv, P->mH, P->st,
-                                     P->s));
       } else {
         LSQ_CU(launch_multi_atax(dA, P->lda, P->m, n, k, P->mZ, P->mpart, P->nsm, P->st, P->s));
         if (tj >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tj + 1], P->s));
@@ -683,7 +703,7 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
     }
     info->refine_steps = nref;
     info->path = LSQ_PREC_FP64;
-    info->inner_kernel = multi_df ? 3 : 4;
+    info->inner_kernel = !multi_df ? 4 : multi_df_supported(n, k, P->ld32) ? 5 : 3;
     info->passes = 2 + nref + iters[0] + iters[1];
     info->status = status;
     info->condest = S.condest;
@@ -736,6 +756,7 @@ void configure_fields(lsq_plan P, const lsq_options *opt) {
     P->pat_valid = false;
   }
   P->sketched = false;
+  P->multi_planes = false;
 }
 
 void free_plan(lsq_plan P) {
@@ -1064,6 +1085,22 @@ lsq_status lsq_apply_normal(lsq_plan P, const double *dA, const double *dz, doub
   else
     LSQ_CU(launch_pass_atax(dA, P->lda, P->m, n, dz, P->part, P->gpass, P->npad, nullptr, P->s));
   LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, nullptr, dh, nullptr, nullptr, nullptr, P->s));
+  LSQ_TRY(read_state(P));
+  return LSQ_OK;
+}
+
+lsq_status lsq_apply_normal_multi(lsq_plan P, const double *dA, const double *dZ, double *dH) {
+  if (!P || !dA || !dZ || !dH) return fail(LSQ_ERR_INVALID, "NULL argument");
+  if (P->k <= 0) return fail(LSQ_ERR_INVALID, "plan was created with nrhs = 0");
+  const int n = (int)P->n, k = P->k;
+  P->launches = 0;
+  if (P->multi_planes && P->use_df) {
+    LSQ_CU(launch_multi_df_pass(P, dZ, dH, nullptr, nullptr));
+  } else {
+    LSQ_CU(launch_multi_atax(dA, P->lda, P->m, n, k, dZ, P->mpart, P->nsm, nullptr, P->s));
+    LSQ_CU(launch_multi_reduce(P->mpart, P->nsm, n, k, nullptr, dH, nullptr, nullptr, nullptr,
+                               P->s));
+  }
   LSQ_TRY(read_state(P));
   return LSQ_OK;
 }

@@ -198,9 +198,11 @@ cudaError_t launch_pass_atax_eft(const double *A, int64_t lda, int64_t m, int n,
                                  int col_exp, double *part, int grid, int npad,
                                  const DevState *gate, cudaStream_t s);
 // FP32 inner pass of the mixed-precision tier: h = A32^T (A32 z) with FP32
-// products and FP32 column sums flushed into FP64 every 32 rows.
+// products and FP32 column sums flushed into FP64 every 32 rows; rows staged
+// by TMA bulk copies (ld32 a multiple of 4, A32 16-byte aligned).  err:
+// LSQ_ERR_TIMEOUT if a copy never landed.
 cudaError_t launch_pass_atax32(const float *A32, int64_t ld32, int64_t m, int n, const double *z,
-                               double *part, int grid, int npad, const DevState *gate,
+                               double *part, int grid, int npad, const DevState *gate, int *err,
                                cudaStream_t s);
 // Inner pass on the hi / lo FP32 planes: row and column sums both in
 // double-float on the FP32 pipe (column sums flushed into FP64 every 8 rows);
@@ -211,6 +213,14 @@ cudaError_t launch_pass_atax_df(const float *Ahi, const float *Alo, int64_t ld32
                                 const double *z, double *part, int grid, int npad,
                                 const DevState *gate, int *err, cudaStream_t s, int batch = 1,
                                 int64_t zstride = 0, int64_t pstride = 0);
+// Many right-hand sides in one read of the hi / lo planes (k_multi_df.cu):
+// the partial sums of H = A^T (A Z) for k <= 64 vectors (Z n x k column-
+// major), CTA g's for vector c at part + (c grid + g) npad.  Needs n <= 256,
+// ld32 % 4 == 0 and one CTA per SM of shared memory (multi_df_supported).
+bool multi_df_supported(int n, int k, int64_t ld32);
+cudaError_t launch_pass_atax_df_multi(const float *Ahi, const float *Alo, int64_t ld32, int64_t m,
+                                      int n, const double *Z, int k, double *part, int grid,
+                                      int npad, const DevState *gate, int *err, cudaStream_t s);
 // out (n x batch, column-major) = scale .* the sums of a batched pass's partials.
 cudaError_t launch_reduce_batched(const double *part, int grid, int npad, int n, int batch,
                                   const double *scale, double *out, const DevState *gate,

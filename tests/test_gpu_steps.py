@@ -311,3 +311,33 @@ def test_gather_sketch_fixed_point(m, n, entry):
     bound_b = trunc_b + k * u * c * np.asarray(S @ np.abs(b)).ravel() + 1e-300
     assert (np.abs(SAg - SA) <= bound_A).all(), np.max(np.abs(SAg - SA) / bound_A)
     assert (np.abs(SAb[:, n] - Sb) <= bound_b).all()
+
+
+@pytest.mark.parametrize("m,n,k", [(40000, 200, 64), (20011, 130, 16), (9001, 256, 64),
+                                   (5003, 37, 8)])
+def test_multi_rhs_inner_pass(m, n, k):
+    """The many-right-hand-side inner pass (every row block of A applied to all
+    k vectors in one read of the hi / lo planes) against the oracle's
+    compensated A^T (A z_c), per element, with the FP64 per-element bound, on
+    vectors spanning 16 decades and columns of A spanning 4; ragged row
+    blocks (m not a multiple of the block) and widths n not a multiple of 4.
+    Then the same with the DMMA pass (inner_fp64_fma = 1)."""
+    rng = np.random.default_rng(m + 7 * n + k)
+    A = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-2, 2, n)
+    B = rng.standard_normal((m, k))
+    Z = rng.standard_normal((k, n)) * 10.0 ** rng.uniform(-8, 8, (k, n))   # vector c = Z[c]
+    for fp64 in (0, 1):
+        plan = lsq.Plan(m, n, seed=3, nrhs=k, inner_fp64_fma=fp64)
+        dA = T(A)
+        X = torch.empty((n, k), dtype=torch.float64, device="cuda")
+        st, info = lsq.lsq_solve_fossils_multi(plan.handle, dA, T(B), k, X)
+        assert info.inner_kernel == (4 if fp64 else 5)
+        Hd = empty(n * k)
+        lsq.lsq_apply_normal_multi(plan.handle, dA, T(np.ascontiguousarray(Z)), Hd)
+        Hh = H(Hd).reshape(k, n)
+        plan.close()
+        absA = np.abs(A)
+        for c in range(k):
+            _, _, h_ref = oracle.residual_dot2(A, np.zeros(m), -Z[c])
+            bound = 4 * (n + m) * u * (absA.T @ (absA @ np.abs(Z[c])))
+            assert (np.abs(Hh[c] - h_ref) <= bound).all(), (fp64, c)
