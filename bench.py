@@ -262,20 +262,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+KERNEL_SRC = os.path.join(ROOT, "paper_2406_03468_gb300", "csrc")
+
+
+def kernel_source_sha256():
+    """sha256 of the inner pass's own source: the atax_df_kernel section of
+    k_pass.cu (from its header comment to the next kernel's) and the device
+    helpers it includes (lsq_dev.cuh).  Edits elsewhere in the library leave
+    it unchanged; any edit to the kernel changes it."""
+    import hashlib
+    src = open(os.path.join(KERNEL_SRC, "k_pass.cu")).read()
+    i = src.index("// Inner pass on the hi / lo FP32 planes of A")
+    j = src.index("// FP32 inner pass of the mixed-precision tier")
+    text = src[i:j] + open(os.path.join(KERNEL_SRC, "lsq_dev.cuh")).read()
+    return hashlib.sha256(text.encode()).hexdigest()
+
+
 def traffic_per_launch():
     """dram read+write bytes per launch of the inner pass from the committed
-    ncu summary, or None when the kernel source changed since it was taken."""
-    import hashlib
+    ncu summary, or None when the kernel's source changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "atax_df_kernel_traffic.txt")
-    src = os.path.join(ROOT, "paper_2406_03468_gb300", "csrc", "k_pass.cu")
     try:
         rec = {}
         for line in open(path):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 rec[k.strip()] = v.strip()
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("k_pass_sha256") != h:
+        if rec.get("kernel_source_sha256") != kernel_source_sha256():
             return None
         return float(rec["bytes_per_launch_full"])
     except (OSError, ValueError, KeyError):
@@ -546,7 +559,7 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
 def timed_solves(lsq, torch, plan, A, b, x, steps, method=0):
     """steps solves bracketed by CUDA events on the plan's (default) stream;
     returns (ms, [info dicts])."""
-    fn = lsq.lsq_solve_fossils if method == 0 else lsq.lsq_solve_spir
+    fn = (lsq.lsq_solve_fossils, lsq.lsq_solve_spir, lsq.lsq_solve_spir_lsqr)[method]
     infos = []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -629,6 +642,10 @@ def run_ours(args):
     ms_spir, spir_infos = timed_solves(lsq, torch, plan, A, b, xs, max(2, args.steps // 2), 1)
     spir_rate = len(spir_infos) / (ms_spir / 1e3)
     x_spir = xs.cpu().numpy().copy()
+    # LSQR-based SPIR on the same plan (context)
+    ms_lq, lq_infos = timed_solves(lsq, torch, plan, A, b, xs, max(2, args.steps // 2), 2)
+    lsqr_rate = len(lq_infos) / (ms_lq / 1e3)
+    x_lsqr = xs.cpu().numpy().copy()
 
     # the same solve with strict-FP64 inner passes (two FP64 FMAs per element)
     plan64 = lsq.Plan(M, N, seed=SKETCH_SEED, timing=1, inner_fp64_fma=1)
@@ -698,6 +715,7 @@ def run_ours(args):
         cond = infos[-1]["condest"]
         accuracy = {"fossils": check_x(P["A"], P["b"], x_fossils, x_qr, R_A, condest=cond),
                     "spir": check_x(P["A"], P["b"], x_spir, x_qr, R_A, condest=cond),
+                    "spir_lsqr": check_x(P["A"], P["b"], x_lsqr, x_qr, R_A, condest=cond),
                     "fossils_strict_fp64": check_x(P["A"], P["b"], x_strict, x_qr, R_A,
                                                    condest=cond)}
         if e2e is not None:
@@ -740,6 +758,8 @@ def run_ours(args):
                                   "sketch_pass_ms": last["ms_sketch_pass"],
                                   "spir_solves_per_s": spir_rate,
                                   "spir_iters": spir_infos[-1]["iters"],
+                                  "spir_lsqr_solves_per_s": lsqr_rate,
+                                  "spir_lsqr_iters": lq_infos[-1]["iters"],
                                   "strict_fp64_inner": strict,
                                   "fp32_tier_1e6x1000": tier,
                                   "multi_rhs_2e6x200_k64": multi,

@@ -169,6 +169,19 @@ lsq_status lsq_solve_fossils(lsq_plan plan, const double *dA, const double *db, 
 lsq_status lsq_solve_spir(lsq_plan plan, const double *dA, const double *db, double *dx,
                           lsq_info *info);
 
+/* LSQR-based SPIR (Sec. 4.2, "SPIR: conjugate gradient or LSQR?"): as
+ * lsq_solve_spir, with each refinement step's least-squares problem
+ * min || r_i - A D^{-1} R^{-1} dy || solved by LSQR (Paige and Saunders)
+ * from dy = 0 in place of CG on its normal equations, and SPIR's two
+ * stopping rules applied to the LSQR step (phi_k / rho_k) w_k.  One pass
+ * over A per LSQR iteration gives both B v and B^T u (the m-vector of the
+ * bidiagonalisation, 8 m bytes, is plan workspace).  The inner passes run
+ * in double-float on the hi / lo FP32 planes of A (inner_fp64_fma = 1: two
+ * FP64 FMAs per element); the FP32 tier is not used (precision AUTO and
+ * FP32_INNER take the FP64 path). */
+lsq_status lsq_solve_spir_lsqr(lsq_plan plan, const double *dA, const double *db, double *dx,
+                               lsq_info *info);
+
 /* FOSSILS for k = opt.nrhs right-hand sides sharing one sketch S [A B] and
  * one QR (Alg. 1 with the augmented columns Q^T S B; Alg. 2 / Alg. 5 per
  * column, each column with its own Polyak vectors and step-1 threshold, the
@@ -187,7 +200,7 @@ lsq_status lsq_solve_fossils_multi(lsq_plan plan, const double *dA, const double
  * (m - 1) lda + n doubles are read), hb (m) and hx (n): copies A and b to
  * plan-owned device memory (allocated on first use, grown when a
  * reconfigured plan needs more, kept with the plan), solves, and copies x
- * back.  method: 0 = FOSSILS, 1 = SPIR.  When the sketch takes its gather
+ * back.  method: 0 = FOSSILS, 1 = SPIR, 2 = LSQR-based SPIR.  When the sketch takes its gather
  * form (m n >= 2^24), A is copied in row chunks of at least 128 MB (16 at
  * most) on a copy stream and the sketch of each chunk (Sec. 4.2) runs as it
  * lands, so the sketch overlaps the copy; each chunk's sums get their own
@@ -289,7 +302,8 @@ typedef struct lsq_server_s *lsq_server;
 lsq_status lsq_server_create(size_t arena_bytes, int max_slots, int64_t m_max, int64_t n_max,
                              lsq_server *out);
 
-/* Submit one FOSSILS (method 0) or SPIR (method 1) solve; returns at once
+/* Submit one FOSSILS (method 0), SPIR (method 1) or LSQR-based SPIR
+ * (method 2) solve; returns at once
  * with a ticket.  opt: m <= m_max, n <= n_max, lda = n (or 0), zeta <= 8,
  * FP64 precision, one right-hand side; the other options as for a plan.
  * A (m x n row-major) and b (m) are host (on_device = 0) or device pointers;

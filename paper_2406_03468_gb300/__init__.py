@@ -14,7 +14,8 @@ from . import _build
 
 __all__ = [
     "LsqError", "LsqOptions", "LsqInfo", "lsq_options_default", "lsq_plan_create",
-    "lsq_plan_destroy", "lsq_plan_configure", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir", "lsq_solve_host",
+    "lsq_plan_destroy", "lsq_plan_configure", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir",
+    "lsq_solve_spir_lsqr", "lsq_solve_host",
     "lsq_solve_fossils_multi",
     "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_sketch_raw", "lsq_get_R", "lsq_apply_normal",
     "lsq_apply_normal_multi", "lsq_residual",
@@ -90,6 +91,7 @@ EXPORTED = {
     "lsq_sketch": (_i32, [_vp, _vp, _vp]),
     "lsq_solve_fossils": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
     "lsq_solve_spir": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
+    "lsq_solve_spir_lsqr": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
     "lsq_solve_host": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
     "lsq_solve_fossils_multi": (_i32, [_vp, _vp, _vp, ctypes.c_int64, _vp,
                                        ctypes.POINTER(LsqInfo)]),
@@ -197,6 +199,10 @@ def lsq_solve_fossils(plan, A, b, x, info=None):
 
 def lsq_solve_spir(plan, A, b, x, info=None):
     return _solve(_lib().lsq_solve_spir, plan, A, b, x, info)
+
+
+def lsq_solve_spir_lsqr(plan, A, b, x, info=None):
+    return _solve(_lib().lsq_solve_spir_lsqr, plan, A, b, x, info)
 
 
 def lsq_solve_fossils_multi(plan, A, B, ldb, X, info=None):
@@ -323,6 +329,7 @@ class Plan:
             pass
 
     def solve(self, A, b, x, method="fossils"):
-        fn = lsq_solve_fossils if method == "fossils" else lsq_solve_spir
+        fn = {"fossils": lsq_solve_fossils, "spir": lsq_solve_spir,
+              "spir_lsqr": lsq_solve_spir_lsqr}[method]
         st, info = fn(self.handle, A, b, x)
         return st, info.as_dict()

@@ -532,10 +532,13 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
 template <int NC, bool VEC>
 __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     resid_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
-                 const double *__restrict__ b, const double *__restrict__ x,
+                 const double *b, const double *__restrict__ x,
                  double *__restrict__ part, double *__restrict__ r2_part, int npad,
-                 float *__restrict__ Ahi, float *__restrict__ Alo, int64_t ld32) {
+                 float *__restrict__ Ahi, float *__restrict__ Alo, int64_t ld32,
+                 const DevState *gate, const double *bscale, double *rout) {
+  if (gate != nullptr && *(volatile const int *)&gate->done) return;
   __shared__ double sh[NC * 64];
+  const double bs = bscale != nullptr ? *bscale : 1.0;
   __shared__ double r2sh[kPassThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t per = (m + gridDim.x - 1) / gridDim.x;
@@ -568,7 +571,11 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
 #pragma unroll
     for (int k = 0; k < 2 * NC; k++) s = fma(a[k], xr[k], s);
     s = warp_sum(s);
-    const double r = b[i] - s;
+    const double r = (bscale != nullptr ? bs * b[i] : b[i]) - s;
+    if (rout != nullptr) {
+      __syncwarp();  // every lane has read b[i] (rout may be b)
+      if (lane == 0) rout[i] = r;
+    }
     r2 = fma(r, r, r2);
 #pragma unroll
     for (int k = 0; k < 2 * NC; k++) g[k] = fma(a[k], r, g[k]);
@@ -721,15 +728,18 @@ cudaError_t launch_pass_atax32(const float *A32, int64_t ld32, int64_t m, int n,
 
 cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, const double *b,
                               const double *x, double *part, double *r2_part, int grid, int npad,
-                              cudaStream_t s, float *Ahi, float *Alo, int64_t ld32) {
+                              cudaStream_t s, float *Ahi, float *Alo, int64_t ld32,
+                              const DevState *gate, const double *bscale, double *rout) {
   const bool vec = vec_ok(A, lda);
   LSQ_PASS_SWITCH(npad, {
     if (vec)
       resid_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, x, part, r2_part,
-                                                           npad, Ahi, Alo, ld32);
+                                                           npad, Ahi, Alo, ld32, gate, bscale,
+                                                           rout);
     else
       resid_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, x, part, r2_part,
-                                                            npad, Ahi, Alo, ld32);
+                                                            npad, Ahi, Alo, ld32, gate, bscale,
+                                                            rout);
   });
   return cudaGetLastError();
 }

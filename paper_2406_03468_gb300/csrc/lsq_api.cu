@@ -83,6 +83,7 @@ struct lsq_plan_s {
   double *t = nullptr, *vbuf = nullptr;
   double *xs = nullptr, *xo = nullptr, *c = nullptr, *g = nullptr, *dy = nullptr;
   double *dyold = nullptr, *z = nullptr, *h = nullptr, *w = nullptr, *res = nullptr, *p = nullptr;
+  double *lsqr_s = nullptr;          // LSQR-SPIR: the m-vector of the bidiagonalisation
   DevState *st = nullptr;
   DevState *st_host = nullptr;
   int *qflag = nullptr;              // QR: per-column "reflector published" flags
@@ -412,7 +413,8 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     LSQ_TRY(join_condest(P));
     LSQ_TRY(read_state(P));
   }
-  const bool tier = tier_ok(P);
+  // method 2 (LSQR-based SPIR) keeps its passes on A's FP64-class forms
+  const bool tier = method != 2 && tier_ok(P);
   const int q32 = tier ? tier_updates(P->st_host->condest, P->eta, max_inner) : 0;
   int q2 = -1;  // set from condest once step 1 has read the device state
   const int nsteps_max = tier ? std::min(LSQ_MAX_REFINE, std::max(nref, 6)) : nref;
@@ -434,7 +436,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     P->planes_pending = false;
     LSQ_CU(launch_pass_resid(dA, P->lda, P->m, n, db, P->xo, P->part, P->r2part, P->gpass,
                              P->npad, P->s, planes ? P->Ahi : nullptr, planes ? P->Alo : nullptr,
-                             P->ld32));
+                             P->ld32, nullptr, nullptr, method == 2 ? P->lsqr_s : nullptr));
     if (tk >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tk + 1], P->s));
     P->launches += 3 + (i == 0 ? 1 : 0) + 1;  // resid, reduce, trsv, [thresh], init
     LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->g, P->r2part, &P->st->r2,
@@ -460,8 +462,11 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     const bool fixed = P->o.fixed_inner > 0;
     const int cap = fixed ? P->o.fixed_inner : tier ? q32 : (i == 0 ? max_inner : q2);
     const int use_thresh = (!fixed && !tier && i == 0) ? 1 : 0;
-    LSQ_CU(launch_inner_init(method, n, P->c, P->dy, P->dyold, P->res, P->p, cap, use_thresh,
-                             P->st, P->s));
+    if (method == 2)
+      LSQ_CU(launch_lsqr_init(n, P->c, i, P->p, P->res, P->dy, cap, use_thresh, P->st, P->s));
+    else
+      LSQ_CU(launch_inner_init(method, n, P->c, P->dy, P->dyold, P->res, P->p, cap, use_thresh,
+                               P->st, P->s));
     for (int it = 0; it < cap; it++) {
       const double *src = (method == 0) ? P->dy : P->p;
       // z = D^{-1} R^{-1} src;  h = D^{-1} A^T (A z);  w = R^{-T} h
@@ -474,7 +479,15 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
         inner_ev[i].push_back(tj);
         LSQ_CU(cudaEventRecord(P->tev[2 * tj], P->s));
       }
-      if (tier)
+      if (method == 2 && P->use_df)
+        LSQ_CU(launch_pass_lsqr_df(P->Ahi, P->Alo, P->ld32, P->m, n, P->z, P->lsqr_s,
+                                   &P->st->lq_bscale, P->part, P->r2part, P->gpass, P->npad, P->st,
+                                   &P->st->err, P->s));
+      else if (method == 2)
+        LSQ_CU(launch_pass_resid(dA, P->lda, P->m, n, P->lsqr_s, P->z, P->part, P->r2part,
+                                 P->gpass, P->npad, P->s, nullptr, nullptr, 0, P->st,
+                                 &P->st->lq_bscale, P->lsqr_s));
+      else if (tier)
         LSQ_CU(launch_pass_atax32(P->Ahi, P->ld32, P->m, n, P->z, P->part, P->gpass, P->npad,
                                   P->st, &P->st->err, P->s));
       else if (P->use_df)
@@ -488,15 +501,18 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
                                 P->s));
       if (tj >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tj + 1], P->s));
       P->launches += 5;
-      LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->h, nullptr, nullptr, P->st,
-                           P->s));
+      LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->h,
+                           method == 2 ? P->r2part : nullptr,
+                           method == 2 ? &P->st->lq_b2 : nullptr, P->st, P->s));
       LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 1, P->h, nullptr, P->w, nullptr, nullptr,
                          nullptr, nullptr, P->st, P->s, 1, 0,
                        &P->st->err));
       if (method == 0)
         LSQ_CU(launch_polyak_update(n, P->c, P->w, P->dy, P->dyold, P->st, P->s));
-      else
+      else if (method == 1)
         LSQ_CU(launch_cg_update(n, P->w, P->p, P->res, P->dy, P->st, P->s));
+      else
+        LSQ_CU(launch_lsqr_update(n, P->w, P->p, P->res, P->dy, P->st, P->s));
       if (use_thresh && (it % kStopPollEvery) == kStopPollEvery - 1 && it + 1 < cap) {
         LSQ_TRY(read_state(P));
         if (P->st_host->done) break;
@@ -544,7 +560,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     cudaEventElapsedTime(&ms, P->ev[0], P->ev[3]);
     info->ms_total = ms;
     info->launches = P->launches;
-    info->inner_kernel = tier ? 2 : P->use_df ? 3 : P->use_eft ? 1 : 0;
+    info->inner_kernel = tier ? 2 : P->use_df ? 3 : (P->use_eft && method != 2) ? 1 : 0;
     if (P->o.timing) {
       for (int k : resid_ev) {
         info->ms_resid_pass += tev_ms(P, k);
@@ -767,7 +783,7 @@ void free_plan(lsq_plan P) {
                   P->stageb, P->stagex, P->Ahi, P->Alo, P->SBb, P->cpartB, P->mpart, P->mpartdf, P->mr2part,
                   P->mT, P->mXs, P->mXo, P->mC, P->mG, P->mDY, P->mDYold, P->mZ, P->mH,
                   P->mW, P->mstate, P->tcnt, P->tlmax, P->colexp, P->cshift,
-                  P->tptr, P->tsrc, P->cpow, P->Qfix, P->Qbfix};
+                  P->tptr, P->tsrc, P->cpow, P->Qfix, P->Qbfix, P->lsqr_s};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->st_host) cudaFreeHost(P->st_host);
@@ -871,6 +887,7 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   for (double **v : vecs) A(dalloc(v, n));
   A(dalloc(&P->st, 1));
   A(dalloc(&P->qflag, n));
+  A(dalloc(&P->lsqr_s, (size_t)P->m_cap));
   A(cudaMallocHost((void **)&P->st_host, sizeof(DevState)));
   A(cudaMallocHost((void **)&P->dcol_host, sizeof(double) * n));
   // hi / lo FP32 planes of A: the double-float inner pass and the FP32 tier read them
@@ -956,6 +973,12 @@ lsq_status lsq_solve_spir(lsq_plan plan, const double *dA, const double *db, dou
   return run_solve(plan, 1, dA, db, dx, info);
 }
 
+lsq_status lsq_solve_spir_lsqr(lsq_plan plan, const double *dA, const double *db, double *dx,
+                               lsq_info *info) {
+  if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  return run_solve(plan, 2, dA, db, dx, info);
+}
+
 lsq_status lsq_solve_fossils_multi(lsq_plan plan, const double *dA, const double *dB,
                                    int64_t ldb, double *dX, lsq_info *info) {
   if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
@@ -966,7 +989,7 @@ lsq_status lsq_solve_host(lsq_plan P, int method, const double *hA, const double
                           lsq_info *info) {
   if (!P) return fail(LSQ_ERR_INVALID, "plan is NULL");
   if (!hA || !hb || !hx) return fail(LSQ_ERR_INVALID, "host buffer is NULL");
-  if (method != 0 && method != 1) return fail(LSQ_ERR_INVALID, "method must be 0 or 1");
+  if (method < 0 || method > 2) return fail(LSQ_ERR_INVALID, "method must be 0, 1 or 2");
   const size_t an = (size_t)(P->m - 1) * P->lda + P->n;  // doubles of A read from the host
   if (an > P->stage_cap) {
     if (P->stageA) cudaFree(P->stageA);

@@ -35,6 +35,10 @@ struct DevState {
   int nonfinite;         // NaN / Inf seen in A or b
   int zero_col;          // a column norm is zero
   int pad;
+  // LSQR (LSQR-based SPIR): the bidiagonalisation's alpha, beta, the
+  // rotation's phibar, rhobar, the next pass's coefficient of s, and the
+  // last pass's ||s||^2
+  double lq_alpha, lq_beta, lq_phibar, lq_rhobar, lq_bscale, lq_b2;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -229,10 +233,13 @@ cudaError_t launch_reduce_batched(const double *part, int grid, int npad, int n,
 // (A^T r is a sum with heavy cancellation -- r is nearly orthogonal to
 // range(A) -- and its rounding reaches x through kappa^2, so it stays FP64.)
 // Ahi != NULL: also write the hi / lo FP32 planes of A (as launch_sketch).
+// bscale != NULL: r = (*bscale) b - A x; rout != NULL: r is written there
+// (rout may equal b); gate: return at once when gate->done (LSQR's pass).
 cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, const double *b,
                               const double *x, double *part, double *r2_part, int grid, int npad,
                               cudaStream_t s, float *Ahi = nullptr, float *Alo = nullptr,
-                              int64_t ld32 = 0);
+                              int64_t ld32 = 0, const DevState *gate = nullptr,
+                              const double *bscale = nullptr, double *rout = nullptr);
 // out[j] = scale[j] * sum_g part[g][j] (scale may be NULL); r2 (if non-NULL)
 // = sum_g r2_part[g]; gated.
 cudaError_t launch_reduce(const double *part, int grid, int npad, int n, const double *scale,
@@ -263,6 +270,21 @@ cudaError_t launch_multi_thresh(int k, double gamma, double rho, const double *x
 cudaError_t launch_sketch_b_to_w(const double *SBb, int d, int n, int k, int zeta, double *W,
                                  DevState *st, cudaStream_t s);
 cudaError_t launch_cm_to_rm(const double *Xcm, int n, int k, double *X, cudaStream_t s);
+
+// LSQR-based SPIR (k_lsqr.cu).  One pass: s <- (*bscale) s - A z, partials
+// of A^T s and ||s||^2, on the hi / lo planes in double-float (the FP64 form
+// is launch_pass_resid with bscale and rout = s); gated.
+cudaError_t launch_pass_lsqr_df(const float *Ahi, const float *Alo, int64_t ld32, int64_t m, int n,
+                                const double *z, double *s, const double *bscale, double *part,
+                                double *r2part, int grid, int npad, const DevState *gate, int *err,
+                                cudaStream_t st);
+// LSQR start from c = R^{-T} D^{-1} A^T r_i (||c||^2 = st->cnorm2[step],
+// ||r_i||^2 = st->r2): v = w = c / ||c||, dy = 0, the scalars in st.
+cudaError_t launch_lsqr_init(int n, const double *c, int step, double *v, double *w, double *dy,
+                             int max_iters, int use_thresh, DevState *st, cudaStream_t s);
+// One LSQR iteration from p = R^{-T} D^{-1} A^T s and st->lq_b2 (gated).
+cudaError_t launch_lsqr_update(int n, const double *p, double *v, double *w, double *dy,
+                               DevState *st, cudaStream_t s);
 
 // Inner-solver kernels (single CTA).
 cudaError_t launch_inner_init(int method, int n, const double *c, double *dy, double *dy_old,

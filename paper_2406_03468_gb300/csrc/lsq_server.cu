@@ -284,8 +284,8 @@ lsq_status lsq_submit(lsq_server S, const lsq_options *opt, int method, const do
     set_last_error("NULL argument");
     return LSQ_ERR_INVALID;
   }
-  if (method != 0 && method != 1) {
-    set_last_error("method must be 0 (FOSSILS) or 1 (SPIR)");
+  if (method < 0 || method > 2) {
+    set_last_error("method must be 0 (FOSSILS), 1 (SPIR) or 2 (LSQR-based SPIR)");
     return LSQ_ERR_INVALID;
   }
   if (opt->m > S->m_max || opt->n > S->n_max || opt->n < 1 || opt->m < opt->n ||

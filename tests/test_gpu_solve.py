@@ -309,3 +309,67 @@ def test_qr_wait_runs_out_and_plan_recovers():
     assert st == 0
     assert oracle.kw_relative(P["A"], P["b"], H(x)) <= 1e-13
     plan.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_spir_lsqr_config1(seed, fp64):
+    """LSQR-based SPIR (Sec. 4.2, "SPIR: conjugate gradient or LSQR?") on the
+    Fig. 1 problem (4000 x 50, kappa = 1e12, ||r|| = 1e-6) against
+    oracle.spir_lsqr: backward error <= 1e-13, forward error within 10x of
+    the oracle QR solve's, the step-1 count within 2 of the oracle's (the
+    first update below the threshold depends on rounding order), the
+    step-2 count equal to q0 - 1 within 1, and ||c_0||, ||c_1|| at the
+    oracle's level.  fp64 = 1: the LSQR passes in FP64 on A."""
+    P = problem_svd(4000, 50, 1e12, 1e-6, seed=seed)
+    A, b, xt = P["A"], P["b"], P["x_true"]
+    st, info, x = _gpu_solve("spir_lsqr", A, b, seed=seed, inner_fp64_fma=fp64)
+    assert st == 0
+    x_qr, R_A = oracle.qr_solve(A, b, return_R=True)
+    be = oracle.kw_relative(A, b, x, R_A=R_A)
+    assert be <= 1e-13, (be, info)
+    assert oracle.forward_error(x, xt) <= 10 * oracle.forward_error(x_qr, xt)
+    ref = oracle.spir_lsqr(A, b, seed=seed)
+    assert abs(info["iters"][0] - ref["iters"][0]) <= 2, (info["iters"], ref["iters"])
+    assert abs(info["iters"][1] - ref["iters"][1]) <= 1
+    assert ref["cnorms"][0] / 5 <= info["cnorm"][0] <= ref["cnorms"][0] * 5
+    assert ref["cnorms"][1] / 10 <= info["cnorm"][1] <= ref["cnorms"][1] * 10
+
+
+@pytest.mark.parametrize("m,n,kappa", [(200003, 500, 1e10), (50021, 130, 1e6)])
+def test_spir_lsqr_config2_shape(m, n, kappa):
+    """LSQR-based SPIR on the config-2 generator at reduced m: backward
+    stable, and within 10x of the larger of the oracle's own LSQR-SPIR /
+    QR spread and the first-order Wedin bound of the oracle QR solution."""
+    P = problem_gaussian(m, n, kappa, 1e-4, seed=5)
+    A, b = P["A"], P["b"]
+    st, info, x = _gpu_solve("spir_lsqr", A, b, seed=9)
+    assert st == 0
+    x_qr, R_A = oracle.qr_solve(A, b, return_R=True)
+    be = oracle.kw_relative(A, b, x, R_A=R_A)
+    assert be <= 1e-13, (be, info)
+    x_sp = oracle.spir_lsqr(A, b, seed=9)["x"]
+    spread = oracle.forward_error(x_sp, x_qr)
+    r = b - A @ x_qr
+    wed = oracle.wedin_bound(info["condest"], 1.0, x_qr, float(np.linalg.norm(r)))
+    assert oracle.forward_error(x, x_qr) <= 10 * max(spread, wed)
+
+
+def test_spir_lsqr_host_entry_and_edges():
+    """method 2 through the host-buffer entry point, and the edge shapes
+    (square, one column, ragged) on the device entry."""
+    P = problem_svd(6000, 64, 1e6, 1e-5, seed=4)
+    A, b = P["A"], P["b"]
+    plan = lsq.Plan(6000, 64, seed=2)
+    xh = np.empty(64)
+    st, info = lsq.lsq_solve_host(plan.handle, 2, A, b, xh)
+    assert st == 0
+    assert oracle.kw_relative(A, b, xh) <= 1e-13
+    plan.close()
+    for (m, n) in ((64, 64), (1000, 1), (513, 33)):
+        rng = np.random.default_rng(m * 7 + n)
+        A = rng.standard_normal((m, n))
+        b = rng.standard_normal(m)
+        st, info, x = _gpu_solve("spir_lsqr", A, b, seed=1)
+        assert st == 0
+        assert oracle.kw_relative(A, b, x) <= 1e-13
