@@ -231,18 +231,30 @@ __device__ void apply_build_regs(double *col, int k, int d, const double (&vr)[V
 // flag hand-off, and the rest of each CTA's FP64 work fills its waits.
 constexpr int kQrMaxLocal = 32;  // columns per CTA (bit mask)
 
-// Column ownership of the cooperative kernel: "snake" order.  Column j lies
-// in round r = j / G at offset o = j mod G and belongs to CTA o in even
-// rounds and to CTA G-1-o in odd ones, as its r-th (local) column.  A
-// column's work grows with j (it receives j reflectors), and pairing each
-// early column with a late one evens the CTAs' totals (the cyclic order
-// j mod G gives the last CTAs of round 0 both heavy columns).
+// Column ownership of the cooperative kernel: "snake" order over units of
+// kQrUnit consecutive columns.  Unit u = j / kQrUnit lies in round
+// r = u / G at offset o = u mod G and belongs to CTA o in even rounds and to
+// CTA G-1-o in odd ones.  A column's work grows with j (it receives j
+// reflectors), and pairing each early unit with a late one evens the CTAs'
+// totals (the cyclic order gives the last CTAs of round 0 both heavy units).
+// Consecutive columns of one unit share a CTA, so the serial chain passes
+// from one CTA to the next once per unit: within a unit, the owner builds
+// reflector j and applies it straight to its own column j + 1 (no flag
+// hand-off, the reflector read from its own shared memory).
+constexpr int kQrUnit = 2;
 __device__ __forceinline__ int qr_owner(int j, int G) {
-  const int r = j / G, o = j - r * G;
+  const int u = j / kQrUnit, r = u / G, o = u - r * G;
   return (r & 1) ? G - 1 - o : o;
 }
+// column of CTA me's local column l (increasing with l)
 __device__ __forceinline__ int qr_col(int me, int l, int G) {
-  return (l & 1) ? (l + 1) * G - 1 - me : l * G + me;
+  const int r = l / kQrUnit, p = l - r * kQrUnit;
+  const int u = r * G + ((r & 1) ? G - 1 - me : me);
+  return u * kQrUnit + p;
+}
+// local index of column j at its owner
+__device__ __forceinline__ int qr_local(int j, int G) {
+  return (j / kQrUnit / G) * kQrUnit + j % kQrUnit;
 }
 enum { kQrDone = 0, kQrBuild = 1, kQrApply = 2, kQrFail = 3, kQrApplyBuild = 4 };
 
@@ -365,7 +377,7 @@ __global__ void __launch_bounds__(kQrThreads, SMEM ? kQrSmemCtasPerSm : kQrGloba
     if (act == kQrDone || act == kQrFail) break;
     if (act == kQrBuild) {
       double uk, beta;
-      make_reflector(colp(k / G), k, d, W + (size_t)k * d, vhead, SMEM, red, uk, beta);
+      make_reflector(colp(qr_local(k, G)), k, d, W + (size_t)k * d, vhead, SMEM, red, uk, beta);
       __syncthreads();
       if (tid == 0) {
         __threadfence();
@@ -382,14 +394,14 @@ __global__ void __launch_bounds__(kQrThreads, SMEM ? kQrSmemCtasPerSm : kQrGloba
     if (act == kQrApplyBuild) {
       if (VR > 0) {
         const double uk = __ldcg(vhead + 2 * k), beta = __ldcg(vhead + 2 * k + 1);
-        const double *vk = own ? colp(k / G) : W + (size_t)k * d;
+        const double *vk = own ? colp(qr_local(k, G)) : W + (size_t)k * d;
         double vr[VR > 0 ? VR : 1];
 #pragma unroll
         for (int r = 0; r < (VR > 0 ? VR : 1); r++) {
           const int i = tid + r * nt;
           vr[r] = (i > k && i < d) ? (own ? vk[i] : __ldcg(vk + i)) : 0.0;
         }
-        apply_build_regs(colp((k + 1) / G), k, d, vr, uk, beta, red, wsh,
+        apply_build_regs(colp(qr_local(k + 1, G)), k, d, vr, uk, beta, red, wsh,
                          W + (size_t)(k + 1) * d, vhead);
       }
       __syncthreads();
@@ -400,7 +412,7 @@ __global__ void __launch_bounds__(kQrThreads, SMEM ? kQrSmemCtasPerSm : kQrGloba
       continue;
     }
     const double uk = __ldcg(vhead + 2 * k), beta = __ldcg(vhead + 2 * k + 1);
-    const double *vk = own ? colp(k / G) : W + (size_t)k * d;
+    const double *vk = own ? colp(qr_local(k, G)) : W + (size_t)k * d;
     double vr[VR > 0 ? VR : 1];
     if (VR > 0) {
 #pragma unroll
@@ -493,7 +505,8 @@ __global__ void extract_r_kernel(const double *__restrict__ W, int d, int n, int
 }  // namespace
 
 int qr_grid(int ncols, int nsm) {
-  return ncols < kQrGlobalCtasPerSm * nsm ? ncols : kQrGlobalCtasPerSm * nsm;
+  const int units = (ncols + kQrUnit - 1) / kQrUnit;
+  return units < kQrGlobalCtasPerSm * nsm ? units : kQrGlobalCtasPerSm * nsm;
 }
 int qr_step_grid(int ncols, int nsm) {
   return ncols < kQrStepCtasPerSm * nsm ? ncols : kQrStepCtasPerSm * nsm;
@@ -527,17 +540,23 @@ cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vhead, int *fl
   // grid: CTAs at kQrGlobalCtasPerSm per SM (qr_grid).  Columns in shared
   // memory at kQrSmemCtasPerSm CTAs per SM if they fit, else in global
   // memory (L2) at kQrGlobalCtasPerSm per SM.
-  auto smem_for = [&](int g) { return (size_t)((ncols + g - 1) / g) * d * sizeof(double); };
+  // local columns per CTA: whole units, dealt over the g CTAs
+  auto nloc_for = [&](int g) {
+    const int units = (ncols + kQrUnit - 1) / kQrUnit;
+    return ((units + g - 1) / g) * kQrUnit;
+  };
+  auto smem_for = [&](int g) { return (size_t)nloc_for(g) * d * sizeof(double); };
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int g1 = ncols < kQrSmemCtasPerSm * nsm ? ncols : kQrSmemCtasPerSm * nsm;
-  if (kQrSmemCtasPerSm * smem_for(g1) <= kQrSmemMax && (ncols + g1 - 1) / g1 <= kQrMaxLocal) {
+  const int units = (ncols + kQrUnit - 1) / kQrUnit;
+  const int g1 = units < kQrSmemCtasPerSm * nsm ? units : kQrSmemCtasPerSm * nsm;
+  if (kQrSmemCtasPerSm * smem_for(g1) <= kQrSmemMax && nloc_for(g1) <= kQrMaxLocal) {
     void *args1[] = {&W, &d, &n, &ncols, &vhead, &flags, &epoch, &st, &timeout_ns};
     return launch_qr_vr<true>(args1, d, g1, smem_for(g1), s);
   }
-  if ((ncols + grid - 1) / grid > kQrMaxLocal) return cudaErrorInvalidConfiguration;
+  if (nloc_for(grid) > kQrMaxLocal) return cudaErrorInvalidConfiguration;
   return launch_qr_vr<false>(args, d, grid, 0, s);
 }
 
