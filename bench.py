@@ -539,6 +539,27 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
                                     "p50_ms": p50 * 1e3, "p99_ms": p99 * 1e3}
     out["stats"] = lsq.lsq_server_stats(srv)
     lsq.lsq_server_destroy(srv)
+    # batched engine: the same problems in batches of `bsize`, each phase one
+    # launch over the batch (closed loop: capacity)
+    bsize = 32
+    elems = max(sum(m * ((n + 3) // 4 * 4) for (m, n, _, _) in probs[i:i + bsize])
+                for i in range(0, count, bsize))
+    bat = lsq.lsq_batch_create(bsize, 256, elems)
+    xs_b = [torch.empty(n, dtype=torch.float64, device=dev) for (m, n, _, _) in probs]
+
+    def run_batched():
+        for i0 in range(0, count, bsize):
+            items = [(probs[i][2], probs[i][3], xs_b[i]) for i in range(i0, min(count, i0 + bsize))]
+            lsq.lsq_batch_solve(bat, items, seeds=[1] * len(items))
+        torch.cuda.synchronize()
+
+    run_batched()  # warm-up (graphs captured, launch shapes tuned)
+    t0 = time.perf_counter()
+    run_batched()
+    bt = time.perf_counter() - t0
+    lsq.lsq_batch_destroy(bat)
+    out["batched"] = {"batch_size": bsize, "capacity_solves_per_s": count / bt,
+                      "vs_slots": (count / bt) / cap, "vs_plain": (count / bt) / plain_rate}
     # a sample of the served results against the oracle's QR solve (the
     # problems' construction has r orthogonal to range(A), so x is known)
     import oracle
@@ -548,7 +569,10 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
         Ah, bh = A.cpu().numpy(), b.cpu().numpy()
         x_qr, R_A = oracle.qr_solve_lapack(Ah, bh, return_R=True)
         ck = check_x(Ah, bh, kept[j], x_qr, R_A, x_true=xtrue[j])
-        ck.update({"problem": j, "m": m, "n": n, "kappa": kappas[j]})
+        ck.update({"problem": j, "m": m, "n": n, "kappa": kappas[j], "path": "server slots"})
+        checks.append(ck)
+        ck = check_x(Ah, bh, xs_b[j].cpu().numpy(), x_qr, R_A, x_true=xtrue[j])
+        ck.update({"problem": j, "m": m, "n": n, "kappa": kappas[j], "path": "batched"})
         checks.append(ck)
     out["checks"] = checks
     del probs

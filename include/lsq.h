@@ -288,6 +288,53 @@ lsq_status lsq_trsv(lsq_plan plan, int trans, const double *dy, double *dx);
 lsq_status lsq_apply_normal_noalloc(const double *dA, int64_t m, int64_t n, int64_t lda,
                                     const double *dz, double *dh, void *cuda_stream);
 
+/* ---- batched solves: many small problems in lockstep -------------------- */
+
+/* Many independent problems (n <= 256 each) solved together, every phase of
+ * the method one launch over all of them: the sketch, each column step of
+ * the QR, the setup after it, and each refinement phase (the launches of
+ * each phase captured once in a CUDA graph and replayed).  The paper solves
+ * one problem at a time; batching is this library's own, for streams of
+ * small problems whose kernels would otherwise last about as long as their
+ * launches.  Per item the method is lsq_solve_fossils / lsq_solve_spir's
+ * with default options (d = 12 n, zeta = 8, column scaling, two refinement
+ * steps, Alg. 4's step-1 stop and Theorem 7.1's step-2 count), except that
+ * the sketch takes the scatter form (FP64 atomic sums) at every size. */
+typedef struct lsq_batch_s *lsq_batch;
+
+typedef struct {
+  int64_t m, n;       /* size: m >= n >= 1, n <= the batch's n_max */
+  const double *A;    /* device: m x n row-major (lda = n) */
+  const double *b;    /* device: m */
+  double *x;          /* device: n, the solution (written) */
+  uint64_t seed;      /* Philox key of the item's sketch */
+  int32_t method;     /* 0: FOSSILS, 1: SPIR */
+  int32_t status;     /* written: the item's lsq_status */
+} lsq_batch_item;
+
+/* Workspace for batches of up to max_items problems with n <= n_max (<= 256)
+ * and sum over items of m * ceil4(n) <= elems_max (the items' FP32 planes),
+ * on the current device, working on cuda_stream (cudaStream_t; NULL: a
+ * stream of its own).  The row-parallel passes take 1, 2 or 4 CTAs per SM,
+ * chosen by timing the batch's residual pass the first time a shape class
+ * (item count and total m n, in powers of two) is seen; the choices are kept
+ * for the process and, when the environment variable LSQ_AUTOTUNE_FILE names
+ * a file, appended to it and read back by later processes.
+ * Errors: LSQ_ERR_INVALID, LSQ_ERR_OOM, LSQ_ERR_CUDA. */
+lsq_status lsq_batch_create(int max_items, int64_t n_max, int64_t elems_max, void *cuda_stream,
+                            lsq_batch *out);
+
+/* Solve count items (1 <= count <= max_items); returns after every x is
+ * written.  items[i].status gets each item's status (LSQ_OK,
+ * LSQ_WARN_RANK_DEFICIENT, LSQ_ERR_NONFINITE, LSQ_ERR_INVALID for a zero
+ * column); infos (count entries, may be NULL) the per-item counts,
+ * condest and ||c_i||.  Returns the first error among the items, else
+ * LSQ_OK; LSQ_ERR_INVALID for bad arguments (nothing run). */
+lsq_status lsq_batch_solve(lsq_batch batch, int count, lsq_batch_item *items, lsq_info *infos);
+
+/* Free the workspace.  NULL is ignored. */
+void lsq_batch_destroy(lsq_batch batch);
+
 /* ---- served stream: continuous batching of independent solves ---------- */
 
 typedef struct lsq_server_s *lsq_server;

@@ -21,6 +21,7 @@ __all__ = [
     "lsq_apply_normal_multi", "lsq_residual",
     "lsq_trsv", "lsq_apply_normal_noalloc", "lsq_last_error", "Plan", "lsq_server_create",
     "lsq_submit", "lsq_poll", "lsq_server_stats", "lsq_server_destroy", "library_path", "EXPORTED",
+    "LsqBatchItem", "lsq_batch_create", "lsq_batch_solve", "lsq_batch_destroy",
     "LSQ_PREC_AUTO", "LSQ_PREC_FP64", "LSQ_PREC_FP32_INNER",
 ]
 
@@ -79,6 +80,12 @@ class LsqInfo(ctypes.Structure):
                 "inner_kernel": self.inner_kernel, "bytes_a": self.bytes_a}
 
 
+class LsqBatchItem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("A", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("x", ctypes.c_void_p), ("seed", ctypes.c_uint64),
+                ("method", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -105,6 +112,9 @@ EXPORTED = {
     "lsq_trsv": (_i32, [_vp, _i32, _vp, _vp]),
     "lsq_apply_normal_noalloc": (_i32, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                         _vp, _vp, _vp]),
+    "lsq_batch_create": (_i32, [_i32, ctypes.c_int64, ctypes.c_int64, _vp, ctypes.POINTER(_vp)]),
+    "lsq_batch_solve": (_i32, [_vp, _i32, ctypes.POINTER(LsqBatchItem), ctypes.POINTER(LsqInfo)]),
+    "lsq_batch_destroy": (None, [_vp]),
     "lsq_server_create": (_i32, [ctypes.c_size_t, _i32, ctypes.c_int64, ctypes.c_int64,
                                  ctypes.POINTER(_vp)]),
     "lsq_submit": (_i32, [_vp, ctypes.POINTER(LsqOptions), _i32, _vp, _vp, _i32,
@@ -265,6 +275,36 @@ def lsq_apply_normal_noalloc(A, m, n, lda, z, h, stream=None):
 
 def lsq_trsv(plan, trans, y, x):
     return _check(_lib().lsq_trsv(plan, int(trans), _ptr(y), _ptr(x)))
+
+
+def lsq_batch_create(max_items, n_max, elems_max, stream=None):
+    """Workspace for batched solves (see include/lsq.h)."""
+    h = _vp()
+    s = getattr(stream, "cuda_stream", stream)
+    _check(_lib().lsq_batch_create(int(max_items), int(n_max), int(elems_max), s,
+                                   ctypes.byref(h)))
+    return h
+
+
+def lsq_batch_solve(batch, problems, seeds=None, methods=None):
+    """problems: list of (A, b, x) device tensors (A m x n row-major);
+    returns (status, [item statuses], [LsqInfo])."""
+    count = len(problems)
+    arr = (LsqBatchItem * count)()
+    infos = (LsqInfo * count)()
+    for i, (A, b, x) in enumerate(problems):
+        arr[i].m, arr[i].n = int(A.shape[0]), int(A.shape[1])
+        arr[i].A, arr[i].b, arr[i].x = _ptr(A), _ptr(b), _ptr(x)
+        arr[i].seed = int(seeds[i]) if seeds is not None else 0
+        arr[i].method = int(methods[i]) if methods is not None else 0
+    st = _lib().lsq_batch_solve(batch, count, arr, infos)
+    if st < 0 and not any(arr[i].status < 0 for i in range(count)):
+        _check(st)  # an error of the call itself, not of an item
+    return st, [arr[i].status for i in range(count)], list(infos)
+
+
+def lsq_batch_destroy(batch):
+    _lib().lsq_batch_destroy(batch)
 
 
 def lsq_server_create(arena_bytes, max_slots, m_max, n_max):

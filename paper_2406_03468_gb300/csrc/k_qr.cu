@@ -238,10 +238,12 @@ constexpr int kQrMaxLocal = 32;  // columns per CTA (bit mask)
 // reflectors), and pairing each early unit with a late one evens the CTAs'
 // totals (the cyclic order gives the last CTAs of round 0 both heavy units).
 // Consecutive columns of one unit share a CTA, so the serial chain passes
-// from one CTA to the next once per unit: within a unit, the owner builds
-// reflector j and applies it straight to its own column j + 1 (no flag
-// hand-off, the reflector read from its own shared memory).
-constexpr int kQrUnit = 2;
+// from one CTA to the next once per unit.  Measured at d = 6000, n = 500:
+// units of 2 took 8.1 ms against 6.6 ms for units of 1 -- within a unit the
+// second column still lacks the previous unit's last reflector when its own
+// chain step comes, and that unfused update costs more than the hand-off it
+// saves -- so units are single columns.
+constexpr int kQrUnit = 1;
 __device__ __forceinline__ int qr_owner(int j, int G) {
   const int u = j / kQrUnit, r = u / G, o = u - r * G;
   return (r & 1) ? G - 1 - o : o;
@@ -450,12 +452,10 @@ __global__ void __launch_bounds__(kQrThreads, SMEM ? kQrSmemCtasPerSm : kQrGloba
 // belongs to CTA j mod G; the owner of column k+1 applies H_k to it and
 // publishes reflector k+1 within step k (lookahead); the reflectors are
 // published as in the cooperative kernel; columns stay in global memory.
-__global__ void __launch_bounds__(kQrThreads)
-    qr_step_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
-                   int k) {
+__device__ void qr_step_body(double *__restrict__ W, int d, int n, int ncols,
+                             double *__restrict__ vhead, int k, int G, int me) {
   __shared__ double red[kQrThreads / 32 * kQrBatch];
   __shared__ double wsh[kQrBatch];
-  const int G = gridDim.x, me = blockIdx.x;
   const int nloc = (ncols - me + G - 1) / G;
   auto colp = [&](int l) -> double * { return W + (size_t)(me + l * G) * d; };
   double uk, beta;
@@ -482,6 +482,21 @@ __global__ void __launch_bounds__(kQrThreads)
     for (; cnt < kQrBatch && l < nloc; cnt++, l++) cols[cnt] = colp(l);
     apply_reflector<true>(cols, cnt, k, d, vk, uk, beta, red, wsh);
   }
+}
+
+__global__ void __launch_bounds__(kQrThreads)
+    qr_step_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
+                   int k) {
+  qr_step_body(W, d, n, ncols, vhead, k, gridDim.x, blockIdx.x);
+}
+
+// The same step for every item of a batch (grid y = item); items with fewer
+// columns than the step are done.
+__global__ void __launch_bounds__(kQrThreads)
+    b_qr_step_kernel(const BItem *__restrict__ items, int k) {
+  const BItem &it = items[blockIdx.y];
+  if (k >= it.n) return;
+  qr_step_body(it.W, it.d, it.n, it.n + 1, it.vhead, k, gridDim.x, blockIdx.x);
 }
 
 __global__ void extract_r_kernel(const double *__restrict__ W, int d, int n, int nb, double *Rcm,
@@ -568,6 +583,11 @@ cudaError_t launch_qr_stepwise(double *W, int d, int n, int ncols, double *vhead
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_b_qr_step(const BItem *items, int count, int qcta, int k, cudaStream_t s) {
+  b_qr_step_kernel<<<dim3(qcta, count), kQrThreads, 0, s>>>(items, k);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_extract_r(const double *W, int d, int n, int nb, double *Rcm, double *Rrm,

@@ -41,14 +41,15 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64
   }
 }
 
-// One thread per column j of S (row j of A).
-__global__ void pattern_kernel(int64_t m, int d, int zeta, uint64_t seed, int32_t *rows,
-                               uint32_t *signbits) {
-  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  int h[kMaxZeta];
+// The zeta rows h[0 .. zeta) (-1 past the ones drawn) and the sign word of
+// column j of S (row j of A), by the spec above.
+template <int ZM>
+__device__ __forceinline__ void column_pattern(int64_t j, int d, int zeta, uint64_t seed,
+                                               int (&h)[ZM], uint32_t &sb_out) {
   int cnt = 0;
   uint32_t sb = 0;
+#pragma unroll
+  for (int k = 0; k < ZM; k++) h[k] = -1;
   // Bounded: at most 1<<16 blocks (the expected count is < 20 even for d = zeta = 32).
   for (uint64_t t = 0; cnt < zeta && t < (1ull << 16); t++) {
     uint64_t c[4] = {(uint64_t)j, t, 0ull, 0ull};
@@ -63,11 +64,28 @@ __global__ void pattern_kernel(int64_t m, int d, int zeta, uint64_t seed, int32_
       if (cnt >= zeta) continue;
       const int hh = (int)(((uint64_t)u * (uint64_t)d) >> 32);
       bool dup = false;
-      for (int k = 0; k < cnt; k++) dup |= (h[k] == hh);
-      if (!dup) h[cnt++] = hh;
+#pragma unroll
+      for (int k = 0; k < ZM; k++) dup |= (k < cnt && h[k] == hh);
+      if (!dup) {
+#pragma unroll
+        for (int k = 0; k < ZM; k++)
+          if (k == cnt) h[k] = hh;
+        cnt++;
+      }
     }
   }
-  for (int k = 0; k < zeta; k++) rows[j * zeta + k] = (k < cnt) ? h[k] : -1;
+  sb_out = sb;
+}
+
+// One thread per column j of S (row j of A).
+__global__ void pattern_kernel(int64_t m, int d, int zeta, uint64_t seed, int32_t *rows,
+                               uint32_t *signbits) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  int h[kMaxZeta];
+  uint32_t sb = 0;
+  column_pattern<kMaxZeta>(j, d, zeta, seed, h, sb);
+  for (int k = 0; k < zeta; k++) rows[j * zeta + k] = h[k];
   signbits[j] = sb;
 }
 
@@ -557,7 +575,169 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
     out[n] = (accumulate ? out[n] : 0.0) + (dob ? (double)accb * cpow[npad] : 0.0);
 }
 
+// ---------------------------------------------------------------------------
+// Batched sketch (many problems in one launch, lsq_batch.cu).  CTA g works on
+// rows of item cta_item[g]: the scatter form of the pass above, with each
+// row's zeta targets drawn inline (each lane of a warp draws the pattern of
+// one of 32 consecutive rows, then the warp walks those rows), the hi / lo
+// planes written as the rows stream, column sums of squares per CTA.
+// zeta <= kBZeta.
+// ---------------------------------------------------------------------------
+constexpr int kBZeta = 8;
+
+template <int NC>
+__device__ void b_sketch_body(const BItem &it, int local, int zeta) {
+  __shared__ double acc[4 * 64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n = it.n, d = it.d, ldsa = n + 1;
+  const int64_t m = it.m;
+  const int64_t per = (m + it.ncta - 1) / it.ncta;
+  const int64_t r0 = min(m, (int64_t)local * per), r1 = min(m, r0 + per);
+  double sq[2 * NC];
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) sq[k] = 0.0;
+  for (int64_t i0 = r0 + 32 * warp; i0 < r1; i0 += 32 * nw) {
+    int hl[kBZeta];
+    uint32_t sbl = 0;
+#pragma unroll
+    for (int t = 0; t < kBZeta; t++) hl[t] = -1;
+    if (i0 + lane < r1) column_pattern<kBZeta>(i0 + lane, d, zeta, it.seed, hl, sbl);
+    const int cnt = (int)min((int64_t)32, r1 - i0);
+    for (int q = 0; q < cnt; q++) {
+      const int64_t i = i0 + q;
+      double a[2 * NC];
+      load_row<NC, false>(it.A + i * n, n, lane, a);
+#pragma unroll
+      for (int k = 0; k < NC; k++) {
+        const int col = 64 * k + 2 * lane;
+        float h0, l0, h1, l1;
+        split_rn(a[2 * k], h0, l0);
+        split_rn(a[2 * k + 1], h1, l1);
+        if (col < n) {
+          __stcs(it.Ahi + i * it.ld32 + col, h0);
+          __stcs(it.Alo + i * it.ld32 + col, l0);
+        }
+        if (col + 1 < n) {
+          __stcs(it.Ahi + i * it.ld32 + col + 1, h1);
+          __stcs(it.Alo + i * it.ld32 + col + 1, l1);
+        }
+        sq[2 * k] = fma(a[2 * k], a[2 * k], sq[2 * k]);
+        sq[2 * k + 1] = fma(a[2 * k + 1], a[2 * k + 1], sq[2 * k + 1]);
+      }
+      const uint32_t sb = __shfl_sync(0xffffffffu, sbl, q);
+      int myh = -1;
+#pragma unroll
+      for (int t = 0; t < kBZeta; t++) {
+        const int ht = __shfl_sync(0xffffffffu, hl[t], q);
+        if (lane == t) myh = ht;
+      }
+      if (lane < zeta && (unsigned)myh < (unsigned)d)
+        atomicAdd(it.SAb + (size_t)myh * ldsa + n, flip_sign(it.b[i], (sb >> lane) & 1u));
+      for (int t = 0; t < zeta; t++) {
+        const int h = __shfl_sync(0xffffffffu, myh, t);
+        if ((unsigned)h >= (unsigned)d) continue;
+        const bool neg = (sb >> t) & 1u;
+        double *dst = it.SAb + (size_t)h * ldsa;
+#pragma unroll
+        for (int k = 0; k < NC; k++) {
+          const int col = 64 * k + 2 * lane;
+          if (col < n) atomicAdd(dst + col, flip_sign(a[2 * k], neg));
+          if (col + 1 < n) atomicAdd(dst + col + 1, flip_sign(a[2 * k + 1], neg));
+        }
+      }
+    }
+  }
+  for (int i = threadIdx.x; i < NC * 64; i += blockDim.x) acc[i] = 0.0;
+  for (int w = 0; w < nw; w++) {
+    __syncthreads();
+    if (warp == w) {
+#pragma unroll
+      for (int k = 0; k < NC; k++) {
+        const int col = 64 * k + 2 * lane;
+        acc[col] += sq[2 * k];
+        acc[col + 1] += sq[2 * k + 1];
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < it.npad; i += blockDim.x)
+    it.part[(size_t)local * it.npad + i] = acc[i];
+}
+
+__global__ void __launch_bounds__(kPassThreads, 2)
+    b_sketch_kernel(const BItem *__restrict__ items, const int *__restrict__ cta_item, int zeta) {
+  const int idx = cta_item[blockIdx.x];
+  const BItem &it = items[idx];
+  const int local = blockIdx.x - it.cta0;
+  switch (it.npad / 64) {
+    case 1: b_sketch_body<1>(it, local, zeta); break;
+    case 2: b_sketch_body<2>(it, local, zeta); break;
+    case 4: b_sketch_body<4>(it, local, zeta); break;
+    default: break;
+  }
+}
+
+// Column norms of each item from its CTAs' partial sums of squares, and the
+// checks of the plan path (non-finite, zero column).
+__global__ void b_colnorm_kernel(const BItem *__restrict__ items) {
+  const BItem &it = items[blockIdx.x];
+  for (int j = threadIdx.x; j < it.n; j += blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < it.ncta; g++) s += it.part[(size_t)g * it.npad + j];
+    const double nrm = sqrt(s);
+    if (!isfinite(nrm)) atomicExch(&it.st->nonfinite, 1);
+    if (nrm == 0.0) atomicExch(&it.st->zero_col, 1);
+    it.dcol[j] = nrm;
+    it.dinv[j] = 1.0 / nrm;
+  }
+}
+
+// W (d x (n+1), column-major) = the item's sketch scaled (dinv zeta^-1/2 per
+// column, zeta^-1/2 for the b column); CTA (x, item) takes the 32 x 32 tiles
+// x, x + gridDim.x, ...
+__global__ void b_transpose_kernel(const BItem *__restrict__ items, double zinv) {
+  __shared__ double tile[32][33];
+  const BItem &it = items[blockIdx.y];
+  const int ncols = it.n + 1, d = it.d;
+  const int tc = (ncols + 31) / 32, th = (d + 31) / 32;
+  for (int tt = blockIdx.x; tt < tc * th; tt += gridDim.x) {
+    const int c0 = (tt % tc) * 32, h0 = (tt / tc) * 32;
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int h = h0 + r, c = c0 + threadIdx.x;
+      if (h < d && c < ncols) {
+        const double v = it.SAb[(size_t)h * ncols + c];
+        if (!isfinite(v)) atomicExch(&it.st->nonfinite, 1);
+        tile[r][threadIdx.x] = v;
+      }
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int c = c0 + r, h = h0 + threadIdx.x;
+      if (h < d && c < ncols) {
+        const double sc = (c < it.n) ? it.dinv[c] * zinv : zinv;
+        it.W[(size_t)c * d + h] = tile[threadIdx.x][r] * sc;
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_b_sketch(const BItem *items, const int *cta_item, int grid, int zeta,
+                            cudaStream_t s) {
+  if (zeta > kBZeta) return cudaErrorInvalidValue;
+  b_sketch_kernel<<<grid, kPassThreads, 0, s>>>(items, cta_item, zeta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_finalize(const BItem *items, int count, int zeta, cudaStream_t s) {
+  b_colnorm_kernel<<<count, 256, 0, s>>>(items);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  b_transpose_kernel<<<dim3(32, count), dim3(32, 8), 0, s>>>(items, 1.0 / sqrt((double)zeta));
+  return cudaGetLastError();
+}
 
 int pass_npad(int n) {
   int nc = 1;

@@ -217,11 +217,9 @@ __device__ double block_normalize(double *sv, int n, double *scratch) {
 
 // sigma_max(R) by power iteration on R^T R and sigma_min(R) by inverse power
 // iteration on (R^T R)^{-1}, from a fixed start vector.
-__global__ void __launch_bounds__(kVecThreads)
-    condest_kernel(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
-                   const double *__restrict__ rinv, const double *__restrict__ Dt, int n, int iters,
-                   DevState *st) {
-  extern __shared__ double sm[];
+__device__ void condest_body(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
+                             const double *__restrict__ rinv, const double *__restrict__ Dt, int n,
+                             int iters, DevState *st, double *sm) {
   double *v = sm, *y = sm + n, *scratch = sm + 2 * n, *tile = scratch + 32;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.0 + 0.25 * (double)((i * 7919) % 17);
   __syncthreads();
@@ -250,6 +248,115 @@ __global__ void __launch_bounds__(kVecThreads)
     const double smin = (winv > 0.0) ? 1.0 / winv : 0.0;
     st->normest = smax;
     st->condest = (smin > 0.0) ? smax / smin : INFINITY;
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+    condest_kernel(const double *__restrict__ Rcm, const double *__restrict__ Rrm,
+                   const double *__restrict__ rinv, const double *__restrict__ Dt, int n, int iters,
+                   DevState *st) {
+  extern __shared__ double sm[];
+  condest_body(Rcm, Rrm, rinv, Dt, n, iters, st, sm);
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms (one CTA of kVecThreads per item, lsq_batch.cu).
+// ---------------------------------------------------------------------------
+
+// Step-2 count: q0 of Theorem 7.1 with kappa := condest and distortion
+// 1.01 eta; Alg. 5 returns dy_(q) after q - 1 updates (as the plan path).
+__device__ int step2_count(double condest, double eta, int max_inner) {
+  const double e = 1.01 * eta;
+  double q0 = 11.0;
+  if (e > 0.0 && isfinite(condest) && condest > 0.0) {
+    const double v = 1.0 + 2.0 * log(1.0 / (condest * kU)) / log(1.0 / e);
+    q0 = v > 11.0 ? v : 11.0;
+  }
+  int q = (int)ceil(q0) - 1;
+  if (q < 1) q = 1;
+  if (q > max_inner) q = max_inner;
+  return q;
+}
+
+// After the QR: R (both layouts), 1/R_ii, t, the scaled diagonal tiles,
+// condest / normest, x0 = R^-1 t (xs; xo = D^-1 xs; ||x0||^2) and q2.
+__global__ void __launch_bounds__(kVecThreads)
+    b_setup_kernel(const BItem *__restrict__ items, int iters, int max_inner) {
+  extern __shared__ double sm[];
+  const BItem &it = items[blockIdx.x];
+  const int n = it.n, d = it.d, nb = (n + 31) / 32;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int j = idx / n, i = idx % n;  // column j, row i
+    const double v = (i <= j) ? it.W[(size_t)j * d + i] : 0.0;
+    it.Rcm[(size_t)j * n + i] = v;
+    it.Rrm[(size_t)i * n + j] = v;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    it.rinv[i] = 1.0 / it.W[(size_t)i * d + i];
+    it.t[i] = it.W[(size_t)n * d + i];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 2 * nb * 1024; idx += blockDim.x) {
+    const int blk = idx / 1024, e = idx % 1024, tr = blk / nb, b = blk % nb;
+    const int jj = e >> 5, l = e & 31, j0 = b * 32, len = min(n, j0 + 32) - j0;
+    const double *Rb = tr ? it.Rrm : it.Rcm;
+    it.Dt[idx] = (jj < len && l < len) ? Rb[(size_t)(j0 + jj) * n + j0 + l] * it.rinv[j0 + l] : 0.0;
+  }
+  __syncthreads();
+  condest_body(it.Rcm, it.Rrm, it.rinv, it.Dt, n, iters, it.st, sm);
+  __syncthreads();
+  double *sy = sm, *scratch = sm + n, *tile = scratch + 32;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sy[i] = it.t[i];
+  __syncthreads();
+  block_trsv(it.Rcm, it.Rrm, it.rinv, it.Dt, n, 0, sy, tile);
+  double nrm = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    it.xs[i] = sy[i];
+    it.xo[i] = it.dinv[i] * sy[i];
+    nrm = fma(sy[i], sy[i], nrm);
+  }
+  nrm = block_sum(nrm, scratch);
+  if (threadIdx.x == 0) {
+    it.st->x0norm2 = nrm;
+    it.st->q2 = step2_count(it.st->condest, it.eta, max_inner);
+    it.st->alpha = it.alpha;
+    it.st->beta = it.beta;
+  }
+}
+
+// The triangular solves of the refinement loop for every item (see
+// launch_b_trsv for the modes).
+__global__ void __launch_bounds__(kVecThreads)
+    b_trsv_kernel(const BItem *__restrict__ items, int mode, int step) {
+  const BItem &it = items[blockIdx.x];
+  if (mode <= 1 && *(volatile const int *)&it.st->done) return;
+  extern __shared__ double sm[];
+  const int n = it.n;
+  double *sy = sm, *scratch = sm + n, *tile = scratch + 32;
+  const double *src = mode == 0 ? (it.method == 0 ? it.dy : it.p)
+                      : mode == 1 ? it.h : mode == 2 ? it.g : it.dy;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sy[i] = src[i];
+  __syncthreads();
+  block_trsv(it.Rcm, it.Rrm, it.rinv, it.Dt, n, (mode == 1 || mode == 2) ? 1 : 0, sy, tile);
+  double nrm = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = sy[i];
+    if (mode == 0) {
+      it.z[i] = it.dinv[i] * x;
+    } else if (mode == 1) {
+      it.w[i] = x;
+    } else if (mode == 2) {
+      it.c[i] = x;
+      nrm = fma(x, x, nrm);
+    } else {
+      const double xs = it.xs[i] + x;
+      it.xs[i] = xs;
+      it.xo[i] = it.dinv[i] * xs;
+    }
+  }
+  if (mode == 2) {
+    nrm = block_sum(nrm, scratch);
+    if (threadIdx.x == 0) it.st->cnorm2[step] = nrm;
   }
 }
 
@@ -554,6 +661,31 @@ cudaError_t launch_trsv(const double *Rcm, const double *Rrm, const double *rinv
   trsv_kernel<<<batch, kVecThreads, smem, s>>>(Rcm, Rrm, rinv, Dt, n, trans, y, in_scale, out,
                                                out_scale, out_scaled, accum, norm2_out, gate,
                                                bstride);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_b_kernels(int nmax) {
+  const size_t smem = (size_t)(2 * nmax + 32 + 3 * kTile) * sizeof(double);
+  cudaError_t e = ensure_smem_attr((const void *)b_setup_kernel, (int)smem);
+  if (e == cudaSuccess) e = ensure_smem_attr((const void *)b_trsv_kernel, (int)smem);
+  return e;
+}
+
+cudaError_t launch_b_setup(const BItem *items, int count, int cond_iters, int max_inner,
+                           int nmax, cudaStream_t s) {
+  const size_t smem = (size_t)(2 * nmax + 32 + 3 * kTile) * sizeof(double);
+  cudaError_t e = ensure_smem_attr((const void *)b_setup_kernel, (int)smem);
+  if (e != cudaSuccess) return e;
+  b_setup_kernel<<<count, kVecThreads, smem, s>>>(items, cond_iters, max_inner);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_trsv(const BItem *items, int count, int mode, int step, int nmax,
+                          cudaStream_t s) {
+  const size_t smem = (size_t)(nmax + 32 + 3 * kTile) * sizeof(double);
+  cudaError_t e = ensure_smem_attr((const void *)b_trsv_kernel, (int)smem);
+  if (e != cudaSuccess) return e;
+  b_trsv_kernel<<<count, kVecThreads, smem, s>>>(items, mode, step);
   return cudaGetLastError();
 }
 

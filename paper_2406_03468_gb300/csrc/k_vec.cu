@@ -12,10 +12,9 @@ namespace lsq {
 
 namespace {
 
-__global__ void __launch_bounds__(kVecThreads)
-    inner_init_kernel(int method, int n, const double *__restrict__ c, double *dy,
-                      double *dy_old, double *res, double *p, int max_iters, int use_thresh,
-                      DevState *st) {
+__device__ void inner_init_body(int method, int n, const double *__restrict__ c, double *dy,
+                                double *dy_old, double *res, double *p, int max_iters,
+                                int use_thresh, DevState *st) {
   __shared__ double scratch[32];
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -41,6 +40,13 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
+__global__ void __launch_bounds__(kVecThreads)
+    inner_init_kernel(int method, int n, const double *__restrict__ c, double *dy,
+                      double *dy_old, double *res, double *p, int max_iters, int use_thresh,
+                      DevState *st) {
+  inner_init_body(method, n, c, dy, dy_old, res, p, max_iters, use_thresh, st);
+}
+
 __device__ __forceinline__ void finish_update(DevState *st, double dn2, bool exhausted) {
   const int it = st->iters + 1;
   st->iters = it;
@@ -50,10 +56,8 @@ __device__ __forceinline__ void finish_update(DevState *st, double dn2, bool exh
   if (stop) st->done = 1;
 }
 
-__global__ void __launch_bounds__(kVecThreads)
-    polyak_update_kernel(int n, const double *__restrict__ c, const double *__restrict__ w,
-                         double *dy, double *dy_old, DevState *st) {
-  if (*(volatile int *)&st->done) return;
+__device__ void polyak_body(int n, const double *__restrict__ c, const double *__restrict__ w,
+                            double *dy, double *dy_old, DevState *st) {
   __shared__ double scratch[32];
   const double alpha = st->alpha, beta = st->beta;
   double s = 0.0;
@@ -69,9 +73,14 @@ __global__ void __launch_bounds__(kVecThreads)
 }
 
 __global__ void __launch_bounds__(kVecThreads)
-    cg_update_kernel(int n, const double *__restrict__ q, double *p, double *res, double *dy,
-                     DevState *st) {
+    polyak_update_kernel(int n, const double *__restrict__ c, const double *__restrict__ w,
+                         double *dy, double *dy_old, DevState *st) {
   if (*(volatile int *)&st->done) return;
+  polyak_body(n, c, w, dy, dy_old, st);
+}
+
+__device__ void cg_body(int n, const double *__restrict__ q, double *p, double *res, double *dy,
+                        DevState *st) {
   __shared__ double scratch[32];
   double pq = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) pq = fma(p[i], q[i], pq);
@@ -98,6 +107,41 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
+__global__ void __launch_bounds__(kVecThreads)
+    cg_update_kernel(int n, const double *__restrict__ q, double *p, double *res, double *dy,
+                     DevState *st) {
+  if (*(volatile int *)&st->done) return;
+  cg_body(n, q, p, res, dy, st);
+}
+
+// Batched forms (one CTA per item, lsq_batch.cu).  b_init: at step 0 the
+// step-1 threshold (as set_thresh) and the cap max_inner with the threshold
+// test; at step 1 the cap q2 (set by b_setup from condest), no threshold.
+__global__ void __launch_bounds__(kVecThreads)
+    b_init_kernel(const BItem *__restrict__ items, int step, int max_inner, double gamma,
+                  double rho) {
+  const BItem &it = items[blockIdx.x];
+  DevState *st = it.st;
+  if (threadIdx.x == 0 && step == 0)
+    st->thresh1 = kU * (gamma * st->normest * sqrt(st->x0norm2) + rho * st->condest * sqrt(st->r2));
+  __syncthreads();
+  const int cap = step == 0 ? max_inner : st->q2;
+  inner_init_body(it.method, it.n, it.c, it.dy, it.dyold, it.res, it.p, cap, step == 0 ? 1 : 0,
+                  st);
+}
+
+__global__ void __launch_bounds__(kVecThreads) b_update_kernel(const BItem *__restrict__ items) {
+  const BItem &it = items[blockIdx.x];
+  if (*(volatile int *)&it.st->done) return;
+  if (it.method == 0) polyak_body(it.n, it.c, it.w, it.dy, it.dyold, it.st);
+  else cg_body(it.n, it.w, it.p, it.res, it.dy, it.st);
+}
+
+__global__ void b_copy_x_kernel(const BItem *__restrict__ items) {
+  const BItem &it = items[blockIdx.x];
+  for (int i = threadIdx.x; i < it.n; i += blockDim.x) it.x[i] = it.xo[i];
+}
+
 __global__ void set_thresh_kernel(double gamma, double rho, DevState *st) {
   st->thresh1 = kU * (gamma * st->normest * sqrt(st->x0norm2) + rho * st->condest * sqrt(st->r2));
 }
@@ -121,6 +165,22 @@ cudaError_t launch_polyak_update(int n, const double *c, const double *w, double
 cudaError_t launch_cg_update(int n, const double *q, double *p, double *res, double *dy,
                              DevState *st, cudaStream_t s) {
   cg_update_kernel<<<1, kVecThreads, 0, s>>>(n, q, p, res, dy, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_init(const BItem *items, int count, int step, int max_inner, double gamma,
+                          double rho, cudaStream_t s) {
+  b_init_kernel<<<count, kVecThreads, 0, s>>>(items, step, max_inner, gamma, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_update(const BItem *items, int count, cudaStream_t s) {
+  b_update_kernel<<<count, kVecThreads, 0, s>>>(items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_copy_x(const BItem *items, int count, cudaStream_t s) {
+  b_copy_x_kernel<<<count, 256, 0, s>>>(items);
   return cudaGetLastError();
 }
 

@@ -34,11 +34,29 @@ struct DevState {
   int err;               // device-side error (LSQ_ERR_TIMEOUT)
   int nonfinite;         // NaN / Inf seen in A or b
   int zero_col;          // a column norm is zero
-  int pad;
+  int q2;                // batched solves: the step-2 update count (Theorem 7.1's q0 - 1)
   // LSQR (LSQR-based SPIR): the bidiagonalisation's alpha, beta, the
   // rotation's phibar, rhobar, the next pass's coefficient of s, and the
   // last pass's ||s||^2
   double lq_alpha, lq_beta, lq_phibar, lq_rhobar, lq_bscale, lq_b2;
+};
+
+// One problem of a batch solved in lockstep (lsq_batch.cu): its sizes, the
+// caller's A, b, x and its slices of the batch workspace.  The table of
+// items lives in device memory; every batched kernel reads its item from it.
+struct BItem {
+  const double *A, *b;  // caller's A (m x n, row-major, lda = n) and b (m), device
+  double *x;            // caller's x (n), device
+  int64_t m;
+  int n, npad, d, ld32;
+  int method;           // 0: FOSSILS, 1: SPIR
+  int cta0, ncta;       // the item's CTAs in the row-parallel launches
+  uint64_t seed;
+  double eta, alpha, beta;  // distortion and Polyak coefficients (Sec. 2.3, 4.2)
+  double *SAb, *W, *part, *r2part, *dcol, *dinv, *Rcm, *Rrm, *rinv, *Dt, *t, *vhead;
+  double *xs, *xo, *c, *g, *dy, *dyold, *z, *h, *w, *res, *p;
+  float *Ahi, *Alo;     // hi / lo FP32 planes (m x ld32)
+  DevState *st;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -285,6 +303,37 @@ cudaError_t launch_lsqr_init(int n, const double *c, int step, double *v, double
 // One LSQR iteration from p = R^{-T} D^{-1} A^T s and st->lq_b2 (gated).
 cudaError_t launch_lsqr_update(int n, const double *p, double *v, double *w, double *dy,
                                DevState *st, cudaStream_t s);
+
+// Batched phases (lsq_batch.cu): every launch covers all `count` items of
+// the table; row-parallel launches take `grid` CTAs, CTA g working on item
+// cta_item[g].  Kernels of the inner loop return at once for an item whose
+// st->done is set.
+// Kernel attributes of the batched kernels for n <= nmax (before any capture).
+cudaError_t prepare_b_kernels(int nmax);
+cudaError_t launch_b_zero(const BItem *items, int count, cudaStream_t s);  // SAb = 0
+cudaError_t launch_b_sketch(const BItem *items, const int *cta_item, int grid, int zeta,
+                            cudaStream_t s);
+cudaError_t launch_b_finalize(const BItem *items, int count, int zeta, cudaStream_t s);
+// QR of every item's sketch, one launch per column step k = -1 .. nmax - 1
+// (qcta CTAs per item).
+cudaError_t launch_b_qr_step(const BItem *items, int count, int qcta, int k, cudaStream_t s);
+// R, 1/R_ii, t, the scaled diagonal tiles, condest / normest, x0 and the
+// step-2 count q2 (into st->max_iters of the item's state, read by b_init).
+cudaError_t launch_b_setup(const BItem *items, int count, int cond_iters, int max_inner,
+                           int nmax, cudaStream_t s);
+// mode 0: z = D^-1 R^-1 (dy or p) (gated); 1: w = R^-T h (gated);
+// 2: c = R^-T g and ||c||^2 into st->cnorm2[step]; 3: xs += R^-1 dy, xo = D^-1 xs.
+cudaError_t launch_b_trsv(const BItem *items, int count, int mode, int step, int nmax,
+                          cudaStream_t s);
+cudaError_t launch_b_resid(const BItem *items, const int *cta_item, int grid, cudaStream_t s);
+cudaError_t launch_b_inner(const BItem *items, const int *cta_item, int grid, cudaStream_t s);
+// mode 0: g = D^-1 sum of the residual partials, st->r2; 1: h (gated).
+cudaError_t launch_b_reduce(const BItem *items, int count, int nmax, int mode, cudaStream_t s);
+// Step thresholds (step 0) and the inner solver's start for step `step`.
+cudaError_t launch_b_init(const BItem *items, int count, int step, int max_inner, double gamma,
+                          double rho, cudaStream_t s);
+cudaError_t launch_b_update(const BItem *items, int count, cudaStream_t s);
+cudaError_t launch_b_copy_x(const BItem *items, int count, cudaStream_t s);
 
 // Inner-solver kernels (single CTA).
 cudaError_t launch_inner_init(int method, int n, const double *c, double *dy, double *dy_old,
