@@ -501,7 +501,8 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
     sample = list(range(0, count, max(1, count // 8)))[:8]
     kept = {}
 
-    def run(gaps, keep=False):
+    def run(gaps, keep=False, server=None):
+        srv_ = server if server is not None else srv
         xb = np.empty(256)
         t_start = time.perf_counter()
         due = t_start + np.cumsum(gaps)
@@ -511,10 +512,10 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
             while i < count and due[i] <= now:
                 m, n, A, b = probs[i]
                 o = lsq.lsq_options_default(m=m, n=n, seed=1)
-                pending[lsq.lsq_submit(srv, o, 0, A, b, 1)] = i
+                pending[lsq.lsq_submit(srv_, o, 0, A, b, 1)] = i
                 i += 1
             for t in list(pending):
-                st, info, l = lsq.lsq_poll(srv, t, xb)
+                st, info, l = lsq.lsq_poll(srv_, t, xb)
                 if st != lsq.LSQ_PENDING:
                     lat.append(l)
                     j = pending[t]
@@ -560,6 +561,22 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
     lsq.lsq_batch_destroy(bat)
     out["batched"] = {"batch_size": bsize, "capacity_solves_per_s": count / bt,
                       "vs_slots": (count / bt) / cap, "vs_plain": (count / bt) / plain_rate}
+    # the batched server: two workers, each taking up to `bsize` queued
+    # requests into one lockstep batch (continuous batching at batch level)
+    bsrv = lsq.lsq_server_create_batched(arena, 2, bsize, 400000, 256)
+    run(np.zeros(count), server=bsrv)  # warm-up
+    bcap, bp50, bp99 = run(np.zeros(count), server=bsrv)
+    served_b = {"workers": 2, "max_batch": bsize, "capacity_solves_per_s": bcap,
+                "closed_loop_p50_ms": bp50 * 1e3, "closed_loop_p99_ms": bp99 * 1e3,
+                "vs_slots": bcap / cap, "vs_plain": bcap / plain_rate}
+    for frac in (0.5, 0.9):
+        rate = frac * bcap
+        gaps = np.random.default_rng(7).exponential(1.0 / rate, count)
+        thr, p50, p99 = run(gaps, server=bsrv)
+        served_b["rate_%.1fC" % frac] = {"offered_per_s": rate, "solves_per_s": thr,
+                                         "p50_ms": p50 * 1e3, "p99_ms": p99 * 1e3}
+    lsq.lsq_server_destroy(bsrv)
+    out["batched_server"] = served_b
     # a sample of the served results against the oracle's QR solve (the
     # problems' construction has r orthogonal to range(A), so x is known)
     import oracle

@@ -312,7 +312,7 @@ typedef struct {
   int32_t status;     /* written: the item's lsq_status */
 } lsq_batch_item;
 
-/* Workspace for batches of up to max_items problems with n <= n_max (<= 256)
+/* Workspace for batches of up to max_items (<= 256) problems with n <= n_max (<= 256)
  * and sum over items of m * ceil4(n) <= elems_max (the items' FP32 planes),
  * on the current device, working on cuda_stream (cudaStream_t; NULL: a
  * stream of its own).  The row-parallel passes take 1, 2 or 4 CTAs per SM,
@@ -348,6 +348,16 @@ typedef struct lsq_server_s *lsq_server;
  * LSQ_ERR_OOM, LSQ_ERR_CUDA. */
 lsq_status lsq_server_create(size_t arena_bytes, int max_slots, int64_t m_max, int64_t n_max,
                              lsq_server *out);
+
+/* As lsq_server_create, but the requests are solved in lockstep batches
+ * (lsq_batch_solve): each of `workers` worker threads owns a batch engine
+ * for up to max_batch (<= 256) problems with n <= n_max (<= 256) and takes, first
+ * come first served, as many queued requests as its batch, its planes and
+ * the arena admit; requests that arrive while batches run wait for the next
+ * free worker.  FOSSILS and SPIR only (method 0 or 1).
+ * Errors: LSQ_ERR_INVALID, LSQ_ERR_OOM, LSQ_ERR_CUDA. */
+lsq_status lsq_server_create_batched(size_t arena_bytes, int workers, int max_batch,
+                                     int64_t m_max, int64_t n_max, lsq_server *out);
 
 /* Submit one FOSSILS (method 0), SPIR (method 1) or LSQR-based SPIR
  * (method 2) solve; returns at once

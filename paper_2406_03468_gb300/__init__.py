@@ -22,6 +22,7 @@ __all__ = [
     "lsq_trsv", "lsq_apply_normal_noalloc", "lsq_last_error", "Plan", "lsq_server_create",
     "lsq_submit", "lsq_poll", "lsq_server_stats", "lsq_server_destroy", "library_path", "EXPORTED",
     "LsqBatchItem", "lsq_batch_create", "lsq_batch_solve", "lsq_batch_destroy",
+    "lsq_server_create_batched",
     "LSQ_PREC_AUTO", "LSQ_PREC_FP64", "LSQ_PREC_FP32_INNER",
 ]
 
@@ -117,6 +118,8 @@ EXPORTED = {
     "lsq_batch_destroy": (None, [_vp]),
     "lsq_server_create": (_i32, [ctypes.c_size_t, _i32, ctypes.c_int64, ctypes.c_int64,
                                  ctypes.POINTER(_vp)]),
+    "lsq_server_create_batched": (_i32, [ctypes.c_size_t, _i32, _i32, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.POINTER(_vp)]),
     "lsq_submit": (_i32, [_vp, ctypes.POINTER(LsqOptions), _i32, _vp, _vp, _i32,
                           ctypes.POINTER(ctypes.c_uint64)]),
     "lsq_poll": (_i32, [_vp, ctypes.c_uint64, _vp, ctypes.POINTER(LsqInfo), _dp]),
@@ -311,6 +314,13 @@ def lsq_server_create(arena_bytes, max_slots, m_max, n_max):
     h = _vp()
     _check(_lib().lsq_server_create(int(arena_bytes), int(max_slots), int(m_max), int(n_max),
                                     ctypes.byref(h)))
+    return h
+
+
+def lsq_server_create_batched(arena_bytes, workers, max_batch, m_max, n_max):
+    h = _vp()
+    _check(_lib().lsq_server_create_batched(int(arena_bytes), int(workers), int(max_batch),
+                                            int(m_max), int(n_max), ctypes.byref(h)))
     return h
 
 

@@ -198,7 +198,9 @@ __global__ void __launch_bounds__(kBThreads, 2)
     b_resid_kernel(const BItem *__restrict__ items, const int *__restrict__ cta_item) {
   __shared__ double sh[4 * 64];
   __shared__ double r2sh[kBThreads / 32];
-  const BItem &it = items[cta_item[blockIdx.x]];
+  const int idx = cta_item[blockIdx.x];
+  if (idx < 0) return;
+  const BItem &it = items[idx];
   const int local = blockIdx.x - it.cta0;
   switch (it.npad / 64) {
     case 1: b_resid_body<1>(it, local, sh, r2sh); break;
@@ -212,7 +214,9 @@ __global__ void __launch_bounds__(kBThreads, 2)
     b_inner_kernel(const BItem *__restrict__ items, const int *__restrict__ cta_item) {
   __shared__ double hacc[kBThreads / 32 * 4 * 64];
   __shared__ double wmax[kBThreads / 32];
-  const BItem &it = items[cta_item[blockIdx.x]];
+  const int idx = cta_item[blockIdx.x];
+  if (idx < 0) return;
+  const BItem &it = items[idx];
   if (*(volatile const int *)&it.st->done) return;
   const int local = blockIdx.x - it.cta0;
   switch (it.npad / 64) {
@@ -260,6 +264,57 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Deal the `grid` CTAs of the row-parallel passes to the items in proportion
+// to m n: every item (all = 1) or only the items whose inner loop is still
+// running (all = 0), so that the last items of a batch get the whole GPU.
+// Writes cta0 / ncta of the table and the CTA -> item map (-1: no item).
+// One CTA; the deal is done by thread 0 in a fixed order.
+__global__ void b_redeal_kernel(BItem *__restrict__ items, int count, int *__restrict__ cta_item,
+                                int grid, int all) {
+  __shared__ int cnt[1024];
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    int act = 0;
+    for (int i = 0; i < count; i++) {
+      const bool on = all || !*(volatile const int *)&items[i].st->done;
+      cnt[i] = on ? 1 : 0;
+      if (on) {
+        tot += (double)items[i].m * items[i].n;
+        act++;
+      }
+    }
+    int used = act;
+    if (act > 0 && grid > act) {
+      const int left = grid - act;
+      for (int i = 0; i < count; i++)
+        if (cnt[i]) {
+          const int f = (int)floor((double)items[i].m * items[i].n / tot * left);
+          cnt[i] += f;
+          used += f;
+        }
+      // the rest one at a time, in item order
+      for (int i = 0; used < grid; i = (i + 1) % count)
+        if (cnt[i]) {
+          cnt[i]++;
+          used++;
+        }
+    }
+    int g = 0;
+    for (int i = 0; i < count; i++) {
+      items[i].cta0 = g;
+      items[i].ncta = cnt[i];
+      g += cnt[i];
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < count; i++) {
+    const int c0 = items[i].cta0, c = items[i].ncta;
+    for (int k = threadIdx.x; k < c; k += blockDim.x) cta_item[c0 + k] = i;
+  }
+  const int g = items[count - 1].cta0 + items[count - 1].ncta;
+  for (int k = g + threadIdx.x; k < grid; k += blockDim.x) cta_item[k] = -1;
+}
+
 // Zero every item's sketch accumulator SAb (d x (n + 1)) before the scatter.
 __global__ void b_zero_kernel(const BItem *__restrict__ items) {
   const BItem &it = items[blockIdx.y];
@@ -270,6 +325,13 @@ __global__ void b_zero_kernel(const BItem *__restrict__ items) {
 }
 
 }  // namespace
+
+cudaError_t launch_b_redeal(BItem *items, int count, int *cta_item, int grid, int all,
+                            cudaStream_t s) {
+  if (count > 1024) return cudaErrorInvalidValue;
+  b_redeal_kernel<<<1, 256, 0, s>>>(items, count, cta_item, grid, all);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_b_zero(const BItem *items, int count, cudaStream_t s) {
   b_zero_kernel<<<dim3(64, count), 256, 0, s>>>(items);

@@ -70,7 +70,7 @@ struct lsq_batch_s {
   char *ws = nullptr;            // per-item n- and d-sized buffers
   size_t ws_per_item = 0;
   float *planes = nullptr;       // hi / lo planes of all items (elems_max floats each)
-  double *part = nullptr, *r2part = nullptr;  // pass partials (grid_max x n_max)
+  double *part = nullptr, *r2part = nullptr;  // pass partials (per item: grid_max x 256)
   int grid_max = 0;
   DevState *st = nullptr;        // one per item
   BItem *d_items = nullptr;
@@ -180,8 +180,8 @@ lsq_status lsq_batch_create(int max_items, int64_t n_max, int64_t elems_max, voi
                             lsq_batch *out) {
   if (!out) return bfail(LSQ_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (max_items < 1 || max_items > 4096 || n_max < 1 || n_max > kBatchNMax || elems_max < n_max)
-    return bfail(LSQ_ERR_INVALID, "need 1 <= max_items <= 4096, 1 <= n_max <= 256, "
+  if (max_items < 1 || max_items > 256 || n_max < 1 || n_max > kBatchNMax || elems_max < n_max)
+    return bfail(LSQ_ERR_INVALID, "need 1 <= max_items <= 256, 1 <= n_max <= 256, "
                                   "elems_max >= n_max");
   lsq_batch B = new lsq_batch_s();
   B->max_items = max_items;
@@ -201,8 +201,10 @@ lsq_status lsq_batch_create(int max_items, int64_t n_max, int64_t elems_max, voi
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(cudaMalloc((void **)&B->ws, L.total * (size_t)max_items));
   A(cudaMalloc((void **)&B->planes, sizeof(float) * 2 * (size_t)elems_max + 256));
-  A(cudaMalloc((void **)&B->part, sizeof(double) * (size_t)B->grid_max * 256));
-  A(cudaMalloc((void **)&B->r2part, sizeof(double) * (size_t)B->grid_max));
+  // each item's partials hold a whole grid (the CTAs are re-dealt to the
+  // unfinished items as the inner loop goes on)
+  A(cudaMalloc((void **)&B->part, sizeof(double) * (size_t)max_items * B->grid_max * 256));
+  A(cudaMalloc((void **)&B->r2part, sizeof(double) * (size_t)max_items * B->grid_max));
   A(cudaMalloc((void **)&B->st, sizeof(DevState) * (size_t)max_items));
   A(cudaMalloc((void **)&B->d_items, sizeof(BItem) * (size_t)max_items));
   A(cudaMalloc((void **)&B->d_cta, sizeof(int) * (size_t)B->grid_max));
@@ -337,13 +339,11 @@ extern "C" lsq_status lsq_batch_solve(lsq_batch B, int count, lsq_batch_item *it
   auto set_grid = [&](int ps) -> lsq_status {
     B->grid = std::max(ps * B->nsm, count);
     B->grid = std::min(B->grid, B->grid_max);
-    int64_t part_off = 0;
     deal_ctas(B, count, B->grid);
     for (int i = 0; i < count; i++) {
       BItem &it = B->h_items[i];
-      it.part = B->part + part_off;
-      it.r2part = B->r2part + it.cta0;
-      part_off += (int64_t)it.ncta * it.npad;
+      it.part = B->part + (size_t)i * B->grid_max * 256;
+      it.r2part = B->r2part + (size_t)i * B->grid_max;
     }
     BCU(cudaMemcpyAsync(B->d_items, B->h_items, sizeof(BItem) * count, cudaMemcpyHostToDevice, B->s));
     BCU(cudaMemcpyAsync(B->d_cta, B->h_cta, sizeof(int) * B->grid, cudaMemcpyHostToDevice, B->s));
@@ -404,7 +404,8 @@ extern "C" lsq_status lsq_batch_solve(lsq_batch B, int count, lsq_batch_item *it
     const double gam = 10.0, rho = 0.4;  // Alg. 4's step-1 stop constants
     for (int step = 0; step < 2; step++) {
       st = capture(B, step == 0 ? &G.step0 : &G.step1, [&]() -> cudaError_t {
-        cudaError_t e = launch_b_resid(B->d_items, B->d_cta, B->grid, B->s);
+        cudaError_t e = launch_b_redeal(B->d_items, count, B->d_cta, B->grid, 1, B->s);
+        if (e == cudaSuccess) e = launch_b_resid(B->d_items, B->d_cta, B->grid, B->s);
         if (e == cudaSuccess) e = launch_b_reduce(B->d_items, count, nmax, 0, B->s);
         if (e == cudaSuccess) e = launch_b_trsv(B->d_items, count, 2, step, nmax, B->s);
         if (e == cudaSuccess) e = launch_b_init(B->d_items, count, step, 100, gam, rho, B->s);
@@ -413,7 +414,8 @@ extern "C" lsq_status lsq_batch_solve(lsq_batch B, int count, lsq_batch_item *it
       if (st < 0) return st;
     }
     st = capture(B, &G.iter, [&]() -> cudaError_t {
-      cudaError_t e = launch_b_trsv(B->d_items, count, 0, 0, nmax, B->s);
+      cudaError_t e = launch_b_redeal(B->d_items, count, B->d_cta, B->grid, 0, B->s);
+      if (e == cudaSuccess) e = launch_b_trsv(B->d_items, count, 0, 0, nmax, B->s);
       if (e == cudaSuccess) e = launch_b_inner(B->d_items, B->d_cta, B->grid, B->s);
       if (e == cudaSuccess) e = launch_b_reduce(B->d_items, count, nmax, 1, B->s);
       if (e == cudaSuccess) e = launch_b_trsv(B->d_items, count, 1, 0, nmax, B->s);

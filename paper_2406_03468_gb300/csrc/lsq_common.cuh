@@ -311,6 +311,10 @@ cudaError_t launch_lsqr_update(int n, const double *p, double *v, double *w, dou
 // Kernel attributes of the batched kernels for n <= nmax (before any capture).
 cudaError_t prepare_b_kernels(int nmax);
 cudaError_t launch_b_zero(const BItem *items, int count, cudaStream_t s);  // SAb = 0
+// Re-deal the row-parallel CTAs over all items (all = 1) or over the items
+// whose inner loop runs (all = 0); each item's partials hold grid entries.
+cudaError_t launch_b_redeal(BItem *items, int count, int *cta_item, int grid, int all,
+                            cudaStream_t s);
 cudaError_t launch_b_sketch(const BItem *items, const int *cta_item, int grid, int zeta,
                             cudaStream_t s);
 cudaError_t launch_b_finalize(const BItem *items, int count, int zeta, cudaStream_t s);

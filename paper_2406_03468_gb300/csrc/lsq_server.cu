@@ -14,6 +14,7 @@
 // one thread per slot those waits do not hold up the other slots.  The QR
 // runs as one ordinary launch per column (no cooperative launch) so that
 // concurrent solves cannot wait on each other's grid barriers.
+#include <algorithm>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -116,10 +117,13 @@ struct lsq_server_s {
   bool stopping = false;
   struct Slot {
     cudaStream_t s = nullptr;
-    lsq_plan plan = nullptr;
+    lsq_plan plan = nullptr;      // slot mode: one solve at a time
+    lsq_batch batch = nullptr;    // batch mode: up to max_batch solves per lockstep batch
     std::thread th;
   };
   std::vector<Slot> slots;
+  int max_batch = 0;              // > 0: batch mode
+  int64_t batch_elems = 0;        // plane capacity of each worker's batch engine
 };
 
 namespace {
@@ -173,6 +177,120 @@ bool run_request(lsq_server S, lsq_server_s::Slot &slot, Request *r) {
   return e == cudaSuccess;
 }
 
+// Batch mode: copy the requests' A and b into their arena regions, solve
+// them as one lockstep batch on the worker's engine, copy each x back.
+// Returns false when the worker's stream could not be drained (the regions
+// may still be in use and are not released).
+bool run_batch(lsq_server S, lsq_server_s::Slot &slot, std::vector<Request *> &rs) {
+  std::vector<lsq_batch_item> items(rs.size());
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; k < rs.size(); k++) {
+    Request *r = rs[k];
+    double *dA = reinterpret_cast<double *>(S->arena_base + r->off);
+    const size_t mn = (size_t)r->opt.m * r->opt.n;
+    double *db = reinterpret_cast<double *>(reinterpret_cast<char *>(dA) + align_up(sizeof(double) * mn));
+    double *dx = reinterpret_cast<double *>(reinterpret_cast<char *>(db) +
+                                            align_up(sizeof(double) * r->opt.m));
+    const cudaMemcpyKind kind = r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dA, r->A, sizeof(double) * mn, kind, slot.s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(db, r->b, sizeof(double) * r->opt.m, kind, slot.s);
+    items[k].m = r->opt.m;
+    items[k].n = r->opt.n;
+    items[k].A = dA;
+    items[k].b = db;
+    items[k].x = dx;
+    items[k].seed = r->opt.seed;
+    items[k].method = r->method;
+    items[k].status = 0;
+  }
+  std::vector<lsq_info> infos(rs.size());
+  lsq_status st = LSQ_OK;
+  std::string err;
+  if (e != cudaSuccess) {
+    st = LSQ_ERR_CUDA;
+    err = cudaGetErrorString(e);
+  } else {
+    st = lsq_batch_solve(slot.batch, (int)rs.size(), items.data(), infos.data());
+    if (st < 0) err = lsq_last_error();
+  }
+  // an error of the call itself (copies, launches) fails every item; an
+  // error of some items (non-finite data, zero column) only those
+  bool item_error = false;
+  for (const lsq_batch_item &q : items) item_error = item_error || q.status < 0;
+  const bool call_failed = st < 0 && !item_error;
+  for (size_t k = 0; k < rs.size(); k++) {
+    Request *r = rs[k];
+    const lsq_status sk = call_failed ? st : (lsq_status)items[k].status;
+    r->status = sk;
+    r->info = infos[k];
+    r->info.status = sk;
+    if (sk >= 0) {
+      r->x.resize(r->opt.n);
+      cudaError_t ex = cudaMemcpyAsync(r->x.data(), items[k].x, sizeof(double) * r->opt.n,
+                                       cudaMemcpyDeviceToHost, slot.s);
+      if (ex != cudaSuccess) {
+        r->status = LSQ_ERR_CUDA;
+        r->err = cudaGetErrorString(ex);
+      }
+    } else {
+      r->err = err.empty() ? "the item failed in its batch" : err;
+    }
+  }
+  e = cudaStreamSynchronize(slot.s);
+  if (e != cudaSuccess)
+    for (Request *r : rs)
+      if (r->status >= 0) {
+        r->status = LSQ_ERR_CUDA;
+        r->err = cudaGetErrorString(e);
+      }
+  return e == cudaSuccess;
+}
+
+int64_t plane_elems(const lsq_options &o) { return o.m * ((o.n + 3) / 4 * 4); }
+
+void batch_worker(lsq_server S, int idx) {
+  cudaSetDevice(S->dev);
+  lsq_server_s::Slot &slot = S->slots[idx];
+  for (;;) {
+    std::vector<Request *> rs;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      for (;;) {
+        if (S->stopping) return;
+        // first come, first served: take requests from the head while the
+        // batch, the worker's planes and the arena have room
+        int64_t elems = 0;
+        while (!S->queue.empty() && (int)rs.size() < S->max_batch) {
+          Request *r = S->queue.front();
+          if (elems + plane_elems(r->opt) > S->batch_elems) break;
+          if (!S->arena->alloc(r->bytes, &r->off)) break;
+          elems += plane_elems(r->opt);
+          rs.push_back(r);
+          S->queue.pop_front();
+          S->running++;
+        }
+        if (!rs.empty()) break;
+        S->cv.wait(lk);
+      }
+    }
+    const double t0 = now_s();
+    for (Request *r : rs) r->t_start = t0;
+    const bool drained = run_batch(S, slot, rs);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      const double t1 = now_s();
+      for (Request *r : rs) {
+        if (drained) S->arena->release(r->off, r->bytes);
+        r->t_end = t1;
+        r->done = true;
+        S->running--;
+        S->completed++;
+      }
+    }
+    S->cv.notify_all();
+  }
+}
+
 void worker(lsq_server S, int idx) {
   cudaSetDevice(S->dev);
   lsq_server_s::Slot &slot = S->slots[idx];
@@ -218,6 +336,7 @@ void destroy_server(lsq_server S) {
     if (sl.th.joinable()) sl.th.join();
   for (auto &sl : S->slots) {
     if (sl.plan) lsq_plan_destroy(sl.plan);
+    if (sl.batch) lsq_batch_destroy(sl.batch);
     if (sl.s) cudaStreamDestroy(sl.s);
   }
   for (auto &kv : S->reqs) delete kv.second;
@@ -278,6 +397,55 @@ lsq_status lsq_server_create(size_t arena_bytes, int max_slots, int64_t m_max, i
   return LSQ_OK;
 }
 
+lsq_status lsq_server_create_batched(size_t arena_bytes, int workers, int max_batch,
+                                     int64_t m_max, int64_t n_max, lsq_server *out) {
+  if (!out) {
+    set_last_error("out is NULL");
+    return LSQ_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (workers < 1 || workers > 8 || max_batch < 1 || max_batch > 256 || m_max < 1 ||
+      n_max < 1 || m_max < n_max || n_max > 256 || arena_bytes < kAlign) {
+    set_last_error("need 1 <= workers <= 8, 1 <= max_batch <= 256, m_max >= n_max >= 1, "
+                   "n_max <= 256");
+    return LSQ_ERR_INVALID;
+  }
+  lsq_server S = new lsq_server_s();
+  S->m_max = m_max;
+  S->n_max = n_max;
+  S->max_batch = max_batch;
+  // each worker's planes hold as many elements as the arena holds entries of A
+  S->batch_elems = std::max<int64_t>((int64_t)(arena_bytes / sizeof(double)),
+                                     m_max * ((n_max + 3) / 4 * 4));
+  cudaError_t e = cudaGetDevice(&S->dev);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&S->arena_base, arena_bytes);
+  if (e != cudaSuccess) {
+    const bool oom = (e == cudaErrorMemoryAllocation);
+    set_last_error(cudaGetErrorString(e));
+    destroy_server(S);
+    return oom ? LSQ_ERR_OOM : LSQ_ERR_CUDA;
+  }
+  S->arena = new Arena(arena_bytes);
+  S->slots.resize(workers);
+  for (int i = 0; i < workers; i++) {
+    e = cudaStreamCreateWithFlags(&S->slots[i].s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      set_last_error(cudaGetErrorString(e));
+      destroy_server(S);
+      return LSQ_ERR_CUDA;
+    }
+    lsq_status st = lsq_batch_create(max_batch, n_max, S->batch_elems, S->slots[i].s,
+                                     &S->slots[i].batch);
+    if (st < 0) {
+      destroy_server(S);
+      return st;
+    }
+  }
+  for (int i = 0; i < workers; i++) S->slots[i].th = std::thread(batch_worker, S, i);
+  *out = S;
+  return LSQ_OK;
+}
+
 lsq_status lsq_submit(lsq_server S, const lsq_options *opt, int method, const double *A,
                       const double *b, int on_device, uint64_t *ticket) {
   if (!S || !opt || !A || !b || !ticket) {
@@ -295,6 +463,14 @@ lsq_status lsq_submit(lsq_server S, const lsq_options *opt, int method, const do
     set_last_error("request outside the server's limits (m <= m_max, n <= n_max, lda = n, "
                    "zeta <= 8, d <= 12 n_max, FP64, one right-hand side)");
     return LSQ_ERR_INVALID;
+  }
+  if (S->max_batch > 0 && method == 2) {
+    set_last_error("a batched server takes FOSSILS (0) and SPIR (1) requests");
+    return LSQ_ERR_INVALID;
+  }
+  if (S->max_batch > 0 && plane_elems(*opt) > S->batch_elems) {
+    set_last_error("request larger than a batch worker's planes");
+    return LSQ_ERR_OOM;
   }
   Request *r = new Request();
   r->opt = *opt;

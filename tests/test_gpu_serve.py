@@ -111,3 +111,45 @@ def test_server_spir_and_host_buffers():
     lsq.lsq_server_destroy(srv)
     assert st == 0
     assert oracle.kw_relative(Ah, bh, x) <= 1e-13
+
+
+def test_batched_server_alone_equals_mix():
+    """The batched server (lsq_server_create_batched): a stream of uneven
+    requests, submitted together so that they share lockstep batches, gives
+    each request the answer it gets alone in a batch of one, within the
+    forward-error level; every answer is backward stable."""
+    from lsq_problems import problem_svd
+    shapes = [(20011, 32, 1e3), (41000, 64, 1e8), (15000, 128, 1e5), (60000, 256, 1e10),
+              (33000, 100, 1e12), (24000, 48, 1e2)]
+    Ps = [problem_svd(m, n, k, 1e-6, seed=900 + i, keep_factors=False)
+          for i, (m, n, k) in enumerate(shapes)]
+    dev = [(T(P["A"]), T(P["b"])) for P in Ps]
+    srv = lsq.lsq_server_create_batched(2 << 30, 2, 8, 80000, 256)
+    tickets = []
+    for i, (A, b) in enumerate(dev):
+        o = lsq.lsq_options_default(m=A.shape[0], n=A.shape[1], seed=5 + i)
+        tickets.append(lsq.lsq_submit(srv, o, i % 2, A, b, 1))
+    xs = {}
+    for i, t in enumerate(tickets):
+        x = np.empty(shapes[i][1])
+        while True:
+            st, info, lat = lsq.lsq_poll(srv, t, x)
+            if st != lsq.LSQ_PENDING:
+                break
+        assert st >= 0
+        xs[i] = x
+    # each alone
+    for i, (A, b) in enumerate(dev):
+        o = lsq.lsq_options_default(m=A.shape[0], n=A.shape[1], seed=5 + i)
+        t = lsq.lsq_submit(srv, o, i % 2, A, b, 1)
+        x = np.empty(shapes[i][1])
+        while True:
+            st, info, lat = lsq.lsq_poll(srv, t, x)
+            if st != lsq.LSQ_PENDING:
+                break
+        assert st >= 0
+        P = Ps[i]
+        wed = oracle.wedin_bound(shapes[i][2], 1.0, P["x_true"], 1e-6)
+        assert np.linalg.norm(x - xs[i]) <= 10 * max(wed, 1e-15) * np.linalg.norm(x), i
+        assert oracle.kw_relative(P["A"], P["b"], xs[i]) <= 1e-13, i
+    lsq.lsq_server_destroy(srv)
