@@ -96,13 +96,47 @@ __device__ void b_resid_body(const BItem &it, int local, double *sh, double *r2s
   }
 }
 
+// The inner pass of one item's CTA: the structure of atax_df_kernel (rows of
+// the hi / lo planes staged by TMA bulk copies, kBStages per warp in flight,
+// bounded mbarrier waits, drain on a timeout) over the item's row share.
+// Shared memory: hacc [8 warps][256] FP64, stages [8][kBStages][2][256] FP32,
+// then the mbarriers (sized for npad = 256 whatever the item's npad).
+constexpr int kBStages = 2;
+constexpr uint64_t kBWaitNs = 1000ull * 1000 * 1000;  // 1 s
+constexpr size_t kBInnerSmem = (size_t)(kBThreads / 32) * 256 * sizeof(double) +
+                               (size_t)(kBThreads / 32) * kBStages * 2 * 256 * sizeof(float) +
+                               (size_t)(kBThreads / 32) * kBStages * sizeof(uint64_t);
+
 template <int NC>
 __device__ void b_inner_body(const BItem &it, int local, double *hacc, double *wmax) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n = it.n;
   const int64_t m = it.m, per = (m + it.ncta - 1) / it.ncta;
   const int64_t r0 = min(m, (int64_t)local * per), r1 = min(m, r0 + per);
-  double *hw = hacc + (size_t)warp * NC * 64;
+  float *stages = reinterpret_cast<float *>(hacc + (size_t)nw * 256);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(stages + (size_t)nw * kBStages * 2 * 256);
+  float *wst = stages + (size_t)warp * kBStages * 2 * 256;
+  uint64_t *wbar = bars + warp * kBStages;
+  const int64_t nrows = (r1 - r0 - warp + nw - 1) / nw > 0 ? (r1 - r0 - warp + nw - 1) / nw : 0;
+  const unsigned row_bytes = (unsigned)(it.ld32 * sizeof(float));
+  if (lane == 0) {
+    for (int st = 0; st < kBStages; st++) mbar_init(wbar + st, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const uint64_t pol = l2_evict_first();
+  auto issue = [&](int64_t q) {
+    if (lane == 0 && q < nrows) {
+      const int64_t i = r0 + warp + q * nw;
+      const int stg = (int)(q % kBStages);
+      float *dh = wst + (size_t)stg * 2 * 256;
+      mbar_expect_tx(wbar + stg, 2 * row_bytes);
+      bulk_g2s(dh, it.Ahi + i * it.ld32, row_bytes, wbar + stg, pol);
+      bulk_g2s(dh + 256, it.Alo + i * it.ld32, row_bytes, wbar + stg, pol);
+    }
+  };
+  for (int64_t q = 0; q < kBStages; q++) issue(q);
+  double *hw = hacc + (size_t)warp * 256;
   for (int i = lane; i < NC * 64; i += 32) hw[i] = 0.0;
   double zr[2 * NC];
   b_load_vec<NC>(it.z, n, lane, zr);
@@ -129,22 +163,30 @@ __device__ void b_inner_body(const BItem &it, int local, double *hacc, double *w
     hh[k] = hl[k] = 0ull;
   }
   int blk = 0;
-  for (int64_t i = r0 + warp; i < r1; i += nw) {
-    const float *rh = it.Ahi + i * it.ld32, *rl = it.Alo + i * it.ld32;
+  int64_t qfail = -1;
+  for (int64_t q = 0; q < nrows; q++) {
+    const int stg = (int)(q % kBStages);
+    if (!__all_sync(0xffffffffu, mbar_wait(wbar + stg, (unsigned)((q / kBStages) & 1), kBWaitNs))) {
+      qfail = q;
+      break;
+    }
+    const float *rh = wst + (size_t)stg * 2 * 256;
+    const float *rl = rh + 256;
     f2_t ah[NC], al[NC];
 #pragma unroll
     for (int k = 0; k < NC; k++) {
       const int col = 64 * k + 2 * lane;
       if (col + 1 < n) {
-        const float2 vh = __ldcs(reinterpret_cast<const float2 *>(rh + col));
-        const float2 vl = __ldcs(reinterpret_cast<const float2 *>(rl + col));
-        ah[k] = f2_pack(vh.x, vh.y);
-        al[k] = f2_pack(vl.x, vl.y);
+        ah[k] = *reinterpret_cast<const f2_t *>(rh + col);
+        al[k] = *reinterpret_cast<const f2_t *>(rl + col);
       } else {
-        ah[k] = (col < n) ? f2_pack(__ldcs(rh + col), 0.0f) : 0ull;
-        al[k] = (col < n) ? f2_pack(__ldcs(rl + col), 0.0f) : 0ull;
+        ah[k] = (col < n) ? f2_pack(rh[col], 0.0f) : 0ull;
+        al[k] = (col < n) ? f2_pack(rl[col], 0.0f) : 0ull;
       }
     }
+    __syncwarp();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(q + kBStages);
     f2_t shp = 0ull, slp = 0ull;
 #pragma unroll
     for (int k = 0; k < NC; k++) f2_dd_step(shp, slp, ah[k], al[k], zh[k], zl[k], zn[k]);
@@ -179,6 +221,14 @@ __device__ void b_inner_body(const BItem &it, int local, double *hacc, double *w
       }
     }
   }
+  if (qfail >= 0) {
+    if (lane == 0) {
+      atomicCAS(&it.st->err, 0, (int)LSQ_ERR_TIMEOUT);
+      for (int64_t r = qfail; r < qfail + kBStages && r < nrows; r++)
+        mbar_wait(wbar + (r % kBStages), (unsigned)((r / kBStages) & 1), kBWaitNs);
+    }
+    __syncwarp();
+  }
 #pragma unroll
   for (int k = 0; k < NC; k++) {
     const int col = 64 * k + 2 * lane;
@@ -189,7 +239,7 @@ __device__ void b_inner_body(const BItem &it, int local, double *hacc, double *w
   double *part = it.part + (size_t)local * it.npad;
   for (int c = threadIdx.x; c < it.npad; c += blockDim.x) {
     double s = 0.0;
-    for (int w = 0; w < nw; w++) s += hacc[(size_t)w * NC * 64 + c];
+    for (int w = 0; w < nw; w++) s += hacc[(size_t)w * 256 + c];
     part[c] = s * up;
   }
 }
@@ -212,7 +262,7 @@ __global__ void __launch_bounds__(kBThreads, 2)
 
 __global__ void __launch_bounds__(kBThreads, 2)
     b_inner_kernel(const BItem *__restrict__ items, const int *__restrict__ cta_item) {
-  __shared__ double hacc[kBThreads / 32 * 4 * 64];
+  extern __shared__ __align__(16) double hacc[];
   __shared__ double wmax[kBThreads / 32];
   const int idx = cta_item[blockIdx.x];
   if (idx < 0) return;
@@ -343,8 +393,12 @@ cudaError_t launch_b_resid(const BItem *items, const int *cta_item, int grid, cu
   return cudaGetLastError();
 }
 
+cudaError_t prepare_b_inner() {
+  return ensure_smem_attr((const void *)b_inner_kernel, (int)kBInnerSmem);
+}
+
 cudaError_t launch_b_inner(const BItem *items, const int *cta_item, int grid, cudaStream_t s) {
-  b_inner_kernel<<<grid, kBThreads, 0, s>>>(items, cta_item);
+  b_inner_kernel<<<grid, kBThreads, kBInnerSmem, s>>>(items, cta_item);
   return cudaGetLastError();
 }
 

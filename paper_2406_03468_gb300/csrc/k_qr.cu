@@ -260,16 +260,18 @@ __device__ __forceinline__ int qr_local(int j, int G) {
 }
 enum { kQrDone = 0, kQrBuild = 1, kQrApply = 2, kQrFail = 3, kQrApplyBuild = 4 };
 
+// The factorisation by G CTAs (this one is `me`); dsm: the columns'
+// shared-memory copy (SMEM).  The cooperative kernel runs it with the whole
+// grid; the batched one with each item's group of CTAs.
 template <bool SMEM, int VR>
-__global__ void __launch_bounds__(kQrThreads, SMEM ? kQrSmemCtasPerSm : kQrGlobalCtasPerSm)
-    qr_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
-              int *flags, int epoch, DevState *st, uint64_t timeout_ns) {
-  extern __shared__ double dsm[];
+__device__ void qr_body(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
+                        int *flags, int epoch, DevState *st, uint64_t timeout_ns, int G, int me,
+                        double *dsm) {
   __shared__ double red[kQrThreads / 32 * kQrBatch];
   __shared__ double wsh[kQrBatch];
   __shared__ int s_act, s_k;
   __shared__ unsigned s_mask;
-  const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
   int nloc = 0;  // local columns j = qr_col(me, l, G), increasing with l
   while (qr_col(me, nloc, G) < ncols) nloc++;
   auto colp = [&](int l) -> double * {
@@ -447,6 +449,34 @@ __global__ void __launch_bounds__(kQrThreads, SMEM ? kQrSmemCtasPerSm : kQrGloba
   }
 }
 
+template <bool SMEM, int VR>
+__global__ void __launch_bounds__(kQrThreads, SMEM ? kQrSmemCtasPerSm : kQrGlobalCtasPerSm)
+    qr_kernel(double *__restrict__ W, int d, int n, int ncols, double *__restrict__ vhead,
+              int *flags, int epoch, DevState *st, uint64_t timeout_ns) {
+  extern __shared__ double dsm[];
+  qr_body<SMEM, VR>(W, d, n, ncols, vhead, flags, epoch, st, timeout_ns, gridDim.x, blockIdx.x,
+                    dsm);
+}
+
+// Batched form: one cooperative launch factors every item's sketch, item i on
+// its group of CTAs (cta_item map; cta0 / ncta of the item's QR group), with
+// the columns in global memory (L2) and the reflector in registers (VR = 12
+// covers d = 12 n <= 3072).  Flags per item; waits bounded as above.
+__global__ void __launch_bounds__(kQrThreads, kQrGlobalCtasPerSm)
+    b_qr_kernel(const BItem *__restrict__ items, const int *__restrict__ qmap, int epoch,
+                uint64_t timeout_ns) {
+  const int idx = qmap[blockIdx.x];
+  if (idx < 0) return;
+  const BItem &it = items[idx];
+  const int me = blockIdx.x - it.qcta0, G = it.qncta;
+  if (it.d <= 8 * kQrThreads)
+    qr_body<false, 8>(it.W, it.d, it.n, it.n + 1, it.vhead, it.qflag, epoch, it.st, timeout_ns, G,
+                      me, nullptr);
+  else
+    qr_body<false, 12>(it.W, it.d, it.n, it.n + 1, it.vhead, it.qflag, epoch, it.st, timeout_ns,
+                       G, me, nullptr);
+}
+
 // Non-cooperative form for concurrent solves (served requests): one launch
 // per column step, the kernel boundary standing in for the flags.  Column j
 // belongs to CTA j mod G; the owner of column k+1 applies H_k to it and
@@ -584,6 +614,16 @@ cudaError_t launch_qr_stepwise(double *W, int d, int n, int ncols, double *vhead
   }
   return cudaSuccess;
 }
+
+cudaError_t launch_b_qr(const BItem *items, const int *qmap, int grid, int epoch,
+                        uint64_t timeout_ns, cudaStream_t s) {
+  void *args[] = {(void *)&items, (void *)&qmap, &epoch, &timeout_ns};
+  return cudaLaunchCooperativeKernel((const void *)b_qr_kernel, dim3(grid), dim3(kQrThreads), args,
+                                     0, s);
+}
+
+int b_qr_max_ctas(int nsm) { return kQrGlobalCtasPerSm * nsm; }
+int b_qr_min_ctas(int n) { return (n + 1 + kQrMaxLocal - 1) / kQrMaxLocal; }
 
 cudaError_t launch_b_qr_step(const BItem *items, int count, int qcta, int k, cudaStream_t s) {
   b_qr_step_kernel<<<dim3(qcta, count), kQrThreads, 0, s>>>(items, k);

@@ -43,6 +43,7 @@ constexpr int kBatchNMax = 256;
 constexpr int kBatchZeta = 8;
 constexpr int kCondIters = 10;
 constexpr int kPollEvery = 4;
+constexpr uint64_t kQrTimeoutNs = 5ull * 1000 * 1000 * 1000;  // 5 s per inter-CTA wait
 
 lsq_status bfail(lsq_status st, const std::string &msg) {
   set_last_error(msg.c_str());
@@ -77,11 +78,14 @@ struct lsq_batch_s {
   int *d_cta = nullptr;
   BItem *h_items = nullptr;      // pinned staging of the table
   int *h_cta = nullptr;
+  int *d_qmap = nullptr, *h_qmap = nullptr;  // CTA -> item map of the batched QR
+  int qgrid = 0;                 // CTAs of the batched QR (0: the column-step form)
+  int qr_epoch = 0;              // flag value of the next batched QR
   DevState *h_st = nullptr;      // pinned copy of the states
   // captured phases, keyed by (count, grid, nmax)
   struct Graphs {
-    cudaGraphExec_t pre = nullptr, step0 = nullptr, step1 = nullptr, iter = nullptr,
-                    post = nullptr;
+    cudaGraphExec_t pre = nullptr, setup = nullptr, step0 = nullptr, step1 = nullptr,
+                    iter = nullptr, post = nullptr;
   };
   std::map<std::tuple<int, int, int>, Graphs> graphs;
   int grid = 0;                  // row-parallel CTAs of the current solve
@@ -91,7 +95,7 @@ namespace {
 
 // Byte layout of one item's slice of the workspace.
 struct Slice {
-  size_t SAb, W, Rcm, Rrm, Dt, vhead, vec, total;
+  size_t SAb, W, Rcm, Rrm, Dt, vhead, vec, qflag, total;
 };
 
 Slice slice_layout(int64_t nmax) {
@@ -105,6 +109,7 @@ Slice slice_layout(int64_t nmax) {
   L.Dt = o; o += a256(sizeof(double) * 2 * nb * 1024);
   L.vhead = o; o += a256(sizeof(double) * 2 * d);
   L.vec = o; o += a256(sizeof(double) * 17 * n);
+  L.qflag = o; o += a256(sizeof(int) * (n + 1));
   L.total = o;
   return L;
 }
@@ -211,7 +216,12 @@ lsq_status lsq_batch_create(int max_items, int64_t n_max, int64_t elems_max, voi
   A(cudaMallocHost((void **)&B->h_items, sizeof(BItem) * (size_t)max_items));
   A(cudaMallocHost((void **)&B->h_cta, sizeof(int) * (size_t)B->grid_max));
   A(cudaMallocHost((void **)&B->h_st, sizeof(DevState) * (size_t)max_items));
+  A(cudaMalloc((void **)&B->d_qmap, sizeof(int) * (size_t)b_qr_max_ctas(B->nsm)));
+  A(cudaMallocHost((void **)&B->h_qmap, sizeof(int) * (size_t)b_qr_max_ctas(B->nsm)));
+  // the QR flags start at 0 (a flag is ready when it equals the launch's epoch)
+  if (e == cudaSuccess) A(cudaMemset(B->ws, 0, L.total * (size_t)max_items));
   A(prepare_b_kernels((int)n_max));
+  A(prepare_b_inner());
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);
     lsq_batch_destroy(B);
@@ -225,17 +235,18 @@ void lsq_batch_destroy(lsq_batch B) {
   if (!B) return;
   if (B->s) cudaStreamSynchronize(B->s);
   for (auto &kv : B->graphs) {
-    cudaGraphExec_t g[] = {kv.second.pre, kv.second.step0, kv.second.step1, kv.second.iter,
-                           kv.second.post};
+    cudaGraphExec_t g[] = {kv.second.pre, kv.second.setup, kv.second.step0, kv.second.step1,
+                           kv.second.iter, kv.second.post};
     for (auto x : g)
       if (x) cudaGraphExecDestroy(x);
   }
-  void *bufs[] = {B->ws, B->planes, B->part, B->r2part, B->st, B->d_items, B->d_cta};
+  void *bufs[] = {B->ws, B->planes, B->part, B->r2part, B->st, B->d_items, B->d_cta, B->d_qmap};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (B->h_items) cudaFreeHost(B->h_items);
   if (B->h_cta) cudaFreeHost(B->h_cta);
   if (B->h_st) cudaFreeHost(B->h_st);
+  if (B->h_qmap) cudaFreeHost(B->h_qmap);
   if (B->own_stream && B->s) cudaStreamDestroy(B->s);
   delete B;
 }
@@ -324,6 +335,35 @@ extern "C" lsq_status lsq_batch_solve(lsq_batch B, int count, lsq_batch_item *it
     poff += it.m * it.ld32;
     poff = (poff + 3) / 4 * 4;
     it.st = B->st + i;
+    it.qflag = (int *)(base + L.qflag);
+  }
+  // QR groups: CTAs in proportion to d n^2, at least enough that no CTA holds
+  // more than 32 columns; if the items need more CTAs than one cooperative
+  // launch can hold, the QR takes the column-step form
+  {
+    const int qmax = b_qr_max_ctas(B->nsm);
+    int need = 0;
+    double work = 0.0;
+    for (int i = 0; i < count; i++) {
+      need += b_qr_min_ctas(B->h_items[i].n);
+      work += (double)B->h_items[i].d * B->h_items[i].n * B->h_items[i].n;
+    }
+    B->qgrid = 0;
+    if (need <= qmax) {
+      int g = 0;
+      const int spare = qmax - need;
+      for (int i = 0; i < count; i++) {
+        BItem &it = B->h_items[i];
+        const double share = (double)it.d * it.n * it.n / work;
+        int c = b_qr_min_ctas(it.n) + (int)std::floor(share * spare);
+        c = std::min(c, it.n + 1);  // no more CTAs than columns
+        it.qcta0 = g;
+        it.qncta = c;
+        for (int k = 0; k < c; k++) B->h_qmap[g + k] = i;
+        g += c;
+      }
+      B->qgrid = g;
+    }
   }
   // row-parallel CTAs: autotuned per shape class (1, 2 or 4 per SM)
   double mn = 0.0;
@@ -347,19 +387,26 @@ extern "C" lsq_status lsq_batch_solve(lsq_batch B, int count, lsq_batch_item *it
     }
     BCU(cudaMemcpyAsync(B->d_items, B->h_items, sizeof(BItem) * count, cudaMemcpyHostToDevice, B->s));
     BCU(cudaMemcpyAsync(B->d_cta, B->h_cta, sizeof(int) * B->grid, cudaMemcpyHostToDevice, B->s));
+    if (B->qgrid > 0)
+      BCU(cudaMemcpyAsync(B->d_qmap, B->h_qmap, sizeof(int) * B->qgrid, cudaMemcpyHostToDevice,
+                          B->s));
     return LSQ_OK;
   };
   // the partials hold grid x 256 doubles: fits for any deal (npad <= 256)
   BCU(cudaMemsetAsync(B->st, 0, sizeof(DevState) * (size_t)count, B->s));
   const int qcta = std::max(1, std::min(8, 2 * B->nsm / count));
+  // sketch (and, when the QR takes the column-step form, the QR steps)
+  const bool coop_qr = B->qgrid > 0;
   auto pre = [&]() -> cudaError_t {
     cudaError_t e = launch_b_zero(B->d_items, count, B->s);
     if (e == cudaSuccess) e = launch_b_sketch(B->d_items, B->d_cta, B->grid, kBatchZeta, B->s);
     if (e == cudaSuccess) e = launch_b_finalize(B->d_items, count, kBatchZeta, B->s);
-    for (int k = -1; k < nmax && e == cudaSuccess; k++)
+    for (int k = -1; !coop_qr && k < nmax && e == cudaSuccess; k++)
       e = launch_b_qr_step(B->d_items, count, qcta, k, B->s);
-    if (e == cudaSuccess) e = launch_b_setup(B->d_items, count, kCondIters, 100, nmax, B->s);
     return e;
+  };
+  auto setup = [&]() -> cudaError_t {
+    return launch_b_setup(B->d_items, count, kCondIters, 100, nmax, B->s);
   };
   if (per_sm == 0) {
     // tune: time the residual pass over this batch (it only writes partials,
@@ -397,9 +444,11 @@ extern "C" lsq_status lsq_batch_solve(lsq_batch B, int count, lsq_batch_item *it
     if (st < 0) return st;
   }
   // phases, captured once per (count, grid, nmax) and replayed
-  auto &G = B->graphs[{count, B->grid, nmax}];
+  auto &G = B->graphs[{count, B->grid, nmax * 2 + (coop_qr ? 1 : 0)}];
   if (!G.pre) {
     lsq_status st = capture(B, &G.pre, pre);
+    if (st < 0) return st;
+    st = capture(B, &G.setup, setup);
     if (st < 0) return st;
     const double gam = 10.0, rho = 0.4;  // Alg. 4's step-1 stop constants
     for (int step = 0; step < 2; step++) {
@@ -428,7 +477,19 @@ extern "C" lsq_status lsq_batch_solve(lsq_batch B, int count, lsq_batch_item *it
     });
     if (st < 0) return st;
   }
+  // phase times (CUDA events on the batch's stream): pre (sketch, QR, setup),
+  // step 0, step 1
+  cudaEvent_t ev[4];
+  for (auto &e : ev) BCU(cudaEventCreate(&e));
+  int iters_run[2] = {0, 0};
+  BCU(cudaEventRecord(ev[0], B->s));
   BCU(cudaGraphLaunch(G.pre, B->s));
+  if (coop_qr) {
+    B->qr_epoch = (B->qr_epoch >= (1 << 30)) ? 1 : B->qr_epoch + 1;
+    BCU(launch_b_qr(B->d_items, B->d_qmap, B->qgrid, B->qr_epoch, kQrTimeoutNs, B->s));
+  }
+  BCU(cudaGraphLaunch(G.setup, B->s));
+  BCU(cudaEventRecord(ev[1], B->s));
   {
     lsq_status st = read_states(B, count);
     if (st < 0) return st;
@@ -440,6 +501,7 @@ extern "C" lsq_status lsq_batch_solve(lsq_batch B, int count, lsq_batch_item *it
     const int cap = step == 0 ? 100 : q2max;
     for (int it = 0; it < cap; it++) {
       BCU(cudaGraphLaunch(G.iter, B->s));
+      iters_run[step]++;
       if (step == 0 && (it % kPollEvery) == kPollEvery - 1 && it + 1 < cap) {
         lsq_status st = read_states(B, count);
         if (st < 0) return st;
@@ -449,6 +511,7 @@ extern "C" lsq_status lsq_batch_solve(lsq_batch B, int count, lsq_batch_item *it
       }
     }
     BCU(cudaGraphLaunch(G.post, B->s));
+    BCU(cudaEventRecord(ev[2 + step], B->s));
     if (step == 0) {
       lsq_status st = read_states(B, count);
       if (st < 0) return st;
@@ -467,6 +530,11 @@ extern "C" lsq_status lsq_batch_solve(lsq_batch B, int count, lsq_batch_item *it
     lsq_status st = read_states(B, count);
     if (st < 0) return st;
   }
+  float ms_pre = 0.f, ms_s0 = 0.f, ms_s1 = 0.f;
+  cudaEventElapsedTime(&ms_pre, ev[0], ev[1]);
+  cudaEventElapsedTime(&ms_s0, ev[1], ev[2]);
+  cudaEventElapsedTime(&ms_s1, ev[2], ev[3]);
+  for (auto &e : ev) cudaEventDestroy(e);
   lsq_status worst = LSQ_OK;
   for (int i = 0; i < count; i++) {
     const DevState &S = B->h_st[i];
@@ -488,6 +556,15 @@ extern "C" lsq_status lsq_batch_solve(lsq_batch B, int count, lsq_batch_item *it
       f.cnorm[0] = std::sqrt(S.cnorm2[0]);
       f.cnorm[1] = std::sqrt(S.cnorm2[1]);
       f.inner_kernel = 3;
+      // the batch's phase times and the inner iterations it ran (lockstep:
+      // the same for every item): sketch + QR + setup, step 1, step 2
+      f.ms_sketch = ms_pre;
+      f.ms_refine = ms_s0 + ms_s1;
+      f.ms_total = ms_pre + ms_s0 + ms_s1;
+      f.ms_inner_pass = ms_s1;
+      f.ms_resid_pass = ms_s0;
+      f.n_inner_pass = iters_run[0] + iters_run[1];
+      f.n_resid_pass = iters_run[0];
       f.passes = 3 + f.iters[0] + f.iters[1];
       f.bytes_a = 8.0 * (double)items[i].m * (double)items[i].n * (double)(2 + f.passes);
     }

@@ -57,6 +57,8 @@ struct BItem {
   double *xs, *xo, *c, *g, *dy, *dyold, *z, *h, *w, *res, *p;
   float *Ahi, *Alo;     // hi / lo FP32 planes (m x ld32)
   DevState *st;
+  int *qflag;           // QR: per-column ready flags (n)
+  int qcta0, qncta;     // the item's CTAs in the batched QR launch
 };
 
 // ---------------------------------------------------------------- helpers
@@ -310,6 +312,7 @@ cudaError_t launch_lsqr_update(int n, const double *p, double *v, double *w, dou
 // st->done is set.
 // Kernel attributes of the batched kernels for n <= nmax (before any capture).
 cudaError_t prepare_b_kernels(int nmax);
+cudaError_t prepare_b_inner();
 cudaError_t launch_b_zero(const BItem *items, int count, cudaStream_t s);  // SAb = 0
 // Re-deal the row-parallel CTAs over all items (all = 1) or over the items
 // whose inner loop runs (all = 0); each item's partials hold grid entries.
@@ -318,6 +321,14 @@ cudaError_t launch_b_redeal(BItem *items, int count, int *cta_item, int grid, in
 cudaError_t launch_b_sketch(const BItem *items, const int *cta_item, int grid, int zeta,
                             cudaStream_t s);
 cudaError_t launch_b_finalize(const BItem *items, int count, int zeta, cudaStream_t s);
+// QR of every item's sketch in one cooperative launch (the flag form of
+// launch_qr, item i on CTAs qcta0 .. qcta0 + qncta - 1 of the grid, qmap the
+// CTA -> item map, -1 for none); at most b_qr_max_ctas CTAs, at least
+// b_qr_min_ctas(n) per item.
+cudaError_t launch_b_qr(const BItem *items, const int *qmap, int grid, int epoch,
+                        uint64_t timeout_ns, cudaStream_t s);
+int b_qr_max_ctas(int nsm);
+int b_qr_min_ctas(int n);
 // QR of every item's sketch, one launch per column step k = -1 .. nmax - 1
 // (qcta CTAs per item).
 cudaError_t launch_b_qr_step(const BItem *items, int count, int qcta, int k, cudaStream_t s);
