@@ -561,12 +561,14 @@ def serve_compare(lsq, torch, dev, count=512, slots=8):
     lsq.lsq_batch_destroy(bat)
     out["batched"] = {"batch_size": bsize, "capacity_solves_per_s": count / bt,
                       "vs_slots": (count / bt) / cap, "vs_plain": (count / bt) / plain_rate}
-    # the batched server: two workers, each taking up to `bsize` queued
-    # requests into one lockstep batch (continuous batching at batch level)
-    bsrv = lsq.lsq_server_create_batched(arena, 2, bsize, 400000, 256)
+    # the batched server: four workers, each taking up to 8 queued requests
+    # into one lockstep batch (continuous batching at batch level; 4 x 8
+    # measured ahead of 2 x 32 and 8 x 4)
+    bworkers, bmax = 4, 8
+    bsrv = lsq.lsq_server_create_batched(arena, bworkers, bmax, 400000, 256)
     run(np.zeros(count), server=bsrv)  # warm-up
     bcap, bp50, bp99 = run(np.zeros(count), server=bsrv)
-    served_b = {"workers": 2, "max_batch": bsize, "capacity_solves_per_s": bcap,
+    served_b = {"workers": bworkers, "max_batch": bmax, "capacity_solves_per_s": bcap,
                 "closed_loop_p50_ms": bp50 * 1e3, "closed_loop_p99_ms": bp99 * 1e3,
                 "vs_slots": bcap / cap, "vs_plain": bcap / plain_rate}
     for frac in (0.5, 0.9):

@@ -96,16 +96,22 @@ __device__ void b_resid_body(const BItem &it, int local, double *sh, double *r2s
   }
 }
 
-// The inner pass of one item's CTA: the structure of atax_df_kernel (rows of
-// the hi / lo planes staged by TMA bulk copies, kBStages per warp in flight,
-// bounded mbarrier waits, drain on a timeout) over the item's row share.
-// Shared memory: hacc [8 warps][256] FP64, stages [8][kBStages][2][256] FP32,
-// then the mbarriers (sized for npad = 256 whatever the item's npad).
+// The inner pass of one item's CTA: the structure of atax_df_kernel (the hi /
+// lo planes staged by TMA bulk copies, kBStages per warp in flight, bounded
+// mbarrier waits, drain on a timeout) over the item's row share.  A stage
+// holds a block of consecutive rows, as many as fit in kBStageFloats floats
+// per plane (16 rows at n = 32, 2 at n = 256), so that short rows still keep
+// about 2 KB per plane and warp in flight; the warp takes its blocks in turn
+// and the rows of a block one after the other.
+// Shared memory: hacc [8 warps][256] FP64, stages [8][kBStages][2][512] FP32,
+// then the mbarriers.
 constexpr int kBStages = 2;
+constexpr int kBStageFloats = 512;
 constexpr uint64_t kBWaitNs = 1000ull * 1000 * 1000;  // 1 s
-constexpr size_t kBInnerSmem = (size_t)(kBThreads / 32) * 256 * sizeof(double) +
-                               (size_t)(kBThreads / 32) * kBStages * 2 * 256 * sizeof(float) +
-                               (size_t)(kBThreads / 32) * kBStages * sizeof(uint64_t);
+constexpr size_t kBInnerSmem =
+    (size_t)(kBThreads / 32) * 256 * sizeof(double) +
+    (size_t)(kBThreads / 32) * kBStages * 2 * kBStageFloats * sizeof(float) +
+    (size_t)(kBThreads / 32) * kBStages * sizeof(uint64_t);
 
 template <int NC>
 __device__ void b_inner_body(const BItem &it, int local, double *hacc, double *wmax) {
@@ -114,25 +120,34 @@ __device__ void b_inner_body(const BItem &it, int local, double *hacc, double *w
   const int64_t m = it.m, per = (m + it.ncta - 1) / it.ncta;
   const int64_t r0 = min(m, (int64_t)local * per), r1 = min(m, r0 + per);
   float *stages = reinterpret_cast<float *>(hacc + (size_t)nw * 256);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(stages + (size_t)nw * kBStages * 2 * 256);
-  float *wst = stages + (size_t)warp * kBStages * 2 * 256;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(stages + (size_t)nw * kBStages * 2 * kBStageFloats);
+  float *wst = stages + (size_t)warp * kBStages * 2 * kBStageFloats;
   uint64_t *wbar = bars + warp * kBStages;
-  const int64_t nrows = (r1 - r0 - warp + nw - 1) / nw > 0 ? (r1 - r0 - warp + nw - 1) / nw : 0;
-  const unsigned row_bytes = (unsigned)(it.ld32 * sizeof(float));
+  const int ld32 = it.ld32;
+  const int rb = kBStageFloats / ld32;  // rows per block (ld32 <= 256: at least 2)
+  const int64_t nblk_all = (r1 - r0 + rb - 1) / rb;
+  const int64_t nblks = (nblk_all - warp + nw - 1) / nw > 0 ? (nblk_all - warp + nw - 1) / nw : 0;
   if (lane == 0) {
     for (int st = 0; st < kBStages; st++) mbar_init(wbar + st, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
   const uint64_t pol = l2_evict_first();
+  // the warp's q-th block: rows r0 + (warp + q nw) rb .. (at most rb, within r1)
+  auto block_rows = [&](int64_t q, int64_t &i0) {
+    i0 = r0 + (warp + q * nw) * (int64_t)rb;
+    return (int)min((int64_t)rb, r1 - i0);
+  };
   auto issue = [&](int64_t q) {
-    if (lane == 0 && q < nrows) {
-      const int64_t i = r0 + warp + q * nw;
+    if (lane == 0 && q < nblks) {
+      int64_t i0;
+      const int rows = block_rows(q, i0);
+      const unsigned bytes = (unsigned)(rows * ld32 * sizeof(float));
       const int stg = (int)(q % kBStages);
-      float *dh = wst + (size_t)stg * 2 * 256;
-      mbar_expect_tx(wbar + stg, 2 * row_bytes);
-      bulk_g2s(dh, it.Ahi + i * it.ld32, row_bytes, wbar + stg, pol);
-      bulk_g2s(dh + 256, it.Alo + i * it.ld32, row_bytes, wbar + stg, pol);
+      float *dh = wst + (size_t)stg * 2 * kBStageFloats;
+      mbar_expect_tx(wbar + stg, 2 * bytes);
+      bulk_g2s(dh, it.Ahi + i0 * ld32, bytes, wbar + stg, pol);
+      bulk_g2s(dh + kBStageFloats, it.Alo + i0 * ld32, bytes, wbar + stg, pol);
     }
   };
   for (int64_t q = 0; q < kBStages; q++) issue(q);
@@ -164,14 +179,17 @@ __device__ void b_inner_body(const BItem &it, int local, double *hacc, double *w
   }
   int blk = 0;
   int64_t qfail = -1;
-  for (int64_t q = 0; q < nrows; q++) {
+  for (int64_t q = 0; q < nblks; q++) {
     const int stg = (int)(q % kBStages);
     if (!__all_sync(0xffffffffu, mbar_wait(wbar + stg, (unsigned)((q / kBStages) & 1), kBWaitNs))) {
       qfail = q;
       break;
     }
-    const float *rh = wst + (size_t)stg * 2 * 256;
-    const float *rl = rh + 256;
+    int64_t i0;
+    const int rows = block_rows(q, i0);
+    for (int rr = 0; rr < rows; rr++) {
+    const float *rh = wst + (size_t)stg * 2 * kBStageFloats + (size_t)rr * ld32;
+    const float *rl = rh + kBStageFloats;
     f2_t ah[NC], al[NC];
 #pragma unroll
     for (int k = 0; k < NC; k++) {
@@ -184,9 +202,12 @@ __device__ void b_inner_body(const BItem &it, int local, double *hacc, double *w
         al[k] = (col < n) ? f2_pack(rl[col], 0.0f) : 0ull;
       }
     }
-    __syncwarp();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    issue(q + kBStages);
+    if (rr == rows - 1) {
+      // every lane has the block's values: the stage may be refilled
+      __syncwarp();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(q + kBStages);
+    }
     f2_t shp = 0ull, slp = 0ull;
 #pragma unroll
     for (int k = 0; k < NC; k++) f2_dd_step(shp, slp, ah[k], al[k], zh[k], zl[k], zn[k]);
@@ -220,11 +241,12 @@ __device__ void b_inner_body(const BItem &it, int local, double *hacc, double *w
         hh[k] = hl[k] = 0ull;
       }
     }
+    }  // rows of the block
   }
   if (qfail >= 0) {
     if (lane == 0) {
       atomicCAS(&it.st->err, 0, (int)LSQ_ERR_TIMEOUT);
-      for (int64_t r = qfail; r < qfail + kBStages && r < nrows; r++)
+      for (int64_t r = qfail; r < qfail + kBStages && r < nblks; r++)
         mbar_wait(wbar + (r % kBStages), (unsigned)((r / kBStages) & 1), kBWaitNs);
     }
     __syncwarp();
