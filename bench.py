@@ -702,6 +702,20 @@ def run_ours(args):
                                         pk_kind, None)}
     x_strict = x64.cpu().numpy().copy()
 
+    # Alg. 4's step-2 test (sketched KW estimate every five updates) in place
+    # of Theorem 7.1's count, on the same problem
+    plankw = lsq.Plan(M, N, seed=SKETCH_SEED, timing=1, kw_stop=1)
+    xkw = torch.empty_like(x)
+    lsq.lsq_solve_fossils(plankw.handle, A, b, xkw)
+    mskw, infoskw = timed_solves(lsq, torch, plankw, A, b, xkw, 2)
+    plankw.close()
+    kwstop = {"solves_per_s": len(infoskw) / (mskw / 1e3), "iters": infoskw[-1]["iters"],
+              "be_sketch_rel": infoskw[-1]["be_sketch_est"] / N ** 0.5,
+              "note": "step 2 ends when the sketched KW estimate (checked after updates 1, 6, "
+                      "11, ...) is below u ||A D^-1||_F; each check is one FP64 pass and a QR "
+                      "of the 2n x n matrix [R; sqrt(lam) I]"}
+    x_kw = xkw.cpu().numpy().copy()
+
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
     if not args.no_e2e:
@@ -760,7 +774,8 @@ def run_ours(args):
                     "spir": check_x(P["A"], P["b"], x_spir, x_qr, R_A, condest=cond),
                     "spir_lsqr": check_x(P["A"], P["b"], x_lsqr, x_qr, R_A, condest=cond),
                     "fossils_strict_fp64": check_x(P["A"], P["b"], x_strict, x_qr, R_A,
-                                                   condest=cond)}
+                                                   condest=cond),
+                    "fossils_kw_stop": check_x(P["A"], P["b"], x_kw, x_qr, R_A, condest=cond)}
         if e2e is not None:
             accuracy["fossils_host_entry"] = check_x(P["A"], P["b"], x_host, x_qr, R_A,
                                                      condest=cond)
@@ -804,6 +819,7 @@ def run_ours(args):
                                   "spir_lsqr_solves_per_s": lsqr_rate,
                                   "spir_lsqr_iters": lq_infos[-1]["iters"],
                                   "strict_fp64_inner": strict,
+                                  "kw_stop_step2": kwstop,
                                   "fp32_tier_1e6x1000": tier,
                                   "multi_rhs_2e6x200_k64": multi,
                                   "served_stream": served}),

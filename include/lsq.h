@@ -93,7 +93,15 @@ typedef struct {
                             returns LSQ_ERR_TIMEOUT and the plan stays usable.  The
                             other device waits (TMA copies, cluster transfers) keep
                             their own limits, so no copy can outlive its CTA */
-  int32_t reserved[5];
+  int32_t kw_stop;       /* 1: end the second refinement step with Alg. 4's test: after
+                            inner updates 1, 6, 11, ... the sketched Karlson-Walden
+                            estimate of the iterate's backward error (eq. (sketched-kw),
+                            theta = ||A D^-1||_F / ||b||) is compared with
+                            u ||A D^-1||_F, and the step stops below it (at most
+                            max_inner updates); 0 (default): Theorem 7.1's q0 - 1
+                            updates.  Each test costs one FP64 pass over A and a QR of
+                            a 2n x n matrix */
+  int32_t reserved[4];
 } lsq_options;
 
 #define LSQ_MAX_N 1024
@@ -125,7 +133,8 @@ typedef struct {
                                      pass for many right-hand sides that applies each
                                      row block of A to all k vectors (A read once) */
   double bytes_a;                 /* bytes of A (and its FP32 copy) streamed by the solve */
-  int32_t reserved[2];
+  double be_sketch_est;           /* kw_stop: the last sketched Karlson-Walden estimate
+                                     (absolute; divide by ||A D^-1||_F), else 0 */
 } lsq_info;
 
 /* Fill *o with the defaults listed above (m, n, lda left 0). */
@@ -260,6 +269,21 @@ lsq_status lsq_apply_normal(lsq_plan plan, const double *dA, const double *dz, d
  * n x k column-major (vector c at offset c n), device.  No scaling is
  * applied.  Errors: LSQ_ERR_INVALID (NULL argument, nrhs = 0 plan). */
 lsq_status lsq_apply_normal_multi(lsq_plan plan, const double *dA, const double *dZ, double *dH);
+
+/* The sketched Karlson-Walden estimate (Sec. 4.1, eq. (sketched-kw)) of the
+ * backward error of x (dx: n, device, original column scaling) on the
+ * column-scaled problem of the plan's last sketch, with theta =
+ * ||A D^-1||_F / ||b|| (Sec. 4.2): theta / sqrt(1 + theta^2 ||x_s||^2) *
+ * || ((SA)^T SA + lam I)^{-1/2} (A D^-1)^T (b - A x) ||, lam = theta^2
+ * ||b - A x||^2 / (1 + theta^2 ||x_s||^2), x_s = D x.  Alg. 4 evaluates it
+ * through the SVD of SA; here (SA)^T SA = R^T R and the norm is
+ * ||R_lam^{-T} g|| with R_lam the R factor of [R; sqrt(lam) I] (Householder
+ * QR of that 2n x n matrix): the same quantity.  The residual is FP64.
+ * *est: host double, absolute (divide by ||A D^-1||_F, sqrt(n) with column
+ * scaling, for the relative value).  Needs lsq_sketch (or a solve) on dA.
+ * Errors: LSQ_ERR_INVALID (NULL argument, no sketch). */
+lsq_status lsq_sketched_kw(lsq_plan plan, const double *dA, const double *db, const double *dx,
+                           double *est);
 
 /* One fused streaming pass over A: dg = A^T (db - A dx) and *r2 = ||b - A x||^2
  * (Alg. 1, the refinement right-hand side before the R^{-T} solve).  r2 is a

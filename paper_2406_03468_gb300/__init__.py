@@ -18,7 +18,7 @@ __all__ = [
     "lsq_solve_spir_lsqr", "lsq_solve_host",
     "lsq_solve_fossils_multi",
     "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_sketch_raw", "lsq_get_R", "lsq_apply_normal",
-    "lsq_apply_normal_multi", "lsq_residual",
+    "lsq_apply_normal_multi", "lsq_residual", "lsq_sketched_kw",
     "lsq_trsv", "lsq_apply_normal_noalloc", "lsq_last_error", "Plan", "lsq_server_create",
     "lsq_submit", "lsq_poll", "lsq_server_stats", "lsq_server_destroy", "library_path", "EXPORTED",
     "LsqBatchItem", "lsq_batch_create", "lsq_batch_solve", "lsq_batch_destroy",
@@ -52,7 +52,8 @@ class LsqOptions(ctypes.Structure):
                 ("stop_gamma", ctypes.c_double), ("stop_rho", ctypes.c_double),
                 ("fixed_inner", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("inner_fp64_fma", ctypes.c_int32), ("nrhs", ctypes.c_int32),
-                ("qr_wait_us", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("qr_wait_us", ctypes.c_int32), ("kw_stop", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class LsqInfo(ctypes.Structure):
@@ -66,7 +67,7 @@ class LsqInfo(ctypes.Structure):
                 ("n_inner_pass", ctypes.c_int32), ("ms_inner_pass", ctypes.c_float),
                 ("n_resid_pass", ctypes.c_int32), ("ms_resid_pass", ctypes.c_float),
                 ("ms_sketch_pass", ctypes.c_float), ("inner_kernel", ctypes.c_int32),
-                ("bytes_a", ctypes.c_double), ("reserved", ctypes.c_int32 * 2)]
+                ("bytes_a", ctypes.c_double), ("be_sketch_est", ctypes.c_double)]
 
     def as_dict(self):
         k = self.refine_steps
@@ -78,7 +79,8 @@ class LsqInfo(ctypes.Structure):
                 "launches": self.launches, "n_inner_pass": self.n_inner_pass,
                 "ms_inner_pass": self.ms_inner_pass, "n_resid_pass": self.n_resid_pass,
                 "ms_resid_pass": self.ms_resid_pass, "ms_sketch_pass": self.ms_sketch_pass,
-                "inner_kernel": self.inner_kernel, "bytes_a": self.bytes_a}
+                "inner_kernel": self.inner_kernel, "bytes_a": self.bytes_a,
+                "be_sketch_est": self.be_sketch_est}
 
 
 class LsqBatchItem(ctypes.Structure):
@@ -110,6 +112,7 @@ EXPORTED = {
     "lsq_apply_normal": (_i32, [_vp, _vp, _vp, _vp]),
     "lsq_apply_normal_multi": (_i32, [_vp, _vp, _vp, _vp]),
     "lsq_residual": (_i32, [_vp, _vp, _vp, _vp, _vp, _dp]),
+    "lsq_sketched_kw": (_i32, [_vp, _vp, _vp, _vp, _dp]),
     "lsq_trsv": (_i32, [_vp, _i32, _vp, _vp]),
     "lsq_apply_normal_noalloc": (_i32, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                         _vp, _vp, _vp]),
@@ -261,6 +264,13 @@ def lsq_apply_normal(plan, A, z, h):
 def lsq_apply_normal_multi(plan, A, Z, H):
     """H = A^T (A Z) for the plan's nrhs vectors (Z, H: n x k column-major)."""
     return _check(_lib().lsq_apply_normal_multi(plan, _ptr(A), _ptr(Z), _ptr(H)))
+
+
+def lsq_sketched_kw(plan, A, b, x):
+    """The sketched Karlson-Walden estimate of x's backward error (absolute)."""
+    est = ctypes.c_double()
+    _check(_lib().lsq_sketched_kw(plan, _ptr(A), _ptr(b), _ptr(x), ctypes.byref(est)))
+    return est.value
 
 
 def lsq_residual(plan, A, b, x, g):

@@ -6,6 +6,8 @@
 //   stop once ||Delta|| <= u (gamma normest ||x_0|| + rho condest ||b - A x_0||).
 // The stop decision is taken on the device (DevState::done) so that the
 // host never waits between iterations.
+#include <algorithm>
+
 #include "lsq_common.cuh"
 
 namespace lsq {
@@ -142,6 +144,63 @@ __global__ void b_copy_x_kernel(const BItem *__restrict__ items) {
   for (int i = threadIdx.x; i < it.n; i += blockDim.x) it.x[i] = it.xo[i];
 }
 
+// ||b||^2 on one CTA (a fixed order).
+__global__ void __launch_bounds__(kVecThreads)
+    bnorm2_kernel(const double *__restrict__ b, int64_t m, DevState *st) {
+  __shared__ double scratch[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s = fma(b[i], b[i], s);
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) st->bnorm2 = s;
+}
+
+// The stacked matrix of the sketched Karlson-Walden estimate (eq. (sketched-
+// kw)): (SA)^T (SA) + lam I = R^T R + lam I = R_lam^T R_lam with R_lam the R
+// factor of [R; sqrt(lam) I], so the estimate is the prefactor times
+// ||R_lam^-T A^T r|| -- the value Alg. 4 computes through the SVD of SA.
+// theta = ||A D^-1||_F / ||b|| on the column-scaled problem (Sec. 4.2).
+__global__ void kw_build_kernel(const double *__restrict__ Rcm, int n,
+                                const double *__restrict__ dcol, const double *__restrict__ dinv,
+                                const double *__restrict__ xs, double *__restrict__ W2,
+                                DevState *st) {
+  __shared__ double scratch[32];
+  __shared__ double s_lam;
+  double a2 = 0.0, x2 = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double c = dcol[j] * dinv[j];
+    a2 = fma(c, c, a2);
+    x2 = fma(xs[j], xs[j], x2);
+  }
+  a2 = block_sum(a2, scratch);
+  x2 = block_sum(x2, scratch);
+  if (threadIdx.x == 0) {
+    const double th2 = a2 / st->bnorm2;
+    const double den = 1.0 + th2 * x2;
+    if (blockIdx.x == 0) st->kw_xn2 = x2;
+    s_lam = th2 * st->kw_r2 / den;
+    st->kw_pref = sqrt(th2) / sqrt(den);
+  }
+  __syncthreads();
+  const double sl = sqrt(s_lam);
+  const int d2 = 2 * n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)d2 * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / d2), i = (int)(idx % d2);
+    double v;
+    if (i < n) v = (i <= j) ? Rcm[(size_t)j * n + i] : 0.0;
+    else v = (i - n == j) ? sl : 0.0;
+    W2[idx] = v;
+  }
+}
+
+__global__ void kw_finish_kernel(DevState *st) { st->kw_est = st->kw_pref * sqrt(st->kw_y2); }
+
+__global__ void scale_vec_kernel(int n, const double *__restrict__ sc, const double *__restrict__ x,
+                                 double *__restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = sc[i] * x[i];
+}
+
 __global__ void set_thresh_kernel(double gamma, double rho, DevState *st) {
   st->thresh1 = kU * (gamma * st->normest * sqrt(st->x0norm2) + rho * st->condest * sqrt(st->r2));
 }
@@ -181,6 +240,30 @@ cudaError_t launch_b_update(const BItem *items, int count, cudaStream_t s) {
 
 cudaError_t launch_b_copy_x(const BItem *items, int count, cudaStream_t s) {
   b_copy_x_kernel<<<count, 256, 0, s>>>(items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bnorm2(const double *b, int64_t m, DevState *st, cudaStream_t s) {
+  bnorm2_kernel<<<1, kVecThreads, 0, s>>>(b, m, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kw_build(const double *Rcm, int n, const double *dcol, const double *dinv,
+                            const double *xs, double *W2, DevState *st, cudaStream_t s) {
+  // every CTA computes lam (the same value) for its share of W2
+  const int64_t cnt = 2 * (int64_t)n * n;
+  const int grid = (int)std::min<int64_t>(64, (cnt + 1023) / 1024);
+  kw_build_kernel<<<grid, 1024, 0, s>>>(Rcm, n, dcol, dinv, xs, W2, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kw_finish(DevState *st, cudaStream_t s) {
+  kw_finish_kernel<<<1, 1, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_vec(int n, const double *sc, const double *x, double *y, cudaStream_t s) {
+  scale_vec_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, sc, x, y);
   return cudaGetLastError();
 }
 

@@ -84,6 +84,11 @@ struct lsq_plan_s {
   double *xs = nullptr, *xo = nullptr, *c = nullptr, *g = nullptr, *dy = nullptr;
   double *dyold = nullptr, *z = nullptr, *h = nullptr, *w = nullptr, *res = nullptr, *p = nullptr;
   double *lsqr_s = nullptr;          // LSQR-SPIR: the m-vector of the bidiagonalisation
+  // sketched Karlson-Walden estimate: [R; sqrt(lam) I] and its R factor
+  double *W2 = nullptr, *R2cm = nullptr, *R2rm = nullptr, *rinv2 = nullptr, *Dt2 = nullptr;
+  double *vhead2 = nullptr, *xk = nullptr, *xko = nullptr, *gk = nullptr;
+  int *qflag2 = nullptr;
+  int qr2_epoch = 0;
   DevState *st = nullptr;
   DevState *st_host = nullptr;
   int *qflag = nullptr;              // QR: per-column "reflector published" flags
@@ -160,6 +165,7 @@ lsq_status validate(const lsq_options *o) {
   if (o->precision < LSQ_PREC_AUTO || o->precision > LSQ_PREC_FP32_INNER)
     return fail(LSQ_ERR_INVALID, "unknown precision");
   if (o->qr_wait_us < 0) return fail(LSQ_ERR_INVALID, "qr_wait_us must be >= 0");
+  if (o->kw_stop != 0 && o->kw_stop != 1) return fail(LSQ_ERR_INVALID, "kw_stop must be 0 or 1");
   if (o->nrhs < 0 || (o->nrhs > 0 && !multi_supported((int)o->n, o->nrhs)))
     return fail(LSQ_ERR_INVALID, "nrhs must be a multiple of 8 in [8, 64] with n <= 256");
   return LSQ_OK;
@@ -399,6 +405,42 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db, bool defer_
   return LSQ_OK;
 }
 
+// Enqueue the sketched Karlson-Walden estimate (eq. (sketched-kw)) of the
+// iterate xs (scaled coordinates) / xo (= D^-1 xs, original) into
+// st->kw_est: one FP64 residual pass (g = D^-1 A^T (b - A xo), ||r||^2), the
+// stacked matrix [R; sqrt(lam) I], its Householder QR (the cooperative QR
+// kernel, d = 2n), the triangular solve R_lam^T y = g and the prefactor.
+// st->bnorm2 must hold ||b||^2.
+lsq_status kw_eval(lsq_plan P, const double *dA, const double *db, const double *xs,
+                   const double *xo) {
+  const int n = (int)P->n;
+  LSQ_CU(launch_pass_resid(dA, P->lda, P->m, n, db, xo, P->part, P->r2part, P->gpass, P->npad,
+                           P->s));
+  LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->gk, P->r2part, &P->st->kw_r2,
+                       nullptr, P->s));
+  LSQ_CU(launch_kw_build(P->Rcm, n, P->dcol, P->dinv, xs, P->W2, P->st, P->s));
+  P->qr2_epoch = (P->qr2_epoch >= (1 << 30)) ? 1 : P->qr2_epoch + 1;
+  LSQ_CU(launch_qr(P->W2, 2 * n, n, n, P->vhead2, P->qflag2, P->qr2_epoch, P->st,
+                   qr_grid(n, P->nsm), qr_timeout_ns(P), P->s));
+  LSQ_CU(launch_extract_r(P->W2, 2 * n, n, 0, P->R2cm, P->R2rm, P->rinv2, nullptr, P->s));
+  LSQ_CU(launch_diag_tiles(P->R2cm, P->R2rm, P->rinv2, n, P->Dt2, P->s));
+  LSQ_CU(launch_trsv(P->R2cm, P->R2rm, P->rinv2, P->Dt2, n, 1, P->gk, nullptr, P->gk, nullptr,
+                     nullptr, nullptr, &P->st->kw_y2, nullptr, P->s, 1, 0, &P->st->err));
+  LSQ_CU(launch_kw_finish(P->st, P->s));
+  P->launches += 9;
+  return LSQ_OK;
+}
+
+// ||A D^-1||_F from the column norms (sqrt(n) with column scaling).
+double scaled_fro(lsq_plan P) {
+  double s = 0.0;
+  for (int j = 0; j < (int)P->n; j++) {
+    const double c = P->o.col_scale ? 1.0 : P->dcol_host[j];
+    s += c * c;
+  }
+  return std::sqrt(s);
+}
+
 lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db, double *dx,
                      lsq_info *info) {
   if (!dx) return fail(LSQ_ERR_INVALID, "x is NULL");
@@ -422,7 +464,7 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
   double bytes_a = mn8 + (P->want32 ? mn8 : 0.0);  // sketch pass (+ hi / lo planes)
   int passes = 1;
   int iters[LSQ_MAX_REFINE] = {0};
-  double resid0 = 0.0, cprev = INFINITY;
+  double resid0 = 0.0, cprev = INFINITY, kw_last = 0.0;
   int nsteps = 0;
   std::vector<int> resid_ev, inner_ev[LSQ_MAX_REFINE];
   for (int i = 0; i < nsteps_max; i++) {
@@ -460,8 +502,12 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
       cprev = cn;
     }
     const bool fixed = P->o.fixed_inner > 0;
-    const int cap = fixed ? P->o.fixed_inner : tier ? q32 : (i == 0 ? max_inner : q2);
+    // Alg. 4's step-2 test (kw_stop): up to max_inner updates, the sketched KW
+    // estimate checked after updates 1, 6, 11, ... (reading: the inner index)
+    const bool kw = P->o.kw_stop && i == 1 && !fixed && !tier;
+    const int cap = fixed ? P->o.fixed_inner : tier ? q32 : (i == 0 || kw) ? max_inner : q2;
     const int use_thresh = (!fixed && !tier && i == 0) ? 1 : 0;
+    if (kw) LSQ_CU(launch_bnorm2(db, P->m, P->st, P->s));
     if (method == 2)
       LSQ_CU(launch_lsqr_init(n, P->c, i, P->p, P->res, P->dy, cap, use_thresh, P->st, P->s));
     else
@@ -516,6 +562,16 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
       if (use_thresh && (it % kStopPollEvery) == kStopPollEvery - 1 && it + 1 < cap) {
         LSQ_TRY(read_state(P));
         if (P->st_host->done) break;
+      }
+      if (kw && it % 5 == 0) {
+        // x_hat = x_s + R^{-1} dy (scaled) and D^{-1} x_hat, then the estimate
+        LSQ_CU(cudaMemcpyAsync(P->xk, P->xs, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->s));
+        LSQ_CU(launch_trsv(P->Rcm, P->Rrm, P->rinv, P->Dt, n, 0, P->dy, nullptr, nullptr, P->dinv,
+                           P->xko, P->xk, nullptr, nullptr, P->s, 1, 0, &P->st->err));
+        LSQ_TRY(kw_eval(P, dA, db, P->xk, P->xko));
+        LSQ_TRY(read_state(P));
+        kw_last = P->st_host->kw_est;
+        if (P->st_host->done || kw_last < kU * scaled_fro(P)) break;
       }
     }
     // x_s += R^{-1} dy ; x_o = D^{-1} x_s
@@ -575,7 +631,10 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
       info->ms_sketch_pass = tev_ms(P, 0);
     }
   }
-  if (info) info->resid0 = resid0;
+  if (info) {
+    info->resid0 = resid0;
+    info->be_sketch_est = kw_last;
+  }
   return status;
 }
 
@@ -783,7 +842,8 @@ void free_plan(lsq_plan P) {
                   P->stageb, P->stagex, P->Ahi, P->Alo, P->SBb, P->cpartB, P->mpart, P->mpartdf, P->mr2part,
                   P->mT, P->mXs, P->mXo, P->mC, P->mG, P->mDY, P->mDYold, P->mZ, P->mH,
                   P->mW, P->mstate, P->tcnt, P->tlmax, P->colexp, P->cshift,
-                  P->tptr, P->tsrc, P->cpow, P->Qfix, P->Qbfix, P->lsqr_s};
+                  P->tptr, P->tsrc, P->cpow, P->Qfix, P->Qbfix, P->lsqr_s, P->W2, P->R2cm,
+                  P->R2rm, P->rinv2, P->Dt2, P->vhead2, P->xk, P->xko, P->gk, P->qflag2};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->st_host) cudaFreeHost(P->st_host);
@@ -888,6 +948,16 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   A(dalloc(&P->st, 1));
   A(dalloc(&P->qflag, n));
   A(dalloc(&P->lsqr_s, (size_t)P->m_cap));
+  A(dalloc(&P->W2, 2 * nn));
+  A(dalloc(&P->R2cm, nn));
+  A(dalloc(&P->R2rm, nn));
+  A(dalloc(&P->rinv2, n));
+  A(dalloc(&P->Dt2, (size_t)2 * ((n + 31) / 32) * 1024));
+  A(dalloc(&P->vhead2, 4 * (size_t)n));
+  A(dalloc(&P->xk, n));
+  A(dalloc(&P->xko, n));
+  A(dalloc(&P->gk, n));
+  A(dalloc(&P->qflag2, n));
   A(cudaMallocHost((void **)&P->st_host, sizeof(DevState)));
   A(cudaMallocHost((void **)&P->dcol_host, sizeof(double) * n));
   // hi / lo FP32 planes of A: the double-float inner pass and the FP32 tier read them
@@ -908,6 +978,7 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   }
   e = cudaMemsetAsync(P->st, 0, sizeof(DevState), P->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->qflag, 0, sizeof(int) * (size_t)P->n_cap, P->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->qflag2, 0, sizeof(int) * (size_t)P->n_cap, P->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
   if (e != cudaSuccess) {
     free_plan(P);
@@ -1125,6 +1196,19 @@ lsq_status lsq_apply_normal_multi(lsq_plan P, const double *dA, const double *dZ
                                P->s));
   }
   LSQ_TRY(read_state(P));
+  return LSQ_OK;
+}
+
+lsq_status lsq_sketched_kw(lsq_plan P, const double *dA, const double *db, const double *dx,
+                           double *est) {
+  if (!P || !dA || !db || !dx || !est) return fail(LSQ_ERR_INVALID, "NULL argument");
+  if (!P->sketched) return fail(LSQ_ERR_INVALID, "call lsq_sketch first");
+  const int n = (int)P->n;
+  LSQ_CU(launch_scale_vec(n, P->dcol, dx, P->xk, P->s));  // x_s = D x
+  LSQ_CU(launch_bnorm2(db, P->m, P->st, P->s));
+  LSQ_TRY(kw_eval(P, dA, db, P->xk, dx));
+  LSQ_TRY(read_state(P));
+  *est = P->st_host->kw_est;
   return LSQ_OK;
 }
 

@@ -39,6 +39,10 @@ struct DevState {
   // rotation's phibar, rhobar, the next pass's coefficient of s, and the
   // last pass's ||s||^2
   double lq_alpha, lq_beta, lq_phibar, lq_rhobar, lq_bscale, lq_b2;
+  // sketched Karlson-Walden estimate (Alg. 4's step-2 test): ||b||^2, and
+  // for the iterate checked ||x||^2 (scaled coordinates), ||r||^2, the
+  // factor theta / sqrt(1 + theta^2 ||x||^2), ||R_lam^-T g||^2, the estimate
+  double bnorm2, kw_xn2, kw_r2, kw_pref, kw_y2, kw_est;
 };
 
 // One problem of a batch solved in lockstep (lsq_batch.cu): its sizes, the
@@ -349,6 +353,18 @@ cudaError_t launch_b_init(const BItem *items, int count, int step, int max_inner
                           double rho, cudaStream_t s);
 cudaError_t launch_b_update(const BItem *items, int count, cudaStream_t s);
 cudaError_t launch_b_copy_x(const BItem *items, int count, cudaStream_t s);
+
+// Sketched Karlson-Walden estimate (k_vec.cu).  launch_bnorm2: st->bnorm2 =
+// ||b||^2.  launch_kw_build: W2 (2n x n, column-major) = [R; sqrt(lam) I]
+// with lam = theta^2 ||r||^2 / (1 + theta^2 ||x||^2), theta^2 = ||A D^-1||_F^2
+// / ||b||^2 (st->kw_r2; ||x||^2 of xs, the scaled x, into st->kw_xn2), and
+// st->kw_pref.  launch_kw_finish:
+// st->kw_est = kw_pref sqrt(kw_y2).  launch_scale_vec: y = s .* x.
+cudaError_t launch_bnorm2(const double *b, int64_t m, DevState *st, cudaStream_t s);
+cudaError_t launch_kw_build(const double *Rcm, int n, const double *dcol, const double *dinv,
+                            const double *xs, double *W2, DevState *st, cudaStream_t s);
+cudaError_t launch_kw_finish(DevState *st, cudaStream_t s);
+cudaError_t launch_scale_vec(int n, const double *sc, const double *x, double *y, cudaStream_t s);
 
 // Inner-solver kernels (single CTA).
 cudaError_t launch_inner_init(int method, int n, const double *c, double *dy, double *dy_old,

@@ -341,3 +341,32 @@ def test_multi_rhs_inner_pass(m, n, k):
             _, _, h_ref = oracle.residual_dot2(A, np.zeros(m), -Z[c])
             bound = 4 * (n + m) * u * (absA.T @ (absA @ np.abs(Z[c])))
             assert (np.abs(Hh[c] - h_ref) <= bound).all(), (fp64, c)
+
+
+@pytest.mark.parametrize("m,n,seed", [(4000, 50, 0), (20011, 130, 3)])
+def test_sketched_kw_estimate(m, n, seed):
+    """lsq_sketched_kw (eq. (sketched-kw), through the QR of [R; sqrt(lam) I])
+    against oracle.sketched_kw (through the SVD of SA), on the column-scaled
+    problem of the same sketch: at perturbed solutions the two agree to
+    1e-4 relative (the estimate is well above the residual's rounding), and
+    at the least-squares solution both sit at the u ||A D^-1||_F level."""
+    P = problem_svd(m, n, 1e10, 1e-6, seed=seed, keep_factors=False)
+    A, b = P["A"], P["b"]
+    plan = lsq.Plan(m, n, seed=seed + 1)
+    dA, db = T(A), T(b)
+    lsq.lsq_sketch(plan.handle, dA, db)
+    dcol = oracle.column_norms(A)
+    As = A / dcol
+    SA, _ = oracle.sketch(As, b, 12 * n, 8, seed + 1)
+    x_qr = oracle.qr_solve(A, b)
+    rng = np.random.default_rng(seed)
+    fro = math.sqrt(n)
+    for scale in (1e-6, 1e-10, 0.0):
+        x = x_qr * (1.0 + scale * rng.standard_normal(n))
+        est = lsq.lsq_sketched_kw(plan.handle, dA, db, T(x))
+        ref = oracle.sketched_kw(SA, As, b, x * dcol)
+        if scale > 0:
+            assert abs(est - ref) <= 1e-4 * ref, (scale, est, ref)
+        else:
+            assert est <= 10 * u * fro and ref <= 10 * u * fro, (est, ref)
+    plan.close()
