@@ -97,10 +97,16 @@ typedef struct {
                             inner updates 1, 6, 11, ... the sketched Karlson-Walden
                             estimate of the iterate's backward error (eq. (sketched-kw),
                             theta = ||A D^-1||_F / ||b||) is compared with
-                            u ||A D^-1||_F, and the step stops below it (at most
+                            u ||A D^-1||_F, u = 2^-52 (Sec. 1.4's value for double;
+                            2^-53 is the rounding level of the solution itself), and
+                            the step stops below it (at most
                             max_inner updates); 0 (default): Theorem 7.1's q0 - 1
-                            updates.  Each test costs one FP64 pass over A and a QR of
-                            a 2n x n matrix */
+                            updates.  Each test costs one compensated FP64 pass over A
+                            (about ten times a plain one) and a QR of a 2n x n matrix.
+                            The second step's inner passes are then strict FP64
+                            (inner_kernel 0): the double-float pass holds A to 2^-48,
+                            which leaves that step's answer a few u ||A||_F from
+                            backward stable on kappa ~ 1e12 problems, above the bound */
   int32_t reserved[4];
 } lsq_options;
 
@@ -278,7 +284,9 @@ lsq_status lsq_apply_normal_multi(lsq_plan plan, const double *dA, const double 
  * ||b - A x||^2 / (1 + theta^2 ||x_s||^2), x_s = D x.  Alg. 4 evaluates it
  * through the SVD of SA; here (SA)^T SA = R^T R and the norm is
  * ||R_lam^{-T} g|| with R_lam the R factor of [R; sqrt(lam) I] (Householder
- * QR of that 2n x n matrix): the same quantity.  The residual is FP64.
+ * QR of that 2n x n matrix): the same quantity.  The residual b - A x and
+ * A^T r are FP64 with compensated (Dot2) sums, so their rounding stays far
+ * below the u ||A D^-1||_F level the estimate is compared with.
  * *est: host double, absolute (divide by ||A D^-1||_F, sqrt(n) with column
  * scaling, for the relative value).  Needs lsq_sketch (or a solve) on dA.
  * Errors: LSQ_ERR_INVALID (NULL argument, no sketch). */
@@ -378,7 +386,9 @@ lsq_status lsq_server_create(size_t arena_bytes, int max_slots, int64_t m_max, i
  * for up to max_batch (<= 256) problems with n <= n_max (<= 256) and takes, first
  * come first served, as many queued requests as its batch, its planes and
  * the arena admit; requests that arrive while batches run wait for the next
- * free worker.  FOSSILS and SPIR only (method 0 or 1).
+ * free worker.  FOSSILS and SPIR only (method 0 or 1).  Device memory: the
+ * arena plus, per worker, FP32 planes of min(arena_bytes / 8,
+ * max_batch m_max n_max) entries (8 bytes each; at least m_max n_max).
  * Errors: LSQ_ERR_INVALID, LSQ_ERR_OOM, LSQ_ERR_CUDA. */
 lsq_status lsq_server_create_batched(size_t arena_bytes, int workers, int max_batch,
                                      int64_t m_max, int64_t n_max, lsq_server *out);

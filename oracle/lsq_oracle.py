@@ -34,6 +34,12 @@ Readings of the paper that this oracle takes (the CUDA path takes the same ones)
   * Alg. 4's step-2 test reads "Mod(i, 5)" with i the refinement index, which
     is 1 throughout step 2; it is read as the inner index j: the sketched
     KW estimate is checked after updates 1, 6, 11, ... of the second solve.
+  * The step-2 test's bound u ||A||_F takes u at the value Sec. 1.4 states
+    for double precision, about 2e-16, i.e. 2^-52 (KW_STOP_U): at 2^-53 the
+    bound sits at the estimate of the correctly rounded least-squares
+    solution itself (the rounding of x alone is a relative perturbation of
+    order 2^-53 per component), so whether the test ever fires is decided by
+    rounding.  Everywhere else u = 2^-53.
   * LSQR-based SPIR solves each step's least-squares problem
     min ||r_i - A D^{-1} R^{-1} dy|| by LSQR from dy = 0, with the same two
     stopping rules applied to the LSQR update (phi_k / rho_k) w_k.
@@ -50,6 +56,7 @@ from . import _cbuild
 from .philox import sparse_sign_matrix
 
 U_ROUNDOFF = 2.0 ** -53
+KW_STOP_U = 2.0 ** -52   # u of Alg. 4's step-2 test (Sec. 1.4's stated value)
 
 _LIB = None
 
@@ -412,7 +419,7 @@ def _solve(method, A, b, d, zeta, seed, eta, col_scale, max_inner, stop_gamma,
             # Alg. 4, second inner solve: every five updates (after updates
             # 1, 6, 11, ...) estimate the backward error of x + R^{-1} dy with
             # the sketched KW estimate (theta = ||A||_F / ||b||, on the column-
-            # normalised A) and stop once it is below u ||A||_F.
+            # normalised A) and stop once it is below u ||A||_F, u = 2^-52.
             nmax = max_inner
             fro = float(np.linalg.norm(P.As))
 
@@ -420,7 +427,7 @@ def _solve(method, A, b, d, zeta, seed, eta, col_scale, max_inner, stop_gamma,
                 if (k_ - 1) % 5 != 0:
                     return False
                 xh = x_ + backsub(P.R, dy_)
-                return sketched_kw(P.SA, P.As, P.b, xh) < U_ROUNDOFF * fro
+                return sketched_kw(P.SA, P.As, P.b, xh) < KW_STOP_U * fro
         if method == "fossils":
             dy, k = _polyak(P, c, P.alpha, P.beta, nmax, th, check)
         elif method == "spir_lsqr":

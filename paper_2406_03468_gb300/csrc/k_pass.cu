@@ -589,6 +589,142 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Compensated residual pass (the sketched Karlson-Walden test of Alg. 4's
+// second refinement step): r = b - A x and g = A^T r with the compensated dot
+// product Dot2 of Ogita, Rump and Oishi (TwoProd by fma, TwoSum, the error
+// terms summed alongside), so r and g carry errors of order u |r| and
+// u |A^T| |r| rather than the u |A| |x| of a plain FP64 residual, which sits
+// at the u ||A||_F threshold of the test.  Per row the lanes' (sum, error)
+// pairs are combined with TwoSum across the warp; r = r_hi + r_lo.  Per
+// column each lane keeps a (sum, error) pair over its rows; the CTA writes
+// both (part2: [grid][2][npad], sums then errors) and reduce_dot2 adds them
+// with TwoSum in a fixed order.  About ten FP64 operations per element and
+// product, against one.  With cs non-NULL the matrix is fl(A diag(cs)) (the
+// column-scaled problem, formed element by element) and x is in its
+// coordinates: Alg. 4 runs its test on the scaled problem, where the scaled
+// iterate is exact rather than rounded by the change of coordinates.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum_d(double a, double b, double &s, double &e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <int NC, bool VEC>
+__global__ void __launch_bounds__(kPassThreads, NC >= 8 ? 1 : kPassCtasPerSm)
+    resid_dot2_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
+                      const double *__restrict__ b, const double *__restrict__ x,
+                      const double *__restrict__ cs, double *__restrict__ part2,
+                      double *__restrict__ r2_part, int npad) {
+  __shared__ double sh[NC * 64];
+  __shared__ double csh[NC * 64];
+  __shared__ double r2sh[kPassThreads / 32];
+  for (int i = threadIdx.x; i < NC * 64; i += blockDim.x) csh[i] = (cs && i < n) ? cs[i] : 1.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = min(m, (int64_t)blockIdx.x * per), r1 = min(m, r0 + per);
+  double xr[2 * NC], gs[2 * NC], gc[2 * NC];
+  load_vec<NC>(x, n, lane, xr);
+#pragma unroll
+  for (int k = 0; k < 2 * NC; k++) gs[k] = gc[k] = 0.0;
+  double r2 = 0.0;
+  for (int64_t i = r0 + warp; i < r1; i += nw) {
+    double a[2 * NC];
+    load_row<NC, VEC>(A + i * lda, n, lane, a);
+    if (cs) {
+#pragma unroll
+      for (int k = 0; k < 2 * NC; k++) a[k] *= csh[64 * (k >> 1) + 2 * lane + (k & 1)];
+    }
+    // this lane's part of b_i - a_i . x (b_i on lane 0)
+    double s = (lane == 0) ? b[i] : 0.0, c = 0.0;
+#pragma unroll
+    for (int k = 0; k < 2 * NC; k++) {
+      const double p = -a[k] * xr[k];
+      const double ep = fma(-a[k], xr[k], -p);
+      double t, es;
+      two_sum_d(s, p, t, es);
+      s = t;
+      c += ep + es;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double os = __shfl_xor_sync(0xffffffffu, s, o);
+      const double oc = __shfl_xor_sync(0xffffffffu, c, o);
+      double t, es;
+      two_sum_d(s, os, t, es);
+      s = t;
+      c += oc + es;
+    }
+    double rh, rl;
+    two_sum_d(s, c, rh, rl);
+    r2 = fma(rh, rh, r2);
+#pragma unroll
+    for (int k = 0; k < 2 * NC; k++) {
+      const double p = a[k] * rh;
+      const double ep = fma(a[k], rh, -p);
+      double t, es;
+      two_sum_d(gs[k], p, t, es);
+      gs[k] = t;
+      gc[k] += ep + es + a[k] * rl;
+    }
+  }
+  if (lane == 0) r2sh[warp] = r2;
+  // the CTA's (sum, error) pairs: sums by TwoSum over the warps in order
+  double *ps = part2 + (size_t)blockIdx.x * 2 * npad, *pc = ps + npad;
+  for (int i = threadIdx.x; i < NC * 64; i += blockDim.x) sh[i] = 0.0;
+  __shared__ double shc[NC * 64];
+  for (int i = threadIdx.x; i < NC * 64; i += blockDim.x) shc[i] = 0.0;
+  for (int w = 0; w < nw; w++) {
+    __syncthreads();
+    if (warp == w) {
+#pragma unroll
+      for (int k = 0; k < 2 * NC; k++) {
+        const int col = 64 * (k >> 1) + 2 * lane + (k & 1);
+        double t, es;
+        two_sum_d(sh[col], gs[k], t, es);
+        sh[col] = t;
+        shc[col] += gc[k] + es;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+    ps[i] = sh[i];
+    pc[i] = shc[i];
+  }
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; w++) t += r2sh[w];
+    r2_part[blockIdx.x] = t;
+  }
+}
+
+// out[j] = scale[j] (sum_g ps[g][j] + sum_g pc[g][j]) with the sums of the
+// partials' sums by TwoSum (one thread per column, a fixed order); *r2 = the
+// residual partials' sum.
+__global__ void reduce_dot2_kernel(const double *__restrict__ part2, int grid, int npad, int n,
+                                   const double *__restrict__ scale, double *__restrict__ out,
+                                   const double *__restrict__ r2_part, double *r2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) {
+    double s = 0.0, c = 0.0;
+    for (int g = 0; g < grid; g++) {
+      double t, es;
+      two_sum_d(s, part2[(size_t)g * 2 * npad + j], t, es);
+      s = t;
+      c += part2[(size_t)g * 2 * npad + npad + j] + es;
+    }
+    out[j] = scale ? scale[j] * (s + c) : s + c;
+  }
+  if (r2 != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int g = 0; g < grid; g++) t += r2_part[g];
+    *r2 = t;
+  }
+}
+
 // out[c n + j] = scale[j] sum_g part[(c grid + g) npad + j] for c < batch
 // (the partials of a batched pass, one block of grid x npad per vector).
 __global__ void reduce_batched_kernel(const double *__restrict__ part, int grid, int npad, int n,
@@ -741,6 +877,28 @@ cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, co
                                                             npad, Ahi, Alo, ld32, gate, bscale,
                                                             rout);
   });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_resid_dot2(const double *A, int64_t lda, int64_t m, int n,
+                                   const double *b, const double *x, const double *cs,
+                                   double *part2, double *r2_part, int grid, int npad,
+                                   cudaStream_t s) {
+  const bool vec = vec_ok(A, lda);
+  LSQ_PASS_SWITCH(npad, {
+    if (vec)
+      resid_dot2_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, x, cs, part2,
+                                                                r2_part, npad);
+    else
+      resid_dot2_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, x, cs, part2,
+                                                                 r2_part, npad);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_dot2(const double *part2, int grid, int npad, int n, const double *scale,
+                               double *out, const double *r2_part, double *r2, cudaStream_t s) {
+  reduce_dot2_kernel<<<(n + 127) / 128, 128, 0, s>>>(part2, grid, npad, n, scale, out, r2_part, r2);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,10 @@
 namespace lsq {
 
 constexpr double kU = 1.1102230246251565e-16;  // unit roundoff of IEEE double, 2^-53
+// u of Alg. 4's step-2 backward-error test: the value Sec. 1.4 states for
+// double precision (about 2e-16, 2^-52); at 2^-53 the bound sits at the
+// estimate of the correctly rounded solution itself
+constexpr double kUKwStop = 2.220446049250313e-16;
 constexpr int kPassThreads = 256;               // threads per CTA of the streaming passes
 constexpr int kPassCtasPerSm = 2;
 constexpr int kVecThreads = 1024;               // threads of the single-CTA vector kernels
@@ -264,6 +268,16 @@ cudaError_t launch_pass_resid(const double *A, int64_t lda, int64_t m, int n, co
                               cudaStream_t s, float *Ahi = nullptr, float *Alo = nullptr,
                               int64_t ld32 = 0, const DevState *gate = nullptr,
                               const double *bscale = nullptr, double *rout = nullptr);
+// Compensated residual pass (Dot2): r = b - A' x and the (sum, error) pairs of
+// A'^T r per CTA into part2 (grid x 2 npad), ||r||^2 partials, with
+// A' = fl(A diag(cs)) when cs is non-NULL, else A; reduce_dot2 adds the pairs
+// with TwoSum (scale may be NULL).
+cudaError_t launch_pass_resid_dot2(const double *A, int64_t lda, int64_t m, int n,
+                                   const double *b, const double *x, const double *cs,
+                                   double *part2, double *r2_part, int grid, int npad,
+                                   cudaStream_t s);
+cudaError_t launch_reduce_dot2(const double *part2, int grid, int npad, int n, const double *scale,
+                               double *out, const double *r2_part, double *r2, cudaStream_t s);
 // out[j] = scale[j] * sum_g part[g][j] (scale may be NULL); r2 (if non-NULL)
 // = sum_g r2_part[g]; gated.
 cudaError_t launch_reduce(const double *part, int grid, int npad, int n, const double *scale,

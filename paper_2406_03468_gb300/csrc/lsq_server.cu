@@ -414,9 +414,12 @@ lsq_status lsq_server_create_batched(size_t arena_bytes, int workers, int max_ba
   S->m_max = m_max;
   S->n_max = n_max;
   S->max_batch = max_batch;
-  // each worker's planes hold as many elements as the arena holds entries of A
-  S->batch_elems = std::max<int64_t>((int64_t)(arena_bytes / sizeof(double)),
-                                     m_max * ((n_max + 3) / 4 * 4));
+  // each worker's planes hold as many elements as the arena holds entries of
+  // A, but never more than max_batch requests of the largest shape need
+  const int64_t npad4 = (n_max + 3) / 4 * 4;
+  S->batch_elems = std::max<int64_t>(
+      std::min<int64_t>((int64_t)(arena_bytes / sizeof(double)), max_batch * m_max * npad4),
+      m_max * npad4);
   cudaError_t e = cudaGetDevice(&S->dev);
   if (e == cudaSuccess) e = cudaMalloc((void **)&S->arena_base, arena_bytes);
   if (e != cudaSuccess) {
