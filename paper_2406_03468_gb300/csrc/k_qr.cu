@@ -580,7 +580,11 @@ cudaError_t launch_qr_vr(void **args, int d, int grid, size_t smem, cudaStream_t
 }
 
 cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vhead, int *flags, int epoch,
-                      DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s) {
+                      DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s,
+                      const QrBlocked *qb) {
+  if (qb != nullptr && qr_blocked_ok(d, n))
+    return launch_qr_blocked(W, d, n, ncols, vhead, qb->tws, st, timeout_ns, s, qb->sp,
+                             const_cast<cudaEvent_t *>(qb->ev));
   void *args[] = {&W, &d, &n, &ncols, &vhead, &flags, &epoch, &st, &timeout_ns};
   // grid: CTAs at kQrGlobalCtasPerSm per SM (qr_grid).  Columns in shared
   // memory at kQrSmemCtasPerSm CTAs per SM if they fit, else in global

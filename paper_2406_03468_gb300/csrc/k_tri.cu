@@ -13,6 +13,7 @@
 // reciprocals computed once per factorisation; that perturbs each diagonal
 // entry by at most two roundings, so the solve stays backward stable.
 #include "lsq_common.cuh"
+#include "lsq_cluster.cuh"
 
 namespace lsq {
 
@@ -389,54 +390,7 @@ constexpr int kMaxBlocks = (LSQ_MAX_N + 31) / 32;
 constexpr uint64_t kClusterWaitNs = 1000ull * 1000 * 1000;  // 1 s
 static_assert(kMaxBlocks <= kUpdateCtas * (kClusterThreads / 32), "one warp per owned block");
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// the same shared-memory variable in CTA `rank` of the cluster
-__device__ __forceinline__ unsigned cluster_addr(const void *p, unsigned rank) {
-  unsigned r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void st_async_f64(unsigned raddr, double v, unsigned rbar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(raddr),
-               "l"(__double_as_longlong(v)), "r"(rbar)
-               : "memory");
-}
-// An mbarrier for one transfer of `bytes`: its one arrival is made here, the
-// phase completes when the remote stores have delivered the bytes.
-__device__ __forceinline__ void xfer_bar_init(uint64_t *bar, unsigned bytes) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool xfer_try(uint64_t *bar) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar))
-      : "memory");
-  return ok != 0;
-}
-__device__ bool xfer_wait(uint64_t *bar) {
-  if (xfer_try(bar)) return true;
-  const uint64_t t0 = global_ns();
-  while (!xfer_try(bar))
-    if (global_ns() - t0 > kClusterWaitNs) return false;
-  return true;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
-}
+__device__ bool xfer_wait(uint64_t *bar) { return xfer_wait_limit(bar, kClusterWaitNs); }
 __device__ __forceinline__ void nbar_arrive(int id, int count) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
@@ -480,7 +434,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
     } else {
       for (int r = 0; r <= last - 2; r++) xfer_bar_init(bars + r, 8u * blk_len(blk_of(r, nb, trans), n));
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_mbarrier_init_cluster();
   }
   __syncthreads();
   cluster_sync_all();  // every barrier is armed before any remote store

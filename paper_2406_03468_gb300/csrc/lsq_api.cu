@@ -99,6 +99,7 @@ struct lsq_plan_s {
   // c0 on the main one; the main stream joins it before the step-1 threshold
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  QrBlocked qb{};                    // blocked QR: T workspace, panel stream, events
   bool condest_pending = false;
   double *stageA = nullptr, *stageb = nullptr, *stagex = nullptr;
   size_t stage_cap = 0;              // doubles of stageA
@@ -384,7 +385,7 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db, bool defer_
     LSQ_CU(launch_qr_stepwise(P->W, P->d, n, n + 1, P->vbuf, qr_step_grid(n + 1, P->nsm), P->s));
   else
     LSQ_CU(launch_qr(P->W, P->d, n, n + 1, P->vbuf, P->qflag, next_epoch(P), P->st,
-                     qr_grid(n + 1, P->nsm), qr_timeout_ns(P), P->s));
+                     qr_grid(n + 1, P->nsm), qr_timeout_ns(P), P->s, &P->qb));
   LSQ_CU(launch_extract_r(P->W, P->d, n, 1, P->Rcm, P->Rrm, P->rinv, P->t, P->s));
   LSQ_CU(launch_diag_tiles(P->Rcm, P->Rrm, P->rinv, n, P->Dt, P->s));
   LSQ_CU(cudaEventRecord(P->ev_fork, P->s));
@@ -432,7 +433,7 @@ lsq_status kw_eval(lsq_plan P, const double *dA, const double *db, const double 
   LSQ_CU(launch_kw_build(P->Rcm, n, P->dcol, P->dinv, xs, P->W2, P->st, P->s));
   P->qr2_epoch = (P->qr2_epoch >= (1 << 30)) ? 1 : P->qr2_epoch + 1;
   LSQ_CU(launch_qr(P->W2, 2 * n, n, n, P->vhead2, P->qflag2, P->qr2_epoch, P->st,
-                   qr_grid(n, P->nsm), qr_timeout_ns(P), P->s));
+                   qr_grid(n, P->nsm), qr_timeout_ns(P), P->s, &P->qb));
   LSQ_CU(launch_extract_r(P->W2, 2 * n, n, 0, P->R2cm, P->R2rm, P->rinv2, nullptr, P->s));
   LSQ_CU(launch_diag_tiles(P->R2cm, P->R2rm, P->rinv2, n, P->Dt2, P->s));
   LSQ_CU(launch_trsv(P->R2cm, P->R2rm, P->rinv2, P->Dt2, n, 1, P->gk, nullptr, P->gk, nullptr,
@@ -705,7 +706,7 @@ lsq_status run_solve_multi(lsq_plan P, const double *dA, const double *dB, int64
   LSQ_CU(launch_sketch_b_to_w(P->SBb, d, n, k, P->zeta, P->W, P->st, P->s));
   LSQ_CU(cudaEventRecord(P->ev[1], P->s));
   LSQ_CU(launch_qr(P->W, d, n, n + k, P->vbuf, P->qflag, next_epoch(P), P->st,
-                   qr_grid(n + k, P->nsm), qr_timeout_ns(P), P->s));
+                   qr_grid(n + k, P->nsm), qr_timeout_ns(P), P->s, &P->qb));
   LSQ_CU(launch_extract_r(P->W, d, n, k, P->Rcm, P->Rrm, P->rinv, P->mT, P->s));
   LSQ_CU(launch_diag_tiles(P->Rcm, P->Rrm, P->rinv, n, P->Dt, P->s));
   LSQ_CU(launch_condest(P->Rcm, P->Rrm, P->rinv, P->Dt, n, kCondestIters, P->st, P->s));
@@ -867,6 +868,10 @@ void free_plan(lsq_plan P) {
   for (auto &e : P->ev)
     if (e) cudaEventDestroy(e);
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  for (auto &e : P->qb.ev)
+    if (e) cudaEventDestroy(e);
+  if (P->qb.sp) cudaStreamDestroy(P->qb.sp);
+  if (P->qb.tws) cudaFree(P->qb.tws);
   for (auto &e : P->chunk_ev)
     if (e) cudaEventDestroy(e);
   if (P->ev_stage) cudaEventDestroy(P->ev_stage);
@@ -988,6 +993,13 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   A(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
   A(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
   A(cudaStreamCreateWithFlags(&P->s2, cudaStreamNonBlocking));
+  {
+    int lo = 0, hi = 0;
+    A(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    A(cudaStreamCreateWithPriority(&P->qb.sp, cudaStreamNonBlocking, hi));
+    for (auto &e : P->qb.ev) A(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    A(dalloc(&P->qb.tws, qr_blocked_tws((int)P->n_cap)));
+  }
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);
     free_plan(P);

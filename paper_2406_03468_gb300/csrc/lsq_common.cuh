@@ -185,8 +185,21 @@ cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad,
 // columns 0..n-1.  vhead: 2 n doubles (u_1, beta per reflector); flags: n ints,
 // flag k set to epoch when reflector k is published (epoch != 0, different
 // from the previous launch's).  Waits are bounded by timeout_ns.
+// With qb (and n, d in qr_blocked_ok's range) the blocked form of
+// k_qr_blocked.cu runs instead: same outputs, panels on qb->sp.
+struct QrBlocked {
+  double *tws;          // qr_blocked_tws(n) doubles: T of every panel
+  cudaStream_t sp;      // the panel stream (high priority)
+  cudaEvent_t ev[5];    // ordering events, timing disabled
+};
 cudaError_t launch_qr(double *W, int d, int n, int ncols, double *vhead, int *flags, int epoch,
-                      DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s);
+                      DevState *st, int grid, uint64_t timeout_ns, cudaStream_t s,
+                      const QrBlocked *qb = nullptr);
+bool qr_blocked_ok(int d, int n);
+size_t qr_blocked_tws(int n);
+cudaError_t launch_qr_blocked(double *W, int d, int n, int ncols, double *vhead, double *tws,
+                              DevState *st, uint64_t timeout_ns, cudaStream_t s, cudaStream_t sp,
+                              cudaEvent_t *ev);
 int qr_grid(int ncols, int nsm);       // CTAs of launch_qr
 int qr_step_grid(int ncols, int nsm);  // CTAs of launch_qr_stepwise
 // The same factorisation as n + 1 ordinary launches (no inter-CTA waits): safe
