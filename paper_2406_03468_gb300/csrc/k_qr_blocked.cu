@@ -453,7 +453,7 @@ cudaError_t launch_qr_blocked(double *W, int d, int n, int ncols, double *vhead,
   // (portable: they pack the GPCs better than 16); the next panel's columns,
   // on the critical path, 2 per CTA in clusters of pc CTAs
   const int uc = 8;
-  e = cudaFuncSetAttribute((const void *)qr_update_kernel<kUpdCols>,
+  e = cudaFuncSetAttribute((const void *)qr_update_kernel<4>,
                            cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void *)qr_update_kernel<2>,
@@ -486,7 +486,7 @@ cudaError_t launch_qr_blocked(double *W, int d, int n, int ncols, double *vhead,
     }
     // the remaining columns on s, once panel p is factored
     if ((e = cudaStreamWaitEvent(s, ev[1 + (p & 1)], 0)) != cudaSuccess) return e;
-    if ((e = launch_update<kUpdCols>(W, d, kb, bw, kn + bwn, ncols, uc, vhead, Tp, st, timeout_ns,
+    if ((e = launch_update<4>(W, d, kb, bw, kn + bwn, ncols, uc, vhead, Tp, st, timeout_ns,
                                      s)) != cudaSuccess)
       return e;
     if ((e = cudaEventRecord(ev[3 + (p & 1)], s)) != cudaSuccess) return e;

@@ -38,7 +38,9 @@ __device__ void inner_init_body(int method, int n, const double *__restrict__ c,
     st->max_iters = max_iters;
     st->use_thresh = use_thresh;
     st->dnorm2 = 0.0;
-    st->done = (max_iters <= 0) ? 1 : 0;
+    // CG with c = 0 (rho = 0) has dy = 0 exactly and no update to make: its
+    // first step would be 0 / 0
+    st->done = (max_iters <= 0 || (method != 0 && !(s > 0.0))) ? 1 : 0;
   }
 }
 

@@ -132,7 +132,21 @@ def test_edge_shapes(m, n):
     for method in ("fossils", "spir"):
         st, info, x = _gpu_solve(method, A, b, seed=1)
         assert st == 0
-        assert oracle.kw_relative(A, b, x) <= 1e-13
+        assert oracle.kw_relative(A, b, x) <= 1e-13, (method, x[:4], info)
+
+
+@pytest.mark.parametrize("m,n", [(1000, 1), (4000, 50), (6000, 100)])
+def test_zero_rhs(m, n):
+    """b = 0: the sketch-and-solve start, every residual and every inner
+    right-hand side are exactly 0, so each method returns x = 0 exactly (CG
+    stops before its first update, whose step would be 0 / 0)."""
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n))
+    b = np.zeros(m)
+    for method in ("fossils", "spir", "spir_lsqr"):
+        st, info, x = _gpu_solve(method, A, b, seed=2)
+        assert st == 0, (method, info)
+        assert np.all(x == 0.0), (method, x[:4], info)
 
 
 @pytest.mark.parametrize("method", ["fossils", "spir"])
@@ -182,6 +196,20 @@ def _config5_width_problem(kappa):
         x_qr, R_A = oracle.qr_solve(P["A"], P["b"], return_R=True)
         _C5[kappa] = (P, x_qr, R_A)
     return _C5[kappa]
+
+
+@pytest.mark.parametrize("m,n", [(1000, 1), (4000, 50), (6000, 100)])
+def test_zero_rhs(m, n):
+    """b = 0: the sketch-and-solve start, every residual and every inner
+    right-hand side are exactly 0, so each method returns x = 0 exactly (CG
+    stops before its first update, whose step would be 0 / 0)."""
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n))
+    b = np.zeros(m)
+    for method in ("fossils", "spir", "spir_lsqr"):
+        st, info, x = _gpu_solve(method, A, b, seed=2)
+        assert st == 0, (method, info)
+        assert np.all(x == 0.0), (method, x[:4], info)
 
 
 @pytest.mark.parametrize("method", ["fossils", "spir"])
