@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tier", action="store_true",
                     help="skip the tier / many-RHS / served comparisons")
-    ap.add_argument("--profile-case", default="", choices=["", "tier", "multi"],
+    ap.add_argument("--profile-case", default="", choices=["", "tier", "multi", "qr"],
                     help="run small solves of one path for ncu captures (no bench line)")
     ap.add_argument("--rows", type=int, default=0,
                     help="override m (small cases for ncu captures; not a bench line)")
@@ -712,8 +712,9 @@ def run_ours(args):
     kwstop = {"solves_per_s": len(infoskw) / (mskw / 1e3), "iters": infoskw[-1]["iters"],
               "be_sketch_rel": infoskw[-1]["be_sketch_est"] / N ** 0.5,
               "note": "step 2 ends when the sketched KW estimate (checked after updates 1, 6, "
-                      "11, ...) is below u ||A D^-1||_F; each check is one FP64 pass and a QR "
-                      "of the 2n x n matrix [R; sqrt(lam) I]"}
+                      "11, ...) is below u ||A D^-1||_F (u = 2^-52); each check is one "
+                      "compensated (Dot2) FP64 pass and a QR of the 2n x n matrix "
+                      "[R; sqrt(lam) I]; step 2's inner passes run in strict FP64"}
     x_kw = xkw.cpu().numpy().copy()
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -839,13 +840,23 @@ def run_ours(args):
 
 def run_profile_case(args):
     """Small cases for ncu captures: `tier` = FP32-inner FOSSILS on 2e5 x 1000
-    (kappa 1e4), `multi` = 64 right-hand sides on 2e5 x 200 (kappa 1e8)."""
+    (kappa 1e4), `multi` = 64 right-hand sides on 2e5 x 200 (kappa 1e8), `qr` =
+    FOSSILS on 30000 x n (n = --cols, default 500; kappa 1e8), whose sketch
+    has the bench workload's d = 12n rows, for the QR kernels."""
     import numpy as np
     import torch
     import paper_2406_03468_gb300 as lsq
     from lsq_problems import problem_gaussian
     dev = torch.device("cuda", 0)
-    if args.profile_case == "tier":
+    if args.profile_case == "qr":
+        n = args.cols or 500
+        P = problem_gaussian(30000, n, 1e8, 1e-6, seed=51)
+        A, b = torch.from_numpy(P["A"]).to(dev), torch.from_numpy(P["b"]).to(dev)
+        plan = lsq.Plan(30000, n, seed=7)
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        for _ in range(max(1, args.steps)):
+            st, info = lsq.lsq_solve_fossils(plan.handle, A, b, x)
+    elif args.profile_case == "tier":
         P = problem_gaussian(200000, 1000, 1e4, 1e-4, seed=31)
         A, b = torch.from_numpy(P["A"]).to(dev), torch.from_numpy(P["b"]).to(dev)
         plan = lsq.Plan(200000, 1000, seed=7, precision=lsq.LSQ_PREC_AUTO)
