@@ -839,8 +839,8 @@ def run_ours(args):
 
 
 def run_profile_case(args):
-    """Small cases for ncu captures: `tier` = FP32-inner FOSSILS on 2e5 x 1000
-    (kappa 1e4), `multi` = 64 right-hand sides on 2e5 x 200 (kappa 1e8), `qr` =
+    """Small cases for ncu captures: `tier` = FP32-inner FOSSILS on m x 1000
+    (m = --rows, default 2e5; kappa 1e4), `multi` = 64 right-hand sides on 2e5 x 200 (kappa 1e8), `qr` =
     FOSSILS on 30000 x n (n = --cols, default 500; kappa 1e8), whose sketch
     has the bench workload's d = 12n rows, for the QR kernels."""
     import numpy as np
@@ -857,9 +857,10 @@ def run_profile_case(args):
         for _ in range(max(1, args.steps)):
             st, info = lsq.lsq_solve_fossils(plan.handle, A, b, x)
     elif args.profile_case == "tier":
-        P = problem_gaussian(200000, 1000, 1e4, 1e-4, seed=31)
+        mt = args.rows or 200000
+        P = problem_gaussian(mt, 1000, 1e4, 1e-4, seed=31)
         A, b = torch.from_numpy(P["A"]).to(dev), torch.from_numpy(P["b"]).to(dev)
-        plan = lsq.Plan(200000, 1000, seed=7, precision=lsq.LSQ_PREC_AUTO)
+        plan = lsq.Plan(mt, 1000, seed=7, precision=lsq.LSQ_PREC_AUTO)
         x = torch.empty(1000, dtype=torch.float64, device=dev)
         for _ in range(max(1, args.steps)):
             st, info = lsq.lsq_solve_fossils(plan.handle, A, b, x)

@@ -336,16 +336,17 @@ __device__ __forceinline__ int biased_exp(double a) {
   return (int)(((unsigned)__double2hiint(a) >> 20) & 0x7ffu);
 }
 
-// One streaming pass over A (no sketch): column sums of squares (partials),
-// the largest biased exponent per column and of b (atomicMax into colexp[0..n)
-// and colexp[npad], zeroed first), and the hi / lo FP32 planes when Ahi != NULL.
-// accumulate = 1 adds the partials to those of earlier rows (A in row chunks).
+// One streaming pass over A (no sketch): column sums of squares (partials,
+// CTA g's at colsq_part + g pstride), the largest biased exponent per column
+// and of b (atomicMax into colexp[0..n) and colexp[bslot], zeroed first), and
+// the hi / lo FP32 planes when Ahi != NULL.  accumulate = 1 adds the partials
+// to those of earlier rows (A in row chunks).  npad = 64 NC columns from A.
 template <int NC, bool VEC>
 __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
     prep_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int n,
                 const double *__restrict__ b, double *__restrict__ colsq_part, int npad,
-                int *colexp, float *__restrict__ Ahi, float *__restrict__ Alo, int64_t ld32,
-                int accumulate) {
+                int pstride, int *colexp, int bslot, float *__restrict__ Ahi,
+                float *__restrict__ Alo, int64_t ld32, int accumulate) {
   __shared__ double acc[NC * 64];
   __shared__ int emax[NC * 64 + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -408,11 +409,11 @@ __global__ void __launch_bounds__(kPassThreads, NC >= 16 ? 1 : kPassCtasPerSm)
   }
   __syncthreads();
   for (int i = threadIdx.x; i < npad; i += blockDim.x) {
-    const size_t o = (size_t)blockIdx.x * npad + i;
+    const size_t o = (size_t)blockIdx.x * pstride + i;
     colsq_part[o] = (accumulate ? colsq_part[o] : 0.0) + acc[i];
     if (i < n && emax[i] > 0) atomicMax(colexp + i, emax[i]);
   }
-  if (threadIdx.x == 0 && emax[NC * 64] > 0) atomicMax(colexp + npad, emax[NC * 64]);
+  if (threadIdx.x == 0 && emax[NC * 64] > 0) atomicMax(colexp + bslot, emax[NC * 64]);
 }
 
 // Fixed-point parameters per column (and b at index npad): with E = the
@@ -820,19 +821,29 @@ cudaError_t launch_sketch_prep(const double *A, int64_t lda, int64_t m, int n, c
   cudaError_t e = cudaMemsetAsync(colexp, 0, sizeof(int) * (size_t)(npad + 1), s);
   if (e != cudaSuccess) return e;
   const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 2 == 0);
-#define LSQ_PREP(NC)                                                                            \
-  (vec ? prep_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, colsq_part, npad, \
-                                                             colexp, Ahi, Alo, ld32,            \
-                                                             accumulate)                        \
-       : prep_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A, lda, m, n, b, colsq_part,     \
-                                                              npad, colexp, Ahi, Alo, ld32,     \
-                                                              accumulate))
+#define LSQ_PREP(NC, A_, N_, B_, PART_, NP_, EXP_, BSLOT_, HI_, LO_)                              \
+  (vec ? prep_kernel<NC, true><<<grid, kPassThreads, 0, s>>>(A_, lda, m, N_, B_, PART_, NP_, npad, \
+                                                             EXP_, BSLOT_, HI_, LO_, ld32,       \
+                                                             accumulate)                         \
+       : prep_kernel<NC, false><<<grid, kPassThreads, 0, s>>>(A_, lda, m, N_, B_, PART_, NP_,    \
+                                                              npad, EXP_, BSLOT_, HI_, LO_,      \
+                                                              ld32, accumulate))
   switch (npad / 64) {
-    case 1: LSQ_PREP(1); break;
-    case 2: LSQ_PREP(2); break;
-    case 4: LSQ_PREP(4); break;
-    case 8: LSQ_PREP(8); break;
-    case 16: LSQ_PREP(16); break;
+    case 1: LSQ_PREP(1, A, n, b, colsq_part, npad, colexp, npad, Ahi, Alo); break;
+    case 2: LSQ_PREP(2, A, n, b, colsq_part, npad, colexp, npad, Ahi, Alo); break;
+    case 4: LSQ_PREP(4, A, n, b, colsq_part, npad, colexp, npad, Ahi, Alo); break;
+    case 8: LSQ_PREP(8, A, n, b, colsq_part, npad, colexp, npad, Ahi, Alo); break;
+    case 16: {
+      // two passes over column halves: the 1024-column form needs 251 registers
+      // (one 8-warp CTA per SM, 3.5 TB/s at 1e6 x 1000); the 512-column form
+      // runs two CTAs per SM.  b's exponent goes to colexp[npad] in both.
+      LSQ_PREP(8, A, 512, b, colsq_part, 512, colexp, npad, Ahi, Alo);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      LSQ_PREP(8, A + 512, n - 512, nullptr, colsq_part + 512, 512, colexp + 512, npad - 512,
+               Ahi ? Ahi + 512 : nullptr, Alo ? Alo + 512 : nullptr);
+      break;
+    }
     default: return cudaErrorInvalidValue;
   }
 #undef LSQ_PREP

@@ -261,7 +261,8 @@ def test_residual_pass_after_sketch(m, n):
     assert abs(r2 - float(r_hi @ r_hi)) <= 1e-12 * float(r_hi @ r_hi)
 
 
-@pytest.mark.parametrize("m,n,entry", [(200003, 100, "device"), (400003, 200, "host")])
+@pytest.mark.parametrize("m,n,entry", [(200003, 100, "device"), (400003, 200, "host"),
+                                        (20011, 1000, "device")])
 def test_gather_sketch_fixed_point(m, n, entry):
     """The gather form of the sketch (m n >= 2^24).  Its raw sums are integer
     work and must equal oracle.fixed_point_sketch bit for bit.  Each list entry is
@@ -270,7 +271,8 @@ def test_gather_sketch_fixed_point(m, n, entry):
     bits of the longest list)), so an entry of S A is off by less than
     cnt_h 2^(L-62) max|A_:j| plus FP64 roundings of the sums.  The host
     entry copies A in row chunks (640 MB here: 5 chunks of >= 128 MB) and
-    sketches each as it lands, one fixed-point scale per chunk."""
+    sketches each as it lands, one fixed-point scale per chunk.  n = 1000
+    takes the column-norm and exponent pass in two column halves."""
     P = problem_svd(m, n, 1e6, 1e-4, seed=13, keep_factors=False)
     A, b = P["A"], P["b"]
     zeta, d, seed = 8, 12 * n, 17
