@@ -458,6 +458,52 @@ def multi_compare(lsq, torch, dev, steps):
     return out
 
 
+def complex_compare(lsq, torch, dev, steps, m=500000, n=256):
+    """Complex least squares at the Prony experiment's m (5e5 rows; n = 256):
+    FOSSILS through lsq_solve_complex (the real embedding, 1e6 x 512, formed
+    by a kernel inside the timed region), checked against the oracle's
+    LAPACK Householder solve of the same embedding."""
+    import numpy as np
+    from lsq_problems import problem_prony
+    P = problem_prony(m, n, seed=3)
+    A, b = P["A"], P["b"]
+    dA = torch.from_numpy(A).to(dev)
+    db = torch.from_numpy(b).to(dev)
+    dx = torch.empty(n, dtype=torch.complex128, device=dev)
+    work = torch.empty(4 * m * n, dtype=torch.float64, device=dev)
+    plan = lsq.Plan(2 * m, 2 * n, seed=7, timing=1)
+    lsq.lsq_solve_complex(plan.handle, 0, dA, db, dx, work)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        _, info = lsq.lsq_solve_complex(plan.handle, 0, dA, db, dx, work)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    info = info.as_dict()
+    plan.close()
+    x = dx.cpu().numpy()
+    del dA, db, work
+    torch.cuda.empty_cache()
+    import oracle
+    t0 = time.perf_counter()
+    E = oracle.real_embedding(A)
+    br = oracle.as_real(b)
+    xr_ref, R_E = oracle.qr_solve_lapack(E, br, return_R=True)
+    x_ref = oracle.as_complex(xr_ref)
+    be = oracle.kw_relative_complex(A, b, x, R_E=R_E)
+    fe = float(np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref))
+    del E
+    return {"workload": "fossils_complex_prony_m%d_n%d" % (m, n), "embedding": "%d x %d real" % (2 * m, 2 * n),
+            "solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iters": info["iters"],
+            "phase_ms": {"sketch": info["ms_sketch"], "qr": info["ms_qr"], "refine": info["ms_refine"]},
+            "condest": info["condest"],
+            "check": {"be_rel": be, "fwd_err_vs_oracle_qr": fe, "ok": bool(be <= 1e-13),
+                      "seconds": time.perf_counter() - t0}}
+
+
 def serve_compare(lsq, torch, dev, count=512, slots=8):
     """Config 3: a stream of `count` independent problems (m log-uniform in
     [2e4, 4e5], n in {32, 64, 128, 256}, kappa log-uniform in [1e2, 1e12],
@@ -755,12 +801,14 @@ def run_ours(args):
 
     tier = None
     multi = None
+    cplx = None
     served = None
     if not args.no_tier and not args.rows and not args.cols:
         del A, b
         torch.cuda.empty_cache()
         tier = tier_compare(lsq, torch, dev, max(2, args.steps // 3))
         multi = multi_compare(lsq, torch, dev, 2)
+        cplx = complex_compare(lsq, torch, dev, 3)
         served = serve_compare(lsq, torch, dev)
 
     # every timed result against the oracle (after the timed regions)
@@ -785,6 +833,8 @@ def run_ours(args):
         accuracy["check_seconds"] = time.perf_counter() - t0
         del R_A
         oks = [v["ok"] for v in accuracy.values() if isinstance(v, dict)]
+        if cplx:
+            oks.append(cplx["check"]["ok"])
         for part in (tier, multi, served):
             if not part:
                 continue
@@ -823,6 +873,7 @@ def run_ours(args):
                                   "kw_stop_step2": kwstop,
                                   "fp32_tier_1e6x1000": tier,
                                   "multi_rhs_2e6x200_k64": multi,
+                                  "complex_prony_5e5x256": cplx,
                                   "served_stream": served}),
                 "accuracy": accuracy, "checks_passed": checks_ok,
                 "clocks": clocks, "e2e": e2e,

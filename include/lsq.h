@@ -197,6 +197,26 @@ lsq_status lsq_solve_spir(lsq_plan plan, const double *dA, const double *db, dou
 lsq_status lsq_solve_spir_lsqr(lsq_plan plan, const double *dA, const double *db, double *dx,
                                lsq_info *info);
 
+/* A complex least-squares problem min ||b - A x||, A in C^{m x n}, b in C^m
+ * (the paper's Prony experiment, Sec. 5 "Runtime and iteration count", and
+ * the first solve of Prony's method in its appendix), by FOSSILS (method 0),
+ * SPIR (1) or LSQR-based SPIR (2) applied to the real embedding
+ *   E[2i][2k] = Re a_ik, E[2i][2k+1] = -Im a_ik,
+ *   E[2i+1][2k] = Im a_ik, E[2i+1][2k+1] = Re a_ik   (E: 2m x 2n),
+ * whose least-squares solution is x with real and imaginary parts
+ * interleaved, so b and x are passed in their complex storage.
+ * plan: created for m_r = 2m, n_r = 2n (n <= LSQ_MAX_N / 2), lda = 0; its
+ * options apply to the embedded problem (d = 12 n_r by default; with kw_stop
+ * the bound is u ||E D^-1||_F = sqrt(2) u ||A D^-1||_F).
+ * dA: m x n complex, row-major, (re, im) interleaved doubles, lda complex
+ * entries per row (0 => n), 16-byte aligned; db: m complex; dx: n complex
+ * (out); dwork: 2m x 2n doubles (16-byte aligned), caller-owned, overwritten
+ * with E.  All device pointers.  info as for the real solves.
+ * Errors: LSQ_ERR_INVALID (NULL, odd plan sizes, lda, alignment, method), and
+ * those of the real solve. */
+lsq_status lsq_solve_complex(lsq_plan plan, int method, const double *dA, int64_t lda,
+                             const double *db, double *dx, double *dwork, lsq_info *info);
+
 /* FOSSILS for k = opt.nrhs right-hand sides sharing one sketch S [A B] and
  * one QR (Alg. 1 with the augmented columns Q^T S B; Alg. 2 / Alg. 5 per
  * column, each column with its own Polyak vectors and step-1 threshold, the

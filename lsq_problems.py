@@ -147,3 +147,26 @@ def problem_multi_rhs_torch(m, n, k, kappa, noise, seed, device="cuda"):
     X = torch.randn(n, k, generator=g, dtype=f64, device=device)
     B = (A @ X + noise * torch.randn(m, k, generator=g, dtype=f64, device=device)).contiguous()
     return {"A": A, "B": B, "X_true": X, "kappa": kappa, "noise": noise}
+
+
+def problem_prony(m, n, seed, noise=1e-6, dt=0.25, spread=3.0):
+    """The first least-squares problem of Prony's method (the paper's appendix
+    on Prony's method, its algorithm's first line), synthetic: measurements
+    f_j = sum_i mu_i z_i^j + eps_j for 0 <= j <= m + n - 1 with
+    z_i = exp(-1j dt lambda_i) on the unit circle, lambda_i uniform in
+    [-spread, spread], mu_i > 0 summing to 1, eps_j complex Gaussian with
+    standard deviation `noise` (the paper: 1e-6).  A[i, j] = f[n - 1 + i - j],
+    b[i] = f[n + i] (0-based), so A is Toeplitz, and with noise-free data b
+    lies in range(A) (the linear-prediction equations); x_true = None."""
+    rng = np.random.default_rng(seed)
+    lam = np.sort(rng.uniform(-spread, spread, n))
+    z = np.exp(-1j * dt * lam)
+    mu = rng.dirichlet(np.ones(n))
+    j = np.arange(m + n)
+    f = (mu[None, :] * np.exp(-1j * dt * np.outer(j, lam))).sum(axis=1)
+    eps = rng.standard_normal(m + n) + 1j * rng.standard_normal(m + n)
+    f = f + noise / np.sqrt(2.0) * eps
+    idx = (n - 1) + np.arange(m)[:, None] - np.arange(n)[None, :]
+    A = np.ascontiguousarray(f[idx])
+    b = np.ascontiguousarray(f[n + np.arange(m)])
+    return {"A": A, "b": b, "z": z, "mu": mu, "lam": lam}

@@ -12,7 +12,8 @@ Modules
 -------
 philox      Philox4x64-10 and the sparse sign embedding spec (Sec. 4.2).
 lsq_oracle  Householder QR solve, sketch, FOSSILS (Alg. 2 / Alg. 4), SPIR
-            (Alg. 3), the Karlson-Walden estimate (Sec. 4.1), q0 (Theorem 7.1).
+            (Alg. 3), the Karlson-Walden estimate (Sec. 4.1), q0 (Theorem 7.1),
+            complex problems through their real embedding.
 liboracle.c plain C loops for the QR, triangular solves and compensated
             residuals, built by _cbuild.build().
 
@@ -31,4 +32,5 @@ from . import lsq_oracle, philox  # noqa: F401
 from .lsq_oracle import (  # noqa: F401
     U_ROUNDOFF, apply_qt, backsub, backsub_t, column_norms, fixed_point_sketch, forward_error, fossils,
     householder_qr, kw_estimate, kw_relative, q0_count, qr_solve, qr_solve_lapack, residual_dot2,
-    sigma_extremes, sketch, sketched_kw, spir, spir_lsqr, step2_updates, wedin_bound)
+    sigma_extremes, sketch, sketched_kw, spir, spir_lsqr, step2_updates, wedin_bound,
+    real_embedding, as_real, as_complex, solve_complex, kw_relative_complex)

@@ -571,3 +571,63 @@ def wedin_bound(kappa, normA, x, resid, u=U_ROUNDOFF):
     Fact 2.4 (Wedin) with eps = u, 2.23 kappa (||x|| + kappa ||r|| / ||A||) u / ||x||."""
     nx = float(np.linalg.norm(x))
     return 2.23 * kappa * (nx + kappa * resid / normA) * u / nx
+
+
+# ---------------------------------------------------------------------------
+# Complex problems (the Prony experiment, Sec. 5 "Runtime and iteration
+# count" and the appendix on Prony's method: A in C^{m x n}, b in C^m)
+# ---------------------------------------------------------------------------
+
+def real_embedding(A):
+    """The real 2m x 2n matrix of a complex m x n one, rows and columns
+    interleaved:
+
+        E[2i,   2k] = Re a_ik,   E[2i,   2k+1] = -Im a_ik,
+        E[2i+1, 2k] = Im a_ik,   E[2i+1, 2k+1] =  Re a_ik,
+
+    so that E [Re x_0, Im x_0, Re x_1, ...] is A x with its real and
+    imaginary parts interleaved: ||E x_r|| = ||A x||, E^T E is the embedding
+    of A^H A (each singular value of A twice), and the complex least-squares
+    problem min ||b - A x|| is the real one min ||b_r - E x_r|| with b_r, x_r
+    the interleaved parts.  ||E||_F = sqrt(2) ||A||_F."""
+    A = np.asarray(A, dtype=np.complex128)
+    m, n = A.shape
+    E = np.empty((2 * m, 2 * n), dtype=np.float64)
+    E[0::2, 0::2] = A.real
+    E[0::2, 1::2] = -A.imag
+    E[1::2, 0::2] = A.imag
+    E[1::2, 1::2] = A.real
+    return E
+
+
+def as_real(v):
+    """Interleaved real view [Re v_0, Im v_0, Re v_1, ...] of a complex vector."""
+    return np.ascontiguousarray(np.asarray(v, dtype=np.complex128)).view(np.float64).copy()
+
+
+def as_complex(v):
+    """The complex vector of an interleaved real one."""
+    return np.ascontiguousarray(np.asarray(v, dtype=np.float64)).view(np.complex128).copy()
+
+
+def solve_complex(method, A, b, **kw):
+    """FOSSILS / SPIR / LSQR-SPIR of a complex problem: the real method on its
+    real embedding (same solution), returning the complex x and the real
+    method's result dict."""
+    fn = {"fossils": fossils, "spir": spir, "spir_lsqr": spir_lsqr}[method]
+    res = fn(real_embedding(A), as_real(b), **kw)
+    return as_complex(res["x"]), res
+
+
+def kw_relative_complex(A, b, xhat, R_E=None):
+    """The Karlson-Walden estimate (Sec. 4.1) of a complex x relative to
+    ||A||_F, theta = ||A||_F / ||b||, evaluated on the real embedding with
+    that theta: the embedding keeps ||b||, ||x|| and ||r|| and maps A^H A and
+    A^H r to E^T E and E^T r_r, so the norm in the estimate is the same
+    number (||E||_F = sqrt(2) ||A||_F is why theta is passed).  R_E: the R
+    factor of the embedding, if already computed."""
+    A = np.asarray(A, dtype=np.complex128)
+    nA = float(np.linalg.norm(A))
+    theta = nA / float(np.linalg.norm(b))
+    return kw_estimate(real_embedding(A), as_real(b), as_real(xhat), theta=theta,
+                       R_A=R_E) / nA

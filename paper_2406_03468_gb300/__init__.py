@@ -15,7 +15,7 @@ from . import _build
 __all__ = [
     "LsqError", "LsqOptions", "LsqInfo", "lsq_options_default", "lsq_plan_create",
     "lsq_plan_destroy", "lsq_plan_configure", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir",
-    "lsq_solve_spir_lsqr", "lsq_solve_host",
+    "lsq_solve_spir_lsqr", "lsq_solve_host", "lsq_solve_complex",
     "lsq_solve_fossils_multi",
     "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_sketch_raw", "lsq_get_R", "lsq_apply_normal",
     "lsq_apply_normal_multi", "lsq_residual", "lsq_sketched_kw",
@@ -105,6 +105,8 @@ EXPORTED = {
     "lsq_solve_host": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(LsqInfo)]),
     "lsq_solve_fossils_multi": (_i32, [_vp, _vp, _vp, ctypes.c_int64, _vp,
                                        ctypes.POINTER(LsqInfo)]),
+    "lsq_solve_complex": (_i32, [_vp, _i32, _vp, ctypes.c_int64, _vp, _vp, _vp,
+                                 ctypes.POINTER(LsqInfo)]),
     "lsq_sketch_pattern": (_i32, [_vp, _vp, _vp]),
     "lsq_get_sketch": (_i32, [_vp, _vp, _vp]),
     "lsq_get_sketch_raw": (_i32, [_vp, _vp]),
@@ -219,6 +221,16 @@ def lsq_solve_spir(plan, A, b, x, info=None):
 
 def lsq_solve_spir_lsqr(plan, A, b, x, info=None):
     return _solve(_lib().lsq_solve_spir_lsqr, plan, A, b, x, info)
+
+
+def lsq_solve_complex(plan, method, A, b, x, work, lda=0, info=None):
+    """Complex least squares through the real embedding.  A (m x n), b (m), x
+    (n): complex128 device tensors; work: 4 m n doubles on the device; plan
+    created for (2m, 2n).  method: 0 FOSSILS, 1 SPIR, 2 LSQR-SPIR."""
+    inf = info if info is not None else LsqInfo()
+    st = _check(_lib().lsq_solve_complex(plan, int(method), _ptr(A), int(lda), _ptr(b), _ptr(x),
+                                         _ptr(work), ctypes.byref(inf)))
+    return st, inf
 
 
 def lsq_solve_fossils_multi(plan, A, B, ldb, X, info=None):

@@ -1079,6 +1079,25 @@ lsq_status lsq_solve_spir_lsqr(lsq_plan plan, const double *dA, const double *db
   return run_solve(plan, 2, dA, db, dx, info);
 }
 
+lsq_status lsq_solve_complex(lsq_plan plan, int method, const double *dA, int64_t lda,
+                             const double *db, double *dx, double *dwork, lsq_info *info) {
+  if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  lsq_plan P = plan;
+  if (!dA || !db || !dx || !dwork) return fail(LSQ_ERR_INVALID, "NULL argument");
+  if (method < 0 || method > 2) return fail(LSQ_ERR_INVALID, "method must be 0, 1 or 2");
+  if (P->m % 2 != 0 || P->n % 2 != 0)
+    return fail(LSQ_ERR_INVALID, "a complex solve needs a plan of 2m x 2n (even sizes)");
+  if (P->lda != P->n) return fail(LSQ_ERR_INVALID, "a complex solve needs the plan's lda = 2n");
+  const int64_t mc = P->m / 2;
+  const int nc = (int)(P->n / 2);
+  if (lda == 0) lda = nc;
+  if (lda < nc) return fail(LSQ_ERR_INVALID, "lda < n");
+  if ((reinterpret_cast<uintptr_t>(dA) & 15) != 0 || (reinterpret_cast<uintptr_t>(dwork) & 15) != 0)
+    return fail(LSQ_ERR_INVALID, "A and work must be 16-byte aligned");
+  LSQ_CU(launch_embed_complex(dA, lda, mc, nc, dwork, P->nsm, P->s));
+  return run_solve(P, method, dwork, db, dx, info);
+}
+
 lsq_status lsq_solve_fossils_multi(lsq_plan plan, const double *dA, const double *dB,
                                    int64_t ldb, double *dX, lsq_info *info) {
   if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");

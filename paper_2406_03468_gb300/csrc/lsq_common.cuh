@@ -185,6 +185,10 @@ cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad,
 // columns 0..n-1.  vhead: 2 n doubles (u_1, beta per reflector); flags: n ints,
 // flag k set to epoch when reflector k is published (epoch != 0, different
 // from the previous launch's).  Waits are bounded by timeout_ns.
+// Real embedding of a complex m x n row-major A (lda complex entries per row,
+// (re, im) interleaved, 16-byte aligned) into E (2m x 2n, row-major).
+cudaError_t launch_embed_complex(const double *A, int64_t lda, int64_t m, int n, double *E,
+                                 int nsm, cudaStream_t s);
 // With qb (and n, d in qr_blocked_ok's range) the blocked form of
 // k_qr_blocked.cu runs instead: same outputs, panels on qb->sp.
 struct QrBlocked {

@@ -17,7 +17,7 @@ import torch
 import oracle
 import paper_2406_03468_gb300 as lsq
 from gpu_util import H, T, empty
-from lsq_problems import problem_gaussian, problem_svd
+from lsq_problems import problem_gaussian, problem_prony, problem_svd
 
 pytestmark = pytest.mark.gpu
 
@@ -426,3 +426,59 @@ def test_kw_stop_step2(method, seed):
     if method == "fossils":
         ref = oracle.fossils(A, b, seed=seed, kw_stop=True)
         assert abs(k2 - ref["iters"][1]) <= 5, (k2, ref["iters"])
+
+
+@pytest.mark.parametrize("method", ["fossils", "spir", "spir_lsqr"])
+@pytest.mark.parametrize("m,n", [(20000, 40), (6001, 300)])
+def test_complex_prony(method, m, n):
+    """Complex least squares (the Prony experiment's first solve, synthetic:
+    Toeplitz A from noisy unit-modulus exponentials, condition ~1e6) through
+    the real embedding on the GPU: the complex Karlson-Walden backward error
+    <= 1e-13, the answer within 10x of the level LAPACK's complex solver and
+    the oracle (the same method on the same embedding and sketch seed) reach,
+    and the step counts of the oracle's run."""
+    P = problem_prony(m, n, seed=7)
+    A, b = P["A"], P["b"]
+    code = {"fossils": 0, "spir": 1, "spir_lsqr": 2}[method]
+    plan = lsq.Plan(2 * m, 2 * n, seed=5)
+    dA = torch.from_numpy(A).cuda()
+    db = torch.from_numpy(b).cuda()
+    dx = torch.empty(n, dtype=torch.complex128, device="cuda")
+    work = torch.empty(4 * m * n, dtype=torch.float64, device="cuda")
+    st, info = lsq.lsq_solve_complex(plan.handle, code, dA, db, dx, work)
+    assert st == 0
+    info = info.as_dict()
+    plan.close()
+    x = dx.cpu().numpy()
+    assert np.all(np.isfinite(x))
+    assert oracle.kw_relative_complex(A, b, x) <= 1e-13, info
+    xl = np.linalg.lstsq(A, b, rcond=None)[0]
+    xo, ref = oracle.solve_complex(method, A, b, seed=5)
+    e_l = np.linalg.norm(xo - xl) / np.linalg.norm(xl)
+    e_g = np.linalg.norm(x - xl) / np.linalg.norm(xl)
+    assert e_g <= 10 * max(e_l, 1e-14), (e_g, e_l)
+    assert abs(info["iters"][0] - ref["iters"][0]) <= 2, (info["iters"], ref["iters"])
+    assert abs(info["iters"][1] - ref["iters"][1]) <= 1, (info["iters"], ref["iters"])
+
+
+def test_complex_entry_errors():
+    """Argument checks of the complex entry: odd plan sizes, lda < n and a
+    misaligned A are refused before any launch; the plan then solves."""
+    P = problem_prony(2000, 8, seed=1)
+    A, b = P["A"], P["b"]
+    dA, db = torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()
+    dx = torch.empty(8, dtype=torch.complex128, device="cuda")
+    work = torch.empty(4 * 2000 * 8, dtype=torch.float64, device="cuda")
+    odd = lsq.Plan(4000, 15, seed=1)
+    with pytest.raises(lsq.LsqError):
+        lsq.lsq_solve_complex(odd.handle, 0, dA, db, dx, work)
+    odd.close()
+    plan = lsq.Plan(4000, 16, seed=1)
+    with pytest.raises(lsq.LsqError):
+        lsq.lsq_solve_complex(plan.handle, 0, dA, db, dx, work, lda=4)
+    with pytest.raises(lsq.LsqError):
+        lsq.lsq_solve_complex(plan.handle, 0, dA.data_ptr() + 8, db, dx, work)
+    st, _ = lsq.lsq_solve_complex(plan.handle, 0, dA, db, dx, work)
+    assert st == 0
+    assert oracle.kw_relative_complex(A, b, dx.cpu().numpy()) <= 1e-13
+    plan.close()
