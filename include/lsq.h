@@ -107,7 +107,10 @@ typedef struct {
                             (inner_kernel 0): the double-float pass holds A to 2^-48,
                             which leaves that step's answer a few u ||A||_F from
                             backward stable on kappa ~ 1e12 problems, above the bound */
-  int32_t reserved[4];
+  int32_t sparse;        /* 1: the plan solves CSR matrices (lsq_solve_csr) and allocates
+                            no FP32 planes or fixed-point copy of A; precision must be
+                            FP64, nrhs and kw_stop 0.  0 (default): dense A */
+  int32_t reserved[3];
 } lsq_options;
 
 #define LSQ_MAX_N 1024
@@ -196,6 +199,23 @@ lsq_status lsq_solve_spir(lsq_plan plan, const double *dA, const double *db, dou
  * FP32_INNER take the FP64 path). */
 lsq_status lsq_solve_spir_lsqr(lsq_plan plan, const double *dA, const double *db, double *dx,
                                lsq_info *info);
+
+/* FOSSILS (method 0), SPIR (1) or LSQR-based SPIR (2) for a sparse A in CSR
+ * form (the paper's SuiteSparse runs, Sec. 5 "Runtime and iteration count",
+ * where SPIR uses d = 3n: set opt.d).  The plan must have been created with
+ * opt.sparse = 1 for this m, n.  row_ptr: m + 1 int64 with row_ptr[0] = 0 and
+ * row_ptr[m] = nnz; col: nnz int32 column indices in [0, n), distinct within
+ * a row (any order); val: nnz FP64 values; db: m; dx: n (out); all device
+ * pointers, read-only except dx.  The sketch scatters the nonzeros (FP64
+ * atomics, so its rounding order is not fixed); the residual and inner
+ * passes run in FP64 over the nonzeros, one warp per row, deterministic for
+ * a fixed plan.  Everything after the sketch is the dense solve's.
+ * Errors: LSQ_ERR_INVALID (NULL, nnz < 0, a structure that is not CSR of an
+ * m x n matrix with nnz entries, a zero column, a dense plan),
+ * LSQ_ERR_NONFINITE, and those of the dense solve. */
+lsq_status lsq_solve_csr(lsq_plan plan, int method, int64_t nnz, const int64_t *row_ptr,
+                         const int32_t *col, const double *val, const double *db, double *dx,
+                         lsq_info *info);
 
 /* A complex least-squares problem min ||b - A x||, A in C^{m x n}, b in C^m
  * (the paper's Prony experiment, Sec. 5 "Runtime and iteration count", and

@@ -170,3 +170,53 @@ def problem_prony(m, n, seed, noise=1e-6, dt=0.25, spread=3.0):
     A = np.ascontiguousarray(f[idx])
     b = np.ascontiguousarray(f[n + np.arange(m)])
     return {"A": A, "b": b, "z": z, "mu": mu, "lam": lam}
+
+
+def problem_sparse(m, n, k, seed, delta=None, noise=1e-6):
+    """Sparse A in CSR form, a synthetic stand-in for the paper's SuiteSparse
+    matrices.  Each row holds k entries (k even, n even) in k / 2 column
+    pairs (2q, 2q + 1): the q of a row run through an arithmetic progression
+    modulo n / 2 with a random start and a random step coprime to n / 2, so
+    they are distinct.  A pair's values are (a, a (1 + delta xi)) with a, xi
+    standard normal (nearly dependent columns, condition ~ 1 / delta), or two
+    independent normals when delta is None.  Columns are then scaled by
+    10^U(-2, 2).  b = A x_true + noise g with x_true, g standard normal
+    (x_true over sqrt(n)).  Returns row_ptr (int64, m + 1), col (int32),
+    val (float64), b, x_true and the column scales."""
+    import math
+    rng = np.random.default_rng(seed)
+    assert k % 2 == 0 and n % 2 == 0 and k // 2 <= n // 2
+    h = n // 2
+    units = np.array([g for g in range(1, h + 1) if math.gcd(g, h) == 1], dtype=np.int64)
+    start = rng.integers(0, h, m)
+    step = units[rng.integers(0, len(units), m)]
+    q = (start[:, None] + np.arange(k // 2)[None, :] * step[:, None]) % h
+    q = np.sort(q, axis=1)
+    col = np.empty((m, k), dtype=np.int32)
+    col[:, 0::2] = 2 * q
+    col[:, 1::2] = 2 * q + 1
+    a = rng.standard_normal((m, k // 2))
+    val = np.empty((m, k))
+    val[:, 0::2] = a
+    if delta is None:
+        val[:, 1::2] = rng.standard_normal((m, k // 2))
+    else:
+        val[:, 1::2] = a * (1.0 + delta * rng.standard_normal((m, k // 2)))
+    scale = 10.0 ** rng.uniform(-2, 2, n)
+    val = val * scale[col]
+    row_ptr = np.arange(m + 1, dtype=np.int64) * k
+    col = col.ravel()
+    val = val.ravel()
+    x_true = rng.standard_normal(n) / np.sqrt(n)
+    Ax = (val.reshape(m, k) * x_true[col.reshape(m, k)]).sum(axis=1)
+    b = Ax + noise * rng.standard_normal(m)
+    return {"row_ptr": row_ptr, "col": col, "val": val, "b": b, "x_true": x_true,
+            "scale": scale}
+
+
+def csr_to_dense(P, m, n):
+    """The dense m x n matrix of problem_sparse's CSR arrays."""
+    A = np.zeros((m, n))
+    rows = np.repeat(np.arange(m), np.diff(P["row_ptr"]))
+    A[rows, P["col"]] = P["val"]
+    return A

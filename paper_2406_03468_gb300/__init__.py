@@ -15,7 +15,7 @@ from . import _build
 __all__ = [
     "LsqError", "LsqOptions", "LsqInfo", "lsq_options_default", "lsq_plan_create",
     "lsq_plan_destroy", "lsq_plan_configure", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir",
-    "lsq_solve_spir_lsqr", "lsq_solve_host", "lsq_solve_complex",
+    "lsq_solve_spir_lsqr", "lsq_solve_host", "lsq_solve_complex", "lsq_solve_csr",
     "lsq_solve_fossils_multi",
     "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_sketch_raw", "lsq_get_R", "lsq_apply_normal",
     "lsq_apply_normal_multi", "lsq_residual", "lsq_sketched_kw",
@@ -53,7 +53,7 @@ class LsqOptions(ctypes.Structure):
                 ("fixed_inner", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("inner_fp64_fma", ctypes.c_int32), ("nrhs", ctypes.c_int32),
                 ("qr_wait_us", ctypes.c_int32), ("kw_stop", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("sparse", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class LsqInfo(ctypes.Structure):
@@ -107,6 +107,8 @@ EXPORTED = {
                                        ctypes.POINTER(LsqInfo)]),
     "lsq_solve_complex": (_i32, [_vp, _i32, _vp, ctypes.c_int64, _vp, _vp, _vp,
                                  ctypes.POINTER(LsqInfo)]),
+    "lsq_solve_csr": (_i32, [_vp, _i32, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
+                             ctypes.POINTER(LsqInfo)]),
     "lsq_sketch_pattern": (_i32, [_vp, _vp, _vp]),
     "lsq_get_sketch": (_i32, [_vp, _vp, _vp]),
     "lsq_get_sketch_raw": (_i32, [_vp, _vp]),
@@ -221,6 +223,17 @@ def lsq_solve_spir(plan, A, b, x, info=None):
 
 def lsq_solve_spir_lsqr(plan, A, b, x, info=None):
     return _solve(_lib().lsq_solve_spir_lsqr, plan, A, b, x, info)
+
+
+def lsq_solve_csr(plan, method, row_ptr, col, val, b, x, info=None):
+    """Sparse A in CSR form: row_ptr (int64, m + 1), col (int32, nnz), val
+    (float64, nnz), b (m), x (n): device tensors; plan created with
+    sparse=1.  method: 0 FOSSILS, 1 SPIR, 2 LSQR-SPIR."""
+    inf = info if info is not None else LsqInfo()
+    nnz = int(val.numel()) if hasattr(val, "numel") else int(len(val))
+    st = _check(_lib().lsq_solve_csr(plan, int(method), nnz, _ptr(row_ptr), _ptr(col), _ptr(val),
+                                     _ptr(b), _ptr(x), ctypes.byref(inf)))
+    return st, inf
 
 
 def lsq_solve_complex(plan, method, A, b, x, work, lda=0, info=None):

@@ -100,6 +100,13 @@ struct lsq_plan_s {
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   QrBlocked qb{};                    // blocked QR: T workspace, panel stream, events
+  // CSR input of the solve in progress (lsq_solve_csr), else all NULL
+  struct {
+    const int64_t *rp = nullptr;
+    const int32_t *col = nullptr;
+    const double *val = nullptr;
+    int64_t nnz = 0;
+  } csr;
   bool condest_pending = false;
   double *stageA = nullptr, *stageb = nullptr, *stagex = nullptr;
   size_t stage_cap = 0;              // doubles of stageA
@@ -170,6 +177,9 @@ lsq_status validate(const lsq_options *o) {
   if (o->kw_stop != 0 && o->kw_stop != 1) return fail(LSQ_ERR_INVALID, "kw_stop must be 0 or 1");
   if (o->nrhs < 0 || (o->nrhs > 0 && !multi_supported((int)o->n, o->nrhs)))
     return fail(LSQ_ERR_INVALID, "nrhs must be a multiple of 8 in [8, 64] with n <= 256");
+  if (o->sparse != 0 && o->sparse != 1) return fail(LSQ_ERR_INVALID, "sparse must be 0 or 1");
+  if (o->sparse && (o->nrhs != 0 || o->kw_stop != 0 || o->precision != LSQ_PREC_FP64))
+    return fail(LSQ_ERR_INVALID, "a sparse plan needs precision FP64, nrhs = 0, kw_stop = 0");
   return LSQ_OK;
 }
 
@@ -310,7 +320,7 @@ bool planes_ok(lsq_plan P) {
 void choose_inner_kernel(lsq_plan P) {
   P->use_eft = false;
   P->use_df = false;
-  if (P->o.inner_fp64_fma) return;
+  if (P->o.inner_fp64_fma || P->csr.rp != nullptr) return;
   if (P->want32 && planes_ok(P)) {
     P->use_df = true;
     return;
@@ -332,7 +342,9 @@ void choose_inner_kernel(lsq_plan P) {
 // defer_planes: on the gather path the prep pass leaves the hi / lo planes to
 // the solve's first residual pass (planes_pending), which reads A anyway.
 lsq_status do_sketch(lsq_plan P, const double *dA, const double *db, bool defer_planes) {
-  if (!dA || !db) return fail(LSQ_ERR_INVALID, "A or b is NULL");
+  if (!db || (!dA && P->csr.rp == nullptr)) return fail(LSQ_ERR_INVALID, "A or b is NULL");
+  if (P->o.sparse && P->csr.rp == nullptr)
+    return fail(LSQ_ERR_INVALID, "the plan was created for CSR input (lsq_solve_csr)");
   const int n = (int)P->n;
   P->launches = 0;
   P->tev_used = 0;
@@ -353,7 +365,20 @@ lsq_status do_sketch(lsq_plan P, const double *dA, const double *db, bool defer_
   const int nch = P->host_chunks;
   P->host_chunks = 0;
   P->planes_pending = false;
-  if (P->use_gather) {
+  if (P->csr.rp != nullptr) {
+    // the structure and values first: a bad index must stop the solve before
+    // any kernel indexes with it
+    LSQ_CU(launch_csr_check(P->csr.rp, P->csr.col, P->csr.val, P->m, n, P->csr.nnz, db, P->st,
+                            P->nsm, P->s));
+    LSQ_TRY(read_state(P));
+    if (P->st_host->err == LSQ_ERR_INVALID)
+      return fail(LSQ_ERR_INVALID, "not a CSR matrix of m x n with nnz entries");
+    if (P->st_host->nonfinite) return fail(LSQ_ERR_NONFINITE, "A or b holds NaN or Inf");
+    LSQ_CU(cudaMemsetAsync(P->SAb, 0, sizeof(double) * (size_t)P->d * (n + 1), P->s));
+    LSQ_CU(launch_csr_sketch(P->csr.rp, P->csr.col, P->csr.val, P->m, n, db, P->d, P->zeta,
+                             P->pat_rows, P->pat_sb, P->SAb, P->cpart, P->gpass, P->npad, P->s));
+    P->launches += 2;
+  } else if (P->use_gather) {
     const bool planes = P->want32 && !defer_planes;
     P->planes_pending = P->want32 && defer_planes;
     // one chunk, or the host entry's row chunks as their copies complete
@@ -472,7 +497,9 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
   const int q32 = tier ? tier_updates(P->st_host->condest, P->eta, max_inner) : 0;
   int q2 = -1;  // set from condest once step 1 has read the device state
   const int nsteps_max = tier ? std::min(LSQ_MAX_REFINE, std::max(nref, 6)) : nref;
-  const double mn8 = 8.0 * (double)P->m * (double)n;
+  // bytes of A per pass: 8 m n dense; 12 nnz + 8 (m + 1) for CSR
+  const double mn8 = P->csr.rp ? 12.0 * (double)P->csr.nnz + 8.0 * (double)(P->m + 1)
+                               : 8.0 * (double)P->m * (double)n;
   double bytes_a = mn8 + (P->want32 ? mn8 : 0.0);  // sketch pass (+ hi / lo planes)
   int passes = 1;
   int iters[LSQ_MAX_REFINE] = {0};
@@ -488,9 +515,15 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
     }
     const bool planes = P->planes_pending;
     P->planes_pending = false;
-    LSQ_CU(launch_pass_resid(dA, P->lda, P->m, n, db, P->xo, P->part, P->r2part, P->gpass,
-                             P->npad, P->s, planes ? P->Ahi : nullptr, planes ? P->Alo : nullptr,
-                             P->ld32, nullptr, nullptr, method == 2 ? P->lsqr_s : nullptr));
+    if (P->csr.rp)
+      LSQ_CU(launch_csr_pass(1, P->csr.rp, P->csr.col, P->csr.val, P->m, db, P->xo, P->part,
+                             P->r2part, P->gpass, P->npad, nullptr, nullptr,
+                             method == 2 ? P->lsqr_s : nullptr, P->s));
+    else
+      LSQ_CU(launch_pass_resid(dA, P->lda, P->m, n, db, P->xo, P->part, P->r2part, P->gpass,
+                               P->npad, P->s, planes ? P->Ahi : nullptr,
+                               planes ? P->Alo : nullptr, P->ld32, nullptr, nullptr,
+                               method == 2 ? P->lsqr_s : nullptr));
     if (tk >= 0) LSQ_CU(cudaEventRecord(P->tev[2 * tk + 1], P->s));
     P->launches += 3 + (i == 0 ? 1 : 0) + 1;  // resid, reduce, trsv, [thresh], init
     LSQ_CU(launch_reduce(P->part, P->gpass, P->npad, n, P->dinv, P->g, P->r2part, &P->st->r2,
@@ -541,7 +574,13 @@ lsq_status run_solve(lsq_plan P, int method, const double *dA, const double *db,
         inner_ev[i].push_back(tj);
         LSQ_CU(cudaEventRecord(P->tev[2 * tj], P->s));
       }
-      if (method == 2 && df)
+      if (P->csr.rp)
+        LSQ_CU(launch_csr_pass(method == 2 ? 1 : 0, P->csr.rp, P->csr.col, P->csr.val, P->m,
+                               method == 2 ? P->lsqr_s : nullptr, P->z, P->part, P->r2part,
+                               P->gpass, P->npad, P->st,
+                               method == 2 ? &P->st->lq_bscale : nullptr,
+                               method == 2 ? P->lsqr_s : nullptr, P->s));
+      else if (method == 2 && df)
         LSQ_CU(launch_pass_lsqr_df(P->Ahi, P->Alo, P->ld32, P->m, n, P->z, P->lsqr_s,
                                    &P->st->lq_bscale, P->part, P->r2part, P->gpass, P->npad, P->st,
                                    &P->st->err, P->s));
@@ -927,7 +966,7 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(dalloc(&P->pat_rows, (size_t)P->m_cap * P->zeta_cap));
   A(dalloc(&P->pat_sb, (size_t)P->m));
-  if (gather_size_ok(P->m_cap, n)) {
+  if (!opt->sparse && gather_size_ok(P->m_cap, n)) {
     A(dalloc(&P->tcnt, (size_t)P->d_cap));
     A(dalloc(&P->tptr, (size_t)P->d_cap + 1));
     A(dalloc(&P->tsrc, (size_t)P->m_cap * P->zeta_cap));
@@ -983,8 +1022,8 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
   A(cudaMallocHost((void **)&P->st_host, sizeof(DevState)));
   A(cudaMallocHost((void **)&P->dcol_host, sizeof(double) * n));
   // hi / lo FP32 planes of A: the double-float inner pass and the FP32 tier read them
-  if (!P->o.inner_fp64_fma || P->o.precision == LSQ_PREC_AUTO ||
-      P->o.precision == LSQ_PREC_FP32_INNER) {
+  if (!P->o.sparse && (!P->o.inner_fp64_fma || P->o.precision == LSQ_PREC_AUTO ||
+                       P->o.precision == LSQ_PREC_FP32_INNER)) {
     A(dalloc(&P->Ahi, (size_t)P->m_cap * ((n + 3) / 4 * 4)));
     A(dalloc(&P->Alo, (size_t)P->m_cap * ((n + 3) / 4 * 4)));
     P->want32 = true;
@@ -1077,6 +1116,28 @@ lsq_status lsq_solve_spir_lsqr(lsq_plan plan, const double *dA, const double *db
                                lsq_info *info) {
   if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
   return run_solve(plan, 2, dA, db, dx, info);
+}
+
+lsq_status lsq_solve_csr(lsq_plan plan, int method, int64_t nnz, const int64_t *row_ptr,
+                         const int32_t *col, const double *val, const double *db, double *dx,
+                         lsq_info *info) {
+  if (!plan) return fail(LSQ_ERR_INVALID, "plan is NULL");
+  lsq_plan P = plan;
+  if (!P->o.sparse) return fail(LSQ_ERR_INVALID, "the plan was not created with sparse = 1");
+  if (!row_ptr || !db || !dx || (nnz > 0 && (!col || !val)))
+    return fail(LSQ_ERR_INVALID, "NULL argument");
+  if (nnz < 0) return fail(LSQ_ERR_INVALID, "nnz < 0");
+  if (method < 0 || method > 2) return fail(LSQ_ERR_INVALID, "method must be 0, 1 or 2");
+  P->csr.rp = row_ptr;
+  P->csr.col = col;
+  P->csr.val = val;
+  P->csr.nnz = nnz;
+  const lsq_status st = run_solve(P, method, nullptr, db, dx, info);
+  P->csr.rp = nullptr;
+  P->csr.col = nullptr;
+  P->csr.val = nullptr;
+  P->csr.nnz = 0;
+  return st;
 }
 
 lsq_status lsq_solve_complex(lsq_plan plan, int method, const double *dA, int64_t lda,
@@ -1250,6 +1311,7 @@ lsq_status lsq_apply_normal_multi(lsq_plan P, const double *dA, const double *dZ
 lsq_status lsq_sketched_kw(lsq_plan P, const double *dA, const double *db, const double *dx,
                            double *est) {
   if (!P || !dA || !db || !dx || !est) return fail(LSQ_ERR_INVALID, "NULL argument");
+  if (P->o.sparse) return fail(LSQ_ERR_INVALID, "the sketched KW estimate needs dense A");
   if (!P->sketched) return fail(LSQ_ERR_INVALID, "call lsq_sketch first");
   const int n = (int)P->n;
   LSQ_CU(launch_scale_vec(n, P->dcol, dx, P->xk, P->s));  // x_s = D x

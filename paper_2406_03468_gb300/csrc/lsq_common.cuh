@@ -185,6 +185,22 @@ cudaError_t launch_sketch_finalize(const double *colsq_part, int grid, int npad,
 // columns 0..n-1.  vhead: 2 n doubles (u_1, beta per reflector); flags: n ints,
 // flag k set to epoch when reflector k is published (epoch != 0, different
 // from the previous launch's).  Waits are bounded by timeout_ns.
+// Sparse A in CSR form (k_csr.cu): the structure / value check (flags in
+// st), the scatter sketch with column sums of squares (partials as the dense
+// sketch's), and the passes: mode 0 inner (column sums of a_i (a_i . x)),
+// mode 1 residual (v = bs b - A x, rout, ||v||^2 partials, column sums of
+// a_i v_i); partials as the dense passes' (grid x npad).
+cudaError_t launch_csr_check(const int64_t *rp, const int32_t *col, const double *val, int64_t m,
+                             int n, int64_t nnz, const double *b, DevState *st, int nsm,
+                             cudaStream_t s);
+cudaError_t launch_csr_sketch(const int64_t *rp, const int32_t *col, const double *val, int64_t m,
+                              int n, const double *b, int d, int zeta, const int32_t *rows,
+                              const uint32_t *signbits, double *SAb, double *colsq_part, int grid,
+                              int npad, cudaStream_t s);
+cudaError_t launch_csr_pass(int mode, const int64_t *rp, const int32_t *col, const double *val,
+                            int64_t m, const double *b, const double *x, double *part,
+                            double *r2_part, int grid, int npad, const DevState *gate,
+                            const double *bscale, double *rout, cudaStream_t s);
 // Real embedding of a complex m x n row-major A (lda complex entries per row,
 // (re, im) interleaved, 16-byte aligned) into E (2m x 2n, row-major).
 cudaError_t launch_embed_complex(const double *A, int64_t lda, int64_t m, int n, double *E,

@@ -32,10 +32,11 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layout_matches_c(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include "lsq.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lsq_options), '
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lsq_options), '
                     'sizeof(lsq_info), offsetof(lsq_options, fixed_inner), '
                     'offsetof(lsq_info, ms_total), offsetof(lsq_options, qr_wait_us), '
-                    'sizeof(lsq_batch_item), offsetof(lsq_batch_item, status)); '
+                    'sizeof(lsq_batch_item), offsetof(lsq_batch_item, status), '
+                    'offsetof(lsq_options, sparse)); '
                     'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
@@ -47,6 +48,7 @@ def test_struct_layout_matches_c(tmp_path):
     assert int(out[4]) == lsq.LsqOptions.qr_wait_us.offset
     assert int(out[5]) == ctypes.sizeof(lsq.LsqBatchItem)
     assert int(out[6]) == lsq.LsqBatchItem.status.offset
+    assert int(out[7]) == lsq.LsqOptions.sparse.offset
 
 
 def test_defaults_and_validation_without_gpu():

@@ -17,7 +17,7 @@ import torch
 import oracle
 import paper_2406_03468_gb300 as lsq
 from gpu_util import H, T, empty
-from lsq_problems import problem_gaussian, problem_prony, problem_svd
+from lsq_problems import csr_to_dense, problem_gaussian, problem_prony, problem_sparse, problem_svd
 
 pytestmark = pytest.mark.gpu
 
@@ -482,3 +482,89 @@ def test_complex_entry_errors():
     assert st == 0
     assert oracle.kw_relative_complex(A, b, dx.cpu().numpy()) <= 1e-13
     plan.close()
+
+
+def _csr_dev(P):
+    return (torch.from_numpy(P["row_ptr"]).cuda(), torch.from_numpy(P["col"]).cuda(),
+            torch.from_numpy(P["val"]).cuda(), torch.from_numpy(P["b"]).cuda())
+
+
+@pytest.mark.parametrize("method", ["fossils", "spir", "spir_lsqr"])
+@pytest.mark.parametrize("m,n,k,delta,d3", [(20011, 130, 8, None, False), (6001, 300, 20, 1e-8, False),
+                                            (6001, 300, 20, 1e-8, True)])
+def test_sparse_csr(method, m, n, k, delta, d3):
+    """Sparse A (CSR; synthetic stand-in for the SuiteSparse runs, with SPIR's
+    d = 3n in one case) on the GPU against the oracle on the same matrix
+    densified: backward error <= 1e-13, forward error within 10x of the
+    oracle QR solve's against x_true, and the oracle's step counts (same
+    seed, so the same sketch pattern).  FOSSILS at d = 3n (eta = 0.58; the
+    paper pairs d = 3n with SPIR) does not meet the step-1 threshold within
+    100 updates at condition 3e8, in the oracle as on the GPU: there the GPU
+    must match the oracle's counts and backward error (within 2x)."""
+    P = problem_sparse(m, n, k, seed=3, delta=delta)
+    A = csr_to_dense(P, m, n)
+    b = P["b"]
+    d = 3 * n if d3 else 0
+    code = {"fossils": 0, "spir": 1, "spir_lsqr": 2}[method]
+    plan = lsq.Plan(m, n, seed=5, sparse=1, d=d)
+    rp, col, val, db = _csr_dev(P)
+    dx = empty(n)
+    st, info = lsq.lsq_solve_csr(plan.handle, code, rp, col, val, db, dx)
+    info = info.as_dict()
+    plan.close()
+    assert st == 0
+    x = H(dx)
+    x_qr, R_A = oracle.qr_solve(A, b, return_R=True)
+    ref = getattr(oracle, method)(A, b, seed=5, d=d or None)
+    be = oracle.kw_relative(A, b, x, R_A=R_A)
+    if method == "fossils" and d3:
+        be_ref = oracle.kw_relative(A, b, ref["x"], R_A=R_A)
+        assert ref["iters"][0] == 100 and be <= 2 * be_ref, (be, be_ref, info)
+    else:
+        assert be <= 1e-13, info
+        xt = P["x_true"]
+        assert oracle.forward_error(x, xt) <= 10 * max(oracle.forward_error(x_qr, xt), 1e-15)
+    assert abs(info["iters"][0] - ref["iters"][0]) <= 2, (info["iters"], ref["iters"])
+    assert abs(info["iters"][1] - ref["iters"][1]) <= 1, (info["iters"], ref["iters"])
+    assert info["inner_kernel"] == 0
+
+
+def test_sparse_csr_checks():
+    """The CSR entry refuses a structure that is not CSR of m x n with nnz
+    entries (a column index out of range, row_ptr[m] != nnz, a decreasing
+    row_ptr) and NaN values before any pass reads them; a dense plan refuses
+    CSR input and a sparse plan dense input; the plan then solves."""
+    m, n, k = 3001, 40, 6
+    P = problem_sparse(m, n, k, seed=9)
+    rp, col, val, db = _csr_dev(P)
+    dx = empty(n)
+    plan = lsq.Plan(m, n, seed=1, sparse=1)
+    bad = col.clone()
+    bad[17] = n
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.lsq_solve_csr(plan.handle, 0, rp, bad, val, db, dx)
+    assert e.value.status == -1
+    badp = rp.clone()
+    badp[m] -= 1
+    with pytest.raises(lsq.LsqError):
+        lsq.lsq_solve_csr(plan.handle, 0, badp, col, val, db, dx)
+    badp = rp.clone()
+    badp[5] = badp[7]
+    with pytest.raises(lsq.LsqError):
+        lsq.lsq_solve_csr(plan.handle, 0, badp, col, val, db, dx)
+    nanv = val.clone()
+    nanv[3] = float("nan")
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.lsq_solve_csr(plan.handle, 0, rp, col, nanv, db, dx)
+    assert e.value.status == -6
+    with pytest.raises(lsq.LsqError):
+        lsq.lsq_solve_fossils(plan.handle, T(csr_to_dense(P, m, n)), db, dx)
+    st, _ = lsq.lsq_solve_csr(plan.handle, 1, rp, col, val, db, dx)
+    assert st == 0
+    A = csr_to_dense(P, m, n)
+    assert oracle.kw_relative(A, P["b"], H(dx)) <= 1e-13
+    plan.close()
+    dense = lsq.Plan(m, n, seed=1)
+    with pytest.raises(lsq.LsqError):
+        lsq.lsq_solve_csr(dense.handle, 0, rp, col, val, db, dx)
+    dense.close()
