@@ -504,6 +504,54 @@ def complex_compare(lsq, torch, dev, steps, m=500000, n=256):
                       "seconds": time.perf_counter() - t0}}
 
 
+def sparse_compare(lsq, torch, dev, steps, m=500000, n=500, k=32):
+    """Sparse A in CSR form (a synthetic stand-in for the SuiteSparse runs:
+    k nonzeros per row in nearly dependent column pairs, condition ~1e8):
+    SPIR with d = 3n (the paper's sparse setting) and FOSSILS with d = 12n
+    through lsq_solve_csr, checked against the oracle's LAPACK Householder
+    solve of the densified matrix."""
+    import numpy as np
+    from lsq_problems import csr_to_dense, problem_sparse
+    P = problem_sparse(m, n, k, seed=8, delta=1e-8)
+    rp = torch.from_numpy(P["row_ptr"]).to(dev)
+    col = torch.from_numpy(P["col"]).to(dev)
+    val = torch.from_numpy(P["val"]).to(dev)
+    db = torch.from_numpy(P["b"]).to(dev)
+    out = {"workload": "sparse_csr_m%d_n%d_nnz%d" % (m, n, m * k)}
+    xs = {}
+    for name, method, d in (("spir_d3n", 1, 3 * n), ("fossils_d12n", 0, 12 * n)):
+        plan = lsq.Plan(m, n, seed=7, sparse=1, d=d, timing=1)
+        dx = torch.empty(n, dtype=torch.float64, device=dev)
+        lsq.lsq_solve_csr(plan.handle, method, rp, col, val, db, dx)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            _, info = lsq.lsq_solve_csr(plan.handle, method, rp, col, val, db, dx)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        info = info.as_dict()
+        plan.close()
+        xs[name] = dx.cpu().numpy()
+        out[name] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iters": info["iters"],
+                     "passes": info["passes"], "ms_inner_pass": info["ms_inner_pass"],
+                     "phase_ms": {"sketch": info["ms_sketch"], "qr": info["ms_qr"],
+                                  "refine": info["ms_refine"]}}
+    del rp, col, val, db
+    torch.cuda.empty_cache()
+    import oracle
+    t0 = time.perf_counter()
+    A = csr_to_dense(P, m, n)
+    x_qr, R_A = oracle.qr_solve_lapack(A, P["b"], return_R=True)
+    for name, x in xs.items():
+        out[name]["check"] = check_x(A, P["b"], x, x_qr, R_A, x_true=P["x_true"])
+    out["check_seconds"] = time.perf_counter() - t0
+    del A
+    return out
+
+
 def serve_compare(lsq, torch, dev, count=512, slots=8):
     """Config 3: a stream of `count` independent problems (m log-uniform in
     [2e4, 4e5], n in {32, 64, 128, 256}, kappa log-uniform in [1e2, 1e12],
@@ -802,6 +850,7 @@ def run_ours(args):
     tier = None
     multi = None
     cplx = None
+    sparse = None
     served = None
     if not args.no_tier and not args.rows and not args.cols:
         del A, b
@@ -809,6 +858,7 @@ def run_ours(args):
         tier = tier_compare(lsq, torch, dev, max(2, args.steps // 3))
         multi = multi_compare(lsq, torch, dev, 2)
         cplx = complex_compare(lsq, torch, dev, 3)
+        sparse = sparse_compare(lsq, torch, dev, 3)
         served = serve_compare(lsq, torch, dev)
 
     # every timed result against the oracle (after the timed regions)
@@ -835,7 +885,7 @@ def run_ours(args):
         oks = [v["ok"] for v in accuracy.values() if isinstance(v, dict)]
         if cplx:
             oks.append(cplx["check"]["ok"])
-        for part in (tier, multi, served):
+        for part in (tier, multi, sparse, served):
             if not part:
                 continue
             for v in part.values():
@@ -874,6 +924,7 @@ def run_ours(args):
                                   "fp32_tier_1e6x1000": tier,
                                   "multi_rhs_2e6x200_k64": multi,
                                   "complex_prony_5e5x256": cplx,
+                                  "sparse_csr_5e5x500": sparse,
                                   "served_stream": served}),
                 "accuracy": accuracy, "checks_passed": checks_ok,
                 "clocks": clocks, "e2e": e2e,
