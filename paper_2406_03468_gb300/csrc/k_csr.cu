@@ -5,10 +5,11 @@
 // after the sketch (QR, triangular solves, refinement) is the dense path's.
 //
 // GB300 design.  A sparse row is a few hundred bytes, so a pass is bound by
-// the FP64 pipe and the row reductions, not by HBM: one warp per row, the
-// row product reduced by shuffles, and the column sums A^T v accumulated by
-// each warp in its own shared-memory copy of the n column sums (a row's
-// column indices are distinct, so a warp's lanes never collide).  The CTA
+// the FP64 pipe and the row reductions, not by HBM: a warp takes 4 rows at a
+// time, reduces their 4 row products together by shuffles, and accumulates
+// the column sums A^T v one row at a time in its own shared-memory copy of
+// the n column sums (a row's column indices are distinct, so a warp's lanes
+// never collide).  The CTA
 // then adds its warps' copies in warp order into its partial, and the
 // partials go through the dense path's fixed-order reduction: the passes are
 // deterministic for a fixed grid.  The sketch scatters each nonzero into its
@@ -87,11 +88,31 @@ __global__ void __launch_bounds__(kCsrThreads)
   csr_flush(csm, npad, colsq_part);
 }
 
+// The row products of 4 rows reduced together: lane L holds partials v[0..3]
+// of rows 0..3; after the exchange across 16 lanes (2 adds), across 8 lanes
+// (1 add) and three butterfly levels (3 adds) lane L holds the full sum of
+// row 2 (L >> 4) + ((L >> 3) & 1): 6 FP64 adds for 4 rows instead of 20
+// (GB300 issues one FP64 warp instruction per 64 cycles per sub-partition).
+// The tree is fixed, so the sums are deterministic.
+__device__ __forceinline__ double reduce4(const double (&v)[4], int lane) {
+  const bool h16 = lane >= 16, h8 = (lane & 8) != 0;
+  const double s0 = h16 ? v[0] : v[2], s1 = h16 ? v[1] : v[3];
+  const double k0 = h16 ? v[2] : v[0], k1 = h16 ? v[3] : v[1];
+  const double w0 = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
+  const double w1 = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
+  double u = (h8 ? w1 : w0) + __shfl_xor_sync(0xffffffffu, h8 ? w0 : w1, 8);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+  return u;
+}
+
 // One pass over the rows.  MODE 0 (inner pass): v_i = a_i . x.  MODE 1
 // (residual pass): v_i = bs b_i - a_i . x with bs = *bscale (1 when NULL),
 // written to rout[i] when rout != NULL, and ||v||^2 partials into r2_part.
-// Both: the column sums sum_i a_i v_i into part[blockIdx.x].  gate: skip the
-// launch once gate->done is set (the inner loop's stop).
+// Both: the column sums sum_i a_i v_i into part[blockIdx.x].  A warp takes
+// 4 consecutive rows at a time: their row products together (reduce4), then
+// each row's column sums with the whole warp.  gate: skip the launch once
+// gate->done is set (the inner loop's stop).
 template <int MODE>
 __global__ void __launch_bounds__(kCsrThreads)
     csr_pass_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
@@ -110,22 +131,35 @@ __global__ void __launch_bounds__(kCsrThreads)
   double r2 = 0.0;
   int64_t r0, r1;
   csr_rows(m, r0, r1);
-  for (int64_t i = r0 + warp; i < r1; i += kCsrWarps) {
-    const int64_t beg = rp[i], end = rp[i + 1];
-    double t = 0.0;
-    for (int64_t p = beg + lane; p < end; p += 32) t = fma(val[p], __ldg(x + col[p]), t);
-    t = warp_sum(t);
-    double v = t;
-    if (MODE == 1) {
-      v = (bscale != nullptr ? bs * b[i] : b[i]) - t;
-      r2 = fma(v, v, r2);
-      if (rout != nullptr && lane == 0) rout[i] = v;
+  for (int64_t i0 = r0 + 4 * warp; i0 < r1; i0 += 4 * kCsrWarps) {
+    int64_t beg[4], end[4];
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const bool in = i0 + q < r1;
+      beg[q] = in ? rp[i0 + q] : 0;
+      end[q] = in ? rp[i0 + q + 1] : 0;
+      double t = 0.0;
+      for (int64_t p = beg[q] + lane; p < end[q]; p += 32) t = fma(val[p], __ldg(x + col[p]), t);
+      v[q] = t;
     }
-    for (int64_t p = beg + lane; p < end; p += 32) {
-      const int j = col[p];
-      hw[j] = fma(val[p], v, hw[j]);
+    const double u = reduce4(v, lane);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (i0 + q >= r1) break;
+      const double t = __shfl_sync(0xffffffffu, u, ((q & 2) ? 16 : 0) + ((q & 1) ? 8 : 0));
+      double c = t;
+      if (MODE == 1) {
+        c = (bscale != nullptr ? bs * b[i0 + q] : b[i0 + q]) - t;
+        r2 = fma(c, c, r2);
+        if (rout != nullptr && lane == 0) rout[i0 + q] = c;
+      }
+      for (int64_t p = beg[q] + lane; p < end[q]; p += 32) {
+        const int j = col[p];
+        hw[j] = fma(val[p], c, hw[j]);
+      }
+      __syncwarp();
     }
-    __syncwarp();
   }
   if (MODE == 1 && lane == 0) r2w[warp] = r2;
   csr_flush(csm, npad, part);
