@@ -61,10 +61,12 @@ __device__ __forceinline__ void note_timeout(DevState *st) {
 
 // dynamic shared memory of the panel kernel: 32 doubles for the mbarriers,
 // the panel rows (kQb x S), the messages (kQb steps x pc CTAs x 2 kQb), U,
-// T, the recursion scratch and the per-step scalars
+// T, the recursion scratch, the per-step scalars and the partial sums of the
+// CTAs' messages
+constexpr int kSumWarps = 4;  // warps adding the CTAs' partials of a step
 size_t panel_smem_bytes(int S, int pc) {
   return sizeof(double) * (32 + (size_t)kQb * S + (size_t)kQb * pc * 2 * kQb +
-                           2 * kQb * kQb + kQb * kQb / 2 + 4 * kQb);
+                           2 * kQb * kQb + kQb * kQb / 2 + 4 * kQb + kSumWarps * 32);
 }
 
 __global__ void __launch_bounds__(kQbThreads, 1)
@@ -83,6 +85,7 @@ __global__ void __launch_bounds__(kQbThreads, 1)
   double *wsh = Xs + kQb * kQb / 2;                    // w_j of a step
   double *Tg = wsh + kQb;                              // beta per column
   double *rsh = Tg + kQb;                              // u_1, R_kk of a step
+  double *ps = rsh + 2 * kQb;                          // kSumWarps x 32 partial sums
   const int Lp = d - kb;                               // trailing rows of the panel
   const int r0 = (int)rank * S;                        // this CTA's first panel row
   const int nr = max(0, min(S, Lp - r0));
@@ -138,14 +141,27 @@ __global__ void __launch_bounds__(kQbThreads, 1)
       st_async_f64(cluster_addr(mine + e, dst), mine[e], cluster_addr(bars + k, dst));
     }
     if (!xfer_wait_limit(bars + k, timeout_ns)) ok = false;
-    // warp 0: the summed message (CTAs in rank order), the reflector, w_j for
-    // the columns j > k and the Gram column y_c^T y_k (c < k); the other
-    // warps wait at the barrier (GB300 runs FP64 sqrt and divide at the FP64
-    // pipe's rate: once per step, not once per warp)
+    // the CTAs' messages summed: warp w < kSumWarps adds CTAs
+    // w pc / kSumWarps .. in rank order, then warp 0 adds the kSumWarps sums
+    // in warp order (a fixed tree: the same bits in every CTA; each FP64 add
+    // of a dependent chain costs ~67 cycles, so 4 + 3 adds instead of 16)
+    if (warp < kSumWarps && lane < msz) {
+      const unsigned per = pc / kSumWarps;
+      double s4 = 0.0;
+      for (unsigned r = warp * per; r < (warp + 1) * per; r++) s4 += mk[(size_t)r * 2 * kQb + lane];
+      ps[warp * 32 + lane] = s4;
+    }
+    __syncthreads();
+    // warp 0: the reflector, w_j for the columns j > k and the Gram column
+    // y_c^T y_k (c < k); the other warps wait at the barrier (GB300 runs FP64
+    // sqrt and divide at the FP64 pipe's rate: once per step, not once per
+    // warp)
     if (warp == 0) {
       double sv = 0.0;
-      if (lane < msz)
-        for (unsigned r = 0; r < pc; r++) sv += mk[(size_t)r * 2 * kQb + lane];
+      if (lane < msz) {
+        sv = ps[lane];
+        for (int w = 1; w < kSumWarps; w++) sv += ps[w * 32 + lane];
+      }
       const double sk = __shfl_sync(0xffffffffu, sv, k);
       const double x1 = __shfl_sync(0xffffffffu, sv, bw + k);
       const double rowj = __shfl_sync(0xffffffffu, sv, (bw + lane) & 31);
@@ -429,9 +445,12 @@ cudaError_t launch_update(double *W, int d, int kb, int bw, int c0, int c1, int 
 
 bool qr_blocked_ok(int d, int n) {
   if (n < kQbMinN || d < n) return false;
-  // the panel's rows must fit the shared memory of a cluster of 8 (16 is
-  // checked at launch time and only widens the range)
-  return panel_smem_bytes(rows_per_cta(d, 8), 8) <= kQbSmemMax;
+  // the panel's rows must fit the shared memory of the panel cluster
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  const int pc = panel_cluster(dev, panel_smem_bytes(rows_per_cta(d, 16), 16));
+  return panel_smem_bytes(rows_per_cta(d, pc), pc) <= kQbSmemMax ||
+         panel_smem_bytes(rows_per_cta(d, 8), 8) <= kQbSmemMax;
 }
 
 size_t qr_blocked_tws(int n) { return (size_t)((n + kQb - 1) / kQb) * kQb * kQb; }

@@ -77,7 +77,8 @@ def test_sketch_and_column_norms(m, n, lda):
     assert (np.abs(SAb[:, n] - Sb) <= bound_b).all()
 
 
-@pytest.mark.parametrize("m,n", [(20011, 130), (4000, 50), (3001, 7), (60000, 500), (13001, 1000)])
+@pytest.mark.parametrize("m,n", [(20011, 130), (4000, 50), (3001, 7), (60000, 500), (13001, 1000),
+                                 (13001, 1024)])
 def test_qr_of_sketch(m, n):
     P, A = _problem(m, n, 1e3, seed=2)
     plan = lsq.Plan(m, n, seed=4)
