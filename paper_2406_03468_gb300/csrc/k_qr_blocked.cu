@@ -59,6 +59,31 @@ __device__ __forceinline__ void note_timeout(DevState *st) {
   atomicCAS(&st->err, 0, (int)LSQ_ERR_TIMEOUT);
 }
 
+// The warp totals of 16 per-lane sums by recursive halving: at each of four
+// exchanges a lane keeps half of its values and adds its partner's copies of
+// them, then one last exchange completes the 32-lane sum.  8 + 4 + 2 + 1 + 1
+// FP64 adds per lane instead of 16 x 5 for 16 separate butterflies (each
+// FP64 add holds the sub-partition's FP64 pipe about 64 cycles).  Lane L
+// returns the total of acc[L >> 1]: bit 4 of L picks the half kept first,
+// bits 3, 2 and 1 the next halves.  A fixed order: the same bits every run.
+__device__ __forceinline__ double warp_sum16(const double (&acc)[kQb], int lane) {
+  static_assert(kQb == 16, "four halvings of 16 values");
+  double a8[8], a4[4], a2[2];
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+#pragma unroll
+  for (int i = 0; i < 8; i++)
+    a8[i] = (h4 ? acc[8 + i] : acc[i]) +
+            __shfl_xor_sync(0xffffffffu, h4 ? acc[i] : acc[8 + i], 16);
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+    a4[i] = (h3 ? a8[4 + i] : a8[i]) + __shfl_xor_sync(0xffffffffu, h3 ? a8[i] : a8[4 + i], 8);
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+    a2[i] = (h2 ? a4[2 + i] : a4[i]) + __shfl_xor_sync(0xffffffffu, h2 ? a4[i] : a4[2 + i], 4);
+  const double a1 = (h1 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h1 ? a2[0] : a2[1], 2);
+  return a1 + __shfl_xor_sync(0xffffffffu, a1, 1);
+}
+
 // dynamic shared memory of the panel kernel: 32 doubles for the mbarriers,
 // the panel rows (kQb x S), the messages (kQb steps x pc CTAs x 2 kQb), U,
 // T, the recursion scratch, the per-step scalars and the partial sums of the
@@ -256,6 +281,7 @@ __global__ void __launch_bounds__(kQbThreads, 2)
   constexpr int WPC = kQbWarps / CPB, MS = kQb * CPB;
   __shared__ __align__(16) double msg[kMaxClusterQ * MS];
   __shared__ double part[kQbWarps * kQb], wsum[MS], wp[MS], u1s[kQb], Ts[kQb * kQb];
+  __shared__ double grp[4 * MS];  // four partial sums per entry (fixed trees below)
   __shared__ uint64_t bar;
   const unsigned rank = cluster_rank(), uc = cluster_nranks();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -298,11 +324,9 @@ __global__ void __launch_bounds__(kQbThreads, 2)
         if (k < bw) acc[k] = fma(__ldg(Y + (size_t)k * d + gi), c, acc[k]);
     }
   }
-#pragma unroll
-  for (int k = 0; k < kQb; k++) acc[k] = warp_sum(acc[k]);
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < kQb; k++) part[warp * kQb + k] = acc[k];
+  {
+    const double v = warp_sum16(acc, lane);
+    if ((lane & 1) == 0) part[warp * kQb + (lane >> 1)] = v;
   }
   __syncthreads();
   double *mine = msg + (size_t)rank * MS;
@@ -319,19 +343,29 @@ __global__ void __launch_bounds__(kQbThreads, 2)
     st_async_f64(cluster_addr(mine + e, dst), mine[e], cluster_addr(&bar, dst));
   }
   const bool ok = xfer_wait_limit(&bar, timeout_ns);
-  if (tid < MS) {
+  // the CTAs' partials summed in four groups of ranks, then the four group
+  // sums (chains of uc / 4 + 2 dependent adds instead of uc)
+  static_assert(4 * MS <= kQbThreads, "a thread per group and entry");
+  const int gq = tid / MS, ge = tid % MS;
+  if (tid < 4 * MS) {
+    const int per = ((int)uc + 3) / 4, rlo = gq * per, rhi = min((int)uc, rlo + per);
     double v = 0.0;
-    for (unsigned r = 0; r < uc; r++) v += msg[(size_t)r * MS + tid];
-    wsum[tid] = v;
+    for (int r = rlo; r < rhi; r++) v += msg[(size_t)r * MS + ge];
+    grp[tid] = v;
   }
   __syncthreads();
-  // (T^T (Y^T C))[k][c] = sum_{a <= k} T[a][k] (Y^T C)[a][c]
-  if (tid < MS) {
-    const int k = tid / CPB, c = tid % CPB;
+  if (tid < MS) wsum[tid] = (grp[tid] + grp[MS + tid]) + (grp[2 * MS + tid] + grp[3 * MS + tid]);
+  __syncthreads();
+  // (T^T (Y^T C))[k][c] = sum_{a <= k} T[a][k] (Y^T C)[a][c], the terms
+  // a = 4 q .. 4 q + 3 by group q, then the four group sums
+  if (tid < 4 * MS) {
+    const int k = ge / CPB, c = ge % CPB, ahi = min(k, 4 * gq + 3);
     double v = 0.0;
-    for (int a = 0; a <= k; a++) v = fma(Ts[a + k * kQb], wsum[a * CPB + c], v);
-    wp[tid] = v;
+    for (int a = 4 * gq; a <= ahi; a++) v = fma(Ts[a + k * kQb], wsum[a * CPB + c], v);
+    grp[tid] = v;
   }
+  __syncthreads();
+  if (tid < MS) wp[tid] = (grp[tid] + grp[MS + tid]) + (grp[2 * MS + tid] + grp[3 * MS + tid]);
   __syncthreads();
   if (has) {
     double wv[kQb];
