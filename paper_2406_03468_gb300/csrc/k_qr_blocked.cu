@@ -48,7 +48,6 @@ namespace {
 constexpr int kQb = 16;                     // panel width
 constexpr int kQbThreads = 256;
 constexpr int kQbWarps = kQbThreads / 32;
-constexpr int kUpdCols = kQbWarps;          // columns per update CTA (one warp each)
 static_assert(kQb == 2 * kQbWarps, "the panel's warps take two columns each");
 constexpr int kMaxClusterQ = 16;
 constexpr int kQbMinN = 64;                 // below: the column-by-column kernel
@@ -82,6 +81,32 @@ __device__ __forceinline__ double warp_sum16(const double (&acc)[kQb], int lane)
     a2[i] = (h2 ? a4[2 + i] : a4[i]) + __shfl_xor_sync(0xffffffffu, h2 ? a4[i] : a4[2 + i], 4);
   const double a1 = (h1 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h1 ? a2[0] : a2[1], 2);
   return a1 + __shfl_xor_sync(0xffffffffu, a1, 1);
+}
+
+// A double with its sign bit set to `neg`, by its bit pattern (no FP64
+// instruction).
+__device__ __forceinline__ double with_sign(double x, bool neg) {
+  return __hiloint2double((__double2hiint(x) & 0x7fffffff) | (neg ? (int)0x80000000 : 0),
+                          __double2loint(x));
+}
+
+// The reflector's scalars of a column from the sum of squares sk of its
+// trailing part x and its first entry x1: nx = ||x|| = sqrt(sk),
+// s = nx with the sign of x1 (+ for x1 = +-0), so that u_1 = x1 + s and
+// R_kk = -s, and yy = nx (nx + |x1|) = 1 / beta (beta = 0 when sk = 0).  On
+// GB300 every FP64 instruction, a compare included, holds its sub-partition's
+// FP64 pipe about 65 cycles and these scalars are on every panel step's
+// critical path, so the signs, the absolute value and the zero test are taken
+// on the bit patterns.
+__device__ __forceinline__ void reflector_scalars(double sk, double x1, double &s, double &yy,
+                                                  double &beta) {
+  const double nx = sqrt(sk);
+  const int xh = __double2hiint(x1);
+  const bool neg = xh < 0 && ((xh & 0x7fffffff) | __double2loint(x1)) != 0;
+  s = with_sign(nx, neg);
+  yy = nx * (nx + with_sign(x1, false));
+  const bool zero = ((__double2hiint(sk) & 0x7fffffff) | __double2loint(sk)) == 0;
+  beta = zero ? 0.0 : 1.0 / yy;
 }
 
 // dynamic shared memory of the panel kernel: 32 doubles for the mbarriers,
@@ -119,9 +144,22 @@ __global__ void __launch_bounds__(kQbThreads, 1)
     for (int k = 0; k < bw; k++) xfer_bar_init(bars + k, 8u * (pc - 1) * (unsigned)msz);
     fence_mbarrier_init_cluster();
   }
-  for (int j = 0; j < bw; j++) {
-    const double *src = W + (size_t)(kb + j) * d + kb + r0;
-    for (int i = tid; i < nr; i += kQbThreads) P[(size_t)j * S + i] = src[i];
+  // the panel's rows into shared memory, kBatch loads in flight per thread
+  // (one L2 round trip per batch instead of one per element)
+  constexpr int kBatch = 4;
+  const int tot = bw * nr;
+  for (int base = 0; base < tot; base += kBatch * kQbThreads) {
+    double v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; u++) {
+      const int t = base + u * kQbThreads + tid, j = nr > 0 ? t / nr : 0;
+      v[u] = t < tot ? W[(size_t)(kb + j) * d + kb + r0 + (t - j * nr)] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; u++) {
+      const int t = base + u * kQbThreads + tid, j = nr > 0 ? t / nr : 0;
+      if (t < tot) P[(size_t)j * S + (t - j * nr)] = v[u];
+    }
   }
   for (int i = tid; i < kQb * kQb; i += kQbThreads) U[i] = 0.0;
   __syncthreads();
@@ -190,22 +228,22 @@ __global__ void __launch_bounds__(kQbThreads, 1)
       const double sk = __shfl_sync(0xffffffffu, sv, k);
       const double x1 = __shfl_sync(0xffffffffu, sv, bw + k);
       const double rowj = __shfl_sync(0xffffffffu, sv, (bw + lane) & 31);
-      const double nx = sqrt(sk);
-      const double sg = x1 >= 0.0 ? 1.0 : -1.0;
-      const double yy = nx * (nx + fabs(x1));  // y_k^T y_k / 2 = 1 / beta
-      const double beta = nx > 0.0 ? 1.0 / yy : 0.0;
-      const double g = sv + sg * nx * rowj;     // y_k^T c_j (j >= k), y_j^T y_k (j < k)
+      double sn, yy, beta;  // sign(x1) ||x||, y_k^T y_k / 2, beta
+      reflector_scalars(sk, x1, sn, yy, beta);
+      const double g = fma(sn, rowj, sv);  // y_k^T c_j (j >= k), y_j^T y_k (j < k)
+      const double w = beta * g;
       if (lane < bw) {
-        if (lane > k) wsh[lane] = beta * g;
+        if (lane > k) wsh[lane] = w;
         if (lane < k) U[lane + k * kQb] = g;
       }
       if (lane == 0) {
+        const double u1 = x1 + sn;
         U[k + k * kQb] = yy;
         Tg[k] = beta;
-        rsh[0] = x1 + sg * nx;  // u_1
-        rsh[1] = -sg * nx;      // R_kk
+        rsh[0] = u1;
+        rsh[1] = with_sign(sn, __double2hiint(sn) >= 0);  // R_kk = -sn
         if (rank == 0) {
-          vhead[2 * (kb + k)] = x1 + sg * nx;
+          vhead[2 * (kb + k)] = u1;
           vhead[2 * (kb + k) + 1] = beta;
         }
       }
@@ -254,9 +292,9 @@ __global__ void __launch_bounds__(kQbThreads, 1)
       __syncthreads();
     }
   }
-  for (int j = 0; j < bw; j++) {
-    double *dst = W + (size_t)(kb + j) * d + kb + r0;
-    for (int i = tid; i < nr; i += kQbThreads) dst[i] = P[(size_t)j * S + i];
+  for (int t = tid; t < tot; t += kQbThreads) {
+    const int j = t / nr;
+    W[(size_t)(kb + j) * d + kb + r0 + (t - j * nr)] = P[(size_t)j * S + (t - j * nr)];
   }
   if (rank == 0)
     for (int i = tid; i < kQb * kQb; i += kQbThreads) Tp[i] = T[i];
