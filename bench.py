@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tier", action="store_true",
                     help="skip the tier / many-RHS / served comparisons")
-    ap.add_argument("--profile-case", default="", choices=["", "tier", "multi", "qr"],
+    ap.add_argument("--profile-case", default="", choices=["", "tier", "multi", "qr", "resid"],
                     help="run small solves of one path for ncu captures (no bench line)")
     ap.add_argument("--rows", type=int, default=0,
                     help="override m (small cases for ncu captures; not a bench line)")
@@ -996,7 +996,9 @@ def run_profile_case(args):
     """Small cases for ncu captures: `tier` = FP32-inner FOSSILS on m x 1000
     (m = --rows, default 2e5; kappa 1e4), `multi` = 64 right-hand sides on 2e5 x 200 (kappa 1e8), `qr` =
     FOSSILS on 30000 x n (n = --cols, default 500; kappa 1e8), whose sketch
-    has the bench workload's d = 12n rows, for the QR kernels."""
+    has the bench workload's d = 12n rows, for the QR kernels, `resid` = FOSSILS
+    on m x n (m = --rows, default 2e5; n = --cols, default 500; kappa 1e10), the
+    bench workload's width with A larger than L2, for the FP64 residual pass."""
     import numpy as np
     import torch
     import paper_2406_03468_gb300 as lsq
@@ -1007,6 +1009,14 @@ def run_profile_case(args):
         P = problem_gaussian(30000, n, 1e8, 1e-6, seed=51)
         A, b = torch.from_numpy(P["A"]).to(dev), torch.from_numpy(P["b"]).to(dev)
         plan = lsq.Plan(30000, n, seed=7)
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        for _ in range(max(1, args.steps)):
+            st, info = lsq.lsq_solve_fossils(plan.handle, A, b, x)
+    elif args.profile_case == "resid":
+        mr, n = args.rows or 200000, args.cols or 500
+        P = problem_gaussian(mr, n, 1e10, 1e-4, seed=61)
+        A, b = torch.from_numpy(P["A"]).to(dev), torch.from_numpy(P["b"]).to(dev)
+        plan = lsq.Plan(mr, n, seed=7)
         x = torch.empty(n, dtype=torch.float64, device=dev)
         for _ in range(max(1, args.steps)):
             st, info = lsq.lsq_solve_fossils(plan.handle, A, b, x)
