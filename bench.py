@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tier", action="store_true",
                     help="skip the tier / many-RHS / served comparisons")
-    ap.add_argument("--profile-case", default="", choices=["", "tier", "multi", "qr", "resid"],
+    ap.add_argument("--profile-case", default="", choices=["", "tier", "multi", "qr", "resid", "csr"],
                     help="run small solves of one path for ncu captures (no bench line)")
     ap.add_argument("--rows", type=int, default=0,
                     help="override m (small cases for ncu captures; not a bench line)")
@@ -998,7 +998,9 @@ def run_profile_case(args):
     FOSSILS on 30000 x n (n = --cols, default 500; kappa 1e8), whose sketch
     has the bench workload's d = 12n rows, for the QR kernels, `resid` = FOSSILS
     on m x n (m = --rows, default 2e5; n = --cols, default 500; kappa 1e10), the
-    bench workload's width with A larger than L2, for the FP64 residual pass."""
+    bench workload's width with A larger than L2, for the FP64 residual pass,
+    `csr` = SPIR (d = 3n) on the bench's sparse CSR workload (5e5 x 500, 32 nonzeros
+    per row), for the CSR passes."""
     import numpy as np
     import torch
     import paper_2406_03468_gb300 as lsq
@@ -1020,6 +1022,16 @@ def run_profile_case(args):
         x = torch.empty(n, dtype=torch.float64, device=dev)
         for _ in range(max(1, args.steps)):
             st, info = lsq.lsq_solve_fossils(plan.handle, A, b, x)
+    elif args.profile_case == "csr":
+        from lsq_problems import problem_sparse
+        mc, n = 500000, 500
+        P = problem_sparse(mc, n, 32, seed=8, delta=1e-8)
+        rp, col, val = (torch.from_numpy(P[k]).to(dev) for k in ("row_ptr", "col", "val"))
+        b = torch.from_numpy(P["b"]).to(dev)
+        plan = lsq.Plan(mc, n, seed=7, sparse=1, d=3 * n)
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        for _ in range(max(1, args.steps)):
+            st, info = lsq.lsq_solve_csr(plan.handle, 1, rp, col, val, b, x)
     elif args.profile_case == "tier":
         mt = args.rows or 200000
         P = problem_gaussian(mt, 1000, 1e4, 1e-4, seed=31)
