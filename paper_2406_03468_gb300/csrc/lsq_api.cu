@@ -958,7 +958,11 @@ lsq_status lsq_plan_create(const lsq_options *opt, void *cuda_stream, lsq_plan *
     free_plan(P);
     return fail(LSQ_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
   }
-  P->gpass = P->nsm * kPassCtasPerSm;
+  // The pass grid sizes the per-CTA partials.  The CSR passes gather their
+  // operands (indices, then the entries they point at) and are bound by load
+  // latency, so a sparse plan fills the SMs to the CSR kernel's occupancy
+  // limit at 500 columns (5 CTAs: registers), not the dense passes' 2.
+  P->gpass = P->nsm * (opt->sparse ? kCsrCtasPerSm : kPassCtasPerSm);
   P->gqr = qr_grid(n + 1, P->nsm);
   // workspace sized for the capacity (equal to the first problem's sizes)
   const size_t nn = (size_t)n * n, dn1 = (size_t)P->d_cap * (n + 1);

@@ -16,6 +16,7 @@ constexpr double kU = 1.1102230246251565e-16;  // unit roundoff of IEEE double, 
 constexpr double kUKwStop = 2.220446049250313e-16;
 constexpr int kPassThreads = 256;               // threads per CTA of the streaming passes
 constexpr int kPassCtasPerSm = 2;
+constexpr int kCsrCtasPerSm = 5;                // CTAs per SM of a sparse plan's pass grid
 constexpr int kVecThreads = 1024;               // threads of the single-CTA vector kernels
 constexpr int kMaxZeta = 32;
 
