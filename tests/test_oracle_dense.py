@@ -6,6 +6,8 @@
 * The QR least-squares solve against an extended-precision (mpmath, 60
   digits) normal-equations solve on tiny inputs, and against LAPACK lstsq.
 * Compensated residual against an exact rational evaluation.
+* The extreme singular values of R on constructed spectra and the 2 x 2
+  closed forms (determinant, Frobenius norm).
 """
 import math
 from fractions import Fraction
@@ -166,3 +168,30 @@ def test_qr_solve_lapack_matches_plain_loops():
     be = O.kw_relative(P["A"], P["b"], xl, R_A=R)
     bel = O.kw_relative(P["A"], P["b"], xl, R_A=Rl)
     assert abs(be - bel) <= 1e-6 * be
+
+
+@pytest.mark.parametrize("n,kappa", [(6, 1e3), (40, 1e10)])
+def test_sigma_extremes_constructed(n, kappa):
+    """sigma_extremes (the extreme singular values of R, used for the condition
+    estimates) on R factors whose singular values are fixed by construction:
+    orthogonal transformations keep them, so the R of U diag(s) V^T (U, V from
+    QRs of Gaussians) has singular values s."""
+    rng = np.random.default_rng(n)
+    s = np.logspace(0, -math.log10(kappa), n) * 3.0
+    U, _ = np.linalg.qr(rng.standard_normal((5 * n, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    R, _ = O.householder_qr((U * s) @ V.T)
+    smax, smin = O.sigma_extremes(R)
+    assert abs(smax - s[0]) <= 1e-13 * s[0]
+    # the smallest one to the accuracy the QR leaves it: ~u sigma_max
+    assert abs(smin - s[-1]) <= 1e-14 * s[0] * n
+
+
+def test_sigma_extremes_two_by_two():
+    """For R = [[a, b], [0, c]]: sigma_max sigma_min = |a c| (the determinant) and
+    sigma_max^2 + sigma_min^2 = a^2 + b^2 + c^2 (the Frobenius norm)."""
+    for a, b, c in [(3.0, 4.0, 2.0), (1.0, 0.0, 1e-8), (-2.0, 7.0, 0.5)]:
+        smax, smin = O.sigma_extremes(np.array([[a, b], [0.0, c]]))
+        assert smax >= smin > 0.0
+        assert abs(smax * smin - abs(a * c)) <= 1e-14 * smax * smax
+        assert abs(smax ** 2 + smin ** 2 - (a * a + b * b + c * c)) <= 1e-14 * (a * a + b * b + c * c)
