@@ -81,6 +81,19 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def replica_rate(ms, units, world, dist=None, dev=None):
+    """Whole-job rate of `world` replicas that each processed `units` units in
+    `ms` milliseconds of their own: the slowest rank's time (the max over ranks,
+    an all-reduce when `dist` is given) bounds the job.  Returns (units per
+    second over all ranks, that max time in ms)."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(ms)], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return units * world / (ms / 1e3), ms
+
+
 def config(extra=None):
     c = {"workload": WORKLOAD, "m": M, "n": N, "d": 12 * N, "zeta": 8, "kappa": KAPPA,
          "method": "fossils", "refinement_steps": 2,
@@ -806,11 +819,7 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     if dist:
         dist.barrier()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = args.steps * world / (ms / 1e3)
+    value, ms = replica_rate(ms, args.steps, world, dist, dev)
     x_fossils = x.cpu().numpy().copy()
 
     # roofline of the dominant kernel: the fused A^T(A z) inner pass
@@ -885,11 +894,7 @@ def run_ours(args):
             walls.append(time.perf_counter() - t1)
             host_infos.append(hinf.as_dict())
         dt = time.perf_counter() - t0
-        rate = k2 * world / dt
-        if dist:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            rate = k2 * world / float(t.item())
+        rate, _ = replica_rate(1e3 * dt, k2, world, dist, dev)
         e2e = {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 8 * M * N + 8 * M,
                "d2h_bytes_per_step": 8 * N, "h2d_link_gbs": link_gbs,
                "sketch_ms_incl_copy": statistics.median(i["ms_sketch"] for i in host_infos),
