@@ -67,3 +67,45 @@ def test_defaults_and_validation_without_gpu():
 def test_build_targets_sm103a_only():
     from paper_2406_03468_gb300 import _build
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+# Each option rule of the plan's validation (run before any CUDA call): a
+# violation returns LSQ_ERR_INVALID; the valid neighbour passes validation
+# and, on a machine without a GPU, stops at the device query (LSQ_ERR_CUDA).
+_RULES = [
+    ({"m": 100, "n": 0}, {"m": 100, "n": 1}),                      # n >= 1
+    ({"m": 100, "n": 10, "lda": 9}, {"m": 100, "n": 10, "lda": 10}),
+    ({"m": 100, "n": 10, "d": 9}, {"m": 100, "n": 10, "d": 10}),   # n <= d
+    ({"m": 100, "n": 10, "d": (1 << 24) + 1}, {"m": 100, "n": 10, "d": 1 << 24}),
+    ({"m": 100, "n": 10, "d": 12, "zeta": 13}, {"m": 100, "n": 10, "d": 12, "zeta": 12}),
+    ({"m": 100, "n": 10, "zeta": 33}, {"m": 100, "n": 10, "zeta": 32}),
+    ({"m": 100, "n": 10, "max_inner": -1}, {"m": 100, "n": 10, "max_inner": 0}),
+    ({"m": 100, "n": 10, "max_refine": 9}, {"m": 100, "n": 10, "max_refine": 8}),
+    ({"m": 100, "n": 10, "max_refine": -1}, {"m": 100, "n": 10, "max_refine": 0}),
+    ({"m": 2000, "n": 1025}, {"m": 2000, "n": 1024}),             # n <= LSQ_MAX_N
+    ({"m": 100, "n": 10, "eta": 1.0}, {"m": 100, "n": 10, "eta": 0.99}),
+    ({"m": 100, "n": 10, "eta": -0.1}, {"m": 100, "n": 10, "eta": 0.0}),
+    ({"m": 100, "n": 10, "precision": 3}, {"m": 100, "n": 10, "precision": 2}),
+    ({"m": 100, "n": 10, "qr_wait_us": -1}, {"m": 100, "n": 10, "qr_wait_us": 0}),
+    ({"m": 100, "n": 10, "kw_stop": 2}, {"m": 100, "n": 10, "kw_stop": 1}),
+    ({"m": 100, "n": 10, "nrhs": 12}, {"m": 100, "n": 10, "nrhs": 16}),   # multiple of 8
+    ({"m": 1000, "n": 300, "nrhs": 8}, {"m": 1000, "n": 256, "nrhs": 8}),  # n <= 256
+    ({"m": 100, "n": 10, "sparse": 2}, {"m": 100, "n": 10, "sparse": 1}),
+    ({"m": 100, "n": 10, "sparse": 1, "nrhs": 8}, {"m": 100, "n": 10, "sparse": 1}),
+    ({"m": 100, "n": 10, "sparse": 1, "kw_stop": 1}, {"m": 100, "n": 10, "sparse": 1}),
+    ({"m": 100, "n": 10, "sparse": 1, "precision": 0}, {"m": 100, "n": 10, "sparse": 1,
+                                                        "precision": 1}),
+]
+
+
+@pytest.mark.parametrize("bad,good", _RULES)
+def test_option_rules_without_gpu(bad, good):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("checks the validation order on a machine without a GPU")
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.lsq_plan_create(lsq.lsq_options_default(**bad))
+    assert e.value.status == -1, (bad, lsq.lsq_last_error())
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.lsq_plan_create(lsq.lsq_options_default(**good))
+    assert e.value.status == -3, (good, lsq.lsq_last_error())
