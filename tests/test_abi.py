@@ -109,3 +109,30 @@ def test_option_rules_without_gpu(bad, good):
     with pytest.raises(lsq.LsqError) as e:
         lsq.lsq_plan_create(lsq.lsq_options_default(**good))
     assert e.value.status == -3, (good, lsq.lsq_last_error())
+
+
+_HANDLE_ENTRIES = [
+    "lsq_plan_configure", "lsq_sketch", "lsq_solve_fossils", "lsq_solve_spir",
+    "lsq_solve_spir_lsqr", "lsq_solve_host", "lsq_solve_fossils_multi", "lsq_solve_complex",
+    "lsq_solve_csr", "lsq_sketch_pattern", "lsq_get_sketch", "lsq_get_sketch_raw", "lsq_get_R",
+    "lsq_apply_normal", "lsq_apply_normal_multi", "lsq_residual", "lsq_sketched_kw", "lsq_trsv",
+    "lsq_batch_solve", "lsq_submit", "lsq_poll", "lsq_server_stats",
+]
+
+
+@pytest.mark.parametrize("name", _HANDLE_ENTRIES)
+def test_null_handle_is_invalid(name):
+    """Every entry point that takes a plan, batch or server handle returns
+    LSQ_ERR_INVALID for a NULL handle (all pointer arguments NULL, sizes 0)
+    before any CUDA call; the destroy calls accept NULL."""
+    import ctypes
+    L = lsq._lib()
+    _, args = lsq.EXPORTED[name]
+    vals = [0 if a in (ctypes.c_int, ctypes.c_long, ctypes.c_ulong) else None for a in args]
+    assert getattr(L, name)(*vals) == -1, lsq.lsq_last_error()
+
+
+def test_destroy_accepts_null():
+    L = lsq._lib()
+    for name in ("lsq_plan_destroy", "lsq_batch_destroy", "lsq_server_destroy"):
+        getattr(L, name)(None)
