@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kQbThreads, 1)
       }
     }
     __syncthreads();
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = tid; t < (int)(pc - 1) * msz; t += kQbThreads) {
       const unsigned q = (unsigned)(t / msz), e = (unsigned)(t % msz);
       const unsigned dst = q < rank ? q : q + 1;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kQbThreads, 1)
     if (warp < kSumWarps && lane < msz) {
       const unsigned per = pc / kSumWarps;
       double s4 = 0.0;
-      #pragma unroll 1
+#pragma unroll 1
       for (unsigned r = warp * per; r < (warp + 1) * per; r++) s4 += mk[(size_t)r * 2 * kQb + lane];
       ps[warp * 32 + lane] = s4;
     }
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kQbThreads, 1)
     __syncthreads();
     // c_j <- c_j - beta y_k (y_k^T c_j) for the panel columns j > k
     const double u1 = rsh[0];
-    #pragma unroll 1
+#pragma unroll 1
     for (int j = k + 1 + warp; j < bw; j += kQbWarps) {
       const double wj = wsh[j];
       double *cj = P + (size_t)j * S;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kQbThreads, 1)
         cj[k] = fma(-wj, u1, cj[k]);
         i += 32;
       }
-      #pragma unroll 1
+#pragma unroll 1
       for (; i < nr; i += 32) cj[i] = fma(-wj, x[i], cj[i]);
     }
     __syncthreads();
